@@ -1,0 +1,218 @@
+/*
+ * bwt.h -- C ABI of the GB300 forward Burrows-Wheeler block sort.
+ *
+ * The operation (Section 3.1 of the paper: the forward transform "sorts the
+ * rotations" of a block, after Burrows and Wheeler 1994):
+ *   a block is n bytes S[0..n-1]; rotation i is S[i..n-1] S[0..i-1];
+ *   SA = the permutation of 0..n-1 ordered by (rotation i as unsigned bytes,
+ *        then i ascending), so identical rotations keep lower-index-first;
+ *   L[k] = S[(SA[k] + n - 1) mod n] is the last column of the sorted matrix;
+ *   primary = the row k with SA[k] = 0, i.e. where the original block sits.
+ * There is no sentinel byte and no bzip2-specific pre-processing.
+ *
+ * Batches: num_blocks independent blocks concatenated in one byte buffer;
+ * block b is in[offsets[b] .. offsets[b+1]). L uses the same layout and
+ * primary[b] is block b's primary index (0-based, relative to the block).
+ *
+ * Memory: every pointer named d_* is device memory owned by the caller. The
+ * plan owns all scratch; it is sized at plan creation from the descriptor
+ * and nothing is allocated per call. All entry points return a bwt_status and
+ * never abort the process; kernels never trap. Device-side failures (a
+ * bounded wait that ran out, a capacity overflow) are recorded in a device
+ * status word and returned by the call, which synchronises its stream before
+ * returning.
+ *
+ * Thread safety: a plan may be used by one host thread at a time.
+ */
+#ifndef BWT_GB300_H
+#define BWT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bwt_plan bwt_plan;
+
+typedef enum {
+    BWT_OK = 0,
+    BWT_EINVAL = 1,     /* bad argument: NULL pointer, empty block, offsets not increasing, size over the plan's limits */
+    BWT_ENOMEM = 2,     /* device or pinned host allocation failed at plan creation */
+    BWT_ECAPACITY = 3,  /* a device-side work list overflowed (internal limit) */
+    BWT_ECUDA = 4,      /* a CUDA runtime call failed; see bwt_last_cuda_error() */
+    BWT_ETIMEOUT = 5,   /* a bounded device-side wait ran out; outputs are undefined */
+    BWT_EMISMATCH = 6,  /* bwt_inverse_check: the inverse of L does not reproduce the block */
+    BWT_ENOMODEL = 7    /* BWT_F_LEARNED without a loaded splitter table */
+} bwt_status;
+
+/* plan flags */
+#define BWT_F_GRAPH            0x1u /* capture the whole batch in a CUDA graph and replay it when the
+                                       block sizes repeat; the prefix-doubling loop is a device-side
+                                       conditional WHILE node, so no host round trip per round */
+#define BWT_F_LEARNED          0x2u /* learned-CDF bucketing before the exact sort (needs a model) */
+#define BWT_F_PER_BLOCK_LAUNCH 0x4u /* comparison mode: sort block after block, one launch chain each */
+#define BWT_F_TIMING           0x8u /* record CUDA events around every radix pass (see bwt_plan_stats) */
+
+typedef struct {
+    uint32_t max_blocks;       /* most blocks per call (>= 1) */
+    uint64_t max_total_bytes;  /* most bytes per call, summed over blocks (< 2^32) */
+    uint32_t max_block_bytes;  /* largest block (1 .. 2^30 - 1) */
+    int radix_bits;            /* LSD digit width: 8 or 11; 0 = the default (8) or the autotuned value */
+    int tile_keys;             /* keys per radix tile: 1024, 2048 or 4096; 0 = default (4096) */
+    uint32_t flags;            /* BWT_F_* */
+    const char* model_path;    /* splitter table for BWT_F_LEARNED (bwt_model_compile output); may be NULL */
+} bwt_plan_desc;
+
+/* Plan statistics of the last bwt_forward_batch call. */
+typedef struct {
+    uint32_t rounds;            /* prefix-doubling rounds executed (over all blocks) */
+    uint32_t radix_bits, tile_keys;
+    uint64_t kernel_launches;   /* kernels launched (graph replays count the kernels they run) */
+    uint64_t radix_launches;    /* onesweep radix-pass launches */
+    uint64_t radix_keys;        /* keys moved by those launches, summed */
+    double radix_ms;            /* their summed device time (only with BWT_F_TIMING) */
+    double radix_bytes;         /* their algorithmic HBM bytes: 24 per u64 key (8 + 4 read, 8 + 4
+                                   written), 13 for the first pass (1 byte read), 16 per u32 key */
+    uint64_t active_elements;   /* rotations re-sorted by doubling rounds, summed over rounds */
+    uint64_t buckets_overflowed;/* learned bucketing: buckets sent to the radix path */
+    uint64_t keys_overflowed;   /* learned bucketing: keys in those buckets */
+    uint32_t max_bucket;        /* learned bucketing: largest bucket */
+    uint32_t graph_replayed;    /* 1 if the last call replayed a cached CUDA graph */
+    uint32_t blocks_routed_plain; /* learned bucketing: blocks whose buckets overflowed too much and
+                                     were sorted by the plain radix path instead */
+    uint32_t pad_;
+} bwt_stats;
+
+/* Create a plan on CUDA device `device` (made current for the call). The plan
+ * allocates all scratch for desc's limits (about 40 bytes per byte of
+ * max_total_bytes). Returns BWT_EINVAL for bad limits, BWT_ENOMEM if the
+ * allocation fails, BWT_ENOMODEL if BWT_F_LEARNED is set and model_path cannot
+ * be read. *out is NULL on failure. */
+bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt_plan** out);
+
+/* Forward BWT of a batch (the definition at the top of this header).
+ *   d_in        device, uint8[offsets[num_blocks]]: the blocks, concatenated.
+ *   offsets     uint64[num_blocks + 1], offsets[0] = 0, strictly increasing
+ *               (empty blocks are BWT_EINVAL). Host or device memory; device
+ *               offsets are copied to the host once per call.
+ *   num_blocks  1 .. max_blocks.
+ *   d_L         device, uint8[offsets[num_blocks]]: the L column, same layout.
+ *   d_primary   device, int32[num_blocks].
+ *   stream      cudaStream_t to run on (NULL = the legacy default stream).
+ * The work is stream-ordered; the call synchronises `stream` before it
+ * returns so it can report device-side status. Outputs are undefined unless
+ * BWT_OK is returned. d_in must not alias d_L. */
+bwt_status bwt_forward_batch(bwt_plan* plan, const uint8_t* d_in, const uint64_t* offsets,
+                             uint32_t num_blocks, uint8_t* d_L, int32_t* d_primary, void* stream);
+
+/* Host-side check of one block: inverts L by the LF walk from `primary`
+ * (Section 3.1: the inverse may start from any row) and compares the result
+ * with `original`. All pointers are host memory of n bytes.
+ * BWT_OK if it reproduces `original`; BWT_EMISMATCH if not, or if L is not a
+ * permutation of `original`; BWT_EINVAL for n = 0, NULL pointers or a primary
+ * outside [0, n). */
+bwt_status bwt_inverse_check(const uint8_t* L, uint64_t n, int32_t primary, const uint8_t* original);
+
+/* Free the plan and all its device and host memory. NULL is accepted. */
+bwt_status bwt_plan_destroy(bwt_plan* plan);
+
+/* ---- plan control and introspection (no paper counterpart) ----------- */
+
+/* Status recorded by the last bwt_forward_batch call on this plan. */
+bwt_status bwt_plan_last_status(const bwt_plan* plan);
+
+/* Copies the statistics of the last call into *out. */
+bwt_status bwt_plan_stats(const bwt_plan* plan, bwt_stats* out);
+
+/* Changes the radix digit width (8 or 11) and tile size (1024, 2048, 4096)
+ * used by later calls; drops any cached graph. */
+bwt_status bwt_plan_set_radix(bwt_plan* plan, int radix_bits, int tile_keys);
+
+/* Test knob for the bounded device waits: `spin_limit` caps every wait loop
+ * (0 = the built-in default of about one second); `withhold_publish` = 1 makes
+ * the first tile of every radix pass skip publishing its counts, so every
+ * later tile's look-back wait runs out and the call returns BWT_ETIMEOUT.
+ * The GPU is never left waiting: each wait gives up after `spin_limit`
+ * polls. */
+bwt_status bwt_plan_debug_waits(bwt_plan* plan, uint32_t spin_limit, int withhold_publish);
+
+/* ---- learned CDF model (the learned bucketing of BWT_F_LEARNED) -------
+ *
+ * The model approximates the CDF of rotation prefixes: input x = the 8
+ * prefix bytes of a rotation divided by 255 (8 floats), target t = the
+ * rotation's sorted row / n. It is an FP32 MLP 8 -> 32 -> 32 -> 1 with ReLU
+ * after both hidden layers; its BWT_MLP_NPARAMS parameters are laid out
+ * row-major as W1[32][8] | b1[32] | W2[32][32] | b2[32] | W3[32] | b3.
+ * The loss of a batch of B samples is mean over samples of (y - t)^2.
+ * A trained model is compiled into BWT_SPLITTERS sorted u64 splitters;
+ * rotation key K (the 8-byte prefix, big-endian) goes to bucket
+ * #{j : splitter[j] <= K}, one of BWT_BUCKETS. Because the bucket is a
+ * monotone function of K, any sorted splitter table gives the exact
+ * transform; the model only decides how even the buckets are. */
+#define BWT_MLP_NPARAMS 1377
+#define BWT_SPLITTERS 4095
+#define BWT_BUCKETS 4096
+
+/* y[s] = f(x[s]) for s < count. d_params: float[BWT_MLP_NPARAMS];
+ * d_x: float[count][8]; d_y: float[count]. Device pointers, async. */
+bwt_status bwt_mlp_forward(const float* d_params, const float* d_x, uint32_t count, float* d_y, void* stream);
+
+/* Gradient of the batch loss with respect to every parameter (d_grad:
+ * float[BWT_MLP_NPARAMS]) and the loss itself (d_loss: float[1], may be
+ * NULL), over samples (d_x[s], d_t[s]), s < count. Deterministic reduction
+ * order. Synchronises `stream`; allocates temporary device memory. */
+bwt_status bwt_mlp_loss_grad(const float* d_params, const float* d_x, const float* d_t, uint32_t count,
+                             float* d_grad, float* d_loss, void* stream);
+
+/* One Adam update (beta1 0.9, beta2 0.999, eps 1e-8; Kingma and Ba 2015) at
+ * step >= 1, in place on d_params, d_m, d_v (all float[BWT_MLP_NPARAMS]). */
+bwt_status bwt_mlp_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v, uint32_t step, float lr,
+                             void* stream);
+
+/* Trains d_params in place with Adam over `epochs` passes of minibatches of
+ * `batch` samples; epoch e visits samples d_order[e * count + 0 .. count - 1]
+ * (a permutation supplied by the caller, so training is reproducible).
+ * d_epoch_loss: float[epochs] mean batch loss per epoch (may be NULL).
+ * Synchronises `stream`; allocates temporary device memory. */
+bwt_status bwt_model_train(float* d_params, const float* d_x, const float* d_t, uint32_t count,
+                           const uint32_t* d_order, uint32_t epochs, uint32_t batch, float lr, float* d_epoch_loss,
+                           void* stream);
+
+/* Training samples produced by the plain sorter: sorts the batch with the
+ * plain path of `plan`, then for every s < count takes the row at global
+ * sorted position d_pos[s] (< total bytes) and writes d_x[s] = the 8 prefix
+ * bytes of that row's rotation / 255 and d_t[s] = its row within its block /
+ * block size. Synchronises `stream`. */
+bwt_status bwt_model_samples(bwt_plan* plan, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
+                             const uint64_t* d_pos, uint32_t count, float* d_x, float* d_t, void* stream);
+
+/* Compiles trained parameters into BWT_SPLITTERS sorted splitters
+ * (d_splitters, device u64): splitter j is found by bisection over the 64-bit
+ * key space as the smallest key whose model output reaches
+ * (j + 1) / BWT_BUCKETS; the table is then sorted. */
+bwt_status bwt_model_compile(const float* d_params, uint64_t* d_splitters, void* stream);
+
+/* Installs a sorted splitter table (host or device memory, BWT_SPLITTERS
+ * entries) in the plan; BWT_EINVAL if it is not non-decreasing. */
+bwt_status bwt_plan_set_splitters(bwt_plan* plan, const uint64_t* splitters);
+
+/* Model files: parameters and compiled splitters (host arrays). The file is
+ * an 8-byte tag "BWTMDL01", then BWT_MLP_NPARAMS little-endian floats, then
+ * BWT_SPLITTERS little-endian u64. load returns BWT_ENOMODEL if the file is
+ * missing or malformed. */
+bwt_status bwt_model_save(const char* path, const float* params, const uint64_t* splitters);
+bwt_status bwt_model_load(const char* path, float* params, uint64_t* splitters);
+
+/* Human-readable name of a status code (static string). */
+const char* bwt_status_string(bwt_status s);
+
+/* Text of the last CUDA error seen by any call in this process (static). */
+const char* bwt_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BWT_GB300_H */

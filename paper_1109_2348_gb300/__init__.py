@@ -1,1 +1,111 @@
-"""GB300-native forward Burrows-Wheeler block sort (placeholder; binding added below)."""
+"""GB300-native forward Burrows-Wheeler block sort.
+
+The transform (the paper's Section 3.1: sort the rotations of the block)
+runs in hand-written sm_103a CUDA behind the C ABI of ``include/bwt.h``;
+this package is the thin Python binding with the same names. PyTorch tensors
+supply device memory and streams only.
+
+    plan = Plan(max_blocks=64, max_total_bytes=64 * 900_000, max_block_bytes=900_000)
+    L, primary = plan.forward(d_bytes, offsets)     # d_bytes: uint8 CUDA tensor
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (BWT_OK, BWTError, F_GRAPH, F_LEARNED, F_PER_BLOCK_LAUNCH, F_TIMING, PlanDesc, Stats,
+                   check)
+
+__all__ = ["Plan", "BWTError", "bwt_inverse_check", "F_GRAPH", "F_LEARNED", "F_PER_BLOCK_LAUNCH", "F_TIMING"]
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """bwt_plan_create / bwt_forward_batch / bwt_plan_destroy."""
+
+    def __init__(self, max_blocks: int, max_total_bytes: int, max_block_bytes: int, radix_bits: int = 0,
+                 tile_keys: int = 0, flags: int = 0, model_path: str | None = None, device: int = 0):
+        self.lib = _lib.load()
+        self.desc = PlanDesc(max_blocks, max_total_bytes, max_block_bytes, radix_bits, tile_keys, flags,
+                             model_path.encode() if model_path else None)
+        h = ctypes.c_void_p()
+        check(self.lib.bwt_plan_create(ctypes.byref(self.desc), device, ctypes.byref(h)), "bwt_plan_create")
+        self.handle = h
+        self.device = device
+        self.flags = flags
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            self.lib.bwt_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def forward_into(self, d_in, offsets, d_L, d_primary, stream=None, raise_on_error: bool = True) -> int:
+        """bwt_forward_batch on caller-owned buffers. `offsets` is a uint64 numpy
+        array, a CPU tensor or a CUDA tensor with num_blocks + 1 entries."""
+        if isinstance(offsets, np.ndarray):
+            off = np.ascontiguousarray(offsets, dtype=np.uint64)
+            off_ptr, nb = off.ctypes.data, off.size - 1
+        else:
+            off_ptr, nb = _ptr(offsets), offsets.numel() - 1
+        st = self.lib.bwt_forward_batch(self.handle, _ptr(d_in), off_ptr, nb, _ptr(d_L), _ptr(d_primary),
+                                        _stream_handle(stream))
+        if raise_on_error:
+            check(st, "bwt_forward_batch")
+        return st
+
+    def forward(self, d_in, offsets, stream=None):
+        """Returns (L uint8 CUDA tensor, primary int32 CUDA tensor)."""
+        import torch
+        nb = (offsets.size if isinstance(offsets, np.ndarray) else offsets.numel()) - 1
+        L = torch.empty_like(d_in)
+        prim = torch.empty(nb, dtype=torch.int32, device=d_in.device)
+        self.forward_into(d_in, offsets, L, prim, stream)
+        return L, prim
+
+    def stats(self) -> dict:
+        s = Stats()
+        check(self.lib.bwt_plan_stats(self.handle, ctypes.byref(s)), "bwt_plan_stats")
+        return s.as_dict()
+
+    def last_status(self) -> int:
+        return self.lib.bwt_plan_last_status(self.handle)
+
+    def set_radix(self, radix_bits: int, tile_keys: int) -> None:
+        check(self.lib.bwt_plan_set_radix(self.handle, radix_bits, tile_keys), "bwt_plan_set_radix")
+
+    def debug_waits(self, spin_limit: int, withhold_publish: bool) -> None:
+        check(self.lib.bwt_plan_debug_waits(self.handle, spin_limit, int(withhold_publish)), "bwt_plan_debug_waits")
+
+
+def bwt_inverse_check(L, primary: int, original) -> int:
+    """Host check: BWT_OK if inverting L from `primary` reproduces `original`."""
+    lib = _lib.load()
+    L = np.ascontiguousarray(L, dtype=np.uint8)
+    o = np.ascontiguousarray(original, dtype=np.uint8)
+    if L.size != o.size:
+        return _lib.BWT_EINVAL
+    return lib.bwt_inverse_check(L.ctypes.data, L.size, int(primary), o.ctypes.data)

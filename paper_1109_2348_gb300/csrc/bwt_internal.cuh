@@ -1,0 +1,160 @@
+// Internal types and device helpers of the GB300 BWT block sort.
+//
+// Positions are global indices into the concatenated batch (u32: a batch is
+// under 2^32 bytes). Within block b, rotation i lives at global index
+// blocks[b].off + i; `rank` is indexed that way. SA holds block-local
+// rotation indices at global sorted positions.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bwt {
+
+// One radix tile: `len` consecutive keys at global position `start`, inside
+// segment `seg` (a block for the first sort, a group for a doubling round).
+// Tiles never straddle segments; a segment's tiles are consecutive and
+// `firstTile` is the index of its first one (where look-back stops).
+struct TileDesc {
+    uint32_t start, len, seg, firstTile;
+    uint32_t segStart, blk, pad0, pad1;
+};
+
+// A group of rotations whose sort keys are still equal: global positions
+// [start, start + len) of block blk.
+struct GroupDesc {
+    uint32_t start, len, blk, pad;
+};
+
+struct BlockInfo {
+    uint32_t off, n;
+};
+
+// Look-back status word: 2 flag bits + 30-bit count.
+constexpr uint32_t ST_AGG = 1u << 30;
+constexpr uint32_t ST_INC = 2u << 30;
+constexpr uint32_t ST_VALUE = (1u << 30) - 1;
+
+// Device error bits (ctrl[CTRL_ERR]).
+constexpr uint32_t ERR_TIMEOUT = 1u;
+constexpr uint32_t ERR_CAPACITY = 2u;
+
+// Group size classes of a doubling round.
+constexpr uint32_t TINY_MAX = 32;    // one warp per group, bitonic in registers
+constexpr uint32_t MED_MAX = 2048;   // one CTA per group, bitonic in shared memory
+// groups above MED_MAX are sorted by the segmented onesweep radix.
+
+// Layout of the plan's device control words.
+enum : int {
+    CTRL_BINS = 0,          // [2][3]: counts of tiny / medium / large groups, double-buffered
+    CTRL_NUM_LTILES = 6,    // tiles of the large-group radix in this round
+    CTRL_ERR = 7,
+    CTRL_ROUNDS = 8,        // doubling rounds executed
+    CTRL_LARGE_KEYS = 9,    // keys in large groups this round
+    CTRL_ACTIVE = 10,       // u64 (words 10, 11): rotations re-sorted, summed over rounds
+    CTRL_SPIN = 12,         // spin limit for bounded waits
+    CTRL_WITHHOLD = 13,     // debug: first tile withholds its look-back publish
+    CTRL_DEPTH = 14,        // prefix length h the current round doubles
+    CTRL_NTILES0 = 15,      // tiles of the first sort
+    CTRL_BODY_ITERS = 16,   // graph mode: iterations of the doubling loop body
+    CTRL_BUCKET_OVF = 17,   // learned: overflowed buckets
+    CTRL_BUCKET_OVF_KEYS = 18,
+    CTRL_BUCKET_MAX = 19,
+    CTRL_TILE_CTR = 32,     // [64] atomic tile counters, one per radix pass
+    CTRL_WORDS = 128
+};
+
+struct Bins {
+    GroupDesc* list[3];
+    uint32_t cap[3];
+    uint32_t* count;                // -> ctrl + CTRL_BINS + 3 * parity
+    unsigned long long* active;     // -> ctrl + CTRL_ACTIVE
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+    return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+__device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) {
+    *reinterpret_cast<volatile uint32_t*>(p) = v;
+}
+
+// Number of valid entries of bin c (a count past the capacity means entries
+// were dropped and ERR_CAPACITY is set).
+__device__ __forceinline__ uint32_t bin_count(const Bins& b, int c) {
+    const uint32_t v = b.count[c];
+    return v < b.cap[c] ? v : b.cap[c];
+}
+
+// Size class of a group.
+__device__ __forceinline__ int size_class(uint32_t len) {
+    return len <= TINY_MAX ? 0 : (len <= MED_MAX ? 1 : 2);
+}
+
+// Append a group to the bin of its size class with one atomic per warp and
+// class, and add its length to the active-rotation counter. All 32 lanes
+// must call it; lanes with want = false add nothing.
+__device__ __forceinline__ void emit_group(const Bins& bins, bool want, uint32_t start, uint32_t len,
+                                           uint32_t blk, uint32_t* err) {
+    const int lane = threadIdx.x & 31;
+    const int cls = want ? size_class(len) : -1;
+    const uint32_t any = __ballot_sync(0xffffffffu, want);
+    if (any == 0) return;
+    const uint32_t lsum = __reduce_add_sync(0xffffffffu, want ? len : 0u);
+    if (lane == __ffs(any) - 1) atomicAdd(bins.active, (unsigned long long)lsum);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        uint32_t m = __ballot_sync(0xffffffffu, cls == c);
+        if (m == 0) continue;
+        int leader = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&bins.count[c], (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (cls == c) {
+            uint32_t slot = base + __popc(m & lanemask_lt());
+            if (slot < bins.cap[c]) {
+                bins.list[c][slot] = GroupDesc{start, len, blk, 0u};
+            } else {
+                atomicOr(err, ERR_CAPACITY);
+            }
+        }
+    }
+}
+
+// Block-wide exclusive scan of one value per thread; returns the prefix and
+// writes the total to *total. `tmp` holds at least THREADS/32 words.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* tmp, uint32_t* total) {
+    constexpr int WARPS = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < WARPS ? tmp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < WARPS) tmp[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    uint32_t warp_prefix = warp > 0 ? tmp[warp - 1] : 0u;
+    *total = tmp[WARPS - 1];
+    __syncthreads();
+    return warp_prefix + x - v;
+}
+
+}  // namespace bwt

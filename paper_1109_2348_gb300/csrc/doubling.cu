@@ -1,0 +1,541 @@
+// Group naming, prefix-doubling rounds and the L-column gather.
+//
+// After the first sort the rotations are ordered by their first 8 bytes.
+// Lexicographic naming (the paper's Section 2.1 names prefix-sum based
+// naming as a GPU building block): every rotation's rank becomes the
+// block-local sorted position of the first member of its group of equal
+// keys, so ranks order groups and equal ranks mean equal prefixes.
+// A prefix-doubling round with shift h (rotations already ordered by their
+// first h bytes) re-sorts every group of size > 1 by
+// key2 = rank[(i + h) mod n], which orders the group by its first 2h bytes,
+// and renames. Sorts stay stable with respect to the rotation index, so
+// groups that reach 2h >= n (identical rotations) keep lower-index-first.
+//
+// Round structure (all gathers of a round finish before any rank is
+// rewritten, so a round reads one consistent rank array):
+//   gather_small (tiny and medium groups) and large_prologue (large groups)
+//   -> sort_small (tiny: warp bitonic; medium: CTA bitonic) and the segmented
+//      radix of the large groups -> rename_large.
+// Refined groups are appended to the next round's size-class bins.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace bwt {
+
+namespace {
+
+// First index f in [lo, k] with K[f] == key, given K sorted non-decreasingly
+// on [lo, k] and K[k] == key: exponential search backward, then bisection.
+template <typename KeyT>
+__device__ __forceinline__ uint32_t first_equal(const KeyT* __restrict__ K, uint32_t lo, uint32_t k, KeyT key) {
+    uint32_t hi_eq = k;    // known equal
+    int64_t below = -1;    // known different (or before lo)
+    uint32_t step = 1;
+    for (;;) {
+        if ((uint64_t)(k - lo) < step) {
+            below = (int64_t)lo - 1;
+            break;
+        }
+        const uint32_t c = k - step;
+        if (K[c] != key) {
+            below = c;
+            break;
+        }
+        hi_eq = c;
+        step <<= 1;
+    }
+    // answer in (below, hi_eq]
+    uint32_t a = (uint32_t)(below + 1), b = hi_eq;
+    while (a < b) {
+        const uint32_t mid = a + ((b - a) >> 1);
+        if (K[mid] == key) b = mid; else a = mid + 1;
+    }
+    return a;
+}
+
+// First index e in (k, hi] with e == hi or K[e] != key, given K[k] == key and
+// K sorted on [k, hi).
+template <typename KeyT>
+__device__ __forceinline__ uint32_t end_equal(const KeyT* __restrict__ K, uint32_t k, uint32_t hi, KeyT key) {
+    uint32_t lo_eq = k;
+    uint32_t above = hi;
+    uint32_t step = 1;
+    for (;;) {
+        if ((uint64_t)(hi - 1 - k) < step) {
+            above = hi;
+            break;
+        }
+        const uint32_t c = k + step;
+        if (K[c] != key) {
+            above = c;
+            break;
+        }
+        lo_eq = c;
+        step <<= 1;
+    }
+    // answer in (lo_eq, above]
+    uint32_t a = lo_eq + 1, b = above;
+    while (a < b) {
+        const uint32_t mid = a + ((b - a) >> 1);
+        if (K[mid] != key) b = mid; else a = mid + 1;
+    }
+    return a;
+}
+
+// ---- first naming ------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict__ K, const uint32_t* __restrict__ SA,
+                                                      const BlockInfo* __restrict__ blocks,
+                                                      const TileDesc* __restrict__ tiles, uint32_t num_tiles,
+                                                      uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl) {
+    if (ld_volatile(&ctrl[CTRL_ERR])) return;  // an earlier stage failed: SA is not a permutation
+    for (uint32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+        const TileDesc td = tiles[t];
+        const BlockInfo bi = blocks[td.blk];
+        const uint32_t lo = bi.off, hi = bi.off + bi.n;
+        for (uint32_t q0 = 0; q0 < td.len; q0 += blockDim.x) {
+            const uint32_t q = q0 + threadIdx.x;
+            const bool valid = q < td.len;
+            bool want = false;
+            uint32_t k = td.start + q, len = 0;
+            if (valid) {
+                const uint64_t key = K[k];
+                const bool head = (k == lo) || (K[k - 1] != key);
+                const uint32_t gs = head ? k : first_equal<uint64_t>(K, lo, k, key);
+                const uint32_t sa = SA[k];
+                if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
+                if (head && bi.n > 8u) {
+                    len = end_equal<uint64_t>(K, k, hi, key) - k;
+                    want = len > 1;
+                }
+            }
+            emit_group(bins, want, k, len, td.blk, &ctrl[CTRL_ERR]);
+        }
+    }
+}
+
+// ---- round: key gathers ------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gather_small(const uint32_t* __restrict__ SA, const uint32_t* __restrict__ rank,
+                                                      const BlockInfo* __restrict__ blocks, Bins cur,
+                                                      const uint32_t* __restrict__ depth, uint32_t* __restrict__ key2) {
+    const uint32_t h = *depth;
+    const uint32_t c0 = bin_count(cur, 0), c1 = bin_count(cur, 1);
+    const uint32_t total = c0 + c1;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += nwarps) {
+        const GroupDesc gd = g < c0 ? cur.list[0][g] : cur.list[1][g - c0];
+        const BlockInfo bi = blocks[gd.blk];
+        for (uint32_t e = lane; e < gd.len; e += 32) {
+            const uint32_t k = gd.start + e;
+            uint32_t r = SA[k] + h;
+            if (r >= bi.n) r -= bi.n;
+            key2[k] = r < bi.n ? rank[bi.off + r] : 0u;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_build_large_tiles(Bins cur, int tile, TileDesc* __restrict__ tiles,
+                                                            uint32_t max_tiles, uint32_t* ctrl) {
+    __shared__ uint32_t tmp[32];
+    __shared__ uint32_t s_keys;
+    if (threadIdx.x == 0) s_keys = 0;
+    __syncthreads();
+    const uint32_t n = bin_count(cur, 2);
+    uint32_t running = 0;
+    for (uint32_t base = 0; base < n; base += 1024) {
+        const uint32_t i = base + threadIdx.x;
+        GroupDesc gd{0, 0, 0, 0};
+        uint32_t nt = 0;
+        if (i < n) {
+            gd = cur.list[2][i];
+            nt = (gd.len + tile - 1) / tile;
+            atomicAdd(&s_keys, gd.len);
+        }
+        uint32_t tot;
+        const uint32_t first = running + block_exclusive_scan<1024>(nt, tmp, &tot);
+        for (uint32_t j = 0; j < nt; ++j) {
+            const uint32_t ti = first + j;
+            if (ti < max_tiles) {
+                TileDesc td;
+                td.start = gd.start + j * tile;
+                td.len = min((uint32_t)tile, gd.len - j * tile);
+                td.seg = i;
+                td.firstTile = first;
+                td.segStart = gd.start;
+                td.blk = gd.blk;
+                td.pad0 = gd.len;
+                td.pad1 = 0;
+                tiles[ti] = td;
+            }
+        }
+        running += tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (running > max_tiles) {
+            atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
+            running = max_tiles;
+        }
+        ctrl[CTRL_NUM_LTILES] = running;
+        ctrl[CTRL_LARGE_KEYS] = s_keys;
+    }
+}
+
+template <int RBITS>
+__global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restrict__ SA,
+                                                        const uint32_t* __restrict__ rank,
+                                                        const BlockInfo* __restrict__ blocks,
+                                                        const TileDesc* __restrict__ tiles,
+                                                        const uint32_t* __restrict__ num_tiles,
+                                                        const uint32_t* __restrict__ depth,
+                                                        uint32_t* __restrict__ kbuf, uint32_t* __restrict__ vbuf,
+                                                        uint32_t* __restrict__ hist, int passes) {
+    constexpr int RADIX = 1 << RBITS;
+    const uint32_t h = *depth;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* sh = reinterpret_cast<uint32_t*>(smem);
+    const int lane = threadIdx.x & 31;
+    const uint32_t nt = *num_tiles;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+        const TileDesc td = tiles[t];
+        const BlockInfo bi = blocks[td.blk];
+        for (uint32_t q0 = 0; q0 < td.len; q0 += blockDim.x) {
+            const uint32_t q = q0 + threadIdx.x;
+            const bool valid = q < td.len;
+            uint32_t k2 = 0;
+            if (valid) {
+                const uint32_t k = td.start + q;
+                const uint32_t sa = SA[k];
+                uint32_t r = sa + h;
+                if (r >= bi.n) r -= bi.n;
+                k2 = r < bi.n ? rank[bi.off + r] : 0u;
+                kbuf[k] = k2;
+                vbuf[k] = sa;
+            }
+            for (int ps = 0; ps < passes; ++ps) {
+                const uint32_t d = valid ? ((k2 >> (ps * RBITS)) & (RADIX - 1)) : (uint32_t)RADIX;
+                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                if (valid && lane == __ffs(peers) - 1) atomicAdd(&sh[ps * RADIX + d], (uint32_t)__popc(peers));
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) {
+            const uint32_t c = sh[i];
+            if (c) atomicAdd(&hist[(size_t)td.seg * passes * RADIX + i], c);
+        }
+        __syncthreads();
+    }
+}
+
+// ---- round: small-group sorts + rename ------------------------------------------
+__global__ void __launch_bounds__(256) k_sort_tiny(uint32_t* __restrict__ SA, const uint32_t* __restrict__ key2,
+                                                   uint32_t* __restrict__ rank, const BlockInfo* __restrict__ blocks,
+                                                   Bins cur, Bins next, const uint32_t* __restrict__ depth,
+                                                   uint32_t* ctrl) {
+    if (ld_volatile(&ctrl[CTRL_ERR])) return;
+    const uint32_t new_depth = 2u * *depth;
+    const uint32_t count = bin_count(cur, 0);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < count; g += nwarps) {
+        const GroupDesc gd = cur.list[0][g];
+        const BlockInfo bi = blocks[gd.blk];
+        const bool valid = lane < gd.len;
+        const uint32_t k = gd.start + lane;
+        uint64_t c = valid ? (((uint64_t)key2[k] << 32) | SA[k]) : ~0ull;
+        // bitonic sort of 32 lanes, ascending
+#pragma unroll
+        for (uint32_t kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+            for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+                const uint64_t o = __shfl_xor_sync(0xffffffffu, c, j);
+                const bool up = (lane & kk) == 0;
+                const bool lower = (lane & j) == 0;
+                c = (lower == up) ? (c < o ? c : o) : (c > o ? c : o);
+            }
+        }
+        const uint32_t key = (uint32_t)(c >> 32), sa = (uint32_t)c;
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+        const bool head = valid && (lane == 0 || prev != key);
+        const uint32_t hm = __ballot_sync(0xffffffffu, head);
+        const uint32_t le = (2u << lane) - 1u;  // lanes <= lane (lane 31 wraps to all ones)
+        const uint32_t start_lane = 31u - __clz(hm & le);
+        const uint32_t above = hm & ~le;
+        const uint32_t end = above ? (uint32_t)(__ffs(above) - 1) : gd.len;
+        if (valid) {
+            SA[k] = sa;
+            if (sa < bi.n) rank[bi.off + sa] = gd.start - bi.off + start_lane;
+        }
+        const uint32_t len = end - lane;
+        const bool want = head && len > 1 && new_depth < bi.n;
+        emit_group(next, want, k, len, gd.blk, &ctrl[CTRL_ERR]);
+    }
+}
+
+__device__ __forceinline__ uint32_t smem_lower_bound(const uint64_t* a, uint32_t n, uint64_t x) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_sort_med(uint32_t* __restrict__ SA, const uint32_t* __restrict__ key2,
+                                                  uint32_t* __restrict__ rank, const BlockInfo* __restrict__ blocks,
+                                                  Bins cur, Bins next, const uint32_t* __restrict__ depth,
+                                                  uint32_t* ctrl) {
+    __shared__ uint64_t comp[MED_MAX];
+    if (ld_volatile(&ctrl[CTRL_ERR])) return;
+    const uint32_t new_depth = 2u * *depth;
+    const uint32_t count = bin_count(cur, 1);
+    for (uint32_t g = blockIdx.x; g < count; g += gridDim.x) {
+        const GroupDesc gd = cur.list[1][g];
+        const BlockInfo bi = blocks[gd.blk];
+        const uint32_t m = gd.len;
+        uint32_t P = 64;
+        while (P < m) P <<= 1;
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+            comp[i] = i < m ? (((uint64_t)key2[gd.start + i] << 32) | SA[gd.start + i]) : ~0ull;
+        __syncthreads();
+        for (uint32_t kk = 2; kk <= P; kk <<= 1) {
+            for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                    const uint32_t ixj = i ^ j;
+                    if (ixj > i) {
+                        const uint64_t a = comp[i], b = comp[ixj];
+                        const bool up = (i & kk) == 0;
+                        if ((a > b) == up) {
+                            comp[i] = b;
+                            comp[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (uint32_t i0 = 0; i0 < m; i0 += blockDim.x) {
+            const uint32_t i = i0 + threadIdx.x;
+            const bool valid = i < m;
+            bool want = false;
+            uint32_t len = 0;
+            if (valid) {
+                const uint64_t c = comp[i];
+                const uint32_t key = (uint32_t)(c >> 32), sa = (uint32_t)c;
+                const bool head = (i == 0) || (uint32_t)(comp[i - 1] >> 32) != key;
+                const uint32_t s = head ? i : smem_lower_bound(comp, m, (uint64_t)key << 32);
+                SA[gd.start + i] = sa;
+                if (sa < bi.n) rank[bi.off + sa] = gd.start - bi.off + s;
+                if (head) {
+                    len = smem_lower_bound(comp, m, (uint64_t)(key + 1) << 32) - i;
+                    want = len > 1 && new_depth < bi.n;
+                }
+            }
+            emit_group(next, want, gd.start + i, len, gd.blk, &ctrl[CTRL_ERR]);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict__ SA, const uint32_t* __restrict__ key2,
+                                                      uint32_t* __restrict__ rank,
+                                                      const BlockInfo* __restrict__ blocks,
+                                                      const TileDesc* __restrict__ tiles,
+                                                      const uint32_t* __restrict__ num_tiles, Bins next,
+                                                      const uint32_t* __restrict__ depth, uint32_t* ctrl) {
+    if (ld_volatile(&ctrl[CTRL_ERR])) return;
+    const uint32_t new_depth = 2u * *depth;
+    const uint32_t nt = *num_tiles;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        const TileDesc td = tiles[t];
+        const BlockInfo bi = blocks[td.blk];
+        const uint32_t lo = td.segStart, hi = td.segStart + td.pad0;
+        for (uint32_t q0 = 0; q0 < td.len; q0 += blockDim.x) {
+            const uint32_t q = q0 + threadIdx.x;
+            const bool valid = q < td.len;
+            bool want = false;
+            const uint32_t k = td.start + q;
+            uint32_t len = 0;
+            if (valid) {
+                const uint32_t key = key2[k];
+                const bool head = (k == lo) || key2[k - 1] != key;
+                const uint32_t gs = head ? k : first_equal<uint32_t>(key2, lo, k, key);
+                const uint32_t sa = SA[k];
+                if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
+                if (head) {
+                    len = end_equal<uint32_t>(key2, k, hi, key) - k;
+                    want = len > 1 && new_depth < bi.n;
+                }
+            }
+            emit_group(next, want, k, len, td.blk, &ctrl[CTRL_ERR]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gather_L(const uint8_t* __restrict__ S, const uint32_t* __restrict__ SA,
+                                                  const BlockInfo* __restrict__ blocks,
+                                                  const TileDesc* __restrict__ tiles, uint32_t num_tiles,
+                                                  uint8_t* __restrict__ L, int32_t* __restrict__ primary) {
+    for (uint32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+        const TileDesc td = tiles[t];
+        const BlockInfo bi = blocks[td.blk];
+        for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) {
+            const uint32_t k = td.start + q;
+            const uint32_t sa = SA[k];
+            const uint32_t src = sa == 0 || sa > bi.n ? bi.n - 1 : sa - 1;
+            L[k] = S[bi.off + src];
+            if (sa == 0) primary[td.blk] = (int32_t)(k - bi.off);
+        }
+    }
+}
+
+int grid_for(uint32_t units, uint32_t per_cta, int cap_per_sm) {
+    const uint64_t want = (units + per_cta - 1) / per_cta;
+    const uint64_t cap = (uint64_t)num_sms() * cap_per_sm;
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, cap));
+}
+
+}  // namespace
+
+cudaError_t launch_name_initial(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks, const TileDesc* tiles,
+                                uint32_t num_tiles, uint32_t* rank, Bins bins, uint32_t* ctrl, cudaStream_t st) {
+    if (!num_tiles) return cudaSuccess;
+    k_name_initial<<<grid_for(num_tiles, 1, 16), 256, 0, st>>>(K, SA, blocks, tiles, num_tiles, rank, bins, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_small(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks, Bins cur,
+                                const uint32_t* depth, uint32_t* key2, const uint32_t* host_counts, cudaStream_t st) {
+    int grid = num_sms() * 16;
+    if (host_counts) {
+        const uint32_t n = host_counts[0] + host_counts[1];
+        if (!n) return cudaSuccess;
+        grid = grid_for(n, 8, 16);
+    }
+    k_gather_small<<<grid, 256, 0, st>>>(SA, rank, blocks, cur, depth, key2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_large_tiles(Bins cur, int tile, TileDesc* tiles, uint32_t max_tiles, uint32_t* ctrl,
+                                     cudaStream_t st) {
+    k_build_large_tiles<<<1, 1024, 0, st>>>(cur, tile, tiles, max_tiles, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_large_prologue(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks,
+                                  const TileDesc* tiles, const uint32_t* num_tiles, const uint32_t* depth,
+                                  uint32_t* kbuf, uint32_t* vbuf, uint32_t* hist, int radix_bits, int passes,
+                                  cudaStream_t st) {
+    const size_t smem = (size_t)passes * (1u << radix_bits) * 4;
+    const int grid = num_sms() * 8;
+    if (radix_bits == 8) {
+        k_large_prologue<8><<<grid, 256, smem, st>>>(SA, rank, blocks, tiles, num_tiles, depth, kbuf, vbuf, hist,
+                                                     passes);
+    } else if (radix_bits == 11) {
+        static bool attr = [] {
+            cudaFuncSetAttribute((void*)k_large_prologue<11>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 4 * 2048 * 4);
+            return true;
+        }();
+        (void)attr;
+        k_large_prologue<11><<<grid, 256, smem, st>>>(SA, rank, blocks, tiles, num_tiles, depth, kbuf, vbuf, hist,
+                                                      passes);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_small(uint32_t* SA, uint32_t* key2, uint32_t* rank, const BlockInfo* blocks, Bins cur,
+                              Bins next, const uint32_t* depth, const uint32_t* host_counts, uint32_t* ctrl,
+                              cudaStream_t st, int* launched) {
+    int g_tiny = num_sms() * 16, g_med = num_sms() * 8;
+    if (host_counts) {
+        g_tiny = host_counts[0] ? grid_for(host_counts[0], 8, 16) : 0;
+        g_med = host_counts[1] ? grid_for(host_counts[1], 1, 8) : 0;
+    }
+    *launched = 0;
+    if (g_tiny) {
+        k_sort_tiny<<<g_tiny, 256, 0, st>>>(SA, key2, rank, blocks, cur, next, depth, ctrl);
+        ++*launched;
+    }
+    if (g_med) {
+        k_sort_med<<<g_med, 256, 0, st>>>(SA, key2, rank, blocks, cur, next, depth, ctrl);
+        ++*launched;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rename_large(const uint32_t* SA, const uint32_t* key2, uint32_t* rank, const BlockInfo* blocks,
+                                const TileDesc* tiles, const uint32_t* num_tiles, Bins next, const uint32_t* depth,
+                                uint32_t* ctrl, cudaStream_t st) {
+    k_rename_large<<<num_sms() * 8, 256, 0, st>>>(SA, key2, rank, blocks, tiles, num_tiles, next, depth, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_L(const uint8_t* S, const uint32_t* SA, const BlockInfo* blocks, const TileDesc* tiles,
+                            uint32_t num_tiles, uint8_t* L, int32_t* primary, cudaStream_t st) {
+    if (!num_tiles) return cudaSuccess;
+    k_gather_L<<<grid_for(num_tiles, 1, 16), 256, 0, st>>>(S, SA, blocks, tiles, num_tiles, L, primary);
+    return cudaGetLastError();
+}
+
+// ---- control kernels --------------------------------------------------------
+
+__global__ void k_reset_ctrl(uint32_t* ctrl, uint32_t spin, uint32_t withhold, uint32_t ntiles0) {
+    for (int i = threadIdx.x; i < CTRL_WORDS; i += blockDim.x) ctrl[i] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctrl[CTRL_SPIN] = spin;
+        ctrl[CTRL_WITHHOLD] = withhold;
+        ctrl[CTRL_NTILES0] = ntiles0;
+        ctrl[CTRL_DEPTH] = 8u;
+    }
+}
+
+// After a round that read bins[par]: advance the depth if the round had
+// work, and (graph mode) set the loop condition from bins[par ^ 1].
+__global__ void k_round_end(uint32_t* ctrl, int par, uint32_t max_n, cudaGraphConditionalHandle cond, int use_cond,
+                            int count_body) {
+    const uint32_t* cur = ctrl + CTRL_BINS + 3 * par;
+    const uint32_t* nxt = ctrl + CTRL_BINS + 3 * (par ^ 1);
+    const bool active = (cur[0] | cur[1] | cur[2]) != 0u;
+    if (active) {
+        ctrl[CTRL_DEPTH] *= 2u;
+        ctrl[CTRL_ROUNDS] += 1u;
+    }
+    if (count_body) ctrl[CTRL_BODY_ITERS] += 1u;
+    if (use_cond) {
+        const bool more = (nxt[0] | nxt[1] | nxt[2]) != 0u && ctrl[CTRL_DEPTH] < max_n && ctrl[CTRL_ROUNDS] < 40u &&
+                          ctrl[CTRL_ERR] == 0u;
+        cudaGraphSetConditional(cond, more ? 1u : 0u);
+    }
+}
+
+__global__ void k_set_cond_initial(const uint32_t* ctrl, uint32_t max_n, cudaGraphConditionalHandle cond) {
+    const uint32_t* c = ctrl + CTRL_BINS;
+    const bool more = (c[0] | c[1] | c[2]) != 0u && ctrl[CTRL_DEPTH] < max_n && ctrl[CTRL_ERR] == 0u;
+    cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+
+cudaError_t launch_reset_ctrl(uint32_t* ctrl, uint32_t spin, uint32_t withhold, uint32_t ntiles0, cudaStream_t st) {
+    k_reset_ctrl<<<1, 128, 0, st>>>(ctrl, spin, withhold, ntiles0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round_end(uint32_t* ctrl, int par, uint32_t max_n, cudaGraphConditionalHandle cond, int use_cond,
+                             int count_body, cudaStream_t st) {
+    k_round_end<<<1, 1, 0, st>>>(ctrl, par, max_n, cond, use_cond, count_body);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_cond_initial(const uint32_t* ctrl, uint32_t max_n, cudaGraphConditionalHandle cond,
+                                    cudaStream_t st) {
+    k_set_cond_initial<<<1, 1, 0, st>>>(ctrl, max_n, cond);
+    return cudaGetLastError();
+}
+
+}  // namespace bwt

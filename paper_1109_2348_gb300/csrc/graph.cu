@@ -1,0 +1,146 @@
+// BWT_F_GRAPH: the whole batch as one CUDA graph, replayed when the block
+// layout and buffers repeat.
+//
+// Graph = reset -> first sort + naming -> set loop condition ->
+//         WHILE(cond) { round on bins[0]; round on bins[1]; set cond } ->
+//         L gather.
+// The body holds two rounds so the double-buffered group bins alternate
+// inside one fixed graph; a round whose input bins are empty is a chain of
+// early-exiting persistent kernels. The loop condition (groups left, depth
+// below the largest block, no device error, at most 40 rounds) is computed
+// on the device, so a replay never returns to the host between rounds.
+#include <cstring>
+#include <vector>
+
+#include "kernels.h"
+#include "plan_internal.h"
+
+using namespace bwt;
+
+#define CKG(call)                                             \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) {                              \
+            status = record_cuda(_e, #call);                  \
+            goto fail;                                        \
+        }                                                     \
+    } while (0)
+
+#define CKS(call)                   \
+    do {                            \
+        status = (call);            \
+        if (status != BWT_OK) goto fail; \
+    } while (0)
+
+static std::vector<uint64_t> graph_key_of(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary) {
+    std::vector<uint64_t> k = {(uint64_t)(uintptr_t)d_in, (uint64_t)(uintptr_t)d_L, (uint64_t)(uintptr_t)d_primary,
+                               (uint64_t)p->rbits, (uint64_t)p->tile, (uint64_t)p->spin_limit,
+                               (uint64_t)p->withhold, (uint64_t)p->nb};
+    k.insert(k.end(), p->h_off, p->h_off + p->nb + 1);
+    return k;
+}
+
+bwt_status bwt::run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st) {
+    std::vector<uint64_t> key = graph_key_of(p, d_in, d_L, d_primary);
+    if (p->graph_exec && key == p->graph_key) {
+        cudaError_t e = cudaGraphLaunch(p->graph_exec, st);
+        if (e != cudaSuccess) return record_cuda(e, "cudaGraphLaunch");
+        p->stats.graph_replayed = 1;
+        p->stats.kernel_launches = 0;
+        p->stats.radix_launches = 0;
+        return BWT_OK;
+    }
+    drop_graph(p);
+
+    bwt_status status = BWT_OK;
+    cudaStream_t cs = nullptr, bs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaStreamCaptureStatus cst;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cudaGraphNode_t cnode;
+    cudaGraph_t body;
+    uint64_t k0, k1, k2, k3, r0, r1, r2, r3;
+
+    CKG(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    CKG(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+    CKG(cudaGraphCreate(&g, 0));
+    CKG(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
+    p->capturing = true;
+    CKG(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    k0 = p->stats.kernel_launches;
+    r0 = p->stats.radix_launches;
+    CKS(reset_ctrl(p, cs));
+    CKS(enqueue_initial_sort(p, d_in, cs));
+    CKG(launch_set_cond_initial(p->ctrl, p->max_n, cond, cs));
+    p->stats.kernel_launches++;
+    k1 = p->stats.kernel_launches;
+    r1 = p->stats.radix_launches;
+    CKG(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CKG(cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp));
+    body = cp.conditional.phGraph_out[0];
+    CKG(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CKG(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    CKS(enqueue_round(p, 0, nullptr, bs));
+    CKG(launch_round_end(p->ctrl, 0, p->max_n, cond, 0, 0, bs));
+    CKS(enqueue_round(p, 1, nullptr, bs));
+    CKG(launch_round_end(p->ctrl, 1, p->max_n, cond, 1, 1, bs));
+    p->stats.kernel_launches += 2;
+    CKG(cudaStreamEndCapture(bs, &body));
+    k2 = p->stats.kernel_launches;
+    r2 = p->stats.radix_launches;
+    CKG(launch_gather_L(d_in, p->sa, p->blocks, p->tiles0, p->ntiles0, d_L, d_primary, cs));
+    p->stats.kernel_launches++;
+    k3 = p->stats.kernel_launches;
+    r3 = p->stats.radix_launches;
+    CKG(cudaStreamEndCapture(cs, &g));
+    p->capturing = false;
+    CKG(cudaGraphInstantiate(&exec, g, 0));
+    p->graph = g;
+    p->graph_exec = exec;
+    p->graph_key = key;
+    p->graph_main_kernels = (k1 - k0) + (k3 - k2);
+    p->graph_body_kernels = k2 - k1;
+    p->graph_main_radix = (r1 - r0) + (r3 - r2);
+    p->graph_body_radix = r2 - r1;
+    cudaStreamDestroy(cs);
+    cudaStreamDestroy(bs);
+    p->stats.kernel_launches = 0;
+    p->stats.radix_launches = 0;
+    {
+        cudaError_t e = cudaGraphLaunch(exec, st);
+        if (e != cudaSuccess) return record_cuda(e, "cudaGraphLaunch");
+    }
+    return BWT_OK;
+
+fail:
+    p->capturing = false;
+    if (cs) {
+        cudaGraph_t tmp = nullptr;
+        cudaStreamEndCapture(cs, &tmp);
+        cudaStreamDestroy(cs);
+    }
+    if (bs) {
+        cudaGraph_t tmp = nullptr;
+        cudaStreamEndCapture(bs, &tmp);
+        cudaStreamDestroy(bs);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return status;
+}
+
+// After a graph run: kernel and round counts from the device control words.
+void bwt::graph_stats(bwt_plan* p) {
+    const uint64_t iters = p->h_ctrl[CTRL_BODY_ITERS];
+    p->stats.rounds = p->h_ctrl[CTRL_ROUNDS];
+    p->stats.kernel_launches = p->graph_main_kernels + iters * p->graph_body_kernels;
+    p->stats.radix_launches = p->graph_main_radix + iters * p->graph_body_radix;
+}

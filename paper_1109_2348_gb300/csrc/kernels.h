@@ -1,0 +1,112 @@
+// Host-side launchers of the BWT kernels (implemented in radix.cu,
+// doubling.cu). All take device pointers and a stream and return the CUDA
+// launch error.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bwt_internal.cuh"
+
+namespace bwt {
+
+// ---- segmented onesweep LSD radix pass -----------------------------------
+
+struct OneSweepParams {
+    const void* kin;              // keys in (u64 or u32); unused when reading S
+    const uint32_t* vin;          // values in
+    void* kout;                   // keys out
+    uint32_t* vout;               // values out
+    const uint8_t* S;             // blocks (first pass of the first sort only)
+    const BlockInfo* blocks;
+    const TileDesc* tiles;
+    const uint32_t* num_tiles;    // device count of tiles
+    const uint32_t* seg_base;     // per segment, per digit: exclusive digit offset in the segment
+    uint32_t seg_base_stride;     // words between consecutive segments' rows
+    uint32_t* status;             // [tile][radix] look-back words, zeroed before the pass
+    uint32_t* tile_counter;       // zeroed before the pass
+    uint32_t* ctrl;               // device control words (spin limit, error)
+    int shift;                    // digit = (key >> shift) & (radix - 1)
+};
+
+// key_bytes: 8 (u64 rotation prefixes), 4 (u32 doubling ranks) or -8 (u64
+// keys whose digit is taken from the u32 value; radix_bits 8 only).
+// from_s: build the u64 keys from the block bytes instead of reading kin.
+cudaError_t launch_onesweep(int key_bytes, bool from_s, int radix_bits, int tile, const OneSweepParams& p,
+                            int grid, cudaStream_t st);
+int onesweep_grid(int key_bytes, bool from_s, int radix_bits, int tile);
+size_t onesweep_smem(int key_bytes, bool from_s, int radix_bits, int tile);
+
+// ---- histograms of the first sort ---------------------------------------
+
+// Byte histogram of every block (d = 8: every pass of the first sort has the
+// block's byte histogram as its digit histogram, because the pass-p digit of
+// rotation i is S[(i + 7 - p) mod n]). hist: [block][256], zeroed.
+cudaError_t launch_hist_bytes(const uint8_t* S, const BlockInfo* blocks, const TileDesc* tiles,
+                              uint32_t num_tiles, uint32_t* hist, cudaStream_t st);
+
+// Per-pass digit histograms of the u64 rotation prefixes for radix_bits = 11:
+// hist: [block][passes][2048], zeroed.
+cudaError_t launch_hist_keys11(const uint8_t* S, const BlockInfo* blocks, const TileDesc* tiles,
+                               uint32_t num_tiles, int tile, uint32_t* hist, cudaStream_t st);
+
+// Exclusive scan of every row of `radix` counts, in place; rows = *num_rows_dev
+// * rows_mult (or rows_host if num_rows_dev is null), at most max_rows.
+cudaError_t launch_scan_rows(uint32_t* hist, int radix, const uint32_t* num_rows_dev, uint32_t rows_mult,
+                             uint32_t rows_host, uint32_t max_rows, cudaStream_t st);
+
+// Zero count * words_per_unit words (count read on the device).
+cudaError_t launch_zero_by_count(uint32_t* p, const uint32_t* count, uint32_t words_per_unit, uint32_t max_words,
+                                 cudaStream_t st);
+
+// ---- naming, doubling rounds, L gather (doubling.cu) --------------------
+
+// First naming after the u64 sort: rank of every rotation = start of its
+// group of equal 8-byte prefixes; groups of size > 1 go to `bins` unless
+// 8 >= n (then they are identical rotations and final).
+cudaError_t launch_name_initial(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks,
+                                const TileDesc* tiles, uint32_t num_tiles, uint32_t* rank, Bins bins,
+                                uint32_t* ctrl, cudaStream_t st);
+
+// Round with prefix length h = *depth: key2[k] = rank[(SA[k] + h) mod n] for
+// every element of the tiny and medium groups in `cur`.
+cudaError_t launch_gather_small(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks, Bins cur,
+                                const uint32_t* depth, uint32_t* key2, const uint32_t* host_counts, cudaStream_t st);
+
+// Builds the radix tile table of the large groups of `cur`, its count and
+// the number of keys in large groups.
+cudaError_t launch_build_large_tiles(Bins cur, int tile, TileDesc* tiles, uint32_t max_tiles, uint32_t* ctrl,
+                                     cudaStream_t st);
+
+// Large groups: gathers key2 and copies SA into (kbuf, vbuf) at the same
+// positions and builds per-group digit histograms hist[group][passes][radix].
+cudaError_t launch_large_prologue(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks,
+                                  const TileDesc* tiles, const uint32_t* num_tiles, const uint32_t* depth,
+                                  uint32_t* kbuf, uint32_t* vbuf, uint32_t* hist, int radix_bits, int passes,
+                                  cudaStream_t st);
+
+// Tiny and medium groups: sort by (key2, SA), rename, emit refined groups.
+cudaError_t launch_sort_small(uint32_t* SA, uint32_t* key2, uint32_t* rank, const BlockInfo* blocks, Bins cur,
+                              Bins next, const uint32_t* depth, const uint32_t* host_counts, uint32_t* ctrl,
+                              cudaStream_t st, int* launched);
+
+// Large groups after their radix sort: rename and emit refined groups.
+cudaError_t launch_rename_large(const uint32_t* SA, const uint32_t* key2, uint32_t* rank, const BlockInfo* blocks,
+                                const TileDesc* tiles, const uint32_t* num_tiles, Bins next, const uint32_t* depth,
+                                uint32_t* ctrl, cudaStream_t st);
+
+// Control words: reset before a batch; advance after a round (and set the
+// graph loop condition); set the condition before the loop.
+cudaError_t launch_reset_ctrl(uint32_t* ctrl, uint32_t spin, uint32_t withhold, uint32_t ntiles0, cudaStream_t st);
+cudaError_t launch_round_end(uint32_t* ctrl, int par, uint32_t max_n, cudaGraphConditionalHandle cond, int use_cond,
+                             int count_body, cudaStream_t st);
+cudaError_t launch_set_cond_initial(const uint32_t* ctrl, uint32_t max_n, cudaGraphConditionalHandle cond,
+                                    cudaStream_t st);
+
+// L[k] = S[(SA[k] + n - 1) mod n]; primary[b] = the k with SA[k] = 0.
+cudaError_t launch_gather_L(const uint8_t* S, const uint32_t* SA, const BlockInfo* blocks, const TileDesc* tiles,
+                            uint32_t num_tiles, uint8_t* L, int32_t* primary, cudaStream_t st);
+
+int num_sms();
+
+}  // namespace bwt

@@ -1,0 +1,586 @@
+// Host side of the C ABI: plan creation, argument checks and the launch
+// sequence of one batch.
+//
+//   per batch:  histograms -> P onesweep passes over the u64 prefixes (the
+//               first pass builds the keys from the bytes) -> naming ->
+//               doubling rounds (gather, small-group sorts, large-group
+//               radix, rename) until no group is left -> L gather.
+//
+// The host reads three group counts per doubling round to decide whether to
+// go on; in BWT_F_GRAPH mode the same launches sit in a CUDA graph whose
+// doubling loop is a conditional WHILE node evaluated on the device.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bwt.h"
+#include "kernels.h"
+#include "plan_internal.h"
+
+using namespace bwt;
+
+static thread_local std::string g_cuda_err = "no error";
+static std::mutex g_err_mu;
+static std::string g_cuda_err_global = "no error";
+
+bwt_status bwt::record_cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return BWT_OK;
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_cuda_err_global = std::string(what) + ": " + cudaGetErrorString(e);
+    return BWT_ECUDA;
+}
+
+#define CK(call)                                               \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return record_cuda(_e, #call);  \
+    } while (0)
+
+extern "C" const char* bwt_last_cuda_error(void) {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    static thread_local std::string copy;
+    copy = g_cuda_err_global;
+    return copy.c_str();
+}
+
+extern "C" const char* bwt_status_string(bwt_status s) {
+    switch (s) {
+    case BWT_OK: return "BWT_OK";
+    case BWT_EINVAL: return "BWT_EINVAL";
+    case BWT_ENOMEM: return "BWT_ENOMEM";
+    case BWT_ECAPACITY: return "BWT_ECAPACITY";
+    case BWT_ECUDA: return "BWT_ECUDA";
+    case BWT_ETIMEOUT: return "BWT_ETIMEOUT";
+    case BWT_EMISMATCH: return "BWT_EMISMATCH";
+    case BWT_ENOMODEL: return "BWT_ENOMODEL";
+    }
+    return "BWT_UNKNOWN";
+}
+
+namespace {
+
+constexpr uint32_t kDefaultSpin = 1u << 24;  // ~1 s of polling with back-off
+
+template <typename T>
+bwt_status dev_alloc(T** p, size_t count, size_t* total) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        record_cuda(e, "cudaMalloc");
+        *p = nullptr;
+        return BWT_ENOMEM;
+    }
+    *total += count * sizeof(T);
+    return BWT_OK;
+}
+
+template <typename T>
+bwt_status host_alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMallocHost((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        record_cuda(e, "cudaMallocHost");
+        *p = nullptr;
+        return BWT_ENOMEM;
+    }
+    return BWT_OK;
+}
+
+int bits_for(uint32_t max_value) {  // bits to hold 0..max_value
+    int b = 0;
+    while (b < 32 && (max_value >> b) != 0) ++b;
+    return b;
+}
+
+bool valid_radix(int rb) { return rb == 8 || rb == 11; }
+bool valid_tile(int t) { return t == 1024 || t == 2048 || t == 4096; }
+
+}  // namespace
+
+void bwt::free_plan_memory(bwt_plan* p) {
+    auto F = [](void* q) {
+        if (q) cudaFree(q);
+    };
+    auto FH = [](void* q) {
+        if (q) cudaFreeHost(q);
+    };
+    F(p->keys[0]); F(p->keys[1]); F(p->vals[0]); F(p->vals[1]); F(p->rank);
+    F(p->tiles0); F(p->ltiles); F(p->blocks); F(p->hist); F(p->status); F(p->ctrl);
+    for (int s = 0; s < 2; ++s)
+        for (int c = 0; c < 3; ++c) F(p->bins[s][c]);
+    F(p->splitters); F(p->bucket_count);
+    FH(p->h_ctrl); FH(p->h_tiles); FH(p->h_blocks); FH(p->h_off);
+    for (auto& e : p->events) cudaEventDestroy(e);
+    p->events.clear();
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->graph_exec = nullptr;
+    p->graph = nullptr;
+}
+
+extern "C" bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt_plan** out) {
+    if (!out) return BWT_EINVAL;
+    *out = nullptr;
+    if (!desc || desc->max_blocks == 0 || desc->max_total_bytes == 0 || desc->max_total_bytes >= (1ull << 32) ||
+        desc->max_block_bytes == 0 || desc->max_block_bytes >= (1u << 30))
+        return BWT_EINVAL;
+    if (desc->radix_bits != 0 && !valid_radix(desc->radix_bits)) return BWT_EINVAL;
+    if (desc->tile_keys != 0 && !valid_tile(desc->tile_keys)) return BWT_EINVAL;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return BWT_EINVAL;
+    CK(cudaSetDevice(device));
+
+    bwt_plan* p = new bwt_plan();
+    p->device = device;
+    p->desc = *desc;
+    p->model_path = desc->model_path ? desc->model_path : "";
+    p->desc.model_path = nullptr;
+    p->rbits = desc->radix_bits ? desc->radix_bits : 8;
+    p->tile = desc->tile_keys ? desc->tile_keys : 4096;
+    p->spin_limit = kDefaultSpin;
+    const uint64_t N = desc->max_total_bytes;
+    const uint32_t B = desc->max_blocks;
+    p->cap_n = N;
+    p->cap_b = B;
+    p->cap_tiles0 = (uint32_t)((N + 1023) / 1024 + B);
+    p->cap_ltiles = (uint32_t)(N / 1024 + N / (MED_MAX + 1) + 2);
+    p->bincap[0] = (uint32_t)(N / 2 + 1);
+    p->bincap[1] = (uint32_t)(N / (TINY_MAX + 1) + 1);
+    p->bincap[2] = (uint32_t)(N / (MED_MAX + 1) + 1);
+    const uint64_t large_groups = p->bincap[2];
+    p->cap_hist = std::max<uint64_t>({(uint64_t)B * 6 * 2048, (uint64_t)B * 256, large_groups * 4 * 256,
+                                      large_groups * 3 * 2048});
+    p->cap_status = (uint64_t)std::max(p->cap_tiles0, p->cap_ltiles) * 2048;
+
+    bwt_status s = BWT_OK;
+    size_t total = 0;
+    auto A = [&](bwt_status r) {
+        if (s == BWT_OK && r != BWT_OK) s = r;
+    };
+    A(dev_alloc(&p->keys[0], N, &total));
+    A(dev_alloc(&p->keys[1], N, &total));
+    A(dev_alloc(&p->vals[0], N, &total));
+    A(dev_alloc(&p->vals[1], N, &total));
+    A(dev_alloc(&p->rank, N, &total));
+    A(dev_alloc(&p->tiles0, p->cap_tiles0, &total));
+    A(dev_alloc(&p->ltiles, p->cap_ltiles, &total));
+    A(dev_alloc(&p->blocks, B, &total));
+    A(dev_alloc(&p->hist, p->cap_hist, &total));
+    A(dev_alloc(&p->status, p->cap_status, &total));
+    A(dev_alloc(&p->ctrl, CTRL_WORDS, &total));
+    for (int par = 0; par < 2; ++par)
+        for (int c = 0; c < 3; ++c) A(dev_alloc(&p->bins[par][c], p->bincap[c], &total));
+    A(host_alloc(&p->h_ctrl, CTRL_WORDS));
+    A(host_alloc(&p->h_tiles, p->cap_tiles0));
+    A(host_alloc(&p->h_blocks, B));
+    A(host_alloc(&p->h_off, (size_t)B + 1));
+    p->device_bytes = total;
+    if (s == BWT_OK && (desc->flags & BWT_F_TIMING)) {
+        p->events.resize(512);
+        for (auto& e : p->events) {
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                s = BWT_ECUDA;
+                break;
+            }
+        }
+    }
+    if (s == BWT_OK && (desc->flags & BWT_F_LEARNED)) s = load_model(p, p->model_path.c_str());
+    if (s != BWT_OK) {
+        free_plan_memory(p);
+        delete p;
+        return s;
+    }
+    *out = p;
+    return BWT_OK;
+}
+
+extern "C" bwt_status bwt_plan_destroy(bwt_plan* plan) {
+    if (!plan) return BWT_OK;
+    cudaSetDevice(plan->device);
+    free_plan_memory(plan);
+    delete plan;
+    return BWT_OK;
+}
+
+extern "C" bwt_status bwt_plan_last_status(const bwt_plan* plan) {
+    return plan ? plan->last : BWT_EINVAL;
+}
+
+extern "C" bwt_status bwt_plan_stats(const bwt_plan* plan, bwt_stats* out) {
+    if (!plan || !out) return BWT_EINVAL;
+    *out = plan->stats;
+    return BWT_OK;
+}
+
+extern "C" bwt_status bwt_plan_set_radix(bwt_plan* plan, int radix_bits, int tile_keys) {
+    if (!plan || !valid_radix(radix_bits) || !valid_tile(tile_keys)) return BWT_EINVAL;
+    plan->rbits = radix_bits;
+    plan->tile = tile_keys;
+    drop_graph(plan);
+    return BWT_OK;
+}
+
+extern "C" bwt_status bwt_plan_debug_waits(bwt_plan* plan, uint32_t spin_limit, int withhold_publish) {
+    if (!plan) return BWT_EINVAL;
+    plan->spin_limit = spin_limit ? spin_limit : kDefaultSpin;
+    plan->withhold = withhold_publish ? 1 : 0;
+    drop_graph(plan);
+    return BWT_OK;
+}
+
+void bwt::drop_graph(bwt_plan* p) {
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->graph_exec = nullptr;
+    p->graph = nullptr;
+    p->graph_key.clear();
+}
+
+// ---------------------------------------------------------------------------
+// Argument checks and per-batch host tables.
+
+bwt_status bwt::prepare_batch(bwt_plan* p, const uint64_t* offsets, uint32_t nb, cudaStream_t st) {
+    if (nb == 0 || nb > p->cap_b || !offsets) return BWT_EINVAL;
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, offsets);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        attr.type = cudaMemoryTypeUnregistered;
+    }
+    CK(cudaStreamSynchronize(st));  // the pinned staging tables of the last call are free again
+    if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) {
+        CK(cudaMemcpyAsync(p->h_off, offsets, sizeof(uint64_t) * (nb + 1), cudaMemcpyDefault, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(p->h_off, offsets, sizeof(uint64_t) * (nb + 1));
+    }
+    const uint64_t* off = p->h_off;
+    if (off[0] != 0) return BWT_EINVAL;
+    for (uint32_t b = 0; b < nb; ++b) {
+        if (off[b + 1] <= off[b]) return BWT_EINVAL;
+        if (off[b + 1] - off[b] > p->desc.max_block_bytes) return BWT_EINVAL;
+    }
+    if (off[nb] > p->cap_n) return BWT_EINVAL;
+    return upload_tables(p, off, nb, st);
+}
+
+// Block and first-sort tile tables for blocks off[b] .. off[b+1] (global
+// positions as given), uploaded from pinned staging memory.
+bwt_status bwt::upload_tables(bwt_plan* p, const uint64_t* off, uint32_t nb, cudaStream_t st) {
+    uint32_t max_n = 0;
+    const uint32_t T = (uint32_t)p->tile;
+    uint32_t nt = 0;
+    for (uint32_t b = 0; b < nb; ++b) {
+        const uint32_t o = (uint32_t)off[b], n = (uint32_t)(off[b + 1] - off[b]);
+        max_n = std::max(max_n, n);
+        p->h_blocks[b] = BlockInfo{o, n};
+        const uint32_t first = nt;
+        for (uint32_t s = 0; s < n; s += T) {
+            TileDesc td;
+            td.start = o + s;
+            td.len = std::min(T, n - s);
+            td.seg = b;
+            td.firstTile = first;
+            td.segStart = o;
+            td.blk = b;
+            td.pad0 = n;
+            td.pad1 = 0;
+            p->h_tiles[nt++] = td;
+        }
+    }
+    p->nb = nb;
+    p->total = (uint32_t)(off[nb] - off[0]);
+    p->max_n = max_n;
+    p->ntiles0 = nt;
+    CK(cudaMemcpyAsync(p->blocks, p->h_blocks, sizeof(BlockInfo) * nb, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p->tiles0, p->h_tiles, sizeof(TileDesc) * nt, cudaMemcpyHostToDevice, st));
+    return BWT_OK;
+}
+
+Bins bwt::bins_of(bwt_plan* p, int par) {
+    Bins b;
+    for (int c = 0; c < 3; ++c) {
+        b.list[c] = p->bins[par][c];
+        b.cap[c] = p->bincap[c];
+    }
+    b.count = p->ctrl + CTRL_BINS + 3 * par;
+    b.active = reinterpret_cast<unsigned long long*>(p->ctrl + CTRL_ACTIVE);
+    return b;
+}
+
+// Records an event pair around a radix launch when timing is on.
+static cudaError_t timed_onesweep(bwt_plan* p, int key_bytes, bool from_s, const OneSweepParams& a,
+                                  double bytes_per_key, uint64_t keys_host, int ctrl_keys_word, cudaStream_t st) {
+    const bool timing = !p->events.empty() && !p->capturing && p->ev_used + 2 <= p->events.size();
+    if (timing) cudaEventRecord(p->events[p->ev_used], st);
+    cudaError_t e = launch_onesweep(key_bytes, from_s, p->rbits, p->tile, a, 0, st);
+    if (timing) {
+        cudaEventRecord(p->events[p->ev_used + 1], st);
+        EvMeta m;
+        m.bytes_per_key = bytes_per_key;
+        m.keys_host = keys_host;
+        m.ctrl_word = ctrl_keys_word;
+        p->ev_meta.push_back(m);
+        p->ev_used += 2;
+    }
+    p->stats.radix_launches++;
+    p->stats.kernel_launches++;
+    return e;
+}
+
+bwt_status bwt::reset_ctrl(bwt_plan* p, cudaStream_t st) {
+    CK(launch_reset_ctrl(p->ctrl, p->spin_limit, (uint32_t)p->withhold, p->ntiles0, st));
+    p->stats.kernel_launches++;
+    return BWT_OK;
+}
+
+// First sort: P passes over the u64 prefixes (the first pass builds the keys
+// from the bytes), then naming into bins[0].
+bwt_status bwt::enqueue_initial_sort(bwt_plan* p, const uint8_t* d_in, cudaStream_t st) {
+    const int rb = p->rbits, RADIX = 1 << rb;
+    const int P = (64 + rb - 1) / rb;
+    const uint32_t nb = p->nb, nt = p->ntiles0;
+    uint32_t* ctrl = p->ctrl;
+    uint32_t seg_stride;
+    if (rb == 8) {
+        CK(cudaMemsetAsync(p->hist, 0, sizeof(uint32_t) * 256 * nb, st));
+        CK(launch_hist_bytes(d_in, p->blocks, p->tiles0, nt, p->hist, st));
+        CK(launch_scan_rows(p->hist, 256, nullptr, 0, nb, nb, st));
+        seg_stride = 256;
+    } else {
+        CK(cudaMemsetAsync(p->hist, 0, sizeof(uint32_t) * 6 * 2048 * nb, st));
+        CK(launch_hist_keys11(d_in, p->blocks, p->tiles0, nt, p->tile, p->hist, st));
+        CK(launch_scan_rows(p->hist, 2048, nullptr, 0, nb * 6, nb * 6, st));
+        seg_stride = 6 * 2048;
+    }
+    p->stats.kernel_launches += 2;
+    for (int ps = 0; ps < P; ++ps) {
+        CK(cudaMemsetAsync(p->status, 0, sizeof(uint32_t) * (size_t)nt * RADIX, st));
+        OneSweepParams a{};
+        a.kin = ps == 0 ? nullptr : p->keys[(ps - 1) & 1];
+        a.vin = ps == 0 ? nullptr : p->vals[(ps - 1) & 1];
+        a.kout = p->keys[ps & 1];
+        a.vout = p->vals[ps & 1];
+        a.S = d_in;
+        a.blocks = p->blocks;
+        a.tiles = p->tiles0;
+        a.num_tiles = ctrl + CTRL_NTILES0;
+        a.seg_base = p->hist + (rb == 8 ? 0 : ps * 2048);
+        a.seg_base_stride = seg_stride;
+        a.status = p->status;
+        a.tile_counter = ctrl + CTRL_TILE_CTR + ps;
+        a.ctrl = ctrl;
+        a.shift = ps * rb;
+        CK(timed_onesweep(p, 8, ps == 0, a, ps == 0 ? 13.0 : 24.0, p->total, -1, st));
+    }
+    p->sa = p->vals[(P - 1) & 1];
+    p->key2 = p->vals[P & 1];
+    p->kA = reinterpret_cast<uint32_t*>(p->keys[P & 1]);
+    p->vA = p->kA + p->cap_n;
+    p->kB = reinterpret_cast<uint32_t*>(p->keys[(P - 1) & 1]);
+    p->vB = p->kB + p->cap_n;
+    return enqueue_naming(p, p->keys[(P - 1) & 1], st);
+}
+
+bwt_status bwt::enqueue_naming(bwt_plan* p, const uint64_t* K, cudaStream_t st) {
+    CK(cudaMemsetAsync(p->ctrl + CTRL_BINS, 0, sizeof(uint32_t) * 6, st));
+    CK(launch_name_initial(K, p->sa, p->blocks, p->tiles0, p->ntiles0, p->rank, bins_of(p, 0), p->ctrl, st));
+    p->stats.kernel_launches++;
+    return BWT_OK;
+}
+
+// One doubling round reading bins[par] and writing bins[par ^ 1]; the prefix
+// length h sits in ctrl[CTRL_DEPTH]. host_counts: the three group counts when
+// the host knows them (else null: persistent grids read them on the device).
+bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts, cudaStream_t st) {
+    const int rb = p->rbits, RADIX = 1 << rb;
+    const int kbits = bits_for(p->max_n - 1);
+    const int P2 = std::max(1, (kbits + rb - 1) / rb);
+    uint32_t* ctrl = p->ctrl;
+    const uint32_t* depth = ctrl + CTRL_DEPTH;
+    Bins cur = bins_of(p, par), nxt = bins_of(p, par ^ 1);
+    CK(cudaMemsetAsync(nxt.count, 0, sizeof(uint32_t) * 3, st));
+    if (!host_counts || host_counts[0] + host_counts[1] > 0) {
+        CK(launch_gather_small(p->sa, p->rank, p->blocks, cur, depth, p->key2, host_counts, st));
+        p->stats.kernel_launches++;
+    }
+    const bool large = !host_counts || host_counts[2] > 0;
+    const uint32_t hist_cap = (uint32_t)std::min<uint64_t>(p->cap_hist, 0xffffffffu);
+    const uint32_t status_cap = (uint32_t)std::min<uint64_t>(p->cap_status, 0xffffffffu);
+    if (large) {
+        CK(launch_build_large_tiles(cur, p->tile, p->ltiles, p->cap_ltiles, ctrl, st));
+        CK(launch_zero_by_count(p->hist, cur.count + 2, (uint32_t)(P2 * RADIX), hist_cap, st));
+        CK(launch_large_prologue(p->sa, p->rank, p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, depth, p->kA, p->vA,
+                                 p->hist, rb, P2, st));
+        CK(launch_scan_rows(p->hist, RADIX, cur.count + 2, (uint32_t)P2, 0, (uint32_t)(p->cap_hist / RADIX), st));
+        p->stats.kernel_launches += 4;
+        for (int ps = 0; ps < P2; ++ps) {
+            CK(launch_zero_by_count(p->status, ctrl + CTRL_NUM_LTILES, (uint32_t)RADIX, status_cap, st));
+            CK(cudaMemsetAsync(ctrl + CTRL_TILE_CTR + 16 + ps, 0, 4, st));
+            p->stats.kernel_launches++;
+            OneSweepParams a{};
+            const bool last = ps == P2 - 1;
+            a.kin = ps == 0 ? p->kA : ((ps - 1) & 1 ? p->kA : p->kB);
+            a.vin = ps == 0 ? p->vA : ((ps - 1) & 1 ? p->vA : p->vB);
+            a.kout = last ? p->key2 : (ps & 1 ? p->kA : p->kB);
+            a.vout = last ? p->sa : (ps & 1 ? p->vA : p->vB);
+            a.blocks = p->blocks;
+            a.tiles = p->ltiles;
+            a.num_tiles = ctrl + CTRL_NUM_LTILES;
+            a.seg_base = p->hist + ps * RADIX;
+            a.seg_base_stride = (uint32_t)(P2 * RADIX);
+            a.status = p->status;
+            a.tile_counter = ctrl + CTRL_TILE_CTR + 16 + ps;
+            a.ctrl = ctrl;
+            a.shift = ps * rb;
+            CK(timed_onesweep(p, 4, false, a, 16.0, 0, CTRL_LARGE_KEYS, st));
+        }
+    }
+    int launched = 0;
+    CK(launch_sort_small(p->sa, p->key2, p->rank, p->blocks, cur, nxt, depth, host_counts, ctrl, st, &launched));
+    p->stats.kernel_launches += launched;
+    if (large) {
+        CK(launch_rename_large(p->sa, p->key2, p->rank, p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, nxt, depth,
+                               ctrl, st));
+        p->stats.kernel_launches++;
+    }
+    return BWT_OK;
+}
+
+bwt_status bwt::finish_status(bwt_plan* p, cudaStream_t st) {
+    CK(cudaMemcpyAsync(p->h_ctrl, p->ctrl, sizeof(uint32_t) * CTRL_WORDS, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const uint32_t err = p->h_ctrl[CTRL_ERR];
+    if (err & ERR_TIMEOUT) return BWT_ETIMEOUT;
+    if (err & ERR_CAPACITY) return BWT_ECAPACITY;
+    return BWT_OK;
+}
+
+void bwt::collect_timing(bwt_plan* p) {
+    for (size_t i = 0; i < p->ev_meta.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->events[2 * i], p->events[2 * i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        const EvMeta& m = p->ev_meta[i];
+        const uint64_t keys = m.keys_host ? m.keys_host : m.keys_dev;
+        p->stats.radix_ms += ms;
+        p->stats.radix_keys += keys;
+        p->radix_bytes += m.bytes_per_key * (double)keys;
+    }
+    p->ev_meta.clear();
+    p->ev_used = 0;
+}
+
+static void resolve_large_keys(bwt_plan* p, uint32_t large_keys) {
+    for (auto& m : p->ev_meta)
+        if (m.ctrl_word >= 0 && !m.resolved) {
+            m.keys_dev = large_keys;
+            m.resolved = true;
+        }
+}
+
+// Doubling rounds with the loop decided on the host (three counts read per
+// round). Starts from bins[0] filled by the naming step.
+bwt_status bwt::run_doubling_host_loop(bwt_plan* p, cudaStream_t st) {
+    int par = 0;
+    uint32_t depth = 8;
+    while (depth < p->max_n && p->stats.rounds < 40) {
+        CK(cudaMemcpyAsync(p->h_ctrl, p->ctrl, sizeof(uint32_t) * 16, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        resolve_large_keys(p, p->h_ctrl[CTRL_LARGE_KEYS]);
+        if (p->h_ctrl[CTRL_ERR]) break;
+        uint32_t counts[3];
+        for (int c = 0; c < 3; ++c) counts[c] = std::min(p->h_ctrl[CTRL_BINS + 3 * par + c], p->bincap[c]);
+        if (counts[0] + counts[1] + counts[2] == 0) break;
+        bwt_status s = enqueue_round(p, par, counts, st);
+        if (s != BWT_OK) return s;
+        CK(launch_round_end(p->ctrl, par, p->max_n, 0, 0, 0, st));
+        p->stats.kernel_launches++;
+        p->stats.rounds++;
+        depth *= 2;
+        par ^= 1;
+    }
+    CK(cudaMemcpyAsync(p->h_ctrl + CTRL_LARGE_KEYS, p->ctrl + CTRL_LARGE_KEYS, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    resolve_large_keys(p, p->h_ctrl[CTRL_LARGE_KEYS]);
+    return BWT_OK;
+}
+
+bwt_status bwt::run_plain_host_loop(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary,
+                                    cudaStream_t st) {
+    bwt_status s;
+    if ((s = reset_ctrl(p, st)) != BWT_OK) return s;
+    if ((s = enqueue_initial_sort(p, d_in, st)) != BWT_OK) return s;
+    if ((s = run_doubling_host_loop(p, st)) != BWT_OK) return s;
+    CK(launch_gather_L(d_in, p->sa, p->blocks, p->tiles0, p->ntiles0, d_L, d_primary, st));
+    p->stats.kernel_launches++;
+    return BWT_OK;
+}
+
+// Comparison mode: every block runs the whole launch chain on its own, one
+// block after another (the batch's tables are rebuilt per block).
+bwt_status bwt::run_per_block(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary,
+                              cudaStream_t st) {
+    const uint32_t nb = p->nb;
+    std::vector<uint64_t> off(p->h_off, p->h_off + nb + 1);
+    uint64_t sub[2];
+    for (uint32_t b = 0; b < nb; ++b) {
+        CK(cudaStreamSynchronize(st));  // pinned staging tables are reused per block
+        sub[0] = 0;
+        sub[1] = off[b + 1] - off[b];
+        bwt_status s = upload_tables(p, sub, 1, st);
+        if (s != BWT_OK) return s;
+        if ((s = run_plain_host_loop(p, d_in + off[b], d_L + off[b], d_primary + b, st)) != BWT_OK) return s;
+        CK(cudaMemcpyAsync(p->h_ctrl, p->ctrl, sizeof(uint32_t) * CTRL_WORDS, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (p->h_ctrl[CTRL_ERR]) return p->h_ctrl[CTRL_ERR] & ERR_TIMEOUT ? BWT_ETIMEOUT : BWT_ECAPACITY;
+    }
+    return BWT_OK;
+}
+
+extern "C" bwt_status bwt_forward_batch(bwt_plan* p, const uint8_t* d_in, const uint64_t* offsets,
+                                        uint32_t num_blocks, uint8_t* d_L, int32_t* d_primary, void* stream) {
+    if (!p || !d_in || !offsets || !d_L || !d_primary) return BWT_EINVAL;
+    if (cudaSetDevice(p->device) != cudaSuccess) return BWT_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::memset(&p->stats, 0, sizeof(p->stats));
+    p->radix_bytes = 0;
+    p->ev_meta.clear();
+    p->ev_used = 0;
+    bwt_status s = prepare_batch(p, offsets, num_blocks, st);
+    if (s == BWT_OK && (const void*)d_in == (const void*)d_L) s = BWT_EINVAL;
+    if (s != BWT_OK) {
+        p->last = s;
+        return s;
+    }
+    p->stats.radix_bits = (uint32_t)p->rbits;
+    p->stats.tile_keys = (uint32_t)p->tile;
+    if (p->desc.flags & BWT_F_PER_BLOCK_LAUNCH) {
+        s = run_per_block(p, d_in, d_L, d_primary, st);
+    } else if (p->desc.flags & BWT_F_LEARNED) {
+        s = run_learned(p, d_in, d_L, d_primary, st);
+    } else if (p->desc.flags & BWT_F_GRAPH) {
+        s = run_graph(p, d_in, d_L, d_primary, st);
+    } else {
+        s = run_plain_host_loop(p, d_in, d_L, d_primary, st);
+    }
+    if (s == BWT_OK) s = finish_status(p, st);
+    else cudaStreamSynchronize(st);
+    if ((p->desc.flags & BWT_F_GRAPH) && !(p->desc.flags & (BWT_F_PER_BLOCK_LAUNCH | BWT_F_LEARNED)))
+        graph_stats(p);
+    if (!p->events.empty()) collect_timing(p);
+    const uint64_t act = (uint64_t)p->h_ctrl[CTRL_ACTIVE] | ((uint64_t)p->h_ctrl[CTRL_ACTIVE + 1] << 32);
+    p->stats.active_elements = act;
+    p->stats.radix_bytes = p->radix_bytes;
+    p->last = s;
+    return s;
+}

@@ -1,0 +1,110 @@
+// Plan object and the host-side pieces shared by plan.cu, graph.cu and
+// learned.cu.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "bwt.h"
+#include "bwt_internal.cuh"
+
+namespace bwt {
+
+struct EvMeta {
+    double bytes_per_key;
+    uint64_t keys_host;  // keys moved, when the host knows it
+    int ctrl_word;       // else: the ctrl word holding it (read after the round), -1 if none
+    uint64_t keys_dev = 0;
+    bool resolved = false;
+};
+
+}  // namespace bwt
+
+struct bwt_plan {
+    int device = 0;
+    bwt_plan_desc desc{};
+    std::string model_path;
+    int rbits = 8, tile = 4096;
+    uint32_t spin_limit = 0;
+    int withhold = 0;
+
+    // capacities
+    uint64_t cap_n = 0;
+    uint32_t cap_b = 0, cap_tiles0 = 0, cap_ltiles = 0;
+    uint32_t bincap[3] = {0, 0, 0};
+    uint64_t cap_hist = 0, cap_status = 0;
+    size_t device_bytes = 0;
+
+    // device memory (plan-owned scratch)
+    uint64_t* keys[2] = {nullptr, nullptr};
+    uint32_t* vals[2] = {nullptr, nullptr};
+    uint32_t* rank = nullptr;
+    bwt::TileDesc* tiles0 = nullptr;
+    bwt::TileDesc* ltiles = nullptr;
+    bwt::BlockInfo* blocks = nullptr;
+    uint32_t* hist = nullptr;
+    uint32_t* status = nullptr;
+    uint32_t* ctrl = nullptr;
+    bwt::GroupDesc* bins[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+
+    // learned bucketing
+    uint64_t* splitters = nullptr;  // [4095] sorted
+    uint32_t* bucket_count = nullptr;
+    bool have_model = false;
+
+    // pinned host staging
+    uint32_t* h_ctrl = nullptr;
+    bwt::TileDesc* h_tiles = nullptr;
+    bwt::BlockInfo* h_blocks = nullptr;
+    uint64_t* h_off = nullptr;
+
+    // current batch
+    uint32_t nb = 0, total = 0, max_n = 0, ntiles0 = 0;
+    uint32_t* sa = nullptr;    // final SA buffer of the current batch
+    uint32_t* key2 = nullptr;  // doubling keys, position-indexed
+    uint32_t *kA = nullptr, *vA = nullptr, *kB = nullptr, *vB = nullptr;
+
+    // timing
+    std::vector<cudaEvent_t> events;
+    std::vector<bwt::EvMeta> ev_meta;
+    size_t ev_used = 0;
+    double radix_bytes = 0;
+
+    // CUDA graph cache
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<uint64_t> graph_key;
+    uint64_t graph_main_kernels = 0, graph_body_kernels = 0;
+    uint64_t graph_main_radix = 0, graph_body_radix = 0;
+    bool capturing = false;
+
+    bwt_stats stats{};
+    bwt_status last = BWT_OK;
+};
+
+namespace bwt {
+
+bwt_status record_cuda(cudaError_t e, const char* what);
+void free_plan_memory(bwt_plan* p);
+void drop_graph(bwt_plan* p);
+bwt_status prepare_batch(bwt_plan* p, const uint64_t* offsets, uint32_t nb, cudaStream_t st);
+bwt_status upload_tables(bwt_plan* p, const uint64_t* off, uint32_t nb, cudaStream_t st);
+Bins bins_of(bwt_plan* p, int par);
+bwt_status reset_ctrl(bwt_plan* p, cudaStream_t st);
+bwt_status enqueue_initial_sort(bwt_plan* p, const uint8_t* d_in, cudaStream_t st);
+bwt_status enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts, cudaStream_t st);
+bwt_status enqueue_naming(bwt_plan* p, const uint64_t* K, cudaStream_t st);
+bwt_status finish_status(bwt_plan* p, cudaStream_t st);
+void collect_timing(bwt_plan* p);
+bwt_status run_plain_host_loop(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st);
+bwt_status run_doubling_host_loop(bwt_plan* p, cudaStream_t st);
+bwt_status run_per_block(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st);
+bwt_status run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st);
+bwt_status run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st);
+bwt_status load_model(bwt_plan* p, const char* path);
+void graph_stats(bwt_plan* p);
+
+}  // namespace bwt

@@ -1,0 +1,476 @@
+// Segmented, stable onesweep LSD radix pass and the histograms it needs.
+//
+// The first sort of the BWT (the paper's Section 3.1: "sort the rotations")
+// orders every rotation by its 8-byte prefix, packed big-endian into a u64,
+// and carries the rotation index as the value. A segment is a block (first
+// sort) or a group of still-equal rotations (prefix-doubling rounds); tiles
+// never straddle segments, so one launch sorts every segment of a batch.
+//
+// One pass = one launch. A CTA takes the next tile index from an atomic
+// counter, ranks its keys by digit with warp-level __match_any_sync (stable:
+// warp-striped order, warps in order), publishes its per-digit counts, looks
+// back over the preceding tiles of its segment for the exclusive prefix
+// (decoupled look-back; each wait is bounded and sets ERR_TIMEOUT when it
+// runs out), stages the tile in shared memory in digit order and scatters it
+// with runs of consecutive destinations. Keys are read once and written once
+// per pass: 2 x (8 + 4) bytes per u64 key.
+#include <algorithm>
+#include <cstdio>
+
+#include "kernels.h"
+
+namespace bwt {
+
+namespace {
+
+constexpr int OS_THREADS = 256;
+constexpr int OS_WARPS = OS_THREADS / 32;
+
+template <typename KeyT, int RBITS, int TILE, bool FROM_S>
+struct OneSweepLayout {
+    static constexpr int RADIX = 1 << RBITS;
+    static constexpr size_t WHIST = (size_t)OS_WARPS * RADIX * 2;
+    static constexpr size_t STAGE = (size_t)TILE * (sizeof(KeyT) + 4);
+    static constexpr size_t BYTES = FROM_S ? (size_t)TILE + 16 : 0;
+    static constexpr size_t U0 = WHIST > STAGE ? WHIST : STAGE;
+    static constexpr size_t U = ((U0 > BYTES ? U0 : BYTES) + 15) & ~(size_t)15;
+    static constexpr size_t TOTAL = U + 2 * RADIX * 4 + 32 * 4 + 16;
+};
+
+__device__ __forceinline__ uint64_t pack8(const uint8_t* b) {
+    uint64_t k = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) k = (k << 8) | b[j];
+    return k;
+}
+
+// VDIG: the digit comes from the value (the rotation index) instead of the
+// key; used to put overflow buckets of the learned bucketing in index order
+// before their key passes.
+template <typename KeyT, int RBITS, int TILE, bool FROM_S, bool VDIG = false>
+__global__ void __launch_bounds__(OS_THREADS) k_onesweep(OneSweepParams p) {
+    using Lay = OneSweepLayout<KeyT, RBITS, TILE, FROM_S>;
+    constexpr int RADIX = 1 << RBITS;
+    constexpr int ITEMS = TILE / OS_THREADS;
+    constexpr int WKEYS = 32 * ITEMS;
+    constexpr int DPT = RADIX / OS_THREADS;  // digits owned per thread (RADIX >= 256)
+    static_assert(RADIX >= OS_THREADS, "one digit per thread at least");
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint16_t* whist = reinterpret_cast<uint16_t*>(smem);
+    KeyT* skeys = reinterpret_cast<KeyT*>(smem);
+    uint32_t* svals = reinterpret_cast<uint32_t*>(smem + (size_t)TILE * sizeof(KeyT));
+    uint8_t* sbytes = smem;
+    uint32_t* digit_start = reinterpret_cast<uint32_t*>(smem + Lay::U);
+    uint32_t* gbase = digit_start + RADIX;
+    uint32_t* scan_tmp = gbase + RADIX;
+    uint32_t* s_tile = scan_tmp + 32;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t num_tiles = *p.num_tiles;
+    const uint32_t spin_limit = p.ctrl[CTRL_SPIN];
+    const uint32_t withhold = p.ctrl[CTRL_WITHHOLD];
+    const KeyT* kin = static_cast<const KeyT*>(p.kin);
+    KeyT* kout = static_cast<KeyT*>(p.kout);
+    const uint32_t lt = lanemask_lt();
+
+    for (;;) {
+        if (tid == 0) *s_tile = atomicAdd(p.tile_counter, 1u);
+        __syncthreads();
+        const uint32_t t = *s_tile;
+        if (t >= num_tiles) break;
+        const TileDesc td = p.tiles[t];
+
+        // ---- load the tile (warp-striped: item j of lane l of warp w is
+        //      tile index w*WKEYS + j*32 + l)
+        KeyT key[ITEMS];
+        uint32_t val[ITEMS];
+        if constexpr (FROM_S) {
+            const BlockInfo bi = p.blocks[td.blk];
+            const uint32_t i0 = td.start - bi.off;
+            const uint8_t* Sb = p.S + bi.off;
+            for (uint32_t q = tid; q < td.len + 7; q += OS_THREADS) {
+                uint32_t pos = i0 + q;
+                if (pos >= bi.n) pos = bi.n >= 8 ? pos - bi.n : pos % bi.n;
+                sbytes[q] = Sb[pos];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const uint32_t idx = warp * WKEYS + j * 32 + lane;
+                key[j] = 0;
+                val[j] = 0;
+                if (idx < td.len) {
+                    key[j] = (KeyT)pack8(sbytes + idx);
+                    val[j] = i0 + idx;
+                }
+            }
+            __syncthreads();
+        } else {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const uint32_t idx = warp * WKEYS + j * 32 + lane;
+                key[j] = 0;
+                val[j] = 0;
+                if (idx < td.len) {
+                    key[j] = kin[td.start + idx];
+                    val[j] = p.vin[td.start + idx];
+                }
+            }
+        }
+
+        // ---- per-warp digit counts and stable ranks
+        {
+            uint32_t* w32 = reinterpret_cast<uint32_t*>(whist);
+            for (int i = tid; i < OS_WARPS * RADIX / 2; i += OS_THREADS) w32[i] = 0u;
+        }
+        __syncthreads();
+        uint32_t rkdg[ITEMS];  // rank within warp (low 16) | digit (high 16)
+        uint16_t* my_hist = whist + warp * RADIX;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const uint32_t idx = warp * WKEYS + j * 32 + lane;
+            const bool valid = idx < td.len;
+            uint32_t d = (uint32_t)RADIX;
+            if (valid) {
+                if constexpr (VDIG) d = (val[j] >> p.shift) & (uint32_t)(RADIX - 1);
+                else d = (uint32_t)((key[j] >> p.shift) & (KeyT)(RADIX - 1));
+            }
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const int leader = __ffs(peers) - 1;
+            uint32_t base = 0;
+            if (valid && lane == leader) {
+                base = my_hist[d];
+                my_hist[d] = (uint16_t)(base + __popc(peers));
+            }
+            base = __shfl_sync(0xffffffffu, base, leader);
+            __syncwarp();
+            rkdg[j] = (base + __popc(peers & lt)) | (d << 16);
+        }
+        __syncthreads();
+
+        // ---- tile counts per digit, exclusive prefix over warps (in place)
+        uint32_t cnt[DPT];
+        uint32_t tsum = 0;
+#pragma unroll
+        for (int i = 0; i < DPT; ++i) {
+            const int d = tid * DPT + i;
+            uint32_t s = 0;
+#pragma unroll
+            for (int w = 0; w < OS_WARPS; ++w) {
+                const uint32_t c = whist[w * RADIX + d];
+                whist[w * RADIX + d] = (uint16_t)s;
+                s += c;
+            }
+            cnt[i] = s;
+            tsum += s;
+        }
+        uint32_t total;
+        uint32_t ex = block_exclusive_scan<OS_THREADS>(tsum, scan_tmp, &total);
+#pragma unroll
+        for (int i = 0; i < DPT; ++i) {
+            digit_start[tid * DPT + i] = ex;
+            ex += cnt[i];
+        }
+
+        // ---- decoupled look-back over this segment's earlier tiles
+        const bool first = (t == td.firstTile);
+#pragma unroll 1
+        for (int i = 0; i < DPT; ++i) {
+            const int d = tid * DPT + i;
+            uint32_t* mine = p.status + (size_t)t * RADIX + d;
+            uint32_t excl = 0;
+            if (first) {
+                if (!(withhold && t == 0)) st_volatile(mine, ST_INC | cnt[i]);
+            } else {
+                st_volatile(mine, ST_AGG | cnt[i]);
+                uint32_t q = t - 1;
+                for (;;) {
+                    const uint32_t* w = p.status + (size_t)q * RADIX + d;
+                    uint32_t v = ld_volatile(w);
+                    uint32_t it = 0;
+                    while ((v & (ST_AGG | ST_INC)) == 0u) {
+                        if (++it > spin_limit) {
+                            atomicOr(&p.ctrl[CTRL_ERR], ERR_TIMEOUT);
+                            v = ST_INC;  // give up: proceed with a short prefix (stays in bounds)
+                            break;
+                        }
+                        if (it > 32) __nanosleep(64);
+                        v = ld_volatile(w);
+                    }
+                    excl += v & ST_VALUE;
+                    if (v & ST_INC) break;
+                    if (q == td.firstTile) break;  // defensive: the first tile is always inclusive
+                    --q;
+                }
+                st_volatile(mine, ST_INC | ((excl + cnt[i]) & ST_VALUE));
+            }
+            gbase[d] = td.segStart + p.seg_base[(size_t)td.seg * p.seg_base_stride + d] + excl - digit_start[d];
+        }
+        __syncthreads();
+
+        // ---- stage in digit order, then scatter runs
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const uint32_t d = rkdg[j] >> 16;
+            if (d < (uint32_t)RADIX) rkdg[j] = digit_start[d] + whist[warp * RADIX + d] + (rkdg[j] & 0xffffu);
+            else rkdg[j] = 0xffffffffu;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (rkdg[j] != 0xffffffffu) {
+                skeys[rkdg[j]] = key[j];
+                svals[rkdg[j]] = val[j];
+            }
+        }
+        __syncthreads();
+        for (uint32_t q = tid; q < td.len; q += OS_THREADS) {
+            const KeyT k = skeys[q];
+            const uint32_t v = svals[q];
+            uint32_t d;
+            if constexpr (VDIG) d = (v >> p.shift) & (uint32_t)(RADIX - 1);
+            else d = (uint32_t)((k >> p.shift) & (KeyT)(RADIX - 1));
+            const uint32_t dst = gbase[d] + q;
+            kout[dst] = k;
+            p.vout[dst] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// ---- histograms ------------------------------------------------------------
+
+// d = 8: byte histogram of every block. Each thread counts a run of 16
+// consecutive bytes and adds whole runs of equal bytes, so run-heavy blocks
+// do not serialise on one shared-memory counter.
+__global__ void __launch_bounds__(256) k_hist_bytes(const uint8_t* __restrict__ S, const BlockInfo* __restrict__ blocks,
+                                                    const TileDesc* __restrict__ tiles, uint32_t num_tiles,
+                                                    uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[256];
+    for (uint32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+        h[threadIdx.x] = 0;
+        __syncthreads();
+        const TileDesc td = tiles[t];
+        for (uint32_t c0 = threadIdx.x * 16; c0 < td.len; c0 += 256 * 16) {
+            const uint32_t c1 = min(c0 + 16, td.len);
+            uint32_t prev = S[td.start + c0], run = 1;
+            for (uint32_t q = c0 + 1; q < c1; ++q) {
+                const uint32_t b = S[td.start + q];
+                if (b == prev) {
+                    ++run;
+                } else {
+                    atomicAdd(&h[prev], run);
+                    prev = b;
+                    run = 1;
+                }
+            }
+            atomicAdd(&h[prev], run);
+        }
+        __syncthreads();
+        const uint32_t c = h[threadIdx.x];
+        if (c) atomicAdd(&hist[(size_t)td.blk * 256 + threadIdx.x], c);
+        __syncthreads();
+    }
+}
+
+// d = 11: six digit histograms of the u64 prefixes (shifts 0, 11, .., 55).
+template <int TILE>
+__global__ void __launch_bounds__(256) k_hist_keys11(const uint8_t* __restrict__ S, const BlockInfo* __restrict__ blocks,
+                                                     const TileDesc* __restrict__ tiles, uint32_t num_tiles,
+                                                     uint32_t* __restrict__ hist) {
+    constexpr int RADIX = 2048, PASSES = 6;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* h = reinterpret_cast<uint32_t*>(smem);
+    uint8_t* sbytes = smem + PASSES * RADIX * 4;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+        for (int i = threadIdx.x; i < PASSES * RADIX; i += 256) h[i] = 0;
+        const TileDesc td = tiles[t];
+        const BlockInfo bi = blocks[td.blk];
+        const uint32_t i0 = td.start - bi.off;
+        for (uint32_t q = threadIdx.x; q < td.len + 7; q += 256) {
+            uint32_t pos = i0 + q;
+            if (pos >= bi.n) pos = bi.n >= 8 ? pos - bi.n : pos % bi.n;
+            sbytes[q] = S[bi.off + pos];
+        }
+        __syncthreads();
+        for (uint32_t q0 = 0; q0 < td.len; q0 += 256) {
+            const uint32_t q = q0 + threadIdx.x;
+            const bool valid = q < td.len;
+            const uint64_t k = valid ? pack8(sbytes + q) : 0ull;
+#pragma unroll
+            for (int ps = 0; ps < PASSES; ++ps) {
+                const uint32_t d = valid ? (uint32_t)((k >> (11 * ps)) & (RADIX - 1)) : (uint32_t)RADIX;
+                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[ps * RADIX + d], (uint32_t)__popc(peers));
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < PASSES * RADIX; i += 256) {
+            const uint32_t c = h[i];
+            if (c) atomicAdd(&hist[(size_t)td.blk * PASSES * RADIX + i], c);
+        }
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of rows of `radix` counters (one CTA per row, grid-stride).
+__global__ void __launch_bounds__(256) k_scan_rows(uint32_t* __restrict__ hist, int radix,
+                                                   const uint32_t* __restrict__ num_rows_dev, uint32_t rows_mult,
+                                                   uint32_t rows_host, uint32_t max_rows) {
+    __shared__ uint32_t tmp[32];
+    uint64_t r64 = num_rows_dev ? (uint64_t)(*num_rows_dev) * rows_mult : rows_host;
+    const uint32_t rows = (uint32_t)(r64 < max_rows ? r64 : max_rows);
+    const int per = radix / 256;
+    for (uint32_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        uint32_t* row = hist + (size_t)r * radix;
+        uint32_t v[8];
+        uint32_t s = 0;
+        for (int i = 0; i < per; ++i) {
+            v[i] = row[threadIdx.x * per + i];
+            s += v[i];
+        }
+        uint32_t total;
+        uint32_t ex = block_exclusive_scan<256>(s, tmp, &total);
+        for (int i = 0; i < per; ++i) {
+            row[threadIdx.x * per + i] = ex;
+            ex += v[i];
+        }
+    }
+}
+
+__global__ void k_zero_by_count(uint32_t* __restrict__ p, const uint32_t* __restrict__ count, uint32_t per_unit,
+                                uint32_t max_words) {
+    uint64_t n = (uint64_t)(*count) * per_unit;
+    if (n > max_words) n = max_words;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        p[i] = 0u;
+}
+
+template <typename KeyT, int RBITS, int TILE, bool FROM_S, bool VDIG>
+struct OneSweepKernel {
+    static void* fn() { return (void*)k_onesweep<KeyT, RBITS, TILE, FROM_S, VDIG>; }
+    static size_t smem() { return OneSweepLayout<KeyT, RBITS, TILE, FROM_S>::TOTAL; }
+};
+
+struct KernelEntry {
+    void* fn;
+    size_t smem;
+    int grid;
+};
+
+template <typename KeyT, int RBITS, int TILE, bool FROM_S, bool VDIG = false>
+KernelEntry& entry() {
+    static KernelEntry e = [] {
+        KernelEntry x;
+        x.fn = OneSweepKernel<KeyT, RBITS, TILE, FROM_S, VDIG>::fn();
+        x.smem = OneSweepKernel<KeyT, RBITS, TILE, FROM_S, VDIG>::smem();
+        cudaFuncSetAttribute(x.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x.smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, x.fn, OS_THREADS, x.smem);
+        x.grid = std::max(1, per_sm) * num_sms();
+        return x;
+    }();
+    return e;
+}
+
+template <typename KeyT, bool FROM_S>
+KernelEntry* pick(int rbits, int tile) {
+    if (rbits == 8) {
+        if (tile == 1024) return &entry<KeyT, 8, 1024, FROM_S>();
+        if (tile == 2048) return &entry<KeyT, 8, 2048, FROM_S>();
+        if (tile == 4096) return &entry<KeyT, 8, 4096, FROM_S>();
+    } else if (rbits == 11) {
+        if (tile == 1024) return &entry<KeyT, 11, 1024, FROM_S>();
+        if (tile == 2048) return &entry<KeyT, 11, 2048, FROM_S>();
+        if (tile == 4096) return &entry<KeyT, 11, 4096, FROM_S>();
+    }
+    return nullptr;
+}
+
+KernelEntry* pick_vdig(int tile) {
+    if (tile == 1024) return &entry<uint64_t, 8, 1024, false, true>();
+    if (tile == 2048) return &entry<uint64_t, 8, 2048, false, true>();
+    if (tile == 4096) return &entry<uint64_t, 8, 4096, false, true>();
+    return nullptr;
+}
+
+KernelEntry* pick_any(int key_bytes, bool from_s, int rbits, int tile) {
+    if (key_bytes == 8) return from_s ? pick<uint64_t, true>(rbits, tile) : pick<uint64_t, false>(rbits, tile);
+    if (key_bytes == 4 && !from_s) return pick<uint32_t, false>(rbits, tile);
+    if (key_bytes == -8 && !from_s && rbits == 8) return pick_vdig(tile);  // u64 keys, digit from the value
+    return nullptr;
+}
+
+}  // namespace
+
+int num_sms() {
+    static int n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
+    return n;
+}
+
+int onesweep_grid(int key_bytes, bool from_s, int radix_bits, int tile) {
+    KernelEntry* e = pick_any(key_bytes, from_s, radix_bits, tile);
+    return e ? e->grid : 0;
+}
+
+size_t onesweep_smem(int key_bytes, bool from_s, int radix_bits, int tile) {
+    KernelEntry* e = pick_any(key_bytes, from_s, radix_bits, tile);
+    return e ? e->smem : 0;
+}
+
+cudaError_t launch_onesweep(int key_bytes, bool from_s, int radix_bits, int tile, const OneSweepParams& p, int grid,
+                            cudaStream_t st) {
+    KernelEntry* e = pick_any(key_bytes, from_s, radix_bits, tile);
+    if (!e) return cudaErrorInvalidValue;
+    if (grid <= 0 || grid > e->grid) grid = e->grid;
+    OneSweepParams a = p;
+    void* args[] = {&a};
+    return cudaLaunchKernel(e->fn, dim3(grid), dim3(OS_THREADS), args, e->smem, st);
+}
+
+cudaError_t launch_hist_bytes(const uint8_t* S, const BlockInfo* blocks, const TileDesc* tiles, uint32_t num_tiles,
+                              uint32_t* hist, cudaStream_t st) {
+    if (num_tiles == 0) return cudaSuccess;
+    const int grid = (int)std::min<uint32_t>(num_tiles, (uint32_t)num_sms() * 8);
+    k_hist_bytes<<<grid, 256, 0, st>>>(S, blocks, tiles, num_tiles, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_keys11(const uint8_t* S, const BlockInfo* blocks, const TileDesc* tiles, uint32_t num_tiles,
+                               int tile, uint32_t* hist, cudaStream_t st) {
+    if (num_tiles == 0) return cudaSuccess;
+    const size_t smem = 6 * 2048 * 4 + (size_t)tile + 16;
+    static bool attr = [] {
+        cudaFuncSetAttribute((void*)k_hist_keys11<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             6 * 2048 * 4 + 4096 + 16);
+        return true;
+    }();
+    (void)attr;
+    const int grid = (int)std::min<uint32_t>(num_tiles, (uint32_t)num_sms() * 4);
+    k_hist_keys11<4096><<<grid, 256, smem, st>>>(S, blocks, tiles, num_tiles, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_rows(uint32_t* hist, int radix, const uint32_t* num_rows_dev, uint32_t rows_mult,
+                             uint32_t rows_host, uint32_t max_rows, cudaStream_t st) {
+    if (radix != 256 && radix != 2048) return cudaErrorInvalidValue;
+    const int grid = num_rows_dev ? num_sms() * 8 : (int)std::max<uint32_t>(1, std::min<uint32_t>(rows_host, 65535));
+    if (!num_rows_dev && rows_host == 0) return cudaSuccess;
+    k_scan_rows<<<grid, 256, 0, st>>>(hist, radix, num_rows_dev, rows_mult, rows_host, max_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_by_count(uint32_t* p, const uint32_t* count, uint32_t words_per_unit, uint32_t max_words,
+                                 cudaStream_t st) {
+    k_zero_by_count<<<num_sms() * 4, 256, 0, st>>>(p, count, words_per_unit, max_words);
+    return cudaGetLastError();
+}
+
+}  // namespace bwt

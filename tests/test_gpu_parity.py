@@ -1,0 +1,151 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+byte for byte on L and the primary index, for every source, edge cases,
+every radix width and tile size, the batched graph mode and the per-block
+launch mode. Full-size workloads are in test_gpu_full.py."""
+import numpy as np
+import pytest
+
+from paper_1109_2348_gb300 import F_GRAPH, F_PER_BLOCK_LAUNCH, Plan, datagen
+
+from gpu_util import assert_matches_oracle, batch_from_blocks, gpu_bwt
+
+pytestmark = pytest.mark.gpu
+
+
+def test_hand_words_and_tiny_blocks():
+    words = [b"banana", b"abracadabra", b"mississippi", b"abab", b"aaaa", b"b", b"ba", b"abc", b"cba",
+             b"aaaaaaab", b"abababababababab", b"zzzzzzzzz", b"\x00\xff\x00\xff\x00"]
+    blocks = [np.frombuffer(w, dtype=np.uint8) for w in words]
+    buf, off = batch_from_blocks(blocks)
+    L, prim, _ = gpu_bwt(buf, off)
+    assert_matches_oracle(buf, off, L, prim, "words")
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 255, 1023, 1024, 1025,
+                               2047, 2049, 4095, 4096, 4097, 8193])
+def test_sizes_around_tiles(n):
+    rng = np.random.default_rng(n)
+    blocks = [rng.integers(0, 256, n, dtype=np.uint8), rng.integers(0, 2, n, dtype=np.uint8) + 97,
+              np.full(n, 7, dtype=np.uint8), np.resize(rng.integers(0, 256, 3, dtype=np.uint8), n)]
+    buf, off = batch_from_blocks(blocks)
+    L, prim, _ = gpu_bwt(buf, off)
+    assert_matches_oracle(buf, off, L, prim, f"n={n}")
+
+
+@pytest.mark.parametrize("src", range(9))
+def test_every_source_small(src):
+    w = datagen.Workload("t", [src] * 3, [100 + src, 200 + src, 300 + src], [50_000, 12_345, 70_001])
+    buf, off = w.generate()
+    L, prim, st = gpu_bwt(buf, off)
+    assert_matches_oracle(buf, off, L, prim, datagen.SOURCE_NAMES[src])
+
+
+@pytest.mark.parametrize("rb", [8, 11])
+@pytest.mark.parametrize("tile", [1024, 2048, 4096])
+def test_radix_and_tile_variants(rb, tile):
+    w = datagen.Workload("t", [datagen.MARKOV3_Z96, datagen.RUNS16, datagen.UNIFORM, datagen.PERIOD1000,
+                               datagen.FIBONACCI],
+                         [1, 2, 3, 4, 5], [40_000, 30_001, 20_000, 25_000, 33_333])
+    buf, off = w.generate()
+    L, prim, _ = gpu_bwt(buf, off, radix_bits=rb, tile_keys=tile)
+    assert_matches_oracle(buf, off, L, prim, f"rb={rb} tile={tile}")
+
+
+def test_mixed_batch_scaled_down():
+    w = datagen.mixed_64x900k(num_blocks=12, n=60_000)
+    buf, off = w.generate()
+    L, prim, st = gpu_bwt(buf, off)
+    assert_matches_oracle(buf, off, L, prim, "mixed")
+    assert st["rounds"] >= 1 and st["radix_launches"] >= 8
+
+
+def test_degenerate_scaled_down():
+    w = datagen.degenerate_5x900k(n=50_000)
+    buf, off = w.generate()
+    L, prim, st = gpu_bwt(buf, off)
+    assert_matches_oracle(buf, off, L, prim, "degenerate")
+    assert prim[0] == 0
+
+
+def test_graph_mode_equals_oracle_and_replays():
+    w = datagen.uneven_markov3(num_blocks=24, lo=1_000, hi=40_000)
+    buf, off = w.generate()
+    import torch
+    d_in = torch.from_numpy(buf).cuda()
+    with Plan(max_blocks=24, max_total_bytes=buf.size, max_block_bytes=40_000, flags=F_GRAPH) as plan:
+        L = torch.empty_like(d_in)
+        prim = torch.empty(24, dtype=torch.int32, device="cuda")
+        plan.forward_into(d_in, off, L, prim)
+        s1 = plan.stats()
+        assert_matches_oracle(buf, off, L.cpu().numpy(), prim.cpu().numpy(), "graph first")
+        L.zero_()
+        prim.zero_()
+        plan.forward_into(d_in, off, L, prim)
+        s2 = plan.stats()
+        assert s2["graph_replayed"] == 1 and s1["graph_replayed"] == 0
+        assert s2["rounds"] == s1["rounds"] and s2["kernel_launches"] == s1["kernel_launches"]
+        assert_matches_oracle(buf, off, L.cpu().numpy(), prim.cpu().numpy(), "graph replay")
+
+
+def test_graph_mode_degenerate():
+    w = datagen.degenerate_5x900k(n=30_000)
+    buf, off = w.generate()
+    L, prim, st = gpu_bwt(buf, off, flags=F_GRAPH)
+    assert_matches_oracle(buf, off, L, prim, "graph degenerate")
+    assert st["rounds"] >= 10
+
+
+def test_per_block_launch_mode():
+    w = datagen.uneven_markov3(num_blocks=10, lo=100, hi=30_000)
+    buf, off = w.generate()
+    L, prim, st = gpu_bwt(buf, off, flags=F_PER_BLOCK_LAUNCH)
+    assert_matches_oracle(buf, off, L, prim, "per-block")
+
+
+def test_device_offsets_and_reuse_of_plan():
+    import torch
+    w1 = datagen.mixed_64x900k(num_blocks=3, n=10_000)
+    w2 = datagen.Workload("t", [datagen.RUNS16, datagen.CONST], [9, 9], [4_000, 25_000])
+    with Plan(max_blocks=4, max_total_bytes=40_000, max_block_bytes=25_000) as plan:
+        for w in (w1, w2, w1):
+            buf, off = w.generate()
+            d_in = torch.from_numpy(buf).cuda()
+            d_off = torch.from_numpy(off.view(np.int64)).cuda()
+            L, prim = plan.forward(d_in, d_off)
+            assert_matches_oracle(buf, off, L.cpu().numpy(), prim.cpu().numpy(), w.name)
+
+
+def test_argument_errors():
+    import torch
+    from paper_1109_2348_gb300 import _lib
+    with Plan(max_blocks=2, max_total_bytes=100, max_block_bytes=60) as plan:
+        d = torch.zeros(100, dtype=torch.uint8, device="cuda")
+        L = torch.zeros(100, dtype=torch.uint8, device="cuda")
+        p = torch.zeros(3, dtype=torch.int32, device="cuda")
+        bad = [np.array([0, 10, 10], dtype=np.uint64),      # empty block
+               np.array([1, 10], dtype=np.uint64),          # does not start at 0
+               np.array([0, 61], dtype=np.uint64),          # block over max_block_bytes
+               np.array([0, 50, 101], dtype=np.uint64),     # over max_total_bytes
+               np.array([0, 10, 20, 30], dtype=np.uint64)]  # over max_blocks
+        for off in bad:
+            assert plan.forward_into(d, off, L, p, raise_on_error=False) == _lib.BWT_EINVAL
+        assert plan.forward_into(d, np.array([0, 40], dtype=np.uint64), d, p, raise_on_error=False) == _lib.BWT_EINVAL
+        assert plan.forward_into(d, np.array([0, 40, 100], dtype=np.uint64), L, p, raise_on_error=False) == _lib.BWT_OK
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A look-back wait that nothing will satisfy runs out after the spin limit
+    and the call reports BWT_ETIMEOUT; the next call on the same plan is exact."""
+    import torch
+    from paper_1109_2348_gb300 import _lib
+    w = datagen.Workload("t", [datagen.UNIFORM], [1], [20_000])
+    buf, off = w.generate()
+    d_in = torch.from_numpy(buf).cuda()
+    with Plan(max_blocks=1, max_total_bytes=buf.size, max_block_bytes=buf.size, tile_keys=1024) as plan:
+        L = torch.empty_like(d_in)
+        p = torch.empty(1, dtype=torch.int32, device="cuda")
+        plan.debug_waits(2000, True)
+        assert plan.forward_into(d_in, off, L, p, raise_on_error=False) == _lib.BWT_ETIMEOUT
+        plan.debug_waits(0, False)
+        plan.forward_into(d_in, off, L, p)
+        assert_matches_oracle(buf, off, L.cpu().numpy(), p.cpu().numpy(), "after timeout")
