@@ -44,7 +44,8 @@ typedef enum {
     BWT_ECUDA = 4,      /* a CUDA runtime call failed; see bwt_last_cuda_error() */
     BWT_ETIMEOUT = 5,   /* a bounded device-side wait ran out; outputs are undefined */
     BWT_EMISMATCH = 6,  /* bwt_inverse_check: the inverse of L does not reproduce the block */
-    BWT_ENOMODEL = 7    /* BWT_F_LEARNED without a loaded splitter table */
+    BWT_ENOMODEL = 7,   /* BWT_F_LEARNED without a loaded splitter table */
+    BWT_ETOOBIG = 8     /* bwt_forward_block_noalloc: block larger than BWT_NOALLOC_MAX_BYTES */
 } bwt_status;
 
 /* plan flags */
@@ -204,6 +205,35 @@ bwt_status bwt_plan_set_splitters(bwt_plan* plan, const uint64_t* splitters);
  * missing or malformed. */
 bwt_status bwt_model_save(const char* path, const float* params, const uint64_t* splitters);
 bwt_status bwt_model_load(const char* path, float* params, uint64_t* splitters);
+
+/* ---- forward BWT of one small block without device allocation --------
+ *
+ * The paper has no counterpart to this entry point. It is for callers that
+ * cannot allocate device memory -- for instance a host framework that owns
+ * the GPU's memory through its own pool and forbids allocations outside it,
+ * or a latency-bound pipeline that cannot take the device synchronisation of
+ * cudaMalloc / cudaFree -- and therefore cannot create a bwt_plan.
+ *
+ * It computes the same L and primary index as bwt_forward_batch for one
+ * block of n bytes, 1 <= n <= BWT_NOALLOC_MAX_BYTES, with one CTA on the
+ * current device and the caller's `stream`; it allocates nothing and does
+ * not synchronise. Its scratch is a fixed array of 5 * BWT_NOALLOC_MAX_BYTES
+ * u32 words (1.25 MiB) that lives in the library's device image: every GPU
+ * that loads the library holds it until the process exits. The first call on
+ * a device looks up that array's device address (once per device, with the
+ * device current); make that first call before any stream capture.
+ *   d_in       device, uint8[n]: the block.
+ *   d_L        device, uint8[n]: its L column (must not alias d_in).
+ *   d_primary  device, int32[1]: its primary index.
+ * Returns BWT_ETOOBIG if n > BWT_NOALLOC_MAX_BYTES, BWT_EINVAL for n = 0 or
+ * bad pointers, BWT_ECUDA if the launch fails. All calls share the one
+ * scratch array, so calls whose kernels overlap on the GPU (other streams,
+ * other host threads on the same device) race and give wrong results;
+ * serialise them, e.g. on one stream. Each call writes every scratch word it
+ * reads, so earlier calls' contents do no harm. */
+#define BWT_NOALLOC_MAX_BYTES 65536
+bwt_status bwt_forward_block_noalloc(const uint8_t* d_in, uint32_t n, uint8_t* d_L, int32_t* d_primary,
+                                     void* stream);
 
 /* Human-readable name of a status code (static string). */
 const char* bwt_status_string(bwt_status s);

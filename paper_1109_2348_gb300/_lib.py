@@ -12,9 +12,11 @@ from pathlib import Path
 
 from . import _build
 
-BWT_OK, BWT_EINVAL, BWT_ENOMEM, BWT_ECAPACITY, BWT_ECUDA, BWT_ETIMEOUT, BWT_EMISMATCH, BWT_ENOMODEL = range(8)
+(BWT_OK, BWT_EINVAL, BWT_ENOMEM, BWT_ECAPACITY, BWT_ECUDA, BWT_ETIMEOUT, BWT_EMISMATCH, BWT_ENOMODEL,
+ BWT_ETOOBIG) = range(9)
 STATUS_NAMES = ["BWT_OK", "BWT_EINVAL", "BWT_ENOMEM", "BWT_ECAPACITY", "BWT_ECUDA", "BWT_ETIMEOUT",
-                "BWT_EMISMATCH", "BWT_ENOMODEL"]
+                "BWT_EMISMATCH", "BWT_ENOMODEL", "BWT_ETOOBIG"]
+NOALLOC_MAX_BYTES = 65536
 
 F_GRAPH = 0x1
 F_LEARNED = 0x2
@@ -64,6 +66,7 @@ EXPORTS = [
     "bwt_status_string", "bwt_last_cuda_error",
     "bwt_mlp_forward", "bwt_mlp_loss_grad", "bwt_mlp_adam_step", "bwt_model_train", "bwt_model_samples",
     "bwt_model_compile", "bwt_plan_set_splitters", "bwt_model_save", "bwt_model_load",
+    "bwt_forward_block_noalloc",
 ]
 
 MLP_NPARAMS = 1377
@@ -119,6 +122,8 @@ def load(build_if_missing: bool = True):
     lib.bwt_plan_set_splitters.argtypes = [vp, vp]
     lib.bwt_model_save.argtypes = [ctypes.c_char_p, vp, vp]
     lib.bwt_model_load.argtypes = [ctypes.c_char_p, vp, vp]
+    lib.bwt_forward_block_noalloc.argtypes = [vp, u32, vp, vp, vp]
+    lib.bwt_forward_block_noalloc.restype = ctypes.c_int
     for name in ("bwt_mlp_forward", "bwt_mlp_loss_grad", "bwt_mlp_adam_step", "bwt_model_train",
                  "bwt_model_samples", "bwt_model_compile", "bwt_plan_set_splitters", "bwt_model_save",
                  "bwt_model_load"):

@@ -57,6 +57,7 @@ extern "C" const char* bwt_status_string(bwt_status s) {
     case BWT_ETIMEOUT: return "BWT_ETIMEOUT";
     case BWT_EMISMATCH: return "BWT_EMISMATCH";
     case BWT_ENOMODEL: return "BWT_ENOMODEL";
+    case BWT_ETOOBIG: return "BWT_ETOOBIG";
     }
     return "BWT_UNKNOWN";
 }
