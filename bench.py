@@ -37,10 +37,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--blocks", type=int, default=0, help="use only the first N blocks of the workload")
     ap.add_argument("--mode", choices=["host", "graph", "perblock", "learned"], default="graph")
     ap.add_argument("--radix-bits", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--model", default=None)
+    ap.add_argument("--model", default=None, help="model file for --mode learned (trained in-process if absent)")
+    ap.add_argument("--train-samples", type=int, default=1_000_000)
+    ap.add_argument("--train-epochs", type=int, default=8)
+    ap.add_argument("--compare-plain", action="store_true", help="also time the plain path on the same batch")
+    ap.add_argument("--autotune", action="store_true", help="pick radix bits and tile size on this batch first")
+    ap.add_argument("--autotune-cache", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--verify", action="store_true", help="check every block with the host inverse")
@@ -107,9 +113,36 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload(cfg: int):
+def workload(cfg: int, blocks: int = 0):
     from paper_1109_2348_gb300 import datagen
-    return datagen.config(cfg)
+    w = datagen.config(cfg)
+    if blocks and blocks < w.num_blocks:
+        w = w.subset(range(blocks))
+    return w
+
+
+def rank_workload(cfg: int, blocks: int, rank: int, world: int):
+    """Weak scaling: every rank sorts its own full batch of the workload, with
+    seeds shifted by rank so the ranks' blocks are distinct units. Blocks are
+    independent, so there is no data-path exchange between ranks."""
+    w = workload(cfg, blocks)
+    return w.reseeded(100_000 * rank) if world > 1 else w
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max over ranks (the slowest rank's time defines the job's time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(bytes_per_rank: int, world: int, steps: int, t_ms: float) -> float:
+    """Whole-job input MB/s: bytes all ranks sorted / the slowest rank's time."""
+    return bytes_per_rank * world * steps / (t_ms / 1e3) / 1e6
 
 
 def measured_peaks():
@@ -152,7 +185,7 @@ def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = workload(args.config)
+    w = workload(args.config, args.blocks)
     cores = os.cpu_count() or 1
     sample = cpu_sample(w, cores)
     for _ in range(max(0, args.warmup)):
@@ -184,11 +217,22 @@ def ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workload(args.config)
+    w = rank_workload(args.config, args.blocks, rank, world)
     buf, off = w.generate()
     n = buf.size
     flags = {"host": F_TIMING, "graph": F_GRAPH, "perblock": F_PER_BLOCK_LAUNCH, "learned": F_LEARNED}[args.mode]
     sizes = np.diff(off.astype(np.int64))
+    model_info = None
+    if args.mode == "learned" and not args.model:
+        import tempfile
+        from paper_1109_2348_gb300 import model as mdl
+        t0 = time.perf_counter()
+        trained = mdl.train(num_samples=args.train_samples, epochs=args.train_epochs, device=local)
+        args.model = os.path.join(tempfile.mkdtemp(), "bwt.model")
+        trained.save(args.model)
+        model_info = {"trained_s": round(time.perf_counter() - t0, 2), "samples": args.train_samples,
+                      "epochs": args.train_epochs, "final_loss": float(trained.epoch_loss[-1]),
+                      "train_blocks": "100 x 900000 order-3 Markov, seeds 5000..5099"}
     plan = Plan(max_blocks=w.num_blocks, max_total_bytes=n, max_block_bytes=int(sizes.max()),
                 radix_bits=args.radix_bits, tile_keys=args.tile, flags=flags, model_path=args.model,
                 device=local)
@@ -199,6 +243,12 @@ def ours(args):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
+    tuned = None
+    if args.autotune:
+        import tempfile
+        cache = args.autotune_cache or os.path.join(tempfile.mkdtemp(), "autotune.jsonl")
+        rb, tk, ms = plan.autotune(d_in, off, d_L, d_p, cache_path=cache, repeats=3, stream=stream)
+        tuned = {"radix_bits": rb, "tile_keys": tk, "ms": round(ms, 4)}
     for _ in range(max(3, args.warmup)):
         plan.forward_into(d_in, off, d_L, d_p, stream)
     torch.cuda.synchronize()
@@ -207,8 +257,9 @@ def ours(args):
     # launch); the headline steps below run the plan's own mode
     tplan = None
     if args.mode != "host":
-        tplan = Plan(max_blocks=w.num_blocks, max_total_bytes=n, max_block_bytes=int(sizes.max()),
-                     radix_bits=args.radix_bits, tile_keys=args.tile, flags=F_TIMING, device=local)
+        tb = tuned["radix_bits"] if tuned else args.radix_bits
+        tt = tuned["tile_keys"] if tuned else args.tile
+        tplan = (tb, tt)  # created after the headline steps, so only one plan's scratch is resident
 
     sampler = ClockSampler(local)
     if world > 1:
@@ -230,23 +281,14 @@ def ours(args):
             radix["ms"] += stats["radix_ms"]
             radix["bytes"] += stats["radix_bytes"]
             radix["launches"] += stats["radix_launches"]
-    if tplan is not None:
-        for i in range(args.steps):
-            flush.zero_()
-            tplan.forward_into(d_in, off, d_L, d_p, stream)
-            ts = tplan.stats()
-            radix["ms"] += ts["radix_ms"]
-            radix["bytes"] += ts["radix_bytes"]
-            radix["launches"] += ts["radix_launches"]
     torch.cuda.synchronize()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_ms = float(np.sum(step_ms))
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = n * world * args.steps / (t_ms / 1e3) / 1e6
+    learned_stats = {k: stats[k] for k in ("blocks_routed_plain", "buckets_overflowed", "keys_overflowed",
+                                           "max_bucket", "bucket_sq_sum", "buckets_nonempty")} \
+        if args.mode == "learned" else None
+    t_ms = reduce_max(float(np.sum(step_ms)), world, dev)
+    value = job_value(n, world, args.steps, t_ms)
 
     if args.verify and rank == 0:
         from paper_1109_2348_gb300 import bwt_inverse_check
@@ -274,6 +316,33 @@ def ours(args):
         e2e = {"value": round(n * args.steps / (e_ms / 1e3) / 1e6, 3), "unit": "MB/s",
                "h2d_bytes_per_step": int(n + off.nbytes), "d2h_bytes_per_step": int(n + 4 * w.num_blocks)}
 
+    plain_cmp = None
+    if args.compare_plain or tplan is not None:
+        # the plain path on the same batch: host-driven mode with CUDA events around
+        # every radix launch (the roofline's timing) and the step time for comparison
+        plan.close()
+        tb, tt = tplan if tplan is not None else (args.radix_bits, args.tile)
+        pplan = Plan(max_blocks=w.num_blocks, max_total_bytes=n, max_block_bytes=int(sizes.max()),
+                     radix_bits=tb, tile_keys=tt, flags=F_TIMING, device=local)
+        for _ in range(2):
+            pplan.forward_into(d_in, off, d_L, d_p, stream)
+        pms = []
+        for i in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pplan.forward_into(d_in, off, d_L, d_p, stream)
+            b.record(stream)
+            b.synchronize()
+            pms.append(a.elapsed_time(b))
+            ts = pplan.stats()
+            radix["ms"] += ts["radix_ms"]
+            radix["bytes"] += ts["radix_bytes"]
+            radix["launches"] += ts["radix_launches"]
+        pplan.close()
+        plain_cmp = {"value": round(n * args.steps / (sum(pms) / 1e3) / 1e6, 3), "unit": "MB/s",
+                     "mode": "plain (host-driven rounds, events around each radix launch)",
+                     "ms_per_step": round(sum(pms) / args.steps, 4)}
     peak, peak_kind = measured_peaks()
     roof = None
     if radix["ms"] > 0:
@@ -298,13 +367,19 @@ def ours(args):
                 "config": {"workload": w.name, "blocks": w.num_blocks, "bytes": n, "mode": args.mode,
                            "radix_bits": stats["radix_bits"], "tile_keys": stats["tile_keys"],
                            "rounds": stats["rounds"], "l2": "256 MB flush before every timed step",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"block-sharded x{world} (each rank its own batch, no collective)"},
                 "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "roofline": roof,
                 "cpu_baseline": cpu, "step_ms": [round(x, 3) for x in step_ms]}
+        if plain_cmp:
+            line["plain"] = plain_cmp
+        if tuned:
+            line["config"]["autotuned"] = tuned
+        if learned_stats:
+            line["config"]["learned"] = learned_stats
+        if model_info:
+            line["config"]["model"] = model_info
         print(json.dumps(line), flush=True)
     plan.close()
-    if tplan is not None:
-        tplan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -84,13 +84,17 @@ typedef struct {
     uint32_t blocks_routed_plain; /* learned bucketing: blocks whose buckets overflowed too much and
                                      were sorted by the plain radix path instead */
     uint32_t pad_;
+    uint64_t bucket_sq_sum;     /* learned bucketing: sum over all blocks and buckets of size^2 (the
+                                   in-bucket sort work; smallest when buckets are even) */
+    uint64_t buckets_nonempty;  /* learned bucketing: non-empty buckets over all blocks */
 } bwt_stats;
 
 /* Create a plan on CUDA device `device` (made current for the call). The plan
  * allocates all scratch for desc's limits (about 40 bytes per byte of
  * max_total_bytes). Returns BWT_EINVAL for bad limits, BWT_ENOMEM if the
- * allocation fails, BWT_ENOMODEL if BWT_F_LEARNED is set and model_path cannot
- * be read. *out is NULL on failure. */
+ * allocation fails, BWT_ENOMODEL if BWT_F_LEARNED is set and model_path is
+ * given but cannot be read (without model_path, install splitters with
+ * bwt_plan_set_splitters before the first call). *out is NULL on failure. */
 bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt_plan** out);
 
 /* Forward BWT of a batch (the definition at the top of this header).
@@ -131,6 +135,19 @@ bwt_status bwt_plan_stats(const bwt_plan* plan, bwt_stats* out);
  * used by later calls; drops any cached graph. */
 bwt_status bwt_plan_set_radix(bwt_plan* plan, int radix_bits, int tile_keys);
 
+/* Autotuner (no paper counterpart): times this batch for radix_bits in
+ * {8, 11} x tile_keys in {1024, 2048, 4096} (one untimed run, then `repeats`
+ * runs between CUDA events on `stream`), keeps the fastest in the plan and
+ * reports it through the out-pointers (any may be NULL). With cache_path,
+ * the result is appended to that JSON-lines file under (GPU name, workload
+ * signature = block count, total bytes, largest block, plan flags) and a
+ * later call with the same signature reads it back instead of sweeping.
+ * Arguments as for bwt_forward_batch; d_L and d_primary receive the output
+ * of a final run with the chosen configuration (bwt_plan_stats describes it). */
+bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
+                             uint8_t* d_L, int32_t* d_primary, void* stream, const char* cache_path, int repeats,
+                             int* out_radix_bits, int* out_tile_keys, float* out_ms);
+
 /* Test knob for the bounded device waits: `spin_limit` caps every wait loop
  * (0 = the built-in default of about one second); `withhold_publish` = 1 makes
  * the first tile of every radix pass skip publishing its counts, so every
@@ -142,7 +159,9 @@ bwt_status bwt_plan_debug_waits(bwt_plan* plan, uint32_t spin_limit, int withhol
 /* ---- learned CDF model (the learned bucketing of BWT_F_LEARNED) -------
  *
  * The model approximates the CDF of rotation prefixes: input x = the 8
- * prefix bytes of a rotation divided by 255 (8 floats), target t = the
+ * prefix bytes of a rotation, each normalised through the byte-value table
+ * norm[256] (the CDF of byte values in the training data, midpoint rule:
+ * norm[b] = (#bytes < b + #bytes == b / 2) / #bytes), target t = the
  * rotation's sorted row / n. It is an FP32 MLP 8 -> 32 -> 32 -> 1 with ReLU
  * after both hidden layers; its BWT_MLP_NPARAMS parameters are laid out
  * row-major as W1[32][8] | b1[32] | W2[32][32] | b2[32] | W3[32] | b3.
@@ -181,30 +200,36 @@ bwt_status bwt_model_train(float* d_params, const float* d_x, const float* d_t, 
                            const uint32_t* d_order, uint32_t epochs, uint32_t batch, float lr, float* d_epoch_loss,
                            void* stream);
 
+/* The byte-value normalisation table of n bytes of training data (device
+ * pointers; d_norm: float[256]). Allocates and frees a temporary buffer. */
+bwt_status bwt_model_byte_norm(const uint8_t* d_in, uint64_t n, float* d_norm, void* stream);
+
 /* Training samples produced by the plain sorter: sorts the batch with the
  * plain path of `plan`, then for every s < count takes the row at global
  * sorted position d_pos[s] (< total bytes) and writes d_x[s] = the 8 prefix
- * bytes of that row's rotation / 255 and d_t[s] = its row within its block /
- * block size. Synchronises `stream`. */
+ * bytes of that row's rotation mapped through d_norm and d_t[s] = its row
+ * within its block / block size. Synchronises `stream`. */
 bwt_status bwt_model_samples(bwt_plan* plan, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
-                             const uint64_t* d_pos, uint32_t count, float* d_x, float* d_t, void* stream);
+                             const uint64_t* d_pos, uint32_t count, const float* d_norm, float* d_x, float* d_t,
+                             void* stream);
 
 /* Compiles trained parameters into BWT_SPLITTERS sorted splitters
  * (d_splitters, device u64): splitter j is found by bisection over the 64-bit
- * key space as the smallest key whose model output reaches
- * (j + 1) / BWT_BUCKETS; the table is then sorted. */
-bwt_status bwt_model_compile(const float* d_params, uint64_t* d_splitters, void* stream);
+ * key space as the smallest key whose model output (bytes mapped through
+ * d_norm) reaches (j + 1) / BWT_BUCKETS; the table is then sorted and every
+ * run of equal splitters is spread evenly up to the next distinct one. */
+bwt_status bwt_model_compile(const float* d_params, const float* d_norm, uint64_t* d_splitters, void* stream);
 
 /* Installs a sorted splitter table (host or device memory, BWT_SPLITTERS
  * entries) in the plan; BWT_EINVAL if it is not non-decreasing. */
 bwt_status bwt_plan_set_splitters(bwt_plan* plan, const uint64_t* splitters);
 
-/* Model files: parameters and compiled splitters (host arrays). The file is
- * an 8-byte tag "BWTMDL01", then BWT_MLP_NPARAMS little-endian floats, then
- * BWT_SPLITTERS little-endian u64. load returns BWT_ENOMODEL if the file is
- * missing or malformed. */
-bwt_status bwt_model_save(const char* path, const float* params, const uint64_t* splitters);
-bwt_status bwt_model_load(const char* path, float* params, uint64_t* splitters);
+/* Model files: parameters, byte normalisation and compiled splitters (host
+ * arrays). The file is an 8-byte tag "BWTMDL02", then BWT_MLP_NPARAMS
+ * little-endian floats, 256 floats of norm, then BWT_SPLITTERS little-endian
+ * u64. load returns BWT_ENOMODEL if the file is missing or malformed. */
+bwt_status bwt_model_save(const char* path, const float* params, const float* norm, const uint64_t* splitters);
+bwt_status bwt_model_load(const char* path, float* params, float* norm, uint64_t* splitters);
 
 /* ---- forward BWT of one small block without device allocation --------
  *

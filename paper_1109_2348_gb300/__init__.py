@@ -97,6 +97,17 @@ class Plan:
     def set_radix(self, radix_bits: int, tile_keys: int) -> None:
         check(self.lib.bwt_plan_set_radix(self.handle, radix_bits, tile_keys), "bwt_plan_set_radix")
 
+    def autotune(self, d_in, offsets, d_L, d_primary, cache_path: str | None = None, repeats: int = 3,
+                 stream=None) -> tuple[int, int, float]:
+        """bwt_plan_autotune: returns (radix_bits, tile_keys, mean ms) and keeps them in the plan."""
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        rb, tk, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        check(self.lib.bwt_plan_autotune(self.handle, _ptr(d_in), off.ctypes.data, off.size - 1, _ptr(d_L),
+                                         _ptr(d_primary), _stream_handle(stream),
+                                         cache_path.encode() if cache_path else None, repeats, ctypes.byref(rb),
+                                         ctypes.byref(tk), ctypes.byref(ms)), "bwt_plan_autotune")
+        return rb.value, tk.value, ms.value
+
     def debug_waits(self, spin_limit: int, withhold_publish: bool) -> None:
         check(self.lib.bwt_plan_debug_waits(self.handle, spin_limit, int(withhold_publish)), "bwt_plan_debug_waits")
 

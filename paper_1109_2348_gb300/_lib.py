@@ -53,6 +53,8 @@ class Stats(ctypes.Structure):
         ("graph_replayed", ctypes.c_uint32),
         ("blocks_routed_plain", ctypes.c_uint32),
         ("pad_", ctypes.c_uint32),
+        ("bucket_sq_sum", ctypes.c_uint64),
+        ("buckets_nonempty", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -65,8 +67,8 @@ EXPORTS = [
     "bwt_plan_last_status", "bwt_plan_stats", "bwt_plan_set_radix", "bwt_plan_debug_waits",
     "bwt_status_string", "bwt_last_cuda_error",
     "bwt_mlp_forward", "bwt_mlp_loss_grad", "bwt_mlp_adam_step", "bwt_model_train", "bwt_model_samples",
-    "bwt_model_compile", "bwt_plan_set_splitters", "bwt_model_save", "bwt_model_load",
-    "bwt_forward_block_noalloc",
+    "bwt_model_compile", "bwt_plan_set_splitters", "bwt_model_save", "bwt_model_load", "bwt_model_byte_norm",
+    "bwt_forward_block_noalloc", "bwt_plan_autotune",
 ]
 
 MLP_NPARAMS = 1377
@@ -117,16 +119,21 @@ def load(build_if_missing: bool = True):
     lib.bwt_mlp_loss_grad.argtypes = [vp, vp, vp, u32, vp, vp, vp]
     lib.bwt_mlp_adam_step.argtypes = [vp, vp, vp, vp, u32, f32, vp]
     lib.bwt_model_train.argtypes = [vp, vp, vp, u32, vp, u32, u32, f32, vp, vp]
-    lib.bwt_model_samples.argtypes = [vp, vp, vp, u32, vp, u32, vp, vp, vp]
-    lib.bwt_model_compile.argtypes = [vp, vp, vp]
+    lib.bwt_model_samples.argtypes = [vp, vp, vp, u32, vp, u32, vp, vp, vp, vp]
+    lib.bwt_model_compile.argtypes = [vp, vp, vp, vp]
+    lib.bwt_model_byte_norm.argtypes = [vp, u64, vp, vp]
     lib.bwt_plan_set_splitters.argtypes = [vp, vp]
-    lib.bwt_model_save.argtypes = [ctypes.c_char_p, vp, vp]
-    lib.bwt_model_load.argtypes = [ctypes.c_char_p, vp, vp]
+    lib.bwt_model_save.argtypes = [ctypes.c_char_p, vp, vp, vp]
+    lib.bwt_model_load.argtypes = [ctypes.c_char_p, vp, vp, vp]
+    lib.bwt_plan_autotune.argtypes = [vp, vp, vp, u32, vp, vp, vp, ctypes.c_char_p, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_float)]
+    lib.bwt_plan_autotune.restype = ctypes.c_int
     lib.bwt_forward_block_noalloc.argtypes = [vp, u32, vp, vp, vp]
     lib.bwt_forward_block_noalloc.restype = ctypes.c_int
     for name in ("bwt_mlp_forward", "bwt_mlp_loss_grad", "bwt_mlp_adam_step", "bwt_model_train",
                  "bwt_model_samples", "bwt_model_compile", "bwt_plan_set_splitters", "bwt_model_save",
-                 "bwt_model_load"):
+                 "bwt_model_load", "bwt_model_byte_norm"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

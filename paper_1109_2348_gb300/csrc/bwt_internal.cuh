@@ -40,34 +40,37 @@ constexpr uint32_t ERR_TIMEOUT = 1u;
 constexpr uint32_t ERR_CAPACITY = 2u;
 
 // Group size classes of a doubling round.
-constexpr uint32_t TINY_MAX = 32;    // one warp per group, bitonic in registers
-constexpr uint32_t MED_MAX = 2048;   // one CTA per group, bitonic in shared memory
-// groups above MED_MAX are sorted by the segmented onesweep radix.
+constexpr int NCLS = 5;
+constexpr uint32_t MICRO_MAX = 4;     // one thread per group, sorting network in registers
+constexpr uint32_t TINY_MAX = 32;     // one warp per group, bitonic across the lanes
+constexpr uint32_t SMALL_MAX = 256;   // one warp per group, bitonic in shared memory
+constexpr uint32_t MED_MAX = 2048;    // one CTA per group, bitonic in shared memory
+// groups above MED_MAX (class 4, "large") are sorted by the segmented onesweep radix.
+constexpr int CLS_LARGE = 4;
 
 // Layout of the plan's device control words.
 enum : int {
-    CTRL_BINS = 0,          // [2][3]: counts of tiny / medium / large groups, double-buffered
-    CTRL_NUM_LTILES = 6,    // tiles of the large-group radix in this round
-    CTRL_ERR = 7,
-    CTRL_ROUNDS = 8,        // doubling rounds executed
-    CTRL_LARGE_KEYS = 9,    // keys in large groups this round
-    CTRL_ACTIVE = 10,       // u64 (words 10, 11): rotations re-sorted, summed over rounds
-    CTRL_SPIN = 12,         // spin limit for bounded waits
-    CTRL_WITHHOLD = 13,     // debug: first tile withholds its look-back publish
-    CTRL_DEPTH = 14,        // prefix length h the current round doubles
-    CTRL_NTILES0 = 15,      // tiles of the first sort
-    CTRL_BODY_ITERS = 16,   // graph mode: iterations of the doubling loop body
-    CTRL_BUCKET_OVF = 17,   // learned: overflowed buckets
-    CTRL_BUCKET_OVF_KEYS = 18,
-    CTRL_BUCKET_MAX = 19,
+    CTRL_BINS = 0,          // [2][NCLS]: group counts per size class, double-buffered
+    CTRL_NUM_LTILES = 10,   // tiles of the large-group radix in this round
+    CTRL_ERR = 11,
+    CTRL_ROUNDS = 12,       // doubling rounds executed
+    CTRL_LARGE_KEYS = 13,   // keys in large groups this round
+    CTRL_ACTIVE = 14,       // u64 (words 14, 15): rotations re-sorted, summed over rounds
+    CTRL_SPIN = 16,         // spin limit for bounded waits
+    CTRL_WITHHOLD = 17,     // debug: first tile withholds its look-back publish
+    CTRL_DEPTH = 18,        // prefix length h the current round doubles
+    CTRL_NTILES0 = 19,      // tiles of the first sort
+    CTRL_BODY_ITERS = 20,   // graph mode: iterations of the doubling loop body
+    CTRL_AUX0 = 21,         // learned: tiles of plain-routed blocks
+    CTRL_AUX1 = 22,         // learned: tiles of bucketed blocks
     CTRL_TILE_CTR = 32,     // [64] atomic tile counters, one per radix pass
     CTRL_WORDS = 128
 };
 
 struct Bins {
-    GroupDesc* list[3];
-    uint32_t cap[3];
-    uint32_t* count;                // -> ctrl + CTRL_BINS + 3 * parity
+    GroupDesc* list[NCLS];
+    uint32_t cap[NCLS];
+    uint32_t* count;                // -> ctrl + CTRL_BINS + NCLS * parity
     unsigned long long* active;     // -> ctrl + CTRL_ACTIVE
 };
 
@@ -94,7 +97,7 @@ __device__ __forceinline__ uint32_t bin_count(const Bins& b, int c) {
 
 // Size class of a group.
 __device__ __forceinline__ int size_class(uint32_t len) {
-    return len <= TINY_MAX ? 0 : (len <= MED_MAX ? 1 : 2);
+    return len <= MICRO_MAX ? 0 : len <= TINY_MAX ? 1 : len <= SMALL_MAX ? 2 : len <= MED_MAX ? 3 : 4;
 }
 
 // Append a group to the bin of its size class with one atomic per warp and
@@ -109,7 +112,7 @@ __device__ __forceinline__ void emit_group(const Bins& bins, bool want, uint32_t
     const uint32_t lsum = __reduce_add_sync(0xffffffffu, want ? len : 0u);
     if (lane == __ffs(any) - 1) atomicAdd(bins.active, (unsigned long long)lsum);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < NCLS; ++c) {
         uint32_t m = __ballot_sync(0xffffffffu, cls == c);
         if (m == 0) continue;
         int leader = __ffs(m) - 1;

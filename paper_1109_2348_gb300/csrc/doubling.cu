@@ -1,21 +1,25 @@
 // Group naming, prefix-doubling rounds and the L-column gather.
 //
 // After the first sort the rotations are ordered by their first 8 bytes.
-// Lexicographic naming (the paper's Section 2.1 names prefix-sum based
-// naming as a GPU building block): every rotation's rank becomes the
-// block-local sorted position of the first member of its group of equal
-// keys, so ranks order groups and equal ranks mean equal prefixes.
-// A prefix-doubling round with shift h (rotations already ordered by their
-// first h bytes) re-sorts every group of size > 1 by
-// key2 = rank[(i + h) mod n], which orders the group by its first 2h bytes,
-// and renames. Sorts stay stable with respect to the rotation index, so
-// groups that reach 2h >= n (identical rotations) keep lower-index-first.
+// Lexicographic naming (the paper's Section 2.1 names it among the GPU
+// building blocks): every rotation's rank becomes the block-local sorted
+// position of the first member of its group of equal keys, so ranks order
+// groups and equal ranks mean equal prefixes. A prefix-doubling round with
+// shift h (rotations already ordered by their first h bytes) re-sorts every
+// group of size > 1 by key2 = rank[(i + h) mod n], which orders the group by
+// its first 2h bytes, and renames. Within a group the rotations are kept in
+// increasing index order between rounds (every sort is stable or breaks ties
+// by the index), so groups that reach 2h >= n -- identical rotations -- end
+// lower-index-first.
 //
 // Round structure (all gathers of a round finish before any rank is
 // rewritten, so a round reads one consistent rank array):
-//   gather_small (tiny and medium groups) and large_prologue (large groups)
-//   -> sort_small (tiny: warp bitonic; medium: CTA bitonic) and the segmented
-//      radix of the large groups -> rename_large.
+//   gather (micro: thread per group; tiny/small/medium: warp per group) and
+//   large_prologue (large groups, by tile)
+//   -> sorts: micro (sorting network in registers), tiny (bitonic across a
+//      warp's lanes), small (warp bitonic in shared memory), medium (CTA
+//      bitonic in shared memory), large (segmented onesweep radix)
+//   -> renames (fused into the small sorts; rename_large for large groups).
 // Refined groups are appended to the next round's size-class bins.
 #include <algorithm>
 
@@ -29,8 +33,8 @@ namespace {
 // on [lo, k] and K[k] == key: exponential search backward, then bisection.
 template <typename KeyT>
 __device__ __forceinline__ uint32_t first_equal(const KeyT* __restrict__ K, uint32_t lo, uint32_t k, KeyT key) {
-    uint32_t hi_eq = k;    // known equal
-    int64_t below = -1;    // known different (or before lo)
+    uint32_t hi_eq = k;
+    int64_t below = -1;
     uint32_t step = 1;
     for (;;) {
         if ((uint64_t)(k - lo) < step) {
@@ -45,7 +49,6 @@ __device__ __forceinline__ uint32_t first_equal(const KeyT* __restrict__ K, uint
         hi_eq = c;
         step <<= 1;
     }
-    // answer in (below, hi_eq]
     uint32_t a = (uint32_t)(below + 1), b = hi_eq;
     while (a < b) {
         const uint32_t mid = a + ((b - a) >> 1);
@@ -74,7 +77,6 @@ __device__ __forceinline__ uint32_t end_equal(const KeyT* __restrict__ K, uint32
         lo_eq = c;
         step <<= 1;
     }
-    // answer in (lo_eq, above]
     uint32_t a = lo_eq + 1, b = above;
     while (a < b) {
         const uint32_t mid = a + ((b - a) >> 1);
@@ -83,48 +85,116 @@ __device__ __forceinline__ uint32_t end_equal(const KeyT* __restrict__ K, uint32
     return a;
 }
 
+template <typename T>
+__device__ __forceinline__ uint32_t smem_lower_bound(const T* a, uint32_t n, T x) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t smem_upper_bound(const T* a, uint32_t n, T x) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Names every element of one sorted tile: the tile's keys sit in sk[0..len),
+// its first run may have begun before the tile (it begins at carry_start)
+// and its last run may continue after it (it ends at carry_end). Writes
+// rank[rotation] = block-local start of the element's group and emits the
+// groups of size > 1 that start inside the tile. All threads of the CTA call.
+template <typename KeyT>
+__device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t tstart, uint32_t carry_start,
+                                          uint32_t carry_end, const uint32_t* __restrict__ SA, BlockInfo bi,
+                                          uint32_t blk, uint32_t* __restrict__ rank, const Bins& bins, bool emit_ok,
+                                          uint32_t* err) {
+    for (uint32_t q0 = 0; q0 < len; q0 += blockDim.x) {
+        const uint32_t q = q0 + threadIdx.x;
+        const bool valid = q < len;
+        bool want = false;
+        uint32_t glen = 0;
+        const uint32_t k = tstart + q;
+        if (valid) {
+            const KeyT key = sk[q];
+            const uint32_t lb = smem_lower_bound<KeyT>(sk, len, key);
+            const uint32_t gs = lb == 0 ? carry_start : tstart + lb;
+            const uint32_t sa = SA[k];
+            if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
+            if (gs == k && emit_ok) {
+                const uint32_t ub = smem_upper_bound<KeyT>(sk, len, key);
+                glen = (ub == len ? carry_end : tstart + ub) - k;
+                want = glen > 1;
+            }
+        }
+        emit_group(bins, want, k, glen, blk, err);
+    }
+}
+
 // ---- first naming ------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict__ K, const uint32_t* __restrict__ SA,
                                                       const BlockInfo* __restrict__ blocks,
                                                       const TileDesc* __restrict__ tiles, uint32_t num_tiles,
                                                       uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl) {
+    __shared__ uint64_t sk[4096];
+    __shared__ uint32_t s_carry[2];
     if (ld_volatile(&ctrl[CTRL_ERR])) return;  // an earlier stage failed: SA is not a permutation
     for (uint32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
         const uint32_t lo = bi.off, hi = bi.off + bi.n;
-        for (uint32_t q0 = 0; q0 < td.len; q0 += blockDim.x) {
-            const uint32_t q = q0 + threadIdx.x;
-            const bool valid = q < td.len;
-            bool want = false;
-            uint32_t k = td.start + q, len = 0;
-            if (valid) {
-                const uint64_t key = K[k];
-                const bool head = (k == lo) || (K[k - 1] != key);
-                const uint32_t gs = head ? k : first_equal<uint64_t>(K, lo, k, key);
-                const uint32_t sa = SA[k];
-                if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
-                if (head && bi.n > 8u) {
-                    len = end_equal<uint64_t>(K, k, hi, key) - k;
-                    want = len > 1;
-                }
-            }
-            emit_group(bins, want, k, len, td.blk, &ctrl[CTRL_ERR]);
+        for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) sk[q] = K[td.start + q];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint32_t last = td.start + td.len - 1;
+            s_carry[0] = (td.start == lo || K[td.start - 1] != sk[0]) ? td.start
+                                                                      : first_equal<uint64_t>(K, lo, td.start, sk[0]);
+            s_carry[1] = (last + 1 == hi || K[last + 1] != sk[td.len - 1])
+                             ? last + 1
+                             : end_equal<uint64_t>(K, last, hi, sk[td.len - 1]);
         }
+        __syncthreads();
+        name_tile<uint64_t>(sk, td.len, td.start, s_carry[0], s_carry[1], SA, bi, td.blk, rank, bins, bi.n > 8u,
+                            &ctrl[CTRL_ERR]);
+        __syncthreads();
     }
 }
 
 // ---- round: key gathers ------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gather_micro(const uint32_t* __restrict__ SA, const uint32_t* __restrict__ rank,
+                                                      const BlockInfo* __restrict__ blocks, Bins cur,
+                                                      const uint32_t* __restrict__ depth, uint32_t* __restrict__ key2) {
+    const uint32_t h = *depth;
+    const uint32_t count = bin_count(cur, 0);
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < count; g += gridDim.x * blockDim.x) {
+        const GroupDesc gd = cur.list[0][g];
+        const BlockInfo bi = blocks[gd.blk];
+        for (uint32_t e = 0; e < gd.len; ++e) {
+            const uint32_t k = gd.start + e;
+            uint32_t r = SA[k] + h;
+            if (r >= bi.n) r -= bi.n;
+            key2[k] = r < bi.n ? rank[bi.off + r] : 0u;
+        }
+    }
+}
+
+// tiny, small and medium groups: one warp per group
 __global__ void __launch_bounds__(256) k_gather_small(const uint32_t* __restrict__ SA, const uint32_t* __restrict__ rank,
                                                       const BlockInfo* __restrict__ blocks, Bins cur,
                                                       const uint32_t* __restrict__ depth, uint32_t* __restrict__ key2) {
     const uint32_t h = *depth;
-    const uint32_t c0 = bin_count(cur, 0), c1 = bin_count(cur, 1);
-    const uint32_t total = c0 + c1;
+    const uint32_t c1 = bin_count(cur, 1), c2 = bin_count(cur, 2), c3 = bin_count(cur, 3);
+    const uint32_t total = c1 + c2 + c3;
     const int lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
     for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += nwarps) {
-        const GroupDesc gd = g < c0 ? cur.list[0][g] : cur.list[1][g - c0];
+        const GroupDesc gd = g < c1 ? cur.list[1][g] : (g < c1 + c2 ? cur.list[2][g - c1] : cur.list[3][g - c1 - c2]);
         const BlockInfo bi = blocks[gd.blk];
         for (uint32_t e = lane; e < gd.len; e += 32) {
             const uint32_t k = gd.start + e;
@@ -141,14 +211,14 @@ __global__ void __launch_bounds__(1024) k_build_large_tiles(Bins cur, int tile, 
     __shared__ uint32_t s_keys;
     if (threadIdx.x == 0) s_keys = 0;
     __syncthreads();
-    const uint32_t n = bin_count(cur, 2);
+    const uint32_t n = bin_count(cur, CLS_LARGE);
     uint32_t running = 0;
     for (uint32_t base = 0; base < n; base += 1024) {
         const uint32_t i = base + threadIdx.x;
         GroupDesc gd{0, 0, 0, 0};
         uint32_t nt = 0;
         if (i < n) {
-            gd = cur.list[2][i];
+            gd = cur.list[CLS_LARGE][i];
             nt = (gd.len + tile - 1) / tile;
             atomicAdd(&s_keys, gd.len);
         }
@@ -231,22 +301,92 @@ __global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restri
 }
 
 // ---- round: small-group sorts + rename ------------------------------------------
+
+// micro groups (2..4 rotations): one thread each, a 4-input sorting network
+__global__ void __launch_bounds__(256) k_sort_micro(uint32_t* __restrict__ SA, const uint32_t* __restrict__ key2,
+                                                    uint32_t* __restrict__ rank, const BlockInfo* __restrict__ blocks,
+                                                    Bins cur, Bins next, const uint32_t* __restrict__ depth,
+                                                    uint32_t* ctrl) {
+    if (ld_volatile(&ctrl[CTRL_ERR])) return;
+    const uint32_t new_depth = 2u * *depth;
+    const uint32_t count = bin_count(cur, 0);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < count; base += stride) {
+        const uint32_t g = base + lane;
+        const bool valid = g < count;
+        GroupDesc gd{0, 0, 0, 0};
+        BlockInfo bi{0, 0};
+        uint64_t c[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+        if (valid) {
+            gd = cur.list[0][g];
+            bi = blocks[gd.blk];
+            for (uint32_t e = 0; e < gd.len && e < 4; ++e)
+                c[e] = ((uint64_t)key2[gd.start + e] << 32) | SA[gd.start + e];
+        }
+        auto cx = [](uint64_t& a, uint64_t& b) {
+            const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+            a = lo;
+            b = hi;
+        };
+        cx(c[0], c[1]);
+        cx(c[2], c[3]);
+        cx(c[0], c[2]);
+        cx(c[1], c[3]);
+        cx(c[1], c[2]);
+        bool want0 = false, want1 = false;
+        uint32_t s0 = 0, l0 = 0, s1 = 0, l1 = 0;
+        if (valid) {
+            uint32_t gstart[4] = {0, 0, 0, 0};
+            uint32_t cur_start = 0;
+            for (uint32_t e = 0; e < gd.len && e < 4; ++e) {
+                if (e > 0 && (uint32_t)(c[e] >> 32) != (uint32_t)(c[e - 1] >> 32)) cur_start = e;
+                gstart[e] = cur_start;
+            }
+            int emitted = 0;
+            for (uint32_t e = 0; e < gd.len && e < 4; ++e) {
+                const uint32_t sa = (uint32_t)c[e];
+                SA[gd.start + e] = sa;
+                if (sa < bi.n) rank[bi.off + sa] = gd.start - bi.off + gstart[e];
+                if (gstart[e] == e) {
+                    uint32_t f = e + 1;
+                    while (f < gd.len && f < 4 && gstart[f] == e) ++f;
+                    if (f - e > 1 && new_depth < bi.n) {
+                        if (emitted == 0) {
+                            want0 = true;
+                            s0 = gd.start + e;
+                            l0 = f - e;
+                        } else {
+                            want1 = true;
+                            s1 = gd.start + e;
+                            l1 = f - e;
+                        }
+                        ++emitted;
+                    }
+                }
+            }
+        }
+        emit_group(next, want0, s0, l0, gd.blk, &ctrl[CTRL_ERR]);
+        emit_group(next, want1, s1, l1, gd.blk, &ctrl[CTRL_ERR]);
+    }
+}
+
+// tiny groups (5..32): one warp each, bitonic across the lanes
 __global__ void __launch_bounds__(256) k_sort_tiny(uint32_t* __restrict__ SA, const uint32_t* __restrict__ key2,
                                                    uint32_t* __restrict__ rank, const BlockInfo* __restrict__ blocks,
                                                    Bins cur, Bins next, const uint32_t* __restrict__ depth,
                                                    uint32_t* ctrl) {
     if (ld_volatile(&ctrl[CTRL_ERR])) return;
     const uint32_t new_depth = 2u * *depth;
-    const uint32_t count = bin_count(cur, 0);
+    const uint32_t count = bin_count(cur, 1);
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
     for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < count; g += nwarps) {
-        const GroupDesc gd = cur.list[0][g];
+        const GroupDesc gd = cur.list[1][g];
         const BlockInfo bi = blocks[gd.blk];
         const bool valid = lane < gd.len;
         const uint32_t k = gd.start + lane;
         uint64_t c = valid ? (((uint64_t)key2[k] << 32) | SA[k]) : ~0ull;
-        // bitonic sort of 32 lanes, ascending
 #pragma unroll
         for (uint32_t kk = 2; kk <= 32; kk <<= 1) {
 #pragma unroll
@@ -275,15 +415,88 @@ __global__ void __launch_bounds__(256) k_sort_tiny(uint32_t* __restrict__ SA, co
     }
 }
 
-__device__ __forceinline__ uint32_t smem_lower_bound(const uint64_t* a, uint32_t n, uint64_t x) {
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
+template <int NT>
+__device__ __forceinline__ void coop_sync() {
+    if constexpr (NT == 32) __syncwarp(); else __syncthreads();
 }
 
+// Sorts comp[0..P) (P a power of two) by bitonic merging; NT threads
+// cooperate (a warp or the CTA), t is the thread's index among them.
+template <int NT>
+__device__ __forceinline__ void coop_bitonic(uint64_t* comp, uint32_t P, uint32_t t) {
+    for (uint32_t kk = 2; kk <= P; kk <<= 1) {
+        for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = t; i < P; i += NT) {
+                const uint32_t ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a = comp[i], b = comp[ixj];
+                    const bool up = (i & kk) == 0;
+                    if ((a > b) == up) {
+                        comp[i] = b;
+                        comp[ixj] = a;
+                    }
+                }
+            }
+            coop_sync<NT>();
+        }
+    }
+}
+
+// Loads a group's (key2, SA) composites, sorts them, writes SA back, renames
+// and emits refined groups. NT threads (a warp or the CTA) cooperate.
+template <int NT>
+__device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDesc& gd, const BlockInfo& bi,
+                                                  uint32_t* __restrict__ SA, const uint32_t* __restrict__ key2,
+                                                  uint32_t* __restrict__ rank, const Bins& next, uint32_t new_depth,
+                                                  uint32_t* err, uint32_t t) {
+    const uint32_t m = gd.len;
+    uint32_t P = 32;
+    while (P < m) P <<= 1;
+    for (uint32_t i = t; i < P; i += NT)
+        comp[i] = i < m ? (((uint64_t)key2[gd.start + i] << 32) | SA[gd.start + i]) : ~0ull;
+    coop_sync<NT>();
+    coop_bitonic<NT>(comp, P, t);
+    for (uint32_t i0 = 0; i0 < m; i0 += NT) {
+        const uint32_t i = i0 + t;
+        const bool valid = i < m;
+        bool want = false;
+        uint32_t len = 0;
+        if (valid) {
+            const uint64_t c = comp[i];
+            const uint32_t key = (uint32_t)(c >> 32), sa = (uint32_t)c;
+            const bool head = (i == 0) || (uint32_t)(comp[i - 1] >> 32) != key;
+            const uint32_t s = head ? i : smem_lower_bound<uint64_t>(comp, m, (uint64_t)key << 32);
+            SA[gd.start + i] = sa;
+            if (sa < bi.n) rank[bi.off + sa] = gd.start - bi.off + s;
+            if (head) {
+                len = smem_lower_bound<uint64_t>(comp, m, (uint64_t)(key + 1) << 32) - i;
+                want = len > 1 && new_depth < bi.n;
+            }
+        }
+        emit_group(next, want, gd.start + i, len, gd.blk, err);
+    }
+    coop_sync<NT>();
+}
+
+// small groups (33..256): one warp each, bitonic in the warp's shared memory
+__global__ void __launch_bounds__(256) k_sort_small(uint32_t* __restrict__ SA, const uint32_t* __restrict__ key2,
+                                                    uint32_t* __restrict__ rank, const BlockInfo* __restrict__ blocks,
+                                                    Bins cur, Bins next, const uint32_t* __restrict__ depth,
+                                                    uint32_t* ctrl) {
+    __shared__ uint64_t comp[8][SMALL_MAX];
+    if (ld_volatile(&ctrl[CTRL_ERR])) return;
+    const uint32_t new_depth = 2u * *depth;
+    const uint32_t count = bin_count(cur, 2);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < count; g += nwarps) {
+        const GroupDesc gd = cur.list[2][g];
+        const BlockInfo bi = blocks[gd.blk];
+        sort_rename_group<32>(comp[warp], gd, bi, SA, key2, rank, next, new_depth, &ctrl[CTRL_ERR], lane);
+    }
+}
+
+// medium groups (257..2048): one CTA each, bitonic in shared memory
 __global__ void __launch_bounds__(256) k_sort_med(uint32_t* __restrict__ SA, const uint32_t* __restrict__ key2,
                                                   uint32_t* __restrict__ rank, const BlockInfo* __restrict__ blocks,
                                                   Bins cur, Bins next, const uint32_t* __restrict__ depth,
@@ -291,61 +504,25 @@ __global__ void __launch_bounds__(256) k_sort_med(uint32_t* __restrict__ SA, con
     __shared__ uint64_t comp[MED_MAX];
     if (ld_volatile(&ctrl[CTRL_ERR])) return;
     const uint32_t new_depth = 2u * *depth;
-    const uint32_t count = bin_count(cur, 1);
+    const uint32_t count = bin_count(cur, 3);
     for (uint32_t g = blockIdx.x; g < count; g += gridDim.x) {
-        const GroupDesc gd = cur.list[1][g];
+        const GroupDesc gd = cur.list[3][g];
         const BlockInfo bi = blocks[gd.blk];
-        const uint32_t m = gd.len;
-        uint32_t P = 64;
-        while (P < m) P <<= 1;
-        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
-            comp[i] = i < m ? (((uint64_t)key2[gd.start + i] << 32) | SA[gd.start + i]) : ~0ull;
-        __syncthreads();
-        for (uint32_t kk = 2; kk <= P; kk <<= 1) {
-            for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-                    const uint32_t ixj = i ^ j;
-                    if (ixj > i) {
-                        const uint64_t a = comp[i], b = comp[ixj];
-                        const bool up = (i & kk) == 0;
-                        if ((a > b) == up) {
-                            comp[i] = b;
-                            comp[ixj] = a;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        for (uint32_t i0 = 0; i0 < m; i0 += blockDim.x) {
-            const uint32_t i = i0 + threadIdx.x;
-            const bool valid = i < m;
-            bool want = false;
-            uint32_t len = 0;
-            if (valid) {
-                const uint64_t c = comp[i];
-                const uint32_t key = (uint32_t)(c >> 32), sa = (uint32_t)c;
-                const bool head = (i == 0) || (uint32_t)(comp[i - 1] >> 32) != key;
-                const uint32_t s = head ? i : smem_lower_bound(comp, m, (uint64_t)key << 32);
-                SA[gd.start + i] = sa;
-                if (sa < bi.n) rank[bi.off + sa] = gd.start - bi.off + s;
-                if (head) {
-                    len = smem_lower_bound(comp, m, (uint64_t)(key + 1) << 32) - i;
-                    want = len > 1 && new_depth < bi.n;
-                }
-            }
-            emit_group(next, want, gd.start + i, len, gd.blk, &ctrl[CTRL_ERR]);
-        }
-        __syncthreads();
+        sort_rename_group<256>(comp, gd, bi, SA, key2, rank, next, new_depth, &ctrl[CTRL_ERR], threadIdx.x);
     }
 }
 
+// large groups after their radix sort: rename by tile (binary search in the
+// tile in shared memory; one global search per tile end for runs that cross
+// it) and emit refined groups
 __global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict__ SA, const uint32_t* __restrict__ key2,
                                                       uint32_t* __restrict__ rank,
                                                       const BlockInfo* __restrict__ blocks,
                                                       const TileDesc* __restrict__ tiles,
                                                       const uint32_t* __restrict__ num_tiles, Bins next,
                                                       const uint32_t* __restrict__ depth, uint32_t* ctrl) {
+    __shared__ uint32_t sk[4096];
+    __shared__ uint32_t s_carry[2];
     if (ld_volatile(&ctrl[CTRL_ERR])) return;
     const uint32_t new_depth = 2u * *depth;
     const uint32_t nt = *num_tiles;
@@ -353,25 +530,21 @@ __global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
         const uint32_t lo = td.segStart, hi = td.segStart + td.pad0;
-        for (uint32_t q0 = 0; q0 < td.len; q0 += blockDim.x) {
-            const uint32_t q = q0 + threadIdx.x;
-            const bool valid = q < td.len;
-            bool want = false;
-            const uint32_t k = td.start + q;
-            uint32_t len = 0;
-            if (valid) {
-                const uint32_t key = key2[k];
-                const bool head = (k == lo) || key2[k - 1] != key;
-                const uint32_t gs = head ? k : first_equal<uint32_t>(key2, lo, k, key);
-                const uint32_t sa = SA[k];
-                if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
-                if (head) {
-                    len = end_equal<uint32_t>(key2, k, hi, key) - k;
-                    want = len > 1 && new_depth < bi.n;
-                }
-            }
-            emit_group(next, want, k, len, td.blk, &ctrl[CTRL_ERR]);
+        for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) sk[q] = key2[td.start + q];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint32_t last = td.start + td.len - 1;
+            s_carry[0] = (td.start == lo || key2[td.start - 1] != sk[0])
+                             ? td.start
+                             : first_equal<uint32_t>(key2, lo, td.start, sk[0]);
+            s_carry[1] = (last + 1 == hi || key2[last + 1] != sk[td.len - 1])
+                             ? last + 1
+                             : end_equal<uint32_t>(key2, last, hi, sk[td.len - 1]);
         }
+        __syncthreads();
+        name_tile<uint32_t>(sk, td.len, td.start, s_carry[0], s_carry[1], SA, bi, td.blk, rank, next,
+                            new_depth < bi.n, &ctrl[CTRL_ERR]);
+        __syncthreads();
     }
 }
 
@@ -403,19 +576,28 @@ int grid_for(uint32_t units, uint32_t per_cta, int cap_per_sm) {
 cudaError_t launch_name_initial(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks, const TileDesc* tiles,
                                 uint32_t num_tiles, uint32_t* rank, Bins bins, uint32_t* ctrl, cudaStream_t st) {
     if (!num_tiles) return cudaSuccess;
-    k_name_initial<<<grid_for(num_tiles, 1, 16), 256, 0, st>>>(K, SA, blocks, tiles, num_tiles, rank, bins, ctrl);
+    k_name_initial<<<grid_for(num_tiles, 1, 4), 256, 0, st>>>(K, SA, blocks, tiles, num_tiles, rank, bins, ctrl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_small(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks, Bins cur,
-                                const uint32_t* depth, uint32_t* key2, const uint32_t* host_counts, cudaStream_t st) {
-    int grid = num_sms() * 16;
+                                const uint32_t* depth, uint32_t* key2, const uint32_t* host_counts, cudaStream_t st,
+                                int* launched) {
+    int g_micro = num_sms() * 8, g_warp = num_sms() * 16;
     if (host_counts) {
-        const uint32_t n = host_counts[0] + host_counts[1];
-        if (!n) return cudaSuccess;
-        grid = grid_for(n, 8, 16);
+        g_micro = host_counts[0] ? grid_for(host_counts[0], 256, 8) : 0;
+        const uint32_t n = host_counts[1] + host_counts[2] + host_counts[3];
+        g_warp = n ? grid_for(n, 8, 16) : 0;
     }
-    k_gather_small<<<grid, 256, 0, st>>>(SA, rank, blocks, cur, depth, key2);
+    *launched = 0;
+    if (g_micro) {
+        k_gather_micro<<<g_micro, 256, 0, st>>>(SA, rank, blocks, cur, depth, key2);
+        ++*launched;
+    }
+    if (g_warp) {
+        k_gather_small<<<g_warp, 256, 0, st>>>(SA, rank, blocks, cur, depth, key2);
+        ++*launched;
+    }
     return cudaGetLastError();
 }
 
@@ -452,18 +634,28 @@ cudaError_t launch_large_prologue(const uint32_t* SA, const uint32_t* rank, cons
 cudaError_t launch_sort_small(uint32_t* SA, uint32_t* key2, uint32_t* rank, const BlockInfo* blocks, Bins cur,
                               Bins next, const uint32_t* depth, const uint32_t* host_counts, uint32_t* ctrl,
                               cudaStream_t st, int* launched) {
-    int g_tiny = num_sms() * 16, g_med = num_sms() * 8;
+    int g[4] = {num_sms() * 8, num_sms() * 16, num_sms() * 8, num_sms() * 8};
     if (host_counts) {
-        g_tiny = host_counts[0] ? grid_for(host_counts[0], 8, 16) : 0;
-        g_med = host_counts[1] ? grid_for(host_counts[1], 1, 8) : 0;
+        g[0] = host_counts[0] ? grid_for(host_counts[0], 256, 8) : 0;
+        g[1] = host_counts[1] ? grid_for(host_counts[1], 8, 16) : 0;
+        g[2] = host_counts[2] ? grid_for(host_counts[2], 8, 8) : 0;
+        g[3] = host_counts[3] ? grid_for(host_counts[3], 1, 8) : 0;
     }
     *launched = 0;
-    if (g_tiny) {
-        k_sort_tiny<<<g_tiny, 256, 0, st>>>(SA, key2, rank, blocks, cur, next, depth, ctrl);
+    if (g[0]) {
+        k_sort_micro<<<g[0], 256, 0, st>>>(SA, key2, rank, blocks, cur, next, depth, ctrl);
         ++*launched;
     }
-    if (g_med) {
-        k_sort_med<<<g_med, 256, 0, st>>>(SA, key2, rank, blocks, cur, next, depth, ctrl);
+    if (g[1]) {
+        k_sort_tiny<<<g[1], 256, 0, st>>>(SA, key2, rank, blocks, cur, next, depth, ctrl);
+        ++*launched;
+    }
+    if (g[2]) {
+        k_sort_small<<<g[2], 256, 0, st>>>(SA, key2, rank, blocks, cur, next, depth, ctrl);
+        ++*launched;
+    }
+    if (g[3]) {
+        k_sort_med<<<g[3], 256, 0, st>>>(SA, key2, rank, blocks, cur, next, depth, ctrl);
         ++*launched;
     }
     return cudaGetLastError();
@@ -472,7 +664,7 @@ cudaError_t launch_sort_small(uint32_t* SA, uint32_t* key2, uint32_t* rank, cons
 cudaError_t launch_rename_large(const uint32_t* SA, const uint32_t* key2, uint32_t* rank, const BlockInfo* blocks,
                                 const TileDesc* tiles, const uint32_t* num_tiles, Bins next, const uint32_t* depth,
                                 uint32_t* ctrl, cudaStream_t st) {
-    k_rename_large<<<num_sms() * 8, 256, 0, st>>>(SA, key2, rank, blocks, tiles, num_tiles, next, depth, ctrl);
+    k_rename_large<<<num_sms() * 4, 256, 0, st>>>(SA, key2, rank, blocks, tiles, num_tiles, next, depth, ctrl);
     return cudaGetLastError();
 }
 
@@ -496,28 +688,33 @@ __global__ void k_reset_ctrl(uint32_t* ctrl, uint32_t spin, uint32_t withhold, u
     }
 }
 
+__device__ __forceinline__ bool any_groups(const uint32_t* c) {
+    uint32_t a = 0;
+#pragma unroll
+    for (int i = 0; i < NCLS; ++i) a |= c[i];
+    return a != 0u;
+}
+
 // After a round that read bins[par]: advance the depth if the round had
 // work, and (graph mode) set the loop condition from bins[par ^ 1].
 __global__ void k_round_end(uint32_t* ctrl, int par, uint32_t max_n, cudaGraphConditionalHandle cond, int use_cond,
                             int count_body) {
-    const uint32_t* cur = ctrl + CTRL_BINS + 3 * par;
-    const uint32_t* nxt = ctrl + CTRL_BINS + 3 * (par ^ 1);
-    const bool active = (cur[0] | cur[1] | cur[2]) != 0u;
-    if (active) {
+    const uint32_t* cur = ctrl + CTRL_BINS + NCLS * par;
+    const uint32_t* nxt = ctrl + CTRL_BINS + NCLS * (par ^ 1);
+    if (any_groups(cur)) {
         ctrl[CTRL_DEPTH] *= 2u;
         ctrl[CTRL_ROUNDS] += 1u;
     }
     if (count_body) ctrl[CTRL_BODY_ITERS] += 1u;
     if (use_cond) {
-        const bool more = (nxt[0] | nxt[1] | nxt[2]) != 0u && ctrl[CTRL_DEPTH] < max_n && ctrl[CTRL_ROUNDS] < 40u &&
+        const bool more = any_groups(nxt) && ctrl[CTRL_DEPTH] < max_n && ctrl[CTRL_ROUNDS] < 40u &&
                           ctrl[CTRL_ERR] == 0u;
         cudaGraphSetConditional(cond, more ? 1u : 0u);
     }
 }
 
 __global__ void k_set_cond_initial(const uint32_t* ctrl, uint32_t max_n, cudaGraphConditionalHandle cond) {
-    const uint32_t* c = ctrl + CTRL_BINS;
-    const bool more = (c[0] | c[1] | c[2]) != 0u && ctrl[CTRL_DEPTH] < max_n && ctrl[CTRL_ERR] == 0u;
+    const bool more = any_groups(ctrl + CTRL_BINS) && ctrl[CTRL_DEPTH] < max_n && ctrl[CTRL_ERR] == 0u;
     cudaGraphSetConditional(cond, more ? 1u : 0u);
 }
 

@@ -69,9 +69,10 @@ cudaError_t launch_name_initial(const uint64_t* K, const uint32_t* SA, const Blo
                                 uint32_t* ctrl, cudaStream_t st);
 
 // Round with prefix length h = *depth: key2[k] = rank[(SA[k] + h) mod n] for
-// every element of the tiny and medium groups in `cur`.
+// every element of the micro, tiny, small and medium groups in `cur`.
 cudaError_t launch_gather_small(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks, Bins cur,
-                                const uint32_t* depth, uint32_t* key2, const uint32_t* host_counts, cudaStream_t st);
+                                const uint32_t* depth, uint32_t* key2, const uint32_t* host_counts, cudaStream_t st,
+                                int* launched);
 
 // Builds the radix tile table of the large groups of `cur`, its count and
 // the number of keys in large groups.
@@ -85,7 +86,8 @@ cudaError_t launch_large_prologue(const uint32_t* SA, const uint32_t* rank, cons
                                   uint32_t* kbuf, uint32_t* vbuf, uint32_t* hist, int radix_bits, int passes,
                                   cudaStream_t st);
 
-// Tiny and medium groups: sort by (key2, SA), rename, emit refined groups.
+// Micro, tiny, small and medium groups: sort by (key2, SA), rename, emit
+// refined groups.
 cudaError_t launch_sort_small(uint32_t* SA, uint32_t* key2, uint32_t* rank, const BlockInfo* blocks, Bins cur,
                               Bins next, const uint32_t* depth, const uint32_t* host_counts, uint32_t* ctrl,
                               cudaStream_t st, int* launched);

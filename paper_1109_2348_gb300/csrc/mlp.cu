@@ -178,12 +178,16 @@ __global__ void k_adam(float* __restrict__ params, const float* __restrict__ g, 
 
 // Bisection over the 64-bit key space, one thread per splitter: splitter j
 // is the smallest key x (to 64-bit precision) with F(x) >= (j + 1) / 4096,
-// where F = the MLP evaluated on x's 8 bytes / 255. F need not be monotone;
-// the table is sorted afterwards, and any sorted table gives exact results.
+// where F = the MLP evaluated on x's 8 bytes mapped through norm. F need not
+// be monotone; the table is sorted afterwards, and any sorted table gives
+// exact results.
 __global__ void __launch_bounds__(128) k_compile_splitters(const float* __restrict__ params,
+                                                           const float* __restrict__ norm,
                                                            uint64_t* __restrict__ spl, uint32_t count) {
     __shared__ float P[NP];
+    __shared__ float nrm[256];
     for (int i = threadIdx.x; i < NP; i += blockDim.x) P[i] = params[i];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) nrm[i] = norm[i];
     __syncthreads();
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= count) return;
@@ -193,14 +197,20 @@ __global__ void __launch_bounds__(128) k_compile_splitters(const float* __restri
     for (int it = 0; it < 64 && lo < hi; ++it) {
         const uint64_t mid = lo + ((hi - lo) >> 1);
 #pragma unroll
-        for (int b = 0; b < IN; ++b) xs[b] = (float)((mid >> (56 - 8 * b)) & 0xff) * (1.f / 255.f);
+        for (int b = 0; b < IN; ++b) xs[b] = nrm[(mid >> (56 - 8 * b)) & 0xff];
         const float f = mlp_eval(P, xs, h1, h2);
         if (f >= q) hi = mid; else lo = mid + 1;
     }
     spl[j] = hi;
 }
 
-// Sorts the table in place (count <= 4096, one CTA, bitonic in shared memory).
+// Sorts the table in place (count <= 4096, one CTA, bitonic in shared memory),
+// then spreads every run of equal splitters evenly over the key interval up
+// to the next distinct splitter. Equal splitters come from a model that is
+// flat across an interval and jumps at its end (the model reads the key as
+// eight separate bytes, so it jumps at byte boundaries of the key): the run's
+// share of the distribution lies in that interval, and even spacing there is
+// the linear reading of the model's CDF across it. The table stays sorted.
 __global__ void __launch_bounds__(1024) k_sort_splitters(uint64_t* __restrict__ spl, uint32_t count) {
     __shared__ uint64_t a[4096];
     for (uint32_t i = threadIdx.x; i < 4096; i += blockDim.x) a[i] = i < count ? spl[i] : ~0ull;
@@ -220,6 +230,22 @@ __global__ void __launch_bounds__(1024) k_sort_splitters(uint64_t* __restrict__ 
             }
             __syncthreads();
         }
+    if (threadIdx.x == 0) {
+        uint32_t i = 0;
+        while (i < count) {
+            uint32_t j = i;
+            while (j + 1 < count && a[j + 1] == a[i]) ++j;
+            const uint32_t c = j - i + 1;
+            if (c > 1) {
+                const uint64_t base = a[i];
+                const uint64_t next = j + 1 < count ? a[j + 1] : ~0ull;
+                const unsigned __int128 span = (unsigned __int128)(next - base);
+                for (uint32_t r = 1; r < c; ++r) a[i + r] = base + (uint64_t)(span * r / c);
+            }
+            i = j + 1;
+        }
+    }
+    __syncthreads();
     for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) spl[i] = a[i];
 }
 
@@ -357,10 +383,11 @@ extern "C" bwt_status bwt_model_train(float* d_params, const float* d_x, const f
     return BWT_OK;
 }
 
-extern "C" bwt_status bwt_model_compile(const float* d_params, uint64_t* d_splitters, void* stream) {
-    if (!d_params || !d_splitters) return BWT_EINVAL;
+extern "C" bwt_status bwt_model_compile(const float* d_params, const float* d_norm, uint64_t* d_splitters,
+                                        void* stream) {
+    if (!d_params || !d_norm || !d_splitters) return BWT_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    k_compile_splitters<<<(BWT_SPLITTERS + 127) / 128, 128, 0, st>>>(d_params, d_splitters, BWT_SPLITTERS);
+    k_compile_splitters<<<(BWT_SPLITTERS + 127) / 128, 128, 0, st>>>(d_params, d_norm, d_splitters, BWT_SPLITTERS);
     k_sort_splitters<<<1, 1024, 0, st>>>(d_splitters, BWT_SPLITTERS);
     CKM(cudaGetLastError());
     return BWT_OK;

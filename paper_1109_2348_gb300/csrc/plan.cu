@@ -114,9 +114,10 @@ void bwt::free_plan_memory(bwt_plan* p) {
     F(p->keys[0]); F(p->keys[1]); F(p->vals[0]); F(p->vals[1]); F(p->rank);
     F(p->tiles0); F(p->ltiles); F(p->blocks); F(p->hist); F(p->status); F(p->ctrl);
     for (int s = 0; s < 2; ++s)
-        for (int c = 0; c < 3; ++c) F(p->bins[s][c]);
-    F(p->splitters); F(p->bucket_count);
+        for (int c = 0; c < NCLS; ++c) F(p->bins[s][c]);
+    F(p->splitters); F(p->bucket_count); F(p->bucket_cursor); F(p->route); F(p->bstats); F(p->tiles_aux);
     FH(p->h_ctrl); FH(p->h_tiles); FH(p->h_blocks); FH(p->h_off);
+    FH(p->h_route); FH(p->h_bstats); FH(p->h_tiles_aux);
     for (auto& e : p->events) cudaEventDestroy(e);
     p->events.clear();
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
@@ -153,9 +154,11 @@ extern "C" bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt
     p->cap_tiles0 = (uint32_t)((N + 1023) / 1024 + B);
     p->cap_ltiles = (uint32_t)(N / 1024 + N / (MED_MAX + 1) + 2);
     p->bincap[0] = (uint32_t)(N / 2 + 1);
-    p->bincap[1] = (uint32_t)(N / (TINY_MAX + 1) + 1);
-    p->bincap[2] = (uint32_t)(N / (MED_MAX + 1) + 1);
-    const uint64_t large_groups = p->bincap[2];
+    p->bincap[1] = (uint32_t)(N / (MICRO_MAX + 1) + 1);
+    p->bincap[2] = (uint32_t)(N / (TINY_MAX + 1) + 1);
+    p->bincap[3] = (uint32_t)(N / (SMALL_MAX + 1) + 1);
+    p->bincap[4] = (uint32_t)(N / (MED_MAX + 1) + 1);
+    const uint64_t large_groups = p->bincap[4];
     p->cap_hist = std::max<uint64_t>({(uint64_t)B * 6 * 2048, (uint64_t)B * 256, large_groups * 4 * 256,
                                       large_groups * 3 * 2048});
     p->cap_status = (uint64_t)std::max(p->cap_tiles0, p->cap_ltiles) * 2048;
@@ -177,7 +180,7 @@ extern "C" bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt
     A(dev_alloc(&p->status, p->cap_status, &total));
     A(dev_alloc(&p->ctrl, CTRL_WORDS, &total));
     for (int par = 0; par < 2; ++par)
-        for (int c = 0; c < 3; ++c) A(dev_alloc(&p->bins[par][c], p->bincap[c], &total));
+        for (int c = 0; c < NCLS; ++c) A(dev_alloc(&p->bins[par][c], p->bincap[c], &total));
     A(host_alloc(&p->h_ctrl, CTRL_WORDS));
     A(host_alloc(&p->h_tiles, p->cap_tiles0));
     A(host_alloc(&p->h_blocks, B));
@@ -192,7 +195,7 @@ extern "C" bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt
             }
         }
     }
-    if (s == BWT_OK && (desc->flags & BWT_F_LEARNED)) s = load_model(p, p->model_path.c_str());
+    if (s == BWT_OK && (desc->flags & BWT_F_LEARNED) && !p->model_path.empty()) s = load_model(p, p->model_path.c_str());
     if (s != BWT_OK) {
         free_plan_memory(p);
         delete p;
@@ -307,11 +310,11 @@ bwt_status bwt::upload_tables(bwt_plan* p, const uint64_t* off, uint32_t nb, cud
 
 Bins bwt::bins_of(bwt_plan* p, int par) {
     Bins b;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < NCLS; ++c) {
         b.list[c] = p->bins[par][c];
         b.cap[c] = p->bincap[c];
     }
-    b.count = p->ctrl + CTRL_BINS + 3 * par;
+    b.count = p->ctrl + CTRL_BINS + NCLS * par;
     b.active = reinterpret_cast<unsigned long long*>(p->ctrl + CTRL_ACTIVE);
     return b;
 }
@@ -333,6 +336,7 @@ static cudaError_t timed_onesweep(bwt_plan* p, int key_bytes, bool from_s, const
     }
     p->stats.radix_launches++;
     p->stats.kernel_launches++;
+    p->stats.radix_keys += keys_host;  // device-counted keys are added when the round's counts are read
     return e;
 }
 
@@ -391,7 +395,7 @@ bwt_status bwt::enqueue_initial_sort(bwt_plan* p, const uint8_t* d_in, cudaStrea
 }
 
 bwt_status bwt::enqueue_naming(bwt_plan* p, const uint64_t* K, cudaStream_t st) {
-    CK(cudaMemsetAsync(p->ctrl + CTRL_BINS, 0, sizeof(uint32_t) * 6, st));
+    CK(cudaMemsetAsync(p->ctrl + CTRL_BINS, 0, sizeof(uint32_t) * 2 * NCLS, st));
     CK(launch_name_initial(K, p->sa, p->blocks, p->tiles0, p->ntiles0, p->rank, bins_of(p, 0), p->ctrl, st));
     p->stats.kernel_launches++;
     return BWT_OK;
@@ -407,20 +411,22 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
     uint32_t* ctrl = p->ctrl;
     const uint32_t* depth = ctrl + CTRL_DEPTH;
     Bins cur = bins_of(p, par), nxt = bins_of(p, par ^ 1);
-    CK(cudaMemsetAsync(nxt.count, 0, sizeof(uint32_t) * 3, st));
-    if (!host_counts || host_counts[0] + host_counts[1] > 0) {
-        CK(launch_gather_small(p->sa, p->rank, p->blocks, cur, depth, p->key2, host_counts, st));
-        p->stats.kernel_launches++;
+    CK(cudaMemsetAsync(nxt.count, 0, sizeof(uint32_t) * NCLS, st));
+    {
+        int launched = 0;
+        CK(launch_gather_small(p->sa, p->rank, p->blocks, cur, depth, p->key2, host_counts, st, &launched));
+        p->stats.kernel_launches += launched;
     }
-    const bool large = !host_counts || host_counts[2] > 0;
+    const bool large = !host_counts || host_counts[CLS_LARGE] > 0;
     const uint32_t hist_cap = (uint32_t)std::min<uint64_t>(p->cap_hist, 0xffffffffu);
     const uint32_t status_cap = (uint32_t)std::min<uint64_t>(p->cap_status, 0xffffffffu);
     if (large) {
         CK(launch_build_large_tiles(cur, p->tile, p->ltiles, p->cap_ltiles, ctrl, st));
-        CK(launch_zero_by_count(p->hist, cur.count + 2, (uint32_t)(P2 * RADIX), hist_cap, st));
+        CK(launch_zero_by_count(p->hist, cur.count + CLS_LARGE, (uint32_t)(P2 * RADIX), hist_cap, st));
         CK(launch_large_prologue(p->sa, p->rank, p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, depth, p->kA, p->vA,
                                  p->hist, rb, P2, st));
-        CK(launch_scan_rows(p->hist, RADIX, cur.count + 2, (uint32_t)P2, 0, (uint32_t)(p->cap_hist / RADIX), st));
+        CK(launch_scan_rows(p->hist, RADIX, cur.count + CLS_LARGE, (uint32_t)P2, 0, (uint32_t)(p->cap_hist / RADIX),
+                            st));
         p->stats.kernel_launches += 4;
         for (int ps = 0; ps < P2; ++ps) {
             CK(launch_zero_by_count(p->status, ctrl + CTRL_NUM_LTILES, (uint32_t)RADIX, status_cap, st));
@@ -443,6 +449,7 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
             a.shift = ps * rb;
             CK(timed_onesweep(p, 4, false, a, 16.0, 0, CTRL_LARGE_KEYS, st));
         }
+        p->pending_large_passes = (uint32_t)P2;
     }
     int launched = 0;
     CK(launch_sort_small(p->sa, p->key2, p->rank, p->blocks, cur, nxt, depth, host_counts, ctrl, st, &launched));
@@ -474,7 +481,6 @@ void bwt::collect_timing(bwt_plan* p) {
         const EvMeta& m = p->ev_meta[i];
         const uint64_t keys = m.keys_host ? m.keys_host : m.keys_dev;
         p->stats.radix_ms += ms;
-        p->stats.radix_keys += keys;
         p->radix_bytes += m.bytes_per_key * (double)keys;
     }
     p->ev_meta.clear();
@@ -482,6 +488,10 @@ void bwt::collect_timing(bwt_plan* p) {
 }
 
 static void resolve_large_keys(bwt_plan* p, uint32_t large_keys) {
+    if (p->pending_large_passes) {
+        p->stats.radix_keys += (uint64_t)p->pending_large_passes * large_keys;
+        p->pending_large_passes = 0;
+    }
     for (auto& m : p->ev_meta)
         if (m.ctrl_word >= 0 && !m.resolved) {
             m.keys_dev = large_keys;
@@ -495,13 +505,17 @@ bwt_status bwt::run_doubling_host_loop(bwt_plan* p, cudaStream_t st) {
     int par = 0;
     uint32_t depth = 8;
     while (depth < p->max_n && p->stats.rounds < 40) {
-        CK(cudaMemcpyAsync(p->h_ctrl, p->ctrl, sizeof(uint32_t) * 16, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(p->h_ctrl, p->ctrl, sizeof(uint32_t) * 24, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         resolve_large_keys(p, p->h_ctrl[CTRL_LARGE_KEYS]);
         if (p->h_ctrl[CTRL_ERR]) break;
-        uint32_t counts[3];
-        for (int c = 0; c < 3; ++c) counts[c] = std::min(p->h_ctrl[CTRL_BINS + 3 * par + c], p->bincap[c]);
-        if (counts[0] + counts[1] + counts[2] == 0) break;
+        uint32_t counts[NCLS];
+        uint64_t any = 0;
+        for (int c = 0; c < NCLS; ++c) {
+            counts[c] = std::min(p->h_ctrl[CTRL_BINS + NCLS * par + c], p->bincap[c]);
+            any += counts[c];
+        }
+        if (any == 0) break;
         bwt_status s = enqueue_round(p, par, counts, st);
         if (s != BWT_OK) return s;
         CK(launch_round_end(p->ctrl, par, p->max_n, 0, 0, 0, st));
@@ -555,6 +569,7 @@ extern "C" bwt_status bwt_forward_batch(bwt_plan* p, const uint8_t* d_in, const 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::memset(&p->stats, 0, sizeof(p->stats));
     p->radix_bytes = 0;
+    p->pending_large_passes = 0;
     p->ev_meta.clear();
     p->ev_used = 0;
     bwt_status s = prepare_batch(p, offsets, num_blocks, st);

@@ -34,7 +34,7 @@ struct bwt_plan {
     // capacities
     uint64_t cap_n = 0;
     uint32_t cap_b = 0, cap_tiles0 = 0, cap_ltiles = 0;
-    uint32_t bincap[3] = {0, 0, 0};
+    uint32_t bincap[bwt::NCLS] = {0, 0, 0, 0, 0};
     uint64_t cap_hist = 0, cap_status = 0;
     size_t device_bytes = 0;
 
@@ -48,11 +48,20 @@ struct bwt_plan {
     uint32_t* hist = nullptr;
     uint32_t* status = nullptr;
     uint32_t* ctrl = nullptr;
-    bwt::GroupDesc* bins[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    bwt::GroupDesc* bins[2][bwt::NCLS] = {};
 
-    // learned bucketing
-    uint64_t* splitters = nullptr;  // [4095] sorted
-    uint32_t* bucket_count = nullptr;
+    // learned bucketing (allocated when a model is installed)
+    uint64_t* splitters = nullptr;      // [BWT_SPLITTERS] sorted
+    uint32_t* bucket_count = nullptr;   // [block][BWT_BUCKETS] counts, then starts
+    uint32_t* bucket_cursor = nullptr;  // [block][BWT_BUCKETS] slots taken so far
+    uint32_t* route = nullptr;          // [block] 0 = buckets, 1 = plain radix
+    unsigned long long* bstats = nullptr;  // [block][5] overflow keys, overflow buckets, largest bucket,
+                                           // sum of squared sizes, non-empty buckets
+    bwt::TileDesc* tiles_aux = nullptr; // sub-tables of plain-routed and bucketed blocks
+    uint32_t* h_route = nullptr;
+    unsigned long long* h_bstats = nullptr;
+    bwt::TileDesc* h_tiles_aux = nullptr;
+    uint32_t h_aux[4] = {0, 0, 0, 0};
     bool have_model = false;
 
     // pinned host staging
@@ -72,6 +81,7 @@ struct bwt_plan {
     std::vector<bwt::EvMeta> ev_meta;
     size_t ev_used = 0;
     double radix_bytes = 0;
+    uint32_t pending_large_passes = 0;  // u32 passes enqueued whose key count is still on the device
 
     // CUDA graph cache
     cudaGraph_t graph = nullptr;
@@ -106,5 +116,6 @@ bwt_status run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_
 bwt_status run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st);
 bwt_status load_model(bwt_plan* p, const char* path);
 void graph_stats(bwt_plan* p);
+bwt_status ensure_learned_buffers(bwt_plan* p);
 
 }  // namespace bwt

@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256) k_scan_rows(uint32_t* __restrict__ hist, 
     const int per = radix / 256;
     for (uint32_t r = blockIdx.x; r < rows; r += gridDim.x) {
         uint32_t* row = hist + (size_t)r * radix;
-        uint32_t v[8];
+        uint32_t v[16];
         uint32_t s = 0;
         for (int i = 0; i < per; ++i) {
             v[i] = row[threadIdx.x * per + i];
@@ -460,7 +460,7 @@ cudaError_t launch_hist_keys11(const uint8_t* S, const BlockInfo* blocks, const 
 
 cudaError_t launch_scan_rows(uint32_t* hist, int radix, const uint32_t* num_rows_dev, uint32_t rows_mult,
                              uint32_t rows_host, uint32_t max_rows, cudaStream_t st) {
-    if (radix != 256 && radix != 2048) return cudaErrorInvalidValue;
+    if (radix != 256 && radix != 2048 && radix != 4096) return cudaErrorInvalidValue;
     const int grid = num_rows_dev ? num_sms() * 8 : (int)std::max<uint32_t>(1, std::min<uint32_t>(rows_host, 65535));
     if (!num_rows_dev && rows_host == 0) return cudaSuccess;
     k_scan_rows<<<grid, 256, 0, st>>>(hist, radix, num_rows_dev, rows_mult, rows_host, max_rows);

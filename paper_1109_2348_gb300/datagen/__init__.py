@@ -49,6 +49,8 @@ def _load():
         lib.gen_rng_probe.restype = None
         lib.gen_splitmix_probe.argtypes = [ctypes.c_uint64, ctypes.c_int, u64p]
         lib.gen_splitmix_probe.restype = None
+        lib.gen_permutation.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]
+        lib.gen_permutation.restype = None
         _lib = lib
     return _lib
 
@@ -69,6 +71,12 @@ def uniform_ints(seed: int, count: int, lo: int, hi: int) -> np.ndarray:
 def uniform_unit(seed: int, count: int) -> np.ndarray:
     out = np.empty(count, dtype=np.float64)
     _load().gen_uniform_unit(seed, count, out.ctypes.data)
+    return out
+
+
+def permutation(seed: int, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.uint32)
+    _load().gen_permutation(seed, n, out.ctypes.data)
     return out
 
 
@@ -119,6 +127,14 @@ class Workload:
                              buf.ctypes.data, th) != 0:
             raise ValueError("bad source id in workload")
         return buf, off
+
+    def reseeded(self, offset: int) -> "Workload":
+        """The same shapes and sources with every seed shifted by `offset`:
+        distinct units of work for another rank."""
+        if offset == 0:
+            return self
+        return Workload(self.name + f"+seed{offset}", list(self.sources), [s + offset for s in self.seeds],
+                        list(self.sizes), dict(self.notes))
 
     def subset(self, idx) -> "Workload":
         idx = list(idx)

@@ -321,3 +321,16 @@ void gen_splitmix_probe(uint64_t state, int count, uint64_t *out) {
     uint64_t x = state;
     for (int i = 0; i < count; ++i) out[i] = splitmix64(&x);
 }
+
+/* A uniformly random permutation of 0..n-1 (Fisher-Yates) from one seeded
+ * stream: minibatch orders for training are drawn here, not in the trainer. */
+void gen_permutation(uint64_t seed, uint32_t n, uint32_t *out) {
+    rng_t r;
+    uint64_t x = seed;
+    rng_seed(&r, splitmix64(&x));
+    for (uint32_t i = 0; i < n; ++i) out[i] = i;
+    for (uint32_t i = n; i > 1; --i) {
+        uint32_t j = rng_below(&r, i);
+        uint32_t t = out[i - 1]; out[i - 1] = out[j]; out[j] = t;
+    }
+}

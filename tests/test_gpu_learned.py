@@ -1,0 +1,210 @@
+"""GPU tests of the learned CDF model and the learned bucketing.
+
+* The FP32 forward / loss gradient / Adam kernels against the float64 oracle
+  on fixed weights and batches (relative 1e-4, absolute 1e-6).
+* Training on samples the plain sorter produces lowers the loss; the compiled
+  splitter table is sorted.
+* The learned path equals the oracle byte for byte (held-out Markov blocks,
+  uniform blocks that overflow, degenerate blocks, tiny blocks), whatever the
+  splitter table.
+* What the model gains: on held-out Markov blocks its buckets are far more
+  even than the equal-width splitters of the method without it.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1109_2348_gb300 import F_LEARNED, Plan, _lib, datagen, model
+
+from gpu_util import assert_matches_oracle, gpu_bwt
+
+pytestmark = pytest.mark.gpu
+
+
+def _vp(t):
+    return ctypes.c_void_p(int(t.data_ptr()))
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _batch(seed, B):
+    rng = np.random.default_rng(seed)
+    p = model.init_params(seed).astype(np.float64)
+    p += rng.normal(0, 0.05, p.size)  # biases away from zero so ReLUs are mixed
+    x = rng.integers(0, 256, (B, 8)) / 255.0
+    t = rng.random(B)
+    return p, x, t
+
+
+def test_mlp_forward_matches_oracle():
+    import torch
+    lib = _lib.load()
+    p, x, _ = _batch(1, 1000)
+    d_p = torch.from_numpy(p.astype(np.float32)).cuda()
+    d_x = torch.from_numpy(x.astype(np.float32)).cuda()
+    d_y = torch.empty(1000, dtype=torch.float32, device="cuda")
+    assert lib.bwt_mlp_forward(_vp(d_p), _vp(d_x), 1000, _vp(d_y), _stream()) == 0
+    ref = oracle.mlp_forward(p.astype(np.float32).astype(np.float64), x.astype(np.float32).astype(np.float64))
+    got = d_y.cpu().numpy().astype(np.float64)
+    assert np.allclose(got, ref, rtol=1e-4, atol=1e-6)
+
+
+@pytest.mark.parametrize("B", [1, 63, 64, 4096, 5000])
+def test_mlp_gradient_matches_oracle(B):
+    import torch
+    lib = _lib.load()
+    p, x, t = _batch(B, B)
+    p32, x32, t32 = p.astype(np.float32), x.astype(np.float32), t.astype(np.float32)
+    d = [torch.from_numpy(a).cuda() for a in (p32, x32, t32)]
+    d_g = torch.empty(_lib.MLP_NPARAMS, dtype=torch.float32, device="cuda")
+    d_l = torch.empty(1, dtype=torch.float32, device="cuda")
+    assert lib.bwt_mlp_loss_grad(_vp(d[0]), _vp(d[1]), _vp(d[2]), B, _vp(d_g), _vp(d_l), _stream()) == 0
+    loss, g = oracle.mlp_loss_grad(p32.astype(np.float64), x32.astype(np.float64), t32.astype(np.float64))
+    got = d_g.cpu().numpy().astype(np.float64)
+    assert np.allclose(got, g, rtol=1e-4, atol=1e-6), np.max(np.abs(got - g))
+    assert abs(float(d_l.cpu()[0]) - loss) <= 1e-4 * abs(loss) + 1e-6
+
+
+def test_adam_step_matches_oracle():
+    import torch
+    lib = _lib.load()
+    rng = np.random.default_rng(3)
+    p = rng.normal(0, 1, _lib.MLP_NPARAMS)
+    g = rng.normal(0, 1, _lib.MLP_NPARAMS)
+    m = rng.normal(0, 0.1, _lib.MLP_NPARAMS)
+    v = rng.random(_lib.MLP_NPARAMS) * 0.1
+    d = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (p, g, m, v)]
+    for step in (1, 2, 7):
+        assert lib.bwt_mlp_adam_step(_vp(d[0]), _vp(d[1]), _vp(d[2]), _vp(d[3]), step, ctypes.c_float(1e-3),
+                                     _stream()) == 0
+        oracle.adam_step(p, g, m, v, step, lr=1e-3)
+    for dt, ref in zip(d, (p, g, m, v)):
+        assert np.allclose(dt.cpu().numpy().astype(np.float64), ref, rtol=1e-4, atol=1e-6)
+
+
+@pytest.fixture(scope="module")
+def small_model():
+    w = datagen.learned_train(num_blocks=12, n=200_000)
+    return model.train(w, num_samples=200_000, epochs=6, batch=4096, lr=2e-3, seed=5000)
+
+
+def test_training_lowers_loss_and_compiles_sorted_splitters(small_model):
+    loss = small_model.epoch_loss
+    assert loss[-1] < 0.5 * loss[0], loss
+    assert loss[-1] < 0.01, loss
+    s = small_model.splitters
+    assert s.size == _lib.SPLITTERS and np.all(s[1:] >= s[:-1])
+
+
+def test_training_samples_come_from_the_plain_sort():
+    """A sample's target is its rotation's row / n in the plain sort and its
+    inputs are the rotation's 8 bytes through the byte-value CDF; check both
+    against the oracle's rotation order and a direct count on one block."""
+    w = datagen.learned_train(num_blocks=1, n=30_000)
+    d_x, d_t, d_norm = model.make_samples(w, 500, seed=9)
+    buf, off = w.generate()
+    _, _, SA = oracle.bwt_block(buf, with_sa=True)
+    pos = datagen.uniform_ints(9, 500, 0, int(off[-1]) - 1)
+    x = d_x.cpu().numpy()
+    t = d_t.cpu().numpy()
+    n = buf.size
+    cnt = np.bincount(buf, minlength=256).astype(np.float64)
+    norm_ref = (np.cumsum(cnt) - cnt + 0.5 * cnt) / n
+    assert np.allclose(d_norm.cpu().numpy(), norm_ref, atol=1e-7)
+    for s in range(500):
+        k = int(pos[s])
+        i = SA[k]
+        want = norm_ref[buf[(i + np.arange(8)) % n]]
+        assert np.allclose(x[s], want, atol=1e-6)
+        assert abs(t[s] - k / n) < 1e-6
+
+
+def _learned_run(buf, off, splitters, **kw):
+    import torch
+    sizes = np.diff(off.astype(np.int64))
+    with Plan(max_blocks=off.size - 1, max_total_bytes=buf.size, max_block_bytes=int(sizes.max()), flags=F_LEARNED,
+              **kw) as plan:
+        model.install(plan, splitters)
+        d_in = torch.from_numpy(buf).cuda()
+        L, prim = plan.forward(d_in, off)
+        torch.cuda.synchronize()
+        return L.cpu().numpy(), prim.cpu().numpy(), plan.stats()
+
+
+def test_learned_equals_oracle_on_held_out_blocks(small_model):
+    w = datagen.learned_eval(num_blocks=20, n=150_000)
+    buf, off = w.generate()
+    L, prim, st = _learned_run(buf, off, small_model.splitters)
+    assert_matches_oracle(buf, off, L, prim, "learned held-out")
+    assert st["blocks_routed_plain"] >= 1  # the uniform blocks overflow the Markov-trained buckets
+
+
+@pytest.mark.parametrize("which", ["model", "equal_width"])
+def test_learned_path_exact_for_any_splitters(small_model, which):
+    spl = small_model.splitters if which == "model" else model.equal_width_splitters()
+    w = datagen.Workload("t", [datagen.CONST, datagen.PERIOD7, datagen.FIBONACCI, datagen.RUNS16, datagen.UNIFORM,
+                               datagen.MARKOV3_Z96, datagen.MARKOV2_Z64],
+                         [1, 2, 3, 4, 5, 6, 7], [30_000, 20_001, 25_000, 40_000, 3, 60_000, 7_777])
+    buf, off = w.generate()
+    L, prim, _ = _learned_run(buf, off, spl)
+    assert_matches_oracle(buf, off, L, prim, which)
+
+
+def test_learned_with_radix_variants(small_model):
+    w = datagen.learned_eval(num_blocks=6, n=50_000)
+    buf, off = w.generate()
+    for rb, tile in ((8, 1024), (11, 2048)):
+        L, prim, _ = _learned_run(buf, off, small_model.splitters, radix_bits=rb, tile_keys=tile)
+        assert_matches_oracle(buf, off, L, prim, f"learned rb={rb} tile={tile}")
+
+
+def test_what_the_model_gains(small_model):
+    """The gain of the trained network. Against the plain sort: the learned
+    buckets replace the 8 radix passes, so far fewer keys go through the
+    radix. Against the same bucketing without a model (equal-width buckets on
+    the top 12 key bits): the learned buckets are more even -- more of the
+    4096 buckets are used and the in-bucket sort work (sum of squared bucket
+    sizes) is smaller. All three give the identical transform."""
+    w = datagen.learned_eval(num_blocks=9, n=300_000)  # 9 held-out Markov blocks
+    buf, off = w.generate()
+    L1, p1, s_model = _learned_run(buf, off, small_model.splitters)
+    L2, p2, s_flat = _learned_run(buf, off, model.equal_width_splitters())
+    L3, p3, s_plain = gpu_bwt(buf, off)
+    assert np.array_equal(L1, L2) and np.array_equal(p1, p2)
+    assert np.array_equal(L1, L3) and np.array_equal(p1, p3)
+    assert s_model["blocks_routed_plain"] == 0, s_model
+    assert s_model["radix_keys"] * 4 < s_plain["radix_keys"], (s_model, s_plain)
+    assert s_model["buckets_nonempty"] > 2 * s_flat["buckets_nonempty"], (s_model, s_flat)
+    assert s_model["bucket_sq_sum"] < s_flat["bucket_sq_sum"], (s_model, s_flat)
+
+
+def test_model_file_round_trip(tmp_path, small_model):
+    path = str(tmp_path / "m.bwtmodel")
+    small_model.save(path)
+    m2 = model.TrainedModel.load(path)
+    assert np.array_equal(m2.params, small_model.params) and np.array_equal(m2.splitters, small_model.splitters)
+    assert np.array_equal(m2.norm, small_model.norm)
+    w = datagen.learned_eval(num_blocks=3, n=40_000)
+    buf, off = w.generate()
+    import torch
+    with Plan(max_blocks=3, max_total_bytes=buf.size, max_block_bytes=40_000, flags=F_LEARNED,
+              model_path=path) as plan:
+        L, prim = plan.forward(torch.from_numpy(buf).cuda(), off)
+        assert_matches_oracle(buf, off, L.cpu().numpy(), prim.cpu().numpy(), "model file")
+
+
+def test_learned_without_model_reports_enomodel():
+    import torch
+    with Plan(max_blocks=1, max_total_bytes=100, max_block_bytes=100, flags=F_LEARNED) as plan:
+        d = torch.zeros(100, dtype=torch.uint8, device="cuda")
+        L = torch.empty_like(d)
+        p = torch.empty(1, dtype=torch.int32, device="cuda")
+        assert plan.forward_into(d, np.array([0, 100], dtype=np.uint64), L, p,
+                                 raise_on_error=False) == _lib.BWT_ENOMODEL
+    with pytest.raises(_lib.BWTError):
+        Plan(max_blocks=1, max_total_bytes=100, max_block_bytes=100, flags=F_LEARNED, model_path="/nonexistent/m")

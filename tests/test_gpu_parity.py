@@ -149,3 +149,28 @@ def test_bounded_wait_times_out_and_context_survives():
         plan.debug_waits(0, False)
         plan.forward_into(d_in, off, L, p)
         assert_matches_oracle(buf, off, L.cpu().numpy(), p.cpu().numpy(), "after timeout")
+
+
+def test_autotuner_picks_a_valid_config_and_caches_it(tmp_path):
+    import json
+    import torch
+    w = datagen.uneven_markov3(num_blocks=16, lo=5_000, hi=60_000)
+    buf, off = w.generate()
+    d_in = torch.from_numpy(buf).cuda()
+    cache = str(tmp_path / "tune.jsonl")
+    with Plan(max_blocks=16, max_total_bytes=buf.size, max_block_bytes=60_000, flags=F_GRAPH) as plan:
+        L = torch.empty_like(d_in)
+        p = torch.empty(16, dtype=torch.int32, device="cuda")
+        rb, tile, ms = plan.autotune(d_in, off, L, p, cache_path=cache, repeats=2)
+        assert rb in (8, 11) and tile in (1024, 2048, 4096) and ms > 0
+        st = plan.stats()
+        assert st["radix_bits"] == rb and st["tile_keys"] == tile
+        assert_matches_oracle(buf, off, L.cpu().numpy(), p.cpu().numpy(), "autotuned")
+        lines = [json.loads(x) for x in open(cache)]
+        assert lines[-1]["radix_bits"] == rb and lines[-1]["tile_keys"] == tile
+    with Plan(max_blocks=16, max_total_bytes=buf.size, max_block_bytes=60_000, flags=F_GRAPH) as plan2:
+        L = torch.empty_like(d_in)
+        p = torch.empty(16, dtype=torch.int32, device="cuda")
+        rb2, tile2, _ = plan2.autotune(d_in, off, L, p, cache_path=cache, repeats=2)
+        assert (rb2, tile2) == (rb, tile)
+        assert len(open(cache).readlines()) == 1  # read back, no new sweep
