@@ -83,10 +83,13 @@ typedef struct {
     uint32_t graph_replayed;    /* 1 if the last call replayed a cached CUDA graph */
     uint32_t blocks_routed_plain; /* learned bucketing: blocks whose buckets overflowed too much and
                                      were sorted by the plain radix path instead */
-    uint32_t pad_;
+    uint32_t blocks_routed_flat;  /* learned bucketing: blocks bucketed by equal-width splitters (the top
+                                     12 key bits) because the learned buckets overflowed */
     uint64_t bucket_sq_sum;     /* learned bucketing: sum over all blocks and buckets of size^2 (the
                                    in-bucket sort work; smallest when buckets are even) */
     uint64_t buckets_nonempty;  /* learned bucketing: non-empty buckets over all blocks */
+    uint32_t round_radix_bits;  /* digit width of the doubling rounds' radix */
+    uint32_t pad2_;
 } bwt_stats;
 
 /* Create a plan on CUDA device `device` (made current for the call). The plan
@@ -134,6 +137,11 @@ bwt_status bwt_plan_stats(const bwt_plan* plan, bwt_stats* out);
 /* Changes the radix digit width (8 or 11) and tile size (1024, 2048, 4096)
  * used by later calls; drops any cached graph. */
 bwt_status bwt_plan_set_radix(bwt_plan* plan, int radix_bits, int tile_keys);
+
+/* Digit width (8 or 11) of the segmented radix that sorts large groups in
+ * the prefix-doubling rounds; 0 (the default) means 8. Drops any cached
+ * graph. */
+bwt_status bwt_plan_set_round_radix(bwt_plan* plan, int radix_bits);
 
 /* Autotuner (no paper counterpart): times this batch for radix_bits in
  * {8, 11} x tile_keys in {1024, 2048, 4096} (one untimed run, then `repeats`

@@ -97,6 +97,9 @@ class Plan:
     def set_radix(self, radix_bits: int, tile_keys: int) -> None:
         check(self.lib.bwt_plan_set_radix(self.handle, radix_bits, tile_keys), "bwt_plan_set_radix")
 
+    def set_round_radix(self, radix_bits: int) -> None:
+        check(self.lib.bwt_plan_set_round_radix(self.handle, radix_bits), "bwt_plan_set_round_radix")
+
     def autotune(self, d_in, offsets, d_L, d_primary, cache_path: str | None = None, repeats: int = 3,
                  stream=None) -> tuple[int, int, float]:
         """bwt_plan_autotune: returns (radix_bits, tile_keys, mean ms) and keeps them in the plan."""

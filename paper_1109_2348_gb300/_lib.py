@@ -52,9 +52,11 @@ class Stats(ctypes.Structure):
         ("max_bucket", ctypes.c_uint32),
         ("graph_replayed", ctypes.c_uint32),
         ("blocks_routed_plain", ctypes.c_uint32),
-        ("pad_", ctypes.c_uint32),
+        ("blocks_routed_flat", ctypes.c_uint32),
         ("bucket_sq_sum", ctypes.c_uint64),
         ("buckets_nonempty", ctypes.c_uint64),
+        ("round_radix_bits", ctypes.c_uint32),
+        ("pad2_", ctypes.c_uint32),
     ]
 
     def as_dict(self) -> dict:
@@ -68,7 +70,7 @@ EXPORTS = [
     "bwt_status_string", "bwt_last_cuda_error",
     "bwt_mlp_forward", "bwt_mlp_loss_grad", "bwt_mlp_adam_step", "bwt_model_train", "bwt_model_samples",
     "bwt_model_compile", "bwt_plan_set_splitters", "bwt_model_save", "bwt_model_load", "bwt_model_byte_norm",
-    "bwt_forward_block_noalloc", "bwt_plan_autotune",
+    "bwt_forward_block_noalloc", "bwt_plan_autotune", "bwt_plan_set_round_radix",
 ]
 
 MLP_NPARAMS = 1377
@@ -108,6 +110,8 @@ def load(build_if_missing: bool = True):
     lib.bwt_plan_stats.restype = ctypes.c_int
     lib.bwt_plan_set_radix.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.bwt_plan_set_radix.restype = ctypes.c_int
+    lib.bwt_plan_set_round_radix.argtypes = [vp, ctypes.c_int]
+    lib.bwt_plan_set_round_radix.restype = ctypes.c_int
     lib.bwt_plan_debug_waits.argtypes = [vp, u32, ctypes.c_int]
     lib.bwt_plan_debug_waits.restype = ctypes.c_int
     lib.bwt_status_string.argtypes = [ctypes.c_int]

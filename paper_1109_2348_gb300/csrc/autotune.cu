@@ -96,10 +96,11 @@ extern "C" bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, con
             std::string g, k;
             if (json_field(line, "gpu", &g) && json_field(line, "key", &k) && g == gpu && k == key) best_line = line;
         }
-        std::string rb, tk, ms;
+        std::string rb, tk, ms, rr;
         if (!best_line.empty() && json_field(best_line, "radix_bits", &rb) && json_field(best_line, "tile_keys", &tk)) {
             const int r = std::atoi(rb.c_str()), t = std::atoi(tk.c_str());
-            if (bwt_plan_set_radix(plan, r, t) == BWT_OK) {
+            const int rrb = json_field(best_line, "round_radix_bits", &rr) ? std::atoi(rr.c_str()) : 0;
+            if (bwt_plan_set_radix(plan, r, t) == BWT_OK && bwt_plan_set_round_radix(plan, rrb) == BWT_OK) {
                 if (out_radix_bits) *out_radix_bits = r;
                 if (out_tile_keys) *out_tile_keys = t;
                 if (out_ms) *out_ms = json_field(best_line, "ms", &ms) ? (float)std::atof(ms.c_str()) : 0.f;
@@ -140,10 +141,36 @@ extern "C" bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, con
         }
         if (status != BWT_OK) break;
     }
+    // the doubling rounds' digit width, with the best first-sort choice
+    int best_r = 0;
+    if (status == BWT_OK) {
+        bwt_plan_set_radix(plan, best_b, best_t);
+        float best_round = 1e30f;
+        for (int rbits : {8, 11}) {
+            if ((status = bwt_plan_set_round_radix(plan, rbits)) != BWT_OK) break;
+            if ((status = bwt_forward_batch(plan, d_in, offsets, num_blocks, d_L, d_primary, stream)) != BWT_OK) break;
+            float total = 0.f;
+            for (int r = 0; r < repeats && status == BWT_OK; ++r) {
+                cudaEventRecord(e0, st);
+                status = bwt_forward_batch(plan, d_in, offsets, num_blocks, d_L, d_primary, stream);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                total += ms;
+            }
+            if (status == BWT_OK && total / repeats < best_round) {
+                best_round = total / repeats;
+                best_r = rbits;
+            }
+        }
+        if (best_round < best) best = best_round;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (status != BWT_OK) return status;
     bwt_plan_set_radix(plan, best_b, best_t);
+    bwt_plan_set_round_radix(plan, best_r);
     // one run with the chosen configuration: outputs and statistics are its
     if ((status = bwt_forward_batch(plan, d_in, offsets, num_blocks, d_L, d_primary, stream)) != BWT_OK) return status;
     if (out_radix_bits) *out_radix_bits = best_b;
@@ -152,8 +179,10 @@ extern "C" bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, con
     if (cache_path && *cache_path) {
         FILE* f = std::fopen(cache_path, "a");
         if (f) {
-            std::fprintf(f, "{\"gpu\": \"%s\", \"key\": \"%s\", \"radix_bits\": %d, \"tile_keys\": %d, \"ms\": %.4f}\n",
-                         json_escape(gpu).c_str(), json_escape(key).c_str(), best_b, best_t, best);
+            std::fprintf(f,
+                         "{\"gpu\": \"%s\", \"key\": \"%s\", \"radix_bits\": %d, \"tile_keys\": %d, "
+                         "\"round_radix_bits\": %d, \"ms\": %.4f}\n",
+                         json_escape(gpu).c_str(), json_escape(key).c_str(), best_b, best_t, best_r, best);
             std::fclose(f);
         }
     }

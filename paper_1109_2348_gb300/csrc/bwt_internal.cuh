@@ -88,6 +88,18 @@ __device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) {
     *reinterpret_cast<volatile uint32_t*>(p) = v;
 }
 
+// The 8 bytes sb[idx .. idx + 7] as a big-endian u64 (the rotation's sort
+// key). sb must be 4-byte aligned and readable up to idx + 11: three aligned
+// 32-bit words are funnel-shifted to the byte offset and byte-swapped.
+__device__ __forceinline__ uint64_t pack8_smem(const uint8_t* sb, uint32_t idx) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(sb) + (idx >> 2);
+    const uint32_t sh = (idx & 3u) * 8u;
+    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];
+    const uint32_t lo = __funnelshift_r(w0, w1, sh);  // bytes idx .. idx+3, first byte lowest
+    const uint32_t hi = __funnelshift_r(w1, w2, sh);  // bytes idx+4 .. idx+7
+    return ((uint64_t)__byte_perm(lo, 0, 0x0123) << 32) | __byte_perm(hi, 0, 0x0123);
+}
+
 // Number of valid entries of bin c (a count past the capacity means entries
 // were dropped and ERR_CAPACITY is set).
 __device__ __forceinline__ uint32_t bin_count(const Bins& b, int c) {
@@ -129,6 +141,78 @@ __device__ __forceinline__ void emit_group(const Bins& bins, bool want, uint32_t
         }
     }
 }
+
+// Warp-buffered emission: each warp stages the groups it emits in shared
+// memory, EMIT_BUF per size class, and reserves bin slots with one atomic per
+// flush instead of one per emitting warp step; the active-rotation count is
+// summed per lane and added once at the end. Every lane of the warp must make
+// the same calls (warp-uniform control flow).
+constexpr int EMIT_BUF = 16;
+
+struct WarpEmitter {
+    GroupDesc* buf;              // shared memory, [NCLS][EMIT_BUF]
+    uint32_t n[NCLS];            // staged entries per class (warp-uniform)
+    unsigned long long active;   // this lane's emitted rotations
+
+    __device__ __forceinline__ void init(GroupDesc* warp_buf) {
+        buf = warp_buf;
+#pragma unroll
+        for (int c = 0; c < NCLS; ++c) n[c] = 0;
+        active = 0;
+    }
+
+    __device__ __forceinline__ void flush(const Bins& bins, int c, uint32_t* err) {
+        const int lane = threadIdx.x & 31;
+        __syncwarp();
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&bins.count[c], n[c]);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((uint32_t)lane < n[c]) {
+            const uint32_t slot = base + lane;
+            if (slot < bins.cap[c]) bins.list[c][slot] = buf[c * EMIT_BUF + lane];
+            else atomicOr(err, ERR_CAPACITY);
+        }
+        n[c] = 0;
+        __syncwarp();
+    }
+
+    __device__ __forceinline__ void emit(const Bins& bins, bool want, uint32_t start, uint32_t len, uint32_t blk,
+                                         uint32_t* err) {
+        const int cls = want ? size_class(len) : -1;
+        if (want) active += len;
+        const uint32_t lt = lanemask_lt();
+#pragma unroll
+        for (int c = 0; c < NCLS; ++c) {
+            const uint32_t m = __ballot_sync(0xffffffffu, cls == c);
+            if (m == 0) continue;
+            const uint32_t cnt = __popc(m);
+            if (n[c] + cnt > EMIT_BUF) flush(bins, c, err);
+            if (cnt > EMIT_BUF) {  // more than the buffer holds: reserve and write directly
+                const int leader = __ffs(m) - 1;
+                uint32_t base = 0;
+                if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(&bins.count[c], cnt);
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (cls == c) {
+                    const uint32_t slot = base + __popc(m & lt);
+                    if (slot < bins.cap[c]) bins.list[c][slot] = GroupDesc{start, len, blk, 0u};
+                    else atomicOr(err, ERR_CAPACITY);
+                }
+                continue;
+            }
+            if (cls == c) buf[c * EMIT_BUF + n[c] + __popc(m & lt)] = GroupDesc{start, len, blk, 0u};
+            n[c] += cnt;
+        }
+    }
+
+    __device__ __forceinline__ void finish(const Bins& bins, uint32_t* err) {
+#pragma unroll
+        for (int c = 0; c < NCLS; ++c)
+            if (n[c]) flush(bins, c, err);
+        const unsigned long long tot = __reduce_add_sync(0xffffffffu, (uint32_t)active) +
+                                       ((unsigned long long)__reduce_add_sync(0xffffffffu, (uint32_t)(active >> 32)) << 32);
+        if ((threadIdx.x & 31) == 0 && tot) atomicAdd(bins.active, tot);
+    }
+};
 
 // Block-wide exclusive scan of one value per thread; returns the prefix and
 // writes the total to *total. `tmp` holds at least THREADS/32 words.

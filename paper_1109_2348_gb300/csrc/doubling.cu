@@ -114,7 +114,7 @@ template <typename KeyT>
 __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t tstart, uint32_t carry_start,
                                           uint32_t carry_end, const uint32_t* __restrict__ SA, BlockInfo bi,
                                           uint32_t blk, uint32_t* __restrict__ rank, const Bins& bins, bool emit_ok,
-                                          uint32_t* err) {
+                                          WarpEmitter& em, uint32_t* err) {
     for (uint32_t q0 = 0; q0 < len; q0 += blockDim.x) {
         const uint32_t q = q0 + threadIdx.x;
         const bool valid = q < len;
@@ -123,17 +123,20 @@ __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t
         const uint32_t k = tstart + q;
         if (valid) {
             const KeyT key = sk[q];
-            const uint32_t lb = smem_lower_bound<KeyT>(sk, len, key);
+            const bool differs_prev = q > 0 && sk[q - 1] != key;
+            const uint32_t lb = differs_prev ? q : (q == 0 ? 0u : smem_lower_bound<KeyT>(sk, q, key));
             const uint32_t gs = lb == 0 ? carry_start : tstart + lb;
             const uint32_t sa = SA[k];
             if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
             if (gs == k && emit_ok) {
-                const uint32_t ub = smem_upper_bound<KeyT>(sk, len, key);
+                uint32_t ub;
+                if (q + 1 < len && sk[q + 1] != key) ub = q + 1;
+                else ub = smem_upper_bound<KeyT>(sk, len, key);
                 glen = (ub == len ? carry_end : tstart + ub) - k;
                 want = glen > 1;
             }
         }
-        emit_group(bins, want, k, glen, blk, err);
+        em.emit(bins, want, k, glen, blk, err);
     }
 }
 
@@ -144,7 +147,10 @@ __global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict
                                                       uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl) {
     __shared__ uint64_t sk[4096];
     __shared__ uint32_t s_carry[2];
+    __shared__ GroupDesc ebuf[8][NCLS * EMIT_BUF];
     if (ld_volatile(&ctrl[CTRL_ERR])) return;  // an earlier stage failed: SA is not a permutation
+    WarpEmitter em;
+    em.init(ebuf[threadIdx.x >> 5]);
     for (uint32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
@@ -160,10 +166,11 @@ __global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict
                              : end_equal<uint64_t>(K, last, hi, sk[td.len - 1]);
         }
         __syncthreads();
-        name_tile<uint64_t>(sk, td.len, td.start, s_carry[0], s_carry[1], SA, bi, td.blk, rank, bins, bi.n > 8u,
+        name_tile<uint64_t>(sk, td.len, td.start, s_carry[0], s_carry[1], SA, bi, td.blk, rank, bins, bi.n > 8u, em,
                             &ctrl[CTRL_ERR]);
         __syncthreads();
     }
+    em.finish(bins, &ctrl[CTRL_ERR]);
 }
 
 // ---- round: key gathers ------------------------------------------------------
@@ -307,11 +314,14 @@ __global__ void __launch_bounds__(256) k_sort_micro(uint32_t* __restrict__ SA, c
                                                     uint32_t* __restrict__ rank, const BlockInfo* __restrict__ blocks,
                                                     Bins cur, Bins next, const uint32_t* __restrict__ depth,
                                                     uint32_t* ctrl) {
+    __shared__ GroupDesc ebuf[8][NCLS * EMIT_BUF];
     if (ld_volatile(&ctrl[CTRL_ERR])) return;
     const uint32_t new_depth = 2u * *depth;
     const uint32_t count = bin_count(cur, 0);
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
+    WarpEmitter em;
+    em.init(ebuf[threadIdx.x >> 5]);
     for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < count; base += stride) {
         const uint32_t g = base + lane;
         const bool valid = g < count;
@@ -366,9 +376,10 @@ __global__ void __launch_bounds__(256) k_sort_micro(uint32_t* __restrict__ SA, c
                 }
             }
         }
-        emit_group(next, want0, s0, l0, gd.blk, &ctrl[CTRL_ERR]);
-        emit_group(next, want1, s1, l1, gd.blk, &ctrl[CTRL_ERR]);
+        em.emit(next, want0, s0, l0, gd.blk, &ctrl[CTRL_ERR]);
+        em.emit(next, want1, s1, l1, gd.blk, &ctrl[CTRL_ERR]);
     }
+    em.finish(next, &ctrl[CTRL_ERR]);
 }
 
 // tiny groups (5..32): one warp each, bitonic across the lanes
@@ -376,11 +387,14 @@ __global__ void __launch_bounds__(256) k_sort_tiny(uint32_t* __restrict__ SA, co
                                                    uint32_t* __restrict__ rank, const BlockInfo* __restrict__ blocks,
                                                    Bins cur, Bins next, const uint32_t* __restrict__ depth,
                                                    uint32_t* ctrl) {
+    __shared__ GroupDesc ebuf[8][NCLS * EMIT_BUF];
     if (ld_volatile(&ctrl[CTRL_ERR])) return;
     const uint32_t new_depth = 2u * *depth;
     const uint32_t count = bin_count(cur, 1);
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    WarpEmitter em;
+    em.init(ebuf[threadIdx.x >> 5]);
     for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < count; g += nwarps) {
         const GroupDesc gd = cur.list[1][g];
         const BlockInfo bi = blocks[gd.blk];
@@ -411,8 +425,9 @@ __global__ void __launch_bounds__(256) k_sort_tiny(uint32_t* __restrict__ SA, co
         }
         const uint32_t len = end - lane;
         const bool want = head && len > 1 && new_depth < bi.n;
-        emit_group(next, want, k, len, gd.blk, &ctrl[CTRL_ERR]);
+        em.emit(next, want, k, len, gd.blk, &ctrl[CTRL_ERR]);
     }
+    em.finish(next, &ctrl[CTRL_ERR]);
 }
 
 template <int NT>
@@ -448,7 +463,7 @@ template <int NT>
 __device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDesc& gd, const BlockInfo& bi,
                                                   uint32_t* __restrict__ SA, const uint32_t* __restrict__ key2,
                                                   uint32_t* __restrict__ rank, const Bins& next, uint32_t new_depth,
-                                                  uint32_t* err, uint32_t t) {
+                                                  WarpEmitter& em, uint32_t* err, uint32_t t) {
     const uint32_t m = gd.len;
     uint32_t P = 32;
     while (P < m) P <<= 1;
@@ -473,7 +488,7 @@ __device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDes
                 want = len > 1 && new_depth < bi.n;
             }
         }
-        emit_group(next, want, gd.start + i, len, gd.blk, err);
+        em.emit(next, want, gd.start + i, len, gd.blk, err);
     }
     coop_sync<NT>();
 }
@@ -484,16 +499,20 @@ __global__ void __launch_bounds__(256) k_sort_small(uint32_t* __restrict__ SA, c
                                                     Bins cur, Bins next, const uint32_t* __restrict__ depth,
                                                     uint32_t* ctrl) {
     __shared__ uint64_t comp[8][SMALL_MAX];
+    __shared__ GroupDesc ebuf[8][NCLS * EMIT_BUF];
     if (ld_volatile(&ctrl[CTRL_ERR])) return;
     const uint32_t new_depth = 2u * *depth;
     const uint32_t count = bin_count(cur, 2);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    WarpEmitter em;
+    em.init(ebuf[warp]);
     for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < count; g += nwarps) {
         const GroupDesc gd = cur.list[2][g];
         const BlockInfo bi = blocks[gd.blk];
-        sort_rename_group<32>(comp[warp], gd, bi, SA, key2, rank, next, new_depth, &ctrl[CTRL_ERR], lane);
+        sort_rename_group<32>(comp[warp], gd, bi, SA, key2, rank, next, new_depth, em, &ctrl[CTRL_ERR], lane);
     }
+    em.finish(next, &ctrl[CTRL_ERR]);
 }
 
 // medium groups (257..2048): one CTA each, bitonic in shared memory
@@ -502,14 +521,18 @@ __global__ void __launch_bounds__(256) k_sort_med(uint32_t* __restrict__ SA, con
                                                   Bins cur, Bins next, const uint32_t* __restrict__ depth,
                                                   uint32_t* ctrl) {
     __shared__ uint64_t comp[MED_MAX];
+    __shared__ GroupDesc ebuf[8][NCLS * EMIT_BUF];
     if (ld_volatile(&ctrl[CTRL_ERR])) return;
     const uint32_t new_depth = 2u * *depth;
     const uint32_t count = bin_count(cur, 3);
+    WarpEmitter em;
+    em.init(ebuf[threadIdx.x >> 5]);
     for (uint32_t g = blockIdx.x; g < count; g += gridDim.x) {
         const GroupDesc gd = cur.list[3][g];
         const BlockInfo bi = blocks[gd.blk];
-        sort_rename_group<256>(comp, gd, bi, SA, key2, rank, next, new_depth, &ctrl[CTRL_ERR], threadIdx.x);
+        sort_rename_group<256>(comp, gd, bi, SA, key2, rank, next, new_depth, em, &ctrl[CTRL_ERR], threadIdx.x);
     }
+    em.finish(next, &ctrl[CTRL_ERR]);
 }
 
 // large groups after their radix sort: rename by tile (binary search in the
@@ -523,9 +546,12 @@ __global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict
                                                       const uint32_t* __restrict__ depth, uint32_t* ctrl) {
     __shared__ uint32_t sk[4096];
     __shared__ uint32_t s_carry[2];
+    __shared__ GroupDesc ebuf[8][NCLS * EMIT_BUF];
     if (ld_volatile(&ctrl[CTRL_ERR])) return;
     const uint32_t new_depth = 2u * *depth;
     const uint32_t nt = *num_tiles;
+    WarpEmitter em;
+    em.init(ebuf[threadIdx.x >> 5]);
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
@@ -543,9 +569,10 @@ __global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict
         }
         __syncthreads();
         name_tile<uint32_t>(sk, td.len, td.start, s_carry[0], s_carry[1], SA, bi, td.blk, rank, next,
-                            new_depth < bi.n, &ctrl[CTRL_ERR]);
+                            new_depth < bi.n, em, &ctrl[CTRL_ERR]);
         __syncthreads();
     }
+    em.finish(next, &ctrl[CTRL_ERR]);
 }
 
 __global__ void __launch_bounds__(256) k_gather_L(const uint8_t* __restrict__ S, const uint32_t* __restrict__ SA,

@@ -161,13 +161,13 @@ extern "C" bwt_status bwt_model_samples(bwt_plan* p, const uint8_t* d_in, const 
 //            per block (a 12-step binary search over the splitters in shared
 //            memory);
 //   route:   a block whose over-capacity buckets hold more than a quarter of
-//            its rotations is sorted by the plain radix instead;
+//            its rotations is recounted with equal-width buckets (the top 12
+//            key bits), and sorted by the plain radix if those overflow too;
 //   scatter: rotations go to their bucket's range (per-tile reservation of
 //            each bucket's slots with one atomic per tile and bucket);
-//   sort:    consecutive whole buckets are grouped into chunks of at most
-//            `cap` rotations and each chunk is sorted by (K, i) in shared
-//            memory -- buckets are ordered by K, so a sorted chunk sorts every
-//            bucket in it;
+//   sort:    every bucket is sorted by (K, i): up to 32 rotations across a
+//            warp's lanes, up to 256 in a warp's shared memory, up to 2048 in a
+//            CTA's shared memory;
 //   overflow buckets (> cap) are sorted by the segmented radix: first by the
 //            rotation index (digits taken from the value), then by K, which
 //            leaves equal prefixes in index order as the doubling rounds
@@ -178,10 +178,14 @@ namespace {
 
 constexpr int NBK = BWT_BUCKETS;
 constexpr int NSP = BWT_SPLITTERS;
-constexpr uint32_t BUCKET_CAP = 2048;
+constexpr uint32_t BUCKET_CAP = MED_MAX;  // largest bucket sorted in shared memory
 
-__device__ __forceinline__ uint32_t bucket_of(const uint64_t* spl, uint64_t key) {
-    uint32_t lo = 0, hi = NSP;
+// Bucket of a key: #{j : spl[j] <= key}. first[c] = #{j : spl[j] < c << 56}
+// narrows the search to the splitters that share the key's top byte (the
+// ones below all count, the ones above none).
+__device__ __forceinline__ uint32_t bucket_of(const uint64_t* spl, const uint16_t* first, uint64_t key) {
+    const uint32_t c = (uint32_t)(key >> 56);
+    uint32_t lo = first[c], hi = first[c + 1];
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
         if (spl[mid] <= key) lo = mid + 1; else hi = mid;
@@ -189,11 +193,21 @@ __device__ __forceinline__ uint32_t bucket_of(const uint64_t* spl, uint64_t key)
     return lo;
 }
 
-__device__ __forceinline__ uint64_t pack8b(const uint8_t* b) {
-    uint64_t k = 0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) k = (k << 8) | b[j];
-    return k;
+// Loads the splitters into shared memory and builds the top-byte index.
+__device__ __forceinline__ void load_splitters(const uint64_t* __restrict__ splitters, uint64_t* spl, uint16_t* first) {
+    for (int i = threadIdx.x; i < NSP; i += blockDim.x) spl[i] = splitters[i];
+    __syncthreads();
+    for (int c = threadIdx.x; c < 256; c += blockDim.x) {
+        const uint64_t x = (uint64_t)c << 56;
+        uint32_t lo = 0, hi = NSP;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (spl[mid] < x) lo = mid + 1; else hi = mid;
+        }
+        first[c] = (uint16_t)lo;
+    }
+    if (threadIdx.x == 0) first[256] = (uint16_t)NSP;
+    __syncthreads();
 }
 
 // bytes of rotation positions [i0, i0 + len + 7) of block bi, wrapping
@@ -206,7 +220,7 @@ __device__ __forceinline__ void load_tile_bytes(const uint8_t* S, BlockInfo bi, 
     }
 }
 
-constexpr size_t SPL_BYTES = 4096 * 8;
+constexpr size_t SPL_BYTES = 4096 * 8 + 528;  // splitters + top-byte index (257 u16, padded)
 constexpr size_t CNT_BYTES = 4096 * 4;
 constexpr size_t TILE_BYTES = 4096 + 16;
 constexpr size_t COUNT_SMEM = SPL_BYTES + CNT_BYTES + TILE_BYTES;
@@ -218,10 +232,11 @@ __global__ void __launch_bounds__(256) k_bucket_count(const uint8_t* __restrict_
                                                       uint32_t* __restrict__ counts) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* spl = reinterpret_cast<uint64_t*>(smem);
+    uint16_t* first = reinterpret_cast<uint16_t*>(smem + 4096 * 8);
     uint32_t* h = reinterpret_cast<uint32_t*>(smem + SPL_BYTES);
     uint8_t* sb = smem + SPL_BYTES + CNT_BYTES;
     const int lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < NSP; i += blockDim.x) spl[i] = splitters[i];
+    load_splitters(splitters, spl, first);
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         for (int i = threadIdx.x; i < NBK; i += blockDim.x) h[i] = 0;
         const TileDesc td = tiles[t];
@@ -231,7 +246,7 @@ __global__ void __launch_bounds__(256) k_bucket_count(const uint8_t* __restrict_
         for (uint32_t q0 = 0; q0 < td.len; q0 += blockDim.x) {
             const uint32_t q = q0 + threadIdx.x;
             const bool valid = q < td.len;
-            const uint32_t b = valid ? bucket_of(spl, pack8b(sb + q)) : (uint32_t)NBK;
+            const uint32_t b = valid ? bucket_of(spl, first, pack8_smem(sb, q)) : (uint32_t)NBK;
             const uint32_t peers = __match_any_sync(0xffffffffu, b);
             if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[b], (uint32_t)__popc(peers));
         }
@@ -292,13 +307,13 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(const uint8_t* __restric
                                                         uint32_t* __restrict__ I) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* spl = reinterpret_cast<uint64_t*>(smem);
+    uint16_t* first = reinterpret_cast<uint16_t*>(smem + 4096 * 8);
     uint32_t* lcount = reinterpret_cast<uint32_t*>(smem + SPL_BYTES);
     uint32_t* gbase = reinterpret_cast<uint32_t*>(smem + SPL_BYTES + CNT_BYTES);
     uint8_t* sb = smem + SPL_BYTES + 2 * CNT_BYTES;
     const int lane = threadIdx.x & 31;
-    uint32_t lt;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-    for (int i = threadIdx.x; i < NSP; i += blockDim.x) spl[i] = splitters[i];
+    const uint32_t lt = lanemask_lt();
+    load_splitters(splitters, spl, first);
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         for (int i = threadIdx.x; i < NBK; i += blockDim.x) lcount[i] = 0;
         const TileDesc td = tiles[t];
@@ -312,8 +327,8 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(const uint8_t* __restric
         for (int j = 0; j < ITEMS; ++j) {
             const uint32_t q = j * 256 + threadIdx.x;
             const bool valid = q < td.len;
-            key[j] = valid ? pack8b(sb + q) : 0ull;
-            const uint32_t b = valid ? bucket_of(spl, key[j]) : (uint32_t)NBK;
+            key[j] = valid ? pack8_smem(sb, q) : 0ull;
+            const uint32_t b = valid ? bucket_of(spl, first, key[j]) : (uint32_t)NBK;
             const uint32_t peers = __match_any_sync(0xffffffffu, b);
             const int leader = __ffs(peers) - 1;
             uint32_t base = 0;
@@ -341,93 +356,147 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(const uint8_t* __restric
     }
 }
 
-// Greedy grouping of each bucket-routed block's consecutive buckets into
-// chunks of at most cap rotations; over-capacity buckets become overflow
-// segments. One CTA per block; thread 0 walks the 4096 bucket sizes.
-__global__ void __launch_bounds__(256) k_bucket_chunks(const uint32_t* __restrict__ starts,
+// Every bucket of a bucket-routed block with two or more rotations becomes a
+// group in the size-class bins: classes 0-3 are sorted in place by (K, i),
+// class 4 (more than BUCKET_CAP rotations) goes to the overflow radix. One
+// CTA per block.
+__global__ void __launch_bounds__(256) k_bucket_groups(const uint32_t* __restrict__ starts,
                                                        const BlockInfo* __restrict__ blocks,
-                                                       const uint32_t* __restrict__ route, uint32_t nb, uint32_t cap,
-                                                       Bins out, uint32_t* ctrl) {
-    __shared__ uint32_t st[NBK + 1];
+                                                       const uint32_t* __restrict__ route, uint32_t nb, Bins out,
+                                                       uint32_t* ctrl) {
+    __shared__ GroupDesc ebuf[8][NCLS * EMIT_BUF];
+    WarpEmitter em;
+    em.init(ebuf[threadIdx.x >> 5]);
     for (uint32_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
-        if (route[blk] != 0) continue;  // uniform across the CTA
+        if (route[blk] == 1u) continue;  // plain-routed (uniform across the CTA)
         const BlockInfo bi = blocks[blk];
-        for (int i = threadIdx.x; i < NBK; i += blockDim.x) st[i] = starts[(size_t)blk * NBK + i];
-        if (threadIdx.x == 0) st[NBK] = bi.n;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t cstart = 0, clen = 0;
-            auto push = [&](int cls, uint32_t s0, uint32_t len) {
-                const uint32_t slot = atomicAdd(&out.count[cls], 1u);
-                if (slot < out.cap[cls]) out.list[cls][slot] = GroupDesc{bi.off + s0, len, blk, 0u};
-                else atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
-            };
-            for (int b = 0; b < NBK; ++b) {
-                const uint32_t sz = st[b + 1] - st[b];
-                if (sz > cap) {
-                    if (clen > 1) push(0, cstart, clen);
-                    push(CLS_LARGE, st[b], sz);
-                    cstart = st[b + 1];
-                    clen = 0;
-                } else if (clen + sz > cap) {
-                    if (clen > 1) push(0, cstart, clen);
-                    cstart = st[b];
-                    clen = sz;
-                } else {
-                    clen += sz;
+        const uint32_t* st = starts + (size_t)blk * NBK;
+        for (int b0 = 0; b0 < NBK; b0 += blockDim.x) {
+            const int b = b0 + threadIdx.x;
+            const uint32_t s0 = st[b];
+            const uint32_t s1 = b + 1 < NBK ? st[b + 1] : bi.n;
+            const uint32_t sz = s1 - s0;
+            em.emit(out, sz > 1, bi.off + s0, sz, blk, &ctrl[CTRL_ERR]);
+        }
+    }
+    em.finish(out, &ctrl[CTRL_ERR]);
+}
+
+__device__ __forceinline__ bool pair_gt(uint64_t ak, uint32_t ai, uint64_t bk, uint32_t bi) {
+    return ak > bk || (ak == bk && ai > bi);
+}
+
+// buckets of 2..32 rotations: one warp each, bitonic across the lanes on (K, i)
+__global__ void __launch_bounds__(256) k_bsort_lanes(uint64_t* __restrict__ K, uint32_t* __restrict__ I, Bins g) {
+    const uint32_t c0 = bin_count(g, 0), c1 = bin_count(g, 1);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < c0 + c1; w += nwarps) {
+        const GroupDesc gd = w < c0 ? g.list[0][w] : g.list[1][w - c0];
+        const bool valid = lane < gd.len;
+        uint64_t k = valid ? K[gd.start + lane] : ~0ull;
+        uint32_t v = valid ? I[gd.start + lane] : ~0u;
+#pragma unroll
+        for (uint32_t kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+            for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+                const uint64_t ok = __shfl_xor_sync(0xffffffffu, k, j);
+                const uint32_t ov = __shfl_xor_sync(0xffffffffu, v, j);
+                const bool up = (lane & kk) == 0;
+                const bool lower = (lane & j) == 0;
+                const bool take_other = (lower == up) ? pair_gt(k, v, ok, ov) : pair_gt(ok, ov, k, v);
+                if (take_other) {
+                    k = ok;
+                    v = ov;
                 }
             }
-            if (clen > 1) push(0, cstart, clen);
+        }
+        if (valid) {
+            K[gd.start + lane] = k;
+            I[gd.start + lane] = v;
+        }
+    }
+}
+
+// Sorts (sk, si)[0..P) by (K, i), bitonic; NT threads cooperate.
+template <int NT>
+__device__ __forceinline__ void pair_bitonic(uint64_t* sk, uint32_t* si, uint32_t P, uint32_t t) {
+    for (uint32_t kk = 2; kk <= P; kk <<= 1) {
+        for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = t; i < P; i += NT) {
+                const uint32_t ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a = sk[i], b = sk[ixj];
+                    const uint32_t ai = si[i], bi = si[ixj];
+                    const bool up = (i & kk) == 0;
+                    if (pair_gt(a, ai, b, bi) == up) {
+                        sk[i] = b;
+                        sk[ixj] = a;
+                        si[i] = bi;
+                        si[ixj] = ai;
+                    }
+                }
+            }
+            if constexpr (NT == 32) __syncwarp(); else __syncthreads();
+        }
+    }
+}
+
+// buckets of 33..256 rotations: one warp each, bitonic in shared memory
+__global__ void __launch_bounds__(256) k_bsort_warp(uint64_t* __restrict__ K, uint32_t* __restrict__ I, Bins g) {
+    __shared__ uint64_t sk[8][256];
+    __shared__ uint32_t si[8][256];
+    const uint32_t count = bin_count(g, 2);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += nwarps) {
+        const GroupDesc gd = g.list[2][w];
+        uint32_t P = 64;
+        while (P < gd.len) P <<= 1;
+        for (uint32_t i = lane; i < P; i += 32) {
+            const bool valid = i < gd.len;
+            sk[warp][i] = valid ? K[gd.start + i] : ~0ull;
+            si[warp][i] = valid ? I[gd.start + i] : ~0u;
+        }
+        __syncwarp();
+        pair_bitonic<32>(sk[warp], si[warp], P, lane);
+        for (uint32_t i = lane; i < gd.len; i += 32) {
+            K[gd.start + i] = sk[warp][i];
+            I[gd.start + i] = si[warp][i];
+        }
+        __syncwarp();
+    }
+}
+
+// buckets of 257..BUCKET_CAP rotations: one CTA each, bitonic in shared memory
+__global__ void __launch_bounds__(256) k_bsort_cta(uint64_t* __restrict__ K, uint32_t* __restrict__ I, Bins g) {
+    __shared__ uint64_t sk[BUCKET_CAP];
+    __shared__ uint32_t si[BUCKET_CAP];
+    const uint32_t count = bin_count(g, 3);
+    for (uint32_t c = blockIdx.x; c < count; c += gridDim.x) {
+        const GroupDesc gd = g.list[3][c];
+        uint32_t P = 512;
+        while (P < gd.len) P <<= 1;
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+            const bool valid = i < gd.len;
+            sk[i] = valid ? K[gd.start + i] : ~0ull;
+            si[i] = valid ? I[gd.start + i] : ~0u;
+        }
+        __syncthreads();
+        pair_bitonic<256>(sk, si, P, threadIdx.x);
+        for (uint32_t i = threadIdx.x; i < gd.len; i += blockDim.x) {
+            K[gd.start + i] = sk[i];
+            I[gd.start + i] = si[i];
         }
         __syncthreads();
     }
 }
 
-// Sorts every chunk by (K, i) in shared memory (bitonic; len <= BUCKET_CAP).
-__global__ void __launch_bounds__(256) k_chunk_sort(uint64_t* __restrict__ K, uint32_t* __restrict__ I, Bins chunks) {
-    __shared__ uint64_t sk[BUCKET_CAP];
-    __shared__ uint32_t si[BUCKET_CAP];
-    const uint32_t n = bin_count(chunks, 0);
-    for (uint32_t c = blockIdx.x; c < n; c += gridDim.x) {
-        const GroupDesc g = chunks.list[0][c];
-        uint32_t P = 2;
-        while (P < g.len) P <<= 1;
-        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-            if (i < g.len) {
-                sk[i] = K[g.start + i];
-                si[i] = I[g.start + i];
-            } else {
-                sk[i] = ~0ull;
-                si[i] = ~0u;
-            }
-        }
-        __syncthreads();
-        for (uint32_t kk = 2; kk <= P; kk <<= 1) {
-            for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-                    const uint32_t ixj = i ^ j;
-                    if (ixj > i) {
-                        const uint64_t a = sk[i], b = sk[ixj];
-                        const uint32_t ai = si[i], bi = si[ixj];
-                        const bool gt = a > b || (a == b && ai > bi);
-                        const bool up = (i & kk) == 0;
-                        if (gt == up) {
-                            sk[i] = b;
-                            sk[ixj] = a;
-                            si[i] = bi;
-                            si[ixj] = ai;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        for (uint32_t i = threadIdx.x; i < g.len; i += blockDim.x) {
-            K[g.start + i] = sk[i];
-            I[g.start + i] = si[i];
-        }
-        __syncthreads();
-    }
+__global__ void k_zero_rows_routed(uint32_t* __restrict__ counts, const uint32_t* __restrict__ route, uint32_t nb,
+                                   uint32_t code) {
+    for (uint32_t blk = blockIdx.x; blk < nb; blk += gridDim.x)
+        if (route[blk] == code)
+            for (int i = threadIdx.x; i < NBK; i += blockDim.x) counts[(size_t)blk * NBK + i] = 0;
 }
 
 // Per overflow segment: digit histograms of PI index passes then PK key passes.
@@ -494,6 +563,12 @@ bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
     if (!p->route) CKL(cudaMalloc(&p->route, sizeof(uint32_t) * p->cap_b));
     if (!p->bstats) CKL(cudaMalloc(&p->bstats, sizeof(unsigned long long) * 5 * p->cap_b));
     if (!p->tiles_aux) CKL(cudaMalloc(&p->tiles_aux, sizeof(TileDesc) * p->cap_tiles0));
+    if (!p->splitters_flat) {
+        std::vector<uint64_t> flat(NSP);
+        for (int j = 0; j < NSP; ++j) flat[j] = (uint64_t)(j + 1) << 52;  // bucket = top 12 key bits
+        CKL(cudaMalloc(&p->splitters_flat, sizeof(uint64_t) * NSP));
+        CKL(cudaMemcpy(p->splitters_flat, flat.data(), sizeof(uint64_t) * NSP, cudaMemcpyHostToDevice));
+    }
     if (!p->h_route) CKL(cudaMallocHost(&p->h_route, sizeof(uint32_t) * p->cap_b));
     if (!p->h_bstats) CKL(cudaMallocHost(&p->h_bstats, sizeof(unsigned long long) * 5 * p->cap_b));
     if (!p->h_tiles_aux) CKL(cudaMallocHost(&p->h_tiles_aux, sizeof(TileDesc) * p->cap_tiles0));
@@ -530,35 +605,26 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
     CKL(cudaStreamSynchronize(st));
     p->stats.kernel_launches += 3;
 
-    // 3. route: plain radix for blocks whose overflow exceeds a quarter of the block
-    uint32_t ntp = 0, ntb = 0;
-    std::vector<uint32_t> plain_blocks;
-    uint64_t plain_keys = 0;
+    // 3. route each block: learned buckets (0) if their overflow holds at most a
+    //    quarter of the block; else equal-width buckets (2) if those do; else
+    //    the plain radix (1)
+    std::vector<uint32_t> cand;
     for (uint32_t b = 0; b < nb; ++b) {
-        const BlockInfo bi = p->h_blocks[b];
         const unsigned long long* bs = p->h_bstats + 5 * b;
-        const bool plain = bs[0] * 4 > bi.n;
-        p->h_route[b] = plain ? 1u : 0u;
-        if (plain) {
-            plain_blocks.push_back(b);
-            plain_keys += bi.n;
-            p->stats.blocks_routed_plain++;
-        } else {
-            p->stats.buckets_overflowed += bs[1];
-            p->stats.keys_overflowed += bs[0];
-        }
+        const bool over = bs[0] * 4 > p->h_blocks[b].n;
+        p->h_route[b] = over ? 2u : 0u;
+        if (over) cand.push_back(b);
         p->stats.max_bucket = std::max<uint32_t>(p->stats.max_bucket, (uint32_t)bs[2]);
         p->stats.bucket_sq_sum += bs[3];
         p->stats.buckets_nonempty += bs[4];
     }
-    // sub-tables (first-tile indices relative to each sub-table): plain blocks first, then bucketed
     const uint32_t T = (uint32_t)p->tile;
-    for (int pass = 0; pass < 2; ++pass) {
+    auto build_tiles = [&](uint32_t code, uint32_t base, uint32_t* count) {
+        uint32_t nt_ = 0;
         for (uint32_t b = 0; b < nb; ++b) {
-            if ((p->h_route[b] == 1u) != (pass == 0)) continue;
+            if (p->h_route[b] != code) continue;
             const BlockInfo bi = p->h_blocks[b];
-            const uint32_t base = pass == 0 ? 0 : ntp;
-            const uint32_t first = (pass == 0 ? ntp : ntb) ;
+            const uint32_t first = nt_;
             for (uint32_t o = 0; o < bi.n; o += T) {
                 TileDesc td;
                 td.start = bi.off + o;
@@ -569,17 +635,53 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
                 td.blk = b;
                 td.pad0 = bi.n;
                 td.pad1 = 0;
-                p->h_tiles_aux[base + (pass == 0 ? ntp++ : ntb++)] = td;
+                p->h_tiles_aux[base + nt_++] = td;
             }
         }
+        *count = nt_;
+    };
+    if (!cand.empty()) {
+        uint32_t ntc = 0;
+        build_tiles(2u, 0, &ntc);
+        CKL(cudaMemcpyAsync(p->route, p->h_route, sizeof(uint32_t) * nb, cudaMemcpyHostToDevice, st));
+        CKL(cudaMemcpyAsync(p->tiles_aux, p->h_tiles_aux, sizeof(TileDesc) * ntc, cudaMemcpyHostToDevice, st));
+        k_zero_rows_routed<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->route, nb, 2u);
+        k_bucket_count<<<std::max(1, std::min<int>(ntc, sms * 3)), 256, COUNT_SMEM, st>>>(
+            d_in, p->blocks, p->tiles_aux, ntc, p->splitters_flat, p->bucket_count);
+        k_bucket_stats<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, BUCKET_CAP, nb, p->bstats);
+        CKL(cudaGetLastError());
+        CKL(cudaMemcpyAsync(p->h_bstats, p->bstats, sizeof(unsigned long long) * 5 * nb, cudaMemcpyDeviceToHost, st));
+        CKL(cudaStreamSynchronize(st));
+        p->stats.kernel_launches += 3;
+        for (uint32_t b : cand)
+            if (p->h_bstats[5 * b] * 4 > p->h_blocks[b].n) p->h_route[b] = 1u;
     }
+    uint64_t plain_keys = 0;
+    for (uint32_t b = 0; b < nb; ++b) {
+        const unsigned long long* bs = p->h_bstats + 5 * b;
+        if (p->h_route[b] == 1u) {
+            plain_keys += p->h_blocks[b].n;
+            p->stats.blocks_routed_plain++;
+        } else {
+            if (p->h_route[b] == 2u) p->stats.blocks_routed_flat++;
+            p->stats.buckets_overflowed += bs[1];
+            p->stats.keys_overflowed += bs[0];
+        }
+    }
+    // sub-tables (first-tile indices relative to each sub-table)
+    uint32_t ntp = 0, ntl = 0, ntf = 0;
+    build_tiles(1u, 0, &ntp);
+    build_tiles(0u, ntp, &ntl);
+    build_tiles(2u, ntp + ntl, &ntf);
+    const uint32_t ntb = ntl + ntf;
     CKL(cudaMemcpyAsync(p->route, p->h_route, sizeof(uint32_t) * nb, cudaMemcpyHostToDevice, st));
     CKL(cudaMemcpyAsync(p->tiles_aux, p->h_tiles_aux, sizeof(TileDesc) * (ntp + ntb), cudaMemcpyHostToDevice, st));
     p->h_aux[0] = ntp;
     p->h_aux[1] = ntb;
     CKL(cudaMemcpyAsync(ctrl + CTRL_AUX0, p->h_aux, sizeof(uint32_t) * 2, cudaMemcpyHostToDevice, st));
     const TileDesc* tilesP = p->tiles_aux;
-    const TileDesc* tilesB = p->tiles_aux + ntp;
+    const TileDesc* tilesL = p->tiles_aux + ntp;
+    const TileDesc* tilesF = p->tiles_aux + ntp + ntl;
 
     // 4a. plain-routed blocks: the first sort of the plain path, ending in buffer 0
     const int rb = p->rbits, RADIX = 1 << rb;
@@ -623,28 +725,35 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
         }
     }
 
-    // 4b. bucket-routed blocks: scan, scatter, chunk sort
+    // 4b. bucket-routed blocks: scan, scatter, per-bucket sorts
     Bins aux = bins_of(p, 1);
     CKL(cudaMemsetAsync(aux.count, 0, sizeof(uint32_t) * NCLS, st));
     if (ntb) {
         CKL(launch_scan_rows(p->bucket_count, NBK, nullptr, 0, nb, nb, st));  // counts -> starts in place
         CKL(cudaMemsetAsync(p->bucket_cursor, 0, sizeof(uint32_t) * NBK * nb, st));
-        const int g = std::max(1, std::min<int>(ntb, sms * 2));
-        if (T <= 1024)
-            k_bucket_scatter<4><<<g, 256, SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, p->splitters,
-                                                              p->bucket_count, p->bucket_cursor, p->keys[0], p->vals[0]);
-        else if (T <= 2048)
-            k_bucket_scatter<8><<<g, 256, SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, p->splitters,
-                                                              p->bucket_count, p->bucket_cursor, p->keys[0], p->vals[0]);
-        else
-            k_bucket_scatter<16><<<g, 256, SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, p->splitters,
-                                                               p->bucket_count, p->bucket_cursor, p->keys[0],
-                                                               p->vals[0]);
-        k_bucket_chunks<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->blocks, p->route, nb,
-                                                                       BUCKET_CAP, aux, ctrl);
-        k_chunk_sort<<<sms * 6, 256, 0, st>>>(p->keys[0], p->vals[0], aux);
+        auto scatter = [&](const TileDesc* tl, uint32_t n_t, const uint64_t* spl) {
+            if (!n_t) return;
+            const int g = std::max(1, std::min<int>(n_t, sms * 2));
+            if (T <= 1024)
+                k_bucket_scatter<4><<<g, 256, SCATTER_SMEM, st>>>(d_in, p->blocks, tl, n_t, spl, p->bucket_count,
+                                                                  p->bucket_cursor, p->keys[0], p->vals[0]);
+            else if (T <= 2048)
+                k_bucket_scatter<8><<<g, 256, SCATTER_SMEM, st>>>(d_in, p->blocks, tl, n_t, spl, p->bucket_count,
+                                                                  p->bucket_cursor, p->keys[0], p->vals[0]);
+            else
+                k_bucket_scatter<16><<<g, 256, SCATTER_SMEM, st>>>(d_in, p->blocks, tl, n_t, spl, p->bucket_count,
+                                                                   p->bucket_cursor, p->keys[0], p->vals[0]);
+            p->stats.kernel_launches++;
+        };
+        scatter(tilesL, ntl, p->splitters);
+        scatter(tilesF, ntf, p->splitters_flat);
+        k_bucket_groups<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->blocks, p->route, nb, aux,
+                                                                       ctrl);
+        k_bsort_lanes<<<sms * 8, 256, 0, st>>>(p->keys[0], p->vals[0], aux);
+        k_bsort_warp<<<sms * 8, 256, 0, st>>>(p->keys[0], p->vals[0], aux);
+        k_bsort_cta<<<sms * 8, 256, 0, st>>>(p->keys[0], p->vals[0], aux);
         CKL(cudaGetLastError());
-        p->stats.kernel_launches += 4;
+        p->stats.kernel_launches += 5;
 
         // 4c. overflow buckets: radix on the index, then on the key
         const int PI = std::max(1, (bits_needed(p->max_n - 1) + 7) / 8), PK = 8, PT = PI + PK;

@@ -115,7 +115,7 @@ void bwt::free_plan_memory(bwt_plan* p) {
     F(p->tiles0); F(p->ltiles); F(p->blocks); F(p->hist); F(p->status); F(p->ctrl);
     for (int s = 0; s < 2; ++s)
         for (int c = 0; c < NCLS; ++c) F(p->bins[s][c]);
-    F(p->splitters); F(p->bucket_count); F(p->bucket_cursor); F(p->route); F(p->bstats); F(p->tiles_aux);
+    F(p->splitters); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->route); F(p->bstats); F(p->tiles_aux);
     FH(p->h_ctrl); FH(p->h_tiles); FH(p->h_blocks); FH(p->h_off);
     FH(p->h_route); FH(p->h_bstats); FH(p->h_tiles_aux);
     for (auto& e : p->events) cudaEventDestroy(e);
@@ -231,6 +231,13 @@ extern "C" bwt_status bwt_plan_set_radix(bwt_plan* plan, int radix_bits, int til
     return BWT_OK;
 }
 
+extern "C" bwt_status bwt_plan_set_round_radix(bwt_plan* plan, int radix_bits) {
+    if (!plan || (radix_bits != 0 && !valid_radix(radix_bits))) return BWT_EINVAL;
+    plan->round_bits = radix_bits;
+    drop_graph(plan);
+    return BWT_OK;
+}
+
 extern "C" bwt_status bwt_plan_debug_waits(bwt_plan* plan, uint32_t spin_limit, int withhold_publish) {
     if (!plan) return BWT_EINVAL;
     plan->spin_limit = spin_limit ? spin_limit : kDefaultSpin;
@@ -321,10 +328,11 @@ Bins bwt::bins_of(bwt_plan* p, int par) {
 
 // Records an event pair around a radix launch when timing is on.
 static cudaError_t timed_onesweep(bwt_plan* p, int key_bytes, bool from_s, const OneSweepParams& a,
-                                  double bytes_per_key, uint64_t keys_host, int ctrl_keys_word, cudaStream_t st) {
+                                  double bytes_per_key, uint64_t keys_host, int ctrl_keys_word, cudaStream_t st,
+                                  int radix_bits = 0) {
     const bool timing = !p->events.empty() && !p->capturing && p->ev_used + 2 <= p->events.size();
     if (timing) cudaEventRecord(p->events[p->ev_used], st);
-    cudaError_t e = launch_onesweep(key_bytes, from_s, p->rbits, p->tile, a, 0, st);
+    cudaError_t e = launch_onesweep(key_bytes, from_s, radix_bits ? radix_bits : p->rbits, p->tile, a, 0, st);
     if (timing) {
         cudaEventRecord(p->events[p->ev_used + 1], st);
         EvMeta m;
@@ -405,8 +413,10 @@ bwt_status bwt::enqueue_naming(bwt_plan* p, const uint64_t* K, cudaStream_t st) 
 // length h sits in ctrl[CTRL_DEPTH]. host_counts: the three group counts when
 // the host knows them (else null: persistent grids read them on the device).
 bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts, cudaStream_t st) {
-    const int rb = p->rbits, RADIX = 1 << rb;
     const int kbits = bits_for(p->max_n - 1);
+    // digit width of the large-group radix: the plan's choice, else 8 (an
+    // 11-bit pass costs more than twice an 8-bit one on these groups)
+    const int rb = p->round_bits ? p->round_bits : 8, RADIX = 1 << rb;
     const int P2 = std::max(1, (kbits + rb - 1) / rb);
     uint32_t* ctrl = p->ctrl;
     const uint32_t* depth = ctrl + CTRL_DEPTH;
@@ -447,7 +457,7 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
             a.tile_counter = ctrl + CTRL_TILE_CTR + 16 + ps;
             a.ctrl = ctrl;
             a.shift = ps * rb;
-            CK(timed_onesweep(p, 4, false, a, 16.0, 0, CTRL_LARGE_KEYS, st));
+            CK(timed_onesweep(p, 4, false, a, 16.0, 0, CTRL_LARGE_KEYS, st, rb));
         }
         p->pending_large_passes = (uint32_t)P2;
     }
@@ -579,6 +589,7 @@ extern "C" bwt_status bwt_forward_batch(bwt_plan* p, const uint8_t* d_in, const 
         return s;
     }
     p->stats.radix_bits = (uint32_t)p->rbits;
+    p->stats.round_radix_bits = (uint32_t)(p->round_bits ? p->round_bits : 8);
     p->stats.tile_keys = (uint32_t)p->tile;
     if (p->desc.flags & BWT_F_PER_BLOCK_LAUNCH) {
         s = run_per_block(p, d_in, d_L, d_primary, st);

@@ -28,6 +28,7 @@ struct bwt_plan {
     bwt_plan_desc desc{};
     std::string model_path;
     int rbits = 8, tile = 4096;
+    int round_bits = 0;  // digit width of the doubling rounds' radix (0 = by rank width)
     uint32_t spin_limit = 0;
     int withhold = 0;
 
@@ -52,6 +53,7 @@ struct bwt_plan {
 
     // learned bucketing (allocated when a model is installed)
     uint64_t* splitters = nullptr;      // [BWT_SPLITTERS] sorted
+    uint64_t* splitters_flat = nullptr; // [BWT_SPLITTERS] equal-width fallback (top 12 key bits)
     uint32_t* bucket_count = nullptr;   // [block][BWT_BUCKETS] counts, then starts
     uint32_t* bucket_cursor = nullptr;  // [block][BWT_BUCKETS] slots taken so far
     uint32_t* route = nullptr;          // [block] 0 = buckets, 1 = plain radix

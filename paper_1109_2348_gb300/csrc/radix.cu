@@ -23,38 +23,40 @@ namespace bwt {
 
 namespace {
 
-constexpr int OS_THREADS = 256;
-constexpr int OS_WARPS = OS_THREADS / 32;
+// Threads per radix CTA: 256 for every tile size (measured: a 4096-key tile
+// with 512 threads at <= 64 registers ran slower than 256 threads at 128).
+template <int TILE>
+struct OsThreads {
+    static constexpr int value = 256;
+};
 
 template <typename KeyT, int RBITS, int TILE, bool FROM_S>
 struct OneSweepLayout {
     static constexpr int RADIX = 1 << RBITS;
-    static constexpr size_t WHIST = (size_t)OS_WARPS * RADIX * 2;
+    static constexpr int WARPS = OsThreads<TILE>::value / 32;
+    static constexpr size_t WHIST = (size_t)WARPS * RADIX * 2;
     static constexpr size_t STAGE = (size_t)TILE * (sizeof(KeyT) + 4);
-    static constexpr size_t BYTES = FROM_S ? (size_t)TILE + 16 : 0;
+    static constexpr size_t BYTES = FROM_S ? (size_t)TILE + 16 : 0;  // tile + 7 halo bytes + word over-read
     static constexpr size_t U0 = WHIST > STAGE ? WHIST : STAGE;
     static constexpr size_t U = ((U0 > BYTES ? U0 : BYTES) + 15) & ~(size_t)15;
     static constexpr size_t TOTAL = U + 2 * RADIX * 4 + 32 * 4 + 16;
 };
 
-__device__ __forceinline__ uint64_t pack8(const uint8_t* b) {
-    uint64_t k = 0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) k = (k << 8) | b[j];
-    return k;
-}
-
 // VDIG: the digit comes from the value (the rotation index) instead of the
 // key; used to put overflow buckets of the learned bucketing in index order
 // before their key passes.
 template <typename KeyT, int RBITS, int TILE, bool FROM_S, bool VDIG = false>
-__global__ void __launch_bounds__(OS_THREADS) k_onesweep(OneSweepParams p) {
+__global__ void __launch_bounds__(OsThreads<TILE>::value) k_onesweep(OneSweepParams p) {
     using Lay = OneSweepLayout<KeyT, RBITS, TILE, FROM_S>;
+    constexpr int OS_THREADS = OsThreads<TILE>::value;
+    constexpr int OS_WARPS = OS_THREADS / 32;
     constexpr int RADIX = 1 << RBITS;
     constexpr int ITEMS = TILE / OS_THREADS;
     constexpr int WKEYS = 32 * ITEMS;
-    constexpr int DPT = RADIX / OS_THREADS;  // digits owned per thread (RADIX >= 256)
-    static_assert(RADIX >= OS_THREADS, "one digit per thread at least");
+    // digits owned per thread; with fewer digits than threads, threads
+    // tid < RADIX own one digit each and the others own none
+    constexpr int DPT = RADIX >= OS_THREADS ? RADIX / OS_THREADS : 1;
+    constexpr int OWNERS = RADIX / DPT;
 
     extern __shared__ __align__(16) unsigned char smem[];
     uint16_t* whist = reinterpret_cast<uint16_t*>(smem);
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(OS_THREADS) k_onesweep(OneSweepParams p) {
                 key[j] = 0;
                 val[j] = 0;
                 if (idx < td.len) {
-                    key[j] = (KeyT)pack8(sbytes + idx);
+                    key[j] = (KeyT)pack8_smem(sbytes, idx);
                     val[j] = i0 + idx;
                 }
             }
@@ -150,33 +152,39 @@ __global__ void __launch_bounds__(OS_THREADS) k_onesweep(OneSweepParams p) {
         __syncthreads();
 
         // ---- tile counts per digit, exclusive prefix over warps (in place)
+        const bool owner = tid < OWNERS;
         uint32_t cnt[DPT];
         uint32_t tsum = 0;
 #pragma unroll
         for (int i = 0; i < DPT; ++i) {
-            const int d = tid * DPT + i;
-            uint32_t s = 0;
+            cnt[i] = 0;
+            if (owner) {
+                const int d = tid * DPT + i;
+                uint32_t s = 0;
 #pragma unroll
-            for (int w = 0; w < OS_WARPS; ++w) {
-                const uint32_t c = whist[w * RADIX + d];
-                whist[w * RADIX + d] = (uint16_t)s;
-                s += c;
+                for (int w = 0; w < OS_WARPS; ++w) {
+                    const uint32_t c = whist[w * RADIX + d];
+                    whist[w * RADIX + d] = (uint16_t)s;
+                    s += c;
+                }
+                cnt[i] = s;
+                tsum += s;
             }
-            cnt[i] = s;
-            tsum += s;
         }
         uint32_t total;
         uint32_t ex = block_exclusive_scan<OS_THREADS>(tsum, scan_tmp, &total);
+        if (owner) {
 #pragma unroll
-        for (int i = 0; i < DPT; ++i) {
-            digit_start[tid * DPT + i] = ex;
-            ex += cnt[i];
+            for (int i = 0; i < DPT; ++i) {
+                digit_start[tid * DPT + i] = ex;
+                ex += cnt[i];
+            }
         }
 
         // ---- decoupled look-back over this segment's earlier tiles
         const bool first = (t == td.firstTile);
 #pragma unroll 1
-        for (int i = 0; i < DPT; ++i) {
+        for (int i = 0; i < (owner ? DPT : 0); ++i) {
             const int d = tid * DPT + i;
             uint32_t* mine = p.status + (size_t)t * RADIX + d;
             uint32_t excl = 0;
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(256) k_hist_keys11(const uint8_t* __restrict__
         for (uint32_t q0 = 0; q0 < td.len; q0 += 256) {
             const uint32_t q = q0 + threadIdx.x;
             const bool valid = q < td.len;
-            const uint64_t k = valid ? pack8(sbytes + q) : 0ull;
+            const uint64_t k = valid ? pack8_smem(sbytes, q) : 0ull;
 #pragma unroll
             for (int ps = 0; ps < PASSES; ++ps) {
                 const uint32_t d = valid ? (uint32_t)((k >> (11 * ps)) & (RADIX - 1)) : (uint32_t)RADIX;
@@ -358,6 +366,7 @@ struct KernelEntry {
     void* fn;
     size_t smem;
     int grid;
+    int threads;
 };
 
 template <typename KeyT, int RBITS, int TILE, bool FROM_S, bool VDIG = false>
@@ -367,8 +376,9 @@ KernelEntry& entry() {
         x.fn = OneSweepKernel<KeyT, RBITS, TILE, FROM_S, VDIG>::fn();
         x.smem = OneSweepKernel<KeyT, RBITS, TILE, FROM_S, VDIG>::smem();
         cudaFuncSetAttribute(x.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x.smem);
+        x.threads = OsThreads<TILE>::value;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, x.fn, OS_THREADS, x.smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, x.fn, x.threads, x.smem);
         x.grid = std::max(1, per_sm) * num_sms();
         return x;
     }();
@@ -432,7 +442,7 @@ cudaError_t launch_onesweep(int key_bytes, bool from_s, int radix_bits, int tile
     if (grid <= 0 || grid > e->grid) grid = e->grid;
     OneSweepParams a = p;
     void* args[] = {&a};
-    return cudaLaunchKernel(e->fn, dim3(grid), dim3(OS_THREADS), args, e->smem, st);
+    return cudaLaunchKernel(e->fn, dim3(grid), dim3(e->threads), args, e->smem, st);
 }
 
 cudaError_t launch_hist_bytes(const uint8_t* S, const BlockInfo* blocks, const TileDesc* tiles, uint32_t num_tiles,

@@ -174,3 +174,16 @@ def test_autotuner_picks_a_valid_config_and_caches_it(tmp_path):
         rb2, tile2, _ = plan2.autotune(d_in, off, L, p, cache_path=cache, repeats=2)
         assert (rb2, tile2) == (rb, tile)
         assert len(open(cache).readlines()) == 1  # read back, no new sweep
+
+
+@pytest.mark.parametrize("round_bits", [8, 11])
+def test_round_radix_widths(round_bits):
+    import torch
+    w = datagen.Workload("t", [datagen.RUNS16, datagen.PERIOD7, datagen.FIBONACCI, datagen.MUTATED_UNIT],
+                         [21, 22, 23, 24], [70_000, 66_000, 50_001, 40_000])
+    buf, off = w.generate()
+    with Plan(max_blocks=4, max_total_bytes=buf.size, max_block_bytes=70_000) as plan:
+        plan.set_round_radix(round_bits)
+        L, prim = plan.forward(torch.from_numpy(buf).cuda(), off)
+        assert plan.stats()["round_radix_bits"] == round_bits
+        assert_matches_oracle(buf, off, L.cpu().numpy(), prim.cpu().numpy(), f"round bits {round_bits}")
