@@ -178,7 +178,6 @@ namespace {
 
 constexpr int NBK = BWT_BUCKETS;
 constexpr int NSP = BWT_SPLITTERS;
-constexpr uint32_t BUCKET_CAP = MED_MAX;  // largest bucket sorted in shared memory
 
 // Bucket of a key: #{j : spl[j] <= key}. first[c] = #{j : spl[j] < c << 56}
 // narrows the search to the splitters that share the key's top byte (the
@@ -224,7 +223,6 @@ constexpr size_t SPL_BYTES = 4096 * 8 + 528;  // splitters + top-byte index (257
 constexpr size_t CNT_BYTES = 4096 * 4;
 constexpr size_t TILE_BYTES = 4096 + 16;
 constexpr size_t COUNT_SMEM = SPL_BYTES + CNT_BYTES + TILE_BYTES;
-constexpr size_t SCATTER_SMEM = SPL_BYTES + 2 * CNT_BYTES + TILE_BYTES;
 
 __global__ void __launch_bounds__(256) k_bucket_count(const uint8_t* __restrict__ S, const BlockInfo* __restrict__ blocks,
                                                       const TileDesc* __restrict__ tiles, uint32_t ntiles,
@@ -297,125 +295,184 @@ __global__ void __launch_bounds__(256) k_bucket_stats(const uint32_t* __restrict
     }
 }
 
+// ---- two-level scatter -------------------------------------------------------
+//
+// Writing every rotation straight to its fine bucket scatters a tile over up
+// to 4096 places (about one key each), so nearly every 12-byte write is a
+// separate memory sector. Instead each block's consecutive fine buckets are
+// grouped into chunks of at most CHUNK_CAP rotations (greedy, one thread per
+// block); the scatter writes each tile's keys chunk by chunk in runs, and one
+// CTA per chunk then splits it by fine bucket in shared memory and sorts every
+// bucket by (K, i). A fine bucket larger than CHUNK_CAP is a chunk of its own
+// and goes to the overflow radix.
+constexpr uint32_t CHUNK_CAP = 3072;
+constexpr uint32_t MAXCH = 1024;  // chunks per block (blocks above (MAXCH - 2) * CHUNK_CAP / 2 go plain)
+
+struct ChunkTables {
+    uint16_t* cmap;        // [block][4096] chunk of each fine bucket
+    uint32_t* cbase;       // [block][MAXCH] block-relative start of each chunk
+    uint32_t* ccur;        // [block][MAXCH] slots taken by the scatter
+};
+
+__global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__ starts,
+                                                    const BlockInfo* __restrict__ blocks,
+                                                    const uint32_t* __restrict__ route, uint32_t nb, ChunkTables ct,
+                                                    Bins out, uint32_t* ctrl) {
+    __shared__ uint32_t st[NBK + 1];
+    __shared__ uint16_t cm[NBK];
+    __shared__ uint32_t cb[MAXCH];
+    __shared__ GroupDesc chunks[MAXCH];
+    __shared__ uint32_t s_n[3];  // normal chunks to emit, overflow chunks to emit, chunks total
+    for (uint32_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+        if (route[blk] == 1u) continue;  // plain-routed (uniform across the CTA)
+        const BlockInfo bi = blocks[blk];
+        for (int i = threadIdx.x; i < NBK; i += blockDim.x) st[i] = starts[(size_t)blk * NBK + i];
+        if (threadIdx.x == 0) st[NBK] = bi.n;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t nch = 0, nemit = 0, first = 0, len = 0;
+            auto close = [&](uint32_t last) {
+                if (nch < MAXCH) {
+                    cb[nch] = st[first];
+                    if (len > 1) chunks[nemit++] = GroupDesc{bi.off + st[first], len, blk, first | (last << 16)};
+                }
+                ++nch;
+            };
+            for (uint32_t b = 0; b < (uint32_t)NBK; ++b) {
+                const uint32_t sz = st[b + 1] - st[b];
+                if (sz > CHUNK_CAP) {
+                    if (len > 0) close(b);
+                    cm[b] = (uint16_t)min(nch, MAXCH - 1);
+                    if (nch < MAXCH) cb[nch] = st[b];
+                    ++nch;
+                    const uint32_t slot = atomicAdd(&out.count[CLS_LARGE], 1u);
+                    if (slot < out.cap[CLS_LARGE]) out.list[CLS_LARGE][slot] = GroupDesc{bi.off + st[b], sz, blk, 0u};
+                    else atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
+                    first = b + 1;
+                    len = 0;
+                } else if (len + sz > CHUNK_CAP) {
+                    close(b);
+                    first = b;
+                    len = sz;
+                    cm[b] = (uint16_t)min(nch, MAXCH - 1);
+                } else {
+                    if (len == 0) first = b;
+                    len += sz;
+                    cm[b] = (uint16_t)min(nch, MAXCH - 1);
+                }
+            }
+            if (len > 0) close(NBK);
+            if (nch > MAXCH) atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
+            s_n[0] = nemit;
+            s_n[1] = atomicAdd(&out.count[0], nemit);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < NBK; i += blockDim.x) ct.cmap[(size_t)blk * NBK + i] = cm[i];
+        for (uint32_t i = threadIdx.x; i < MAXCH; i += blockDim.x) {
+            ct.cbase[(size_t)blk * MAXCH + i] = cb[i];
+            ct.ccur[(size_t)blk * MAXCH + i] = 0u;
+        }
+        for (uint32_t i = threadIdx.x; i < s_n[0]; i += blockDim.x) {
+            const uint32_t slot = s_n[1] + i;
+            if (slot < out.cap[0]) out.list[0][slot] = chunks[i];
+            else atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
+        }
+        __syncthreads();
+    }
+}
+
+constexpr size_t CS_STAGE = 4096 * 12;  // staged keys and indexes of one tile (aliases its bytes)
+constexpr size_t CHUNK_SCATTER_SMEM = SPL_BYTES + 3 * MAXCH * 4 + CS_STAGE + 4096 * 2;
+
 template <int ITEMS>
-__global__ void __launch_bounds__(256) k_bucket_scatter(const uint8_t* __restrict__ S,
-                                                        const BlockInfo* __restrict__ blocks,
-                                                        const TileDesc* __restrict__ tiles, uint32_t ntiles,
-                                                        const uint64_t* __restrict__ splitters,
-                                                        const uint32_t* __restrict__ starts,
-                                                        uint32_t* __restrict__ cursor, uint64_t* __restrict__ K,
-                                                        uint32_t* __restrict__ I) {
+__global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict__ S,
+                                                       const BlockInfo* __restrict__ blocks,
+                                                       const TileDesc* __restrict__ tiles, uint32_t ntiles,
+                                                       const uint64_t* __restrict__ splitters, ChunkTables ct,
+                                                       uint64_t* __restrict__ K, uint32_t* __restrict__ I) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* spl = reinterpret_cast<uint64_t*>(smem);
     uint16_t* first = reinterpret_cast<uint16_t*>(smem + 4096 * 8);
     uint32_t* lcount = reinterpret_cast<uint32_t*>(smem + SPL_BYTES);
-    uint32_t* gbase = reinterpret_cast<uint32_t*>(smem + SPL_BYTES + CNT_BYTES);
-    uint8_t* sb = smem + SPL_BYTES + 2 * CNT_BYTES;
+    uint32_t* pre = lcount + MAXCH;
+    uint32_t* gbase = pre + MAXCH;
+    unsigned char* stage = reinterpret_cast<unsigned char*>(gbase + MAXCH);
+    uint8_t* sb = stage;                                         // tile bytes (consumed before staging)
+    uint64_t* stK = reinterpret_cast<uint64_t*>(stage);          // staged keys
+    uint32_t* stI = reinterpret_cast<uint32_t*>(stage + 4096 * 8);
+    uint16_t* stC = reinterpret_cast<uint16_t*>(stage + CS_STAGE);
+    __shared__ uint32_t scan_tmp[32];
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
     load_splitters(splitters, spl, first);
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        for (int i = threadIdx.x; i < NBK; i += blockDim.x) lcount[i] = 0;
+        for (int i = threadIdx.x; i < (int)MAXCH; i += blockDim.x) lcount[i] = 0;
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
         const uint32_t i0 = td.start - bi.off;
+        const uint16_t* cmap = ct.cmap + (size_t)td.blk * NBK;
         load_tile_bytes(S, bi, i0, td.len, sb);
         __syncthreads();
         uint64_t key[ITEMS];
-        uint32_t bl[ITEMS];  // bucket (low 12 bits) | slot within the tile's share of the bucket << 12
+        uint32_t cs[ITEMS];  // chunk (low 10 bits) | slot within the tile's share of the chunk << 10
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const uint32_t q = j * 256 + threadIdx.x;
             const bool valid = q < td.len;
             key[j] = valid ? pack8_smem(sb, q) : 0ull;
-            const uint32_t b = valid ? bucket_of(spl, first, key[j]) : (uint32_t)NBK;
-            const uint32_t peers = __match_any_sync(0xffffffffu, b);
+            const uint32_t c = valid ? cmap[bucket_of(spl, first, key[j])] : MAXCH;
+            const uint32_t peers = __match_any_sync(0xffffffffu, c);
             const int leader = __ffs(peers) - 1;
             uint32_t base = 0;
-            if (valid && lane == leader) base = atomicAdd(&lcount[b], (uint32_t)__popc(peers));
+            if (valid && lane == leader) base = atomicAdd(&lcount[c], (uint32_t)__popc(peers));
             base = __shfl_sync(0xffffffffu, base, leader);
-            bl[j] = valid ? (b | ((base + __popc(peers & lt)) << 12)) : 0xffffffffu;
+            cs[j] = valid ? (c | ((base + __popc(peers & lt)) << 10)) : 0xffffffffu;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < NBK; i += blockDim.x) {
-            const uint32_t c = lcount[i];
-            if (c) gbase[i] = atomicAdd(&cursor[(size_t)td.blk * NBK + i], c);
-        }
-        __syncthreads();
-        const uint32_t* st = starts + (size_t)td.blk * NBK;
+        // tile-local exclusive prefix over chunks and the global reservation
+        {
+            constexpr int PER = MAXCH / 256;
+            uint32_t v[PER], sum = 0;
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if (bl[j] != 0xffffffffu) {
-                const uint32_t b = bl[j] & 4095u;
-                const uint32_t pos = bi.off + st[b] + gbase[b] + (bl[j] >> 12);
-                K[pos] = key[j];
-                I[pos] = i0 + j * 256 + threadIdx.x;
+            for (int i = 0; i < PER; ++i) {
+                v[i] = lcount[threadIdx.x * PER + i];
+                sum += v[i];
+            }
+            uint32_t total;
+            uint32_t ex = block_exclusive_scan<256>(sum, scan_tmp, &total);
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const uint32_t c = threadIdx.x * PER + i;
+                pre[c] = ex;
+                ex += v[i];
+                if (v[i]) gbase[c] = atomicAdd(&ct.ccur[(size_t)td.blk * MAXCH + c], v[i]);
             }
         }
         __syncthreads();
-    }
-}
-
-// Every bucket of a bucket-routed block with two or more rotations becomes a
-// group in the size-class bins: classes 0-3 are sorted in place by (K, i),
-// class 4 (more than BUCKET_CAP rotations) goes to the overflow radix. One
-// CTA per block.
-__global__ void __launch_bounds__(256) k_bucket_groups(const uint32_t* __restrict__ starts,
-                                                       const BlockInfo* __restrict__ blocks,
-                                                       const uint32_t* __restrict__ route, uint32_t nb, Bins out,
-                                                       uint32_t* ctrl) {
-    __shared__ GroupDesc ebuf[8][NCLS * EMIT_BUF];
-    WarpEmitter em;
-    em.init(ebuf[threadIdx.x >> 5]);
-    for (uint32_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
-        if (route[blk] == 1u) continue;  // plain-routed (uniform across the CTA)
-        const BlockInfo bi = blocks[blk];
-        const uint32_t* st = starts + (size_t)blk * NBK;
-        for (int b0 = 0; b0 < NBK; b0 += blockDim.x) {
-            const int b = b0 + threadIdx.x;
-            const uint32_t s0 = st[b];
-            const uint32_t s1 = b + 1 < NBK ? st[b + 1] : bi.n;
-            const uint32_t sz = s1 - s0;
-            em.emit(out, sz > 1, bi.off + s0, sz, blk, &ctrl[CTRL_ERR]);
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (cs[j] != 0xffffffffu) {
+                const uint32_t c = cs[j] & (MAXCH - 1);
+                const uint32_t pos = pre[c] + (cs[j] >> 10);
+                stK[pos] = key[j];
+                stI[pos] = i0 + j * 256 + threadIdx.x;
+                stC[pos] = (uint16_t)c;
+            }
         }
+        __syncthreads();
+        const uint32_t* cbase = ct.cbase + (size_t)td.blk * MAXCH;
+        for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) {
+            const uint32_t c = stC[q];
+            const uint32_t dst = bi.off + cbase[c] + gbase[c] + (q - pre[c]);
+            K[dst] = stK[q];
+            I[dst] = stI[q];
+        }
+        __syncthreads();
     }
-    em.finish(out, &ctrl[CTRL_ERR]);
 }
 
 __device__ __forceinline__ bool pair_gt(uint64_t ak, uint32_t ai, uint64_t bk, uint32_t bi) {
     return ak > bk || (ak == bk && ai > bi);
-}
-
-// buckets of 2..32 rotations: one warp each, bitonic across the lanes on (K, i)
-__global__ void __launch_bounds__(256) k_bsort_lanes(uint64_t* __restrict__ K, uint32_t* __restrict__ I, Bins g) {
-    const uint32_t c0 = bin_count(g, 0), c1 = bin_count(g, 1);
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
-    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < c0 + c1; w += nwarps) {
-        const GroupDesc gd = w < c0 ? g.list[0][w] : g.list[1][w - c0];
-        const bool valid = lane < gd.len;
-        uint64_t k = valid ? K[gd.start + lane] : ~0ull;
-        uint32_t v = valid ? I[gd.start + lane] : ~0u;
-#pragma unroll
-        for (uint32_t kk = 2; kk <= 32; kk <<= 1) {
-#pragma unroll
-            for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-                const uint64_t ok = __shfl_xor_sync(0xffffffffu, k, j);
-                const uint32_t ov = __shfl_xor_sync(0xffffffffu, v, j);
-                const bool up = (lane & kk) == 0;
-                const bool lower = (lane & j) == 0;
-                const bool take_other = (lower == up) ? pair_gt(k, v, ok, ov) : pair_gt(ok, ov, k, v);
-                if (take_other) {
-                    k = ok;
-                    v = ov;
-                }
-            }
-        }
-        if (valid) {
-            K[gd.start + lane] = k;
-            I[gd.start + lane] = v;
-        }
-    }
 }
 
 // Sorts (sk, si)[0..P) by (K, i), bitonic; NT threads cooperate.
@@ -442,51 +499,91 @@ __device__ __forceinline__ void pair_bitonic(uint64_t* sk, uint32_t* si, uint32_
     }
 }
 
-// buckets of 33..256 rotations: one warp each, bitonic in shared memory
-__global__ void __launch_bounds__(256) k_bsort_warp(uint64_t* __restrict__ K, uint32_t* __restrict__ I, Bins g) {
-    __shared__ uint64_t sk[8][256];
-    __shared__ uint32_t si[8][256];
-    const uint32_t count = bin_count(g, 2);
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
-    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += nwarps) {
-        const GroupDesc gd = g.list[2][w];
-        uint32_t P = 64;
-        while (P < gd.len) P <<= 1;
-        for (uint32_t i = lane; i < P; i += 32) {
-            const bool valid = i < gd.len;
-            sk[warp][i] = valid ? K[gd.start + i] : ~0ull;
-            si[warp][i] = valid ? I[gd.start + i] : ~0u;
-        }
-        __syncwarp();
-        pair_bitonic<32>(sk[warp], si[warp], P, lane);
-        for (uint32_t i = lane; i < gd.len; i += 32) {
-            K[gd.start + i] = sk[warp][i];
-            I[gd.start + i] = si[warp][i];
-        }
-        __syncwarp();
-    }
-}
+// One CTA per chunk: split by fine bucket in shared memory, sort every
+// bucket by (K, i) -- buckets up to 256 rotations by one warp each, larger
+// ones by the whole CTA -- and write the chunk back in order.
+constexpr size_t CHUNK_SORT_SMEM = 4096 * 12 + CHUNK_CAP * 12 + 4096 * 4;
 
-// buckets of 257..BUCKET_CAP rotations: one CTA each, bitonic in shared memory
-__global__ void __launch_bounds__(256) k_bsort_cta(uint64_t* __restrict__ K, uint32_t* __restrict__ I, Bins g) {
-    __shared__ uint64_t sk[BUCKET_CAP];
-    __shared__ uint32_t si[BUCKET_CAP];
-    const uint32_t count = bin_count(g, 3);
+__global__ void __launch_bounds__(256) k_chunk_sort(uint64_t* __restrict__ K, uint32_t* __restrict__ I,
+                                                    const uint32_t* __restrict__ starts,
+                                                    const uint64_t* __restrict__ spl_learned,
+                                                    const uint64_t* __restrict__ spl_flat,
+                                                    const uint32_t* __restrict__ route, Bins g) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* aK = reinterpret_cast<uint64_t*>(smem);                      // [4096] load buffer, then scratch
+    uint32_t* aI = reinterpret_cast<uint32_t*>(smem + 4096 * 8);
+    uint64_t* bK = reinterpret_cast<uint64_t*>(smem + 4096 * 12);          // [CHUNK_CAP] split by bucket
+    uint32_t* bI = reinterpret_cast<uint32_t*>(smem + 4096 * 12 + CHUNK_CAP * 8);
+    uint32_t* fend = reinterpret_cast<uint32_t*>(smem + 4096 * 12 + CHUNK_CAP * 12);  // [4096]
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t count = bin_count(g, 0);
     for (uint32_t c = blockIdx.x; c < count; c += gridDim.x) {
-        const GroupDesc gd = g.list[3][c];
-        uint32_t P = 512;
-        while (P < gd.len) P <<= 1;
-        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-            const bool valid = i < gd.len;
-            sk[i] = valid ? K[gd.start + i] : ~0ull;
-            si[i] = valid ? I[gd.start + i] : ~0u;
+        const GroupDesc gd = g.list[0][c];
+        const uint32_t f0 = gd.pad & 0xffffu, f1 = gd.pad >> 16;  // fine buckets [f0, f1)
+        const uint32_t nf = f1 - f0;
+        const uint32_t* st = starts + (size_t)gd.blk * NBK;
+        const uint64_t* spl = route[gd.blk] == 2u ? spl_flat : spl_learned;
+        const uint32_t base = st[f0];
+        for (uint32_t i = threadIdx.x; i < gd.len; i += blockDim.x) {
+            aK[i] = K[gd.start + i];
+            aI[i] = I[gd.start + i];
+        }
+        for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x) fend[f] = st[f0 + f] - base;  // cursors at starts
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < gd.len; i += blockDim.x) {
+            const uint64_t k = aK[i];
+            uint32_t lo = f0, hi = f1 - 1;  // bucket = f0 + #{j in [f0, f1 - 1) : spl[j] <= k}
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (spl[mid] <= k) lo = mid + 1; else hi = mid;
+            }
+            const uint32_t pos = atomicAdd(&fend[lo - f0], 1u);
+            bK[pos] = k;
+            bI[pos] = aI[i];
+        }
+        __syncthreads();  // fend[f] is now the end of bucket f0 + f
+        for (uint32_t f = warp; f < nf; f += blockDim.x / 32) {
+            const uint32_t s0 = f == 0 ? 0u : fend[f - 1], s1 = fend[f];
+            const uint32_t m = s1 - s0;
+            if (m < 2 || m > 256) continue;
+            uint64_t* wk = aK + warp * 256;
+            uint32_t* wi = aI + warp * 256;
+            uint32_t P = 2;
+            while (P < m) P <<= 1;
+            for (uint32_t i = lane; i < P; i += 32) {
+                wk[i] = i < m ? bK[s0 + i] : ~0ull;
+                wi[i] = i < m ? bI[s0 + i] : ~0u;
+            }
+            __syncwarp();
+            pair_bitonic<32>(wk, wi, P, lane);
+            for (uint32_t i = lane; i < m; i += 32) {
+                bK[s0 + i] = wk[i];
+                bI[s0 + i] = wi[i];
+            }
+            __syncwarp();
         }
         __syncthreads();
-        pair_bitonic<256>(sk, si, P, threadIdx.x);
+        for (uint32_t f = 0; f < nf; ++f) {  // CTA-uniform: buckets of 257..CHUNK_CAP rotations
+            const uint32_t s0 = f == 0 ? 0u : fend[f - 1], s1 = fend[f];
+            const uint32_t m = s1 - s0;
+            if (m <= 256) continue;
+            uint32_t P = 512;
+            while (P < m) P <<= 1;
+            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                aK[i] = i < m ? bK[s0 + i] : ~0ull;
+                aI[i] = i < m ? bI[s0 + i] : ~0u;
+            }
+            __syncthreads();
+            pair_bitonic<256>(aK, aI, P, threadIdx.x);
+            for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+                bK[s0 + i] = aK[i];
+                bI[s0 + i] = aI[i];
+            }
+            __syncthreads();
+        }
         for (uint32_t i = threadIdx.x; i < gd.len; i += blockDim.x) {
-            K[gd.start + i] = sk[i];
-            I[gd.start + i] = si[i];
+            K[gd.start + i] = bK[i];
+            I[gd.start + i] = bI[i];
         }
         __syncthreads();
     }
@@ -560,6 +657,8 @@ bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
     if (!p->splitters) CKL(cudaMalloc(&p->splitters, sizeof(uint64_t) * NSP));
     if (!p->bucket_count) CKL(cudaMalloc(&p->bucket_count, sizeof(uint32_t) * nbk));
     if (!p->bucket_cursor) CKL(cudaMalloc(&p->bucket_cursor, sizeof(uint32_t) * nbk));
+    if (!p->chunk_map) CKL(cudaMalloc(&p->chunk_map, sizeof(uint16_t) * nbk));
+    if (!p->chunk_base) CKL(cudaMalloc(&p->chunk_base, sizeof(uint32_t) * nbk));
     if (!p->route) CKL(cudaMalloc(&p->route, sizeof(uint32_t) * p->cap_b));
     if (!p->bstats) CKL(cudaMalloc(&p->bstats, sizeof(unsigned long long) * 5 * p->cap_b));
     if (!p->tiles_aux) CKL(cudaMalloc(&p->tiles_aux, sizeof(TileDesc) * p->cap_tiles0));
@@ -581,12 +680,13 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
     if ((s = ensure_learned_buffers(p)) != BWT_OK) return s;
     static bool attr = [] {
         cudaFuncSetAttribute((void*)k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COUNT_SMEM);
-        cudaFuncSetAttribute((void*)k_bucket_scatter<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SCATTER_SMEM);
-        cudaFuncSetAttribute((void*)k_bucket_scatter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SCATTER_SMEM);
-        cudaFuncSetAttribute((void*)k_bucket_scatter<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SCATTER_SMEM);
+        cudaFuncSetAttribute((void*)k_chunk_scatter<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CHUNK_SCATTER_SMEM);
+        cudaFuncSetAttribute((void*)k_chunk_scatter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CHUNK_SCATTER_SMEM);
+        cudaFuncSetAttribute((void*)k_chunk_scatter<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CHUNK_SCATTER_SMEM);
+        cudaFuncSetAttribute((void*)k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CHUNK_SORT_SMEM);
         return true;
     }();
     (void)attr;
@@ -599,7 +699,7 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
     CKL(cudaMemsetAsync(p->bucket_count, 0, sizeof(uint32_t) * NBK * nb, st));
     k_bucket_count<<<std::max(1, std::min<int>(nt, sms * 3)), 256, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles0, nt,
                                                                                      p->splitters, p->bucket_count);
-    k_bucket_stats<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, BUCKET_CAP, nb, p->bstats);
+    k_bucket_stats<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, nb, p->bstats);
     CKL(cudaGetLastError());
     CKL(cudaMemcpyAsync(p->h_bstats, p->bstats, sizeof(unsigned long long) * 5 * nb, cudaMemcpyDeviceToHost, st));
     CKL(cudaStreamSynchronize(st));
@@ -611,7 +711,8 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
     std::vector<uint32_t> cand;
     for (uint32_t b = 0; b < nb; ++b) {
         const unsigned long long* bs = p->h_bstats + 5 * b;
-        const bool over = bs[0] * 4 > p->h_blocks[b].n;
+        const bool too_big = (uint64_t)p->h_blocks[b].n * 2 > (uint64_t)(MAXCH - 2) * CHUNK_CAP;
+        const bool over = too_big || bs[0] * 4 > p->h_blocks[b].n;
         p->h_route[b] = over ? 2u : 0u;
         if (over) cand.push_back(b);
         p->stats.max_bucket = std::max<uint32_t>(p->stats.max_bucket, (uint32_t)bs[2]);
@@ -648,13 +749,15 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
         k_zero_rows_routed<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->route, nb, 2u);
         k_bucket_count<<<std::max(1, std::min<int>(ntc, sms * 3)), 256, COUNT_SMEM, st>>>(
             d_in, p->blocks, p->tiles_aux, ntc, p->splitters_flat, p->bucket_count);
-        k_bucket_stats<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, BUCKET_CAP, nb, p->bstats);
+        k_bucket_stats<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, nb, p->bstats);
         CKL(cudaGetLastError());
         CKL(cudaMemcpyAsync(p->h_bstats, p->bstats, sizeof(unsigned long long) * 5 * nb, cudaMemcpyDeviceToHost, st));
         CKL(cudaStreamSynchronize(st));
         p->stats.kernel_launches += 3;
         for (uint32_t b : cand)
-            if (p->h_bstats[5 * b] * 4 > p->h_blocks[b].n) p->h_route[b] = 1u;
+            if (p->h_bstats[5 * b] * 4 > p->h_blocks[b].n ||
+                (uint64_t)p->h_blocks[b].n * 2 > (uint64_t)(MAXCH - 2) * CHUNK_CAP)
+                p->h_route[b] = 1u;
     }
     uint64_t plain_keys = 0;
     for (uint32_t b = 0; b < nb; ++b) {
@@ -730,30 +833,29 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
     CKL(cudaMemsetAsync(aux.count, 0, sizeof(uint32_t) * NCLS, st));
     if (ntb) {
         CKL(launch_scan_rows(p->bucket_count, NBK, nullptr, 0, nb, nb, st));  // counts -> starts in place
-        CKL(cudaMemsetAsync(p->bucket_cursor, 0, sizeof(uint32_t) * NBK * nb, st));
+        ChunkTables ct{p->chunk_map, p->chunk_base, p->bucket_cursor};
+        k_chunk_plan<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->blocks, p->route, nb, ct, aux,
+                                                                    ctrl);
         auto scatter = [&](const TileDesc* tl, uint32_t n_t, const uint64_t* spl) {
             if (!n_t) return;
             const int g = std::max(1, std::min<int>(n_t, sms * 2));
             if (T <= 1024)
-                k_bucket_scatter<4><<<g, 256, SCATTER_SMEM, st>>>(d_in, p->blocks, tl, n_t, spl, p->bucket_count,
-                                                                  p->bucket_cursor, p->keys[0], p->vals[0]);
+                k_chunk_scatter<4><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tl, n_t, spl, ct, p->keys[0],
+                                                                       p->vals[0]);
             else if (T <= 2048)
-                k_bucket_scatter<8><<<g, 256, SCATTER_SMEM, st>>>(d_in, p->blocks, tl, n_t, spl, p->bucket_count,
-                                                                  p->bucket_cursor, p->keys[0], p->vals[0]);
+                k_chunk_scatter<8><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tl, n_t, spl, ct, p->keys[0],
+                                                                       p->vals[0]);
             else
-                k_bucket_scatter<16><<<g, 256, SCATTER_SMEM, st>>>(d_in, p->blocks, tl, n_t, spl, p->bucket_count,
-                                                                   p->bucket_cursor, p->keys[0], p->vals[0]);
+                k_chunk_scatter<16><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tl, n_t, spl, ct,
+                                                                        p->keys[0], p->vals[0]);
             p->stats.kernel_launches++;
         };
         scatter(tilesL, ntl, p->splitters);
         scatter(tilesF, ntf, p->splitters_flat);
-        k_bucket_groups<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->blocks, p->route, nb, aux,
-                                                                       ctrl);
-        k_bsort_lanes<<<sms * 8, 256, 0, st>>>(p->keys[0], p->vals[0], aux);
-        k_bsort_warp<<<sms * 8, 256, 0, st>>>(p->keys[0], p->vals[0], aux);
-        k_bsort_cta<<<sms * 8, 256, 0, st>>>(p->keys[0], p->vals[0], aux);
+        k_chunk_sort<<<sms * 2, 256, CHUNK_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->bucket_count, p->splitters,
+                                                            p->splitters_flat, p->route, aux);
         CKL(cudaGetLastError());
-        p->stats.kernel_launches += 5;
+        p->stats.kernel_launches += 2;
 
         // 4c. overflow buckets: radix on the index, then on the key
         const int PI = std::max(1, (bits_needed(p->max_n - 1) + 7) / 8), PK = 8, PT = PI + PK;

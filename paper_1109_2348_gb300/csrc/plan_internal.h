@@ -55,7 +55,9 @@ struct bwt_plan {
     uint64_t* splitters = nullptr;      // [BWT_SPLITTERS] sorted
     uint64_t* splitters_flat = nullptr; // [BWT_SPLITTERS] equal-width fallback (top 12 key bits)
     uint32_t* bucket_count = nullptr;   // [block][BWT_BUCKETS] counts, then starts
-    uint32_t* bucket_cursor = nullptr;  // [block][BWT_BUCKETS] slots taken so far
+    uint32_t* bucket_cursor = nullptr;  // [block][BWT_BUCKETS] slots taken so far (per chunk)
+    uint16_t* chunk_map = nullptr;      // [block][BWT_BUCKETS] chunk of each bucket
+    uint32_t* chunk_base = nullptr;     // [block][BWT_BUCKETS] block-relative start of each chunk
     uint32_t* route = nullptr;          // [block] 0 = buckets, 1 = plain radix
     unsigned long long* bstats = nullptr;  // [block][5] overflow keys, overflow buckets, largest bucket,
                                            // sum of squared sizes, non-empty buckets

@@ -1,0 +1,76 @@
+"""Full-size parity: every benchmark workload at its full size, in the launch
+configuration bench.py times. Workloads 1-4 are compared with the oracle
+byte for byte in full (the oracle runs on all host cores). Workload 5 (1.08
+GB) is checked block by block with the host inverse transform and the
+permutation invariant, and byte for byte against the oracle on a sample of 32
+blocks (the oracle would need over a minute for all 1,200)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, Plan, bwt_inverse_check, datagen, model
+
+from gpu_util import assert_matches_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(w, flags=0, model_path=None, **kw):
+    import torch
+    buf, off = w.generate()
+    sizes = np.diff(off.astype(np.int64))
+    with Plan(max_blocks=w.num_blocks, max_total_bytes=buf.size, max_block_bytes=int(sizes.max()), flags=flags,
+              model_path=model_path, **kw) as plan:
+        d_in = torch.from_numpy(buf).cuda()
+        L, prim = plan.forward(d_in, off)
+        torch.cuda.synchronize()
+        st = plan.stats()
+        return buf, off, L.cpu().numpy(), prim.cpu().numpy(), st
+
+
+def test_workload1_markov2_100k():
+    buf, off, L, prim, _ = _run(datagen.config(1), flags=F_GRAPH)
+    assert_matches_oracle(buf, off, L, prim, "workload 1")
+
+
+def test_workload2_mixed_64x900k_graph():
+    buf, off, L, prim, st = _run(datagen.config(2), flags=F_GRAPH)
+    assert_matches_oracle(buf, off, L, prim, "workload 2")
+    assert st["rounds"] >= 5
+
+
+def test_workload3_degenerate_5x900k():
+    buf, off, L, prim, st = _run(datagen.config(3), flags=F_GRAPH)
+    assert_matches_oracle(buf, off, L, prim, "workload 3")
+    assert prim[0] == 0 and st["rounds"] >= 15  # constant block: identity order after ~17 rounds
+
+
+def test_workload4_uneven_256_graph():
+    buf, off, L, prim, _ = _run(datagen.config(4), flags=F_GRAPH)
+    assert_matches_oracle(buf, off, L, prim, "workload 4")
+
+
+@pytest.fixture(scope="module")
+def trained_model_path(tmp_path_factory):
+    m = model.train(num_samples=1_000_000, epochs=8)
+    path = str(tmp_path_factory.mktemp("model") / "markov3.bwtmodel")
+    m.save(path)
+    return path
+
+
+def test_workload5_learned_1200x900k(trained_model_path):
+    w = datagen.config(5)
+    buf, off, L, prim, st = _run(w, flags=F_LEARNED, model_path=trained_model_path)
+    assert st["blocks_routed_plain"] == 0
+    for b in range(w.num_blocks):
+        s, e = int(off[b]), int(off[b + 1])
+        assert np.array_equal(np.bincount(L[s:e], minlength=256), np.bincount(buf[s:e], minlength=256))
+        assert bwt_inverse_check(L[s:e], int(prim[b]), buf[s:e]) == 0, b
+    sample = list(range(0, 1200, 38))[:32]
+    sub = w.subset(sample)
+    sbuf, soff = sub.generate()
+    ref_L, ref_p = oracle.bwt_batch(sbuf, soff)
+    for j, b in enumerate(sample):
+        s, e = int(off[b]), int(off[b + 1])
+        assert np.array_equal(L[s:e], ref_L[int(soff[j]):int(soff[j + 1])]), b
+        assert prim[b] == ref_p[j], b
