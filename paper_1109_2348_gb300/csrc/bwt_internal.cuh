@@ -244,4 +244,61 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
     return warp_prefix + x - v;
 }
 
+template <typename T>
+__device__ __forceinline__ uint32_t smem_lower_bound(const T* a, uint32_t n, T x) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t smem_upper_bound(const T* a, uint32_t n, T x) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Names every element of one sorted tile: the tile's keys sit in sk[0..len),
+// its first run may have begun before the tile (it begins at carry_start)
+// and its last run may continue after it (it ends at carry_end). Writes
+// rank[rotation] = block-local start of the element's group and emits the
+// groups of size > 1 that start inside the tile. SA is the global SA, or with
+// SA_LOCAL the tile's own entries (SA[q] for tile element q). All threads of
+// the CTA call.
+template <typename KeyT, bool SA_LOCAL = false>
+__device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t tstart, uint32_t carry_start,
+                                          uint32_t carry_end, const uint32_t* __restrict__ SA, BlockInfo bi,
+                                          uint32_t blk, uint32_t* __restrict__ rank, const Bins& bins, bool emit_ok,
+                                          WarpEmitter& em, uint32_t* err) {
+    for (uint32_t q0 = 0; q0 < len; q0 += blockDim.x) {
+        const uint32_t q = q0 + threadIdx.x;
+        const bool valid = q < len;
+        bool want = false;
+        uint32_t glen = 0;
+        const uint32_t k = tstart + q;
+        if (valid) {
+            const KeyT key = sk[q];
+            const bool differs_prev = q > 0 && sk[q - 1] != key;
+            const uint32_t lb = differs_prev ? q : (q == 0 ? 0u : smem_lower_bound<KeyT>(sk, q, key));
+            const uint32_t gs = lb == 0 ? carry_start : tstart + lb;
+            const uint32_t sa = SA_LOCAL ? SA[q] : SA[k];
+            if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
+            if (gs == k && emit_ok) {
+                uint32_t ub;
+                if (q + 1 < len && sk[q + 1] != key) ub = q + 1;
+                else ub = smem_upper_bound<KeyT>(sk, len, key);
+                glen = (ub == len ? carry_end : tstart + ub) - k;
+                want = glen > 1;
+            }
+        }
+        em.emit(bins, want, k, glen, blk, err);
+    }
+}
+
 }  // namespace bwt

@@ -85,65 +85,15 @@ __device__ __forceinline__ uint32_t end_equal(const KeyT* __restrict__ K, uint32
     return a;
 }
 
-template <typename T>
-__device__ __forceinline__ uint32_t smem_lower_bound(const T* a, uint32_t n, T x) {
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-template <typename T>
-__device__ __forceinline__ uint32_t smem_upper_bound(const T* a, uint32_t n, T x) {
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (a[mid] <= x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// Names every element of one sorted tile: the tile's keys sit in sk[0..len),
-// its first run may have begun before the tile (it begins at carry_start)
-// and its last run may continue after it (it ends at carry_end). Writes
-// rank[rotation] = block-local start of the element's group and emits the
-// groups of size > 1 that start inside the tile. All threads of the CTA call.
-template <typename KeyT>
-__device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t tstart, uint32_t carry_start,
-                                          uint32_t carry_end, const uint32_t* __restrict__ SA, BlockInfo bi,
-                                          uint32_t blk, uint32_t* __restrict__ rank, const Bins& bins, bool emit_ok,
-                                          WarpEmitter& em, uint32_t* err) {
-    for (uint32_t q0 = 0; q0 < len; q0 += blockDim.x) {
-        const uint32_t q = q0 + threadIdx.x;
-        const bool valid = q < len;
-        bool want = false;
-        uint32_t glen = 0;
-        const uint32_t k = tstart + q;
-        if (valid) {
-            const KeyT key = sk[q];
-            const bool differs_prev = q > 0 && sk[q - 1] != key;
-            const uint32_t lb = differs_prev ? q : (q == 0 ? 0u : smem_lower_bound<KeyT>(sk, q, key));
-            const uint32_t gs = lb == 0 ? carry_start : tstart + lb;
-            const uint32_t sa = SA[k];
-            if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
-            if (gs == k && emit_ok) {
-                uint32_t ub;
-                if (q + 1 < len && sk[q + 1] != key) ub = q + 1;
-                else ub = smem_upper_bound<KeyT>(sk, len, key);
-                glen = (ub == len ? carry_end : tstart + ub) - k;
-                want = glen > 1;
-            }
-        }
-        em.emit(bins, want, k, glen, blk, err);
-    }
-}
-
 // ---- first naming ------------------------------------------------------------
+// seg_bounds: every tile's segment [segStart, segStart + pad0) is a whole
+// range of groups (its first element starts a group, its last ends one), so
+// the carries never look past it; else the carries search the whole block.
+// num_tiles_dev, when non-null, holds the tile count on the device.
 __global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict__ K, const uint32_t* __restrict__ SA,
                                                       const BlockInfo* __restrict__ blocks,
                                                       const TileDesc* __restrict__ tiles, uint32_t num_tiles,
+                                                      const uint32_t* __restrict__ num_tiles_dev, bool seg_bounds,
                                                       uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl) {
     __shared__ uint64_t sk[4096];
     __shared__ uint32_t s_carry[2];
@@ -151,10 +101,12 @@ __global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict
     if (ld_volatile(&ctrl[CTRL_ERR])) return;  // an earlier stage failed: SA is not a permutation
     WarpEmitter em;
     em.init(ebuf[threadIdx.x >> 5]);
+    if (num_tiles_dev) num_tiles = *num_tiles_dev;
     for (uint32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
-        const uint32_t lo = bi.off, hi = bi.off + bi.n;
+        const uint32_t lo = seg_bounds ? td.segStart : bi.off;
+        const uint32_t hi = seg_bounds ? td.segStart + td.pad0 : bi.off + bi.n;
         for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) sk[q] = K[td.start + q];
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -603,7 +555,15 @@ int grid_for(uint32_t units, uint32_t per_cta, int cap_per_sm) {
 cudaError_t launch_name_initial(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks, const TileDesc* tiles,
                                 uint32_t num_tiles, uint32_t* rank, Bins bins, uint32_t* ctrl, cudaStream_t st) {
     if (!num_tiles) return cudaSuccess;
-    k_name_initial<<<grid_for(num_tiles, 1, 4), 256, 0, st>>>(K, SA, blocks, tiles, num_tiles, rank, bins, ctrl);
+    k_name_initial<<<grid_for(num_tiles, 1, 4), 256, 0, st>>>(K, SA, blocks, tiles, num_tiles, nullptr, false, rank,
+                                                              bins, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_name_segments(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks,
+                                 const TileDesc* tiles, const uint32_t* num_tiles_dev, uint32_t* rank, Bins bins,
+                                 uint32_t* ctrl, cudaStream_t st) {
+    k_name_initial<<<num_sms() * 4, 256, 0, st>>>(K, SA, blocks, tiles, 0u, num_tiles_dev, true, rank, bins, ctrl);
     return cudaGetLastError();
 }
 

@@ -68,6 +68,13 @@ cudaError_t launch_name_initial(const uint64_t* K, const uint32_t* SA, const Blo
                                 const TileDesc* tiles, uint32_t num_tiles, uint32_t* rank, Bins bins,
                                 uint32_t* ctrl, cudaStream_t st);
 
+// The same over tiles of segments that are whole ranges of groups (tiles
+// from launch_build_large_tiles; count on the device): carries stay inside
+// each tile's segment, so keys outside the segments are never read.
+cudaError_t launch_name_segments(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks,
+                                 const TileDesc* tiles, const uint32_t* num_tiles_dev, uint32_t* rank, Bins bins,
+                                 uint32_t* ctrl, cudaStream_t st);
+
 // Round with prefix length h = *depth: key2[k] = rank[(SA[k] + h) mod n] for
 // every element of the micro, tiny, small and medium groups in `cur`.
 cudaError_t launch_gather_small(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks, Bins cur,

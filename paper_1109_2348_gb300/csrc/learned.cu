@@ -163,16 +163,18 @@ extern "C" bwt_status bwt_model_samples(bwt_plan* p, const uint8_t* d_in, const 
 //   route:   a block whose over-capacity buckets hold more than a quarter of
 //            its rotations is recounted with equal-width buckets (the top 12
 //            key bits), and sorted by the plain radix if those overflow too;
-//   scatter: rotations go to their bucket's range (per-tile reservation of
-//            each bucket's slots with one atomic per tile and bucket);
-//   sort:    every bucket is sorted by (K, i): up to 32 rotations across a
-//            warp's lanes, up to 256 in a warp's shared memory, up to 2048 in a
-//            CTA's shared memory;
-//   overflow buckets (> cap) are sorted by the segmented radix: first by the
+//   plan:    consecutive buckets are grouped into chunks of at most 3328
+//            rotations (a bucket above that is an overflow bucket);
+//   scatter: each tile's rotations go to their chunk's range in runs (one
+//            slot reservation per tile and chunk);
+//   sort:    one CTA per chunk merge-sorts it by (K, i) in shared memory,
+//            writes its SA and names it (a chunk is a whole key range, so
+//            its groups begin and end inside it);
+//   overflow buckets are sorted by the segmented radix: first by the
 //            rotation index (digits taken from the value), then by K, which
 //            leaves equal prefixes in index order as the doubling rounds
-//            require.
-// Then naming, prefix doubling and the L gather run as on the plain path.
+//            require, and named inside their own bounds.
+// Then prefix doubling and the L gather run as on the plain path.
 
 namespace {
 
@@ -224,6 +226,12 @@ constexpr size_t CNT_BYTES = 4096 * 4;
 constexpr size_t TILE_BYTES = 4096 + 16;
 constexpr size_t COUNT_SMEM = SPL_BYTES + CNT_BYTES + TILE_BYTES;
 
+// A CTA counts COUNT_SPAN consecutive tiles into its shared histogram before
+// adding it to the block's row (one global atomic per non-empty bucket and
+// span instead of per tile); a span that crosses into the next block
+// flushes at the boundary.
+constexpr uint32_t COUNT_SPAN = 16;
+
 __global__ void __launch_bounds__(256) k_bucket_count(const uint8_t* __restrict__ S, const BlockInfo* __restrict__ blocks,
                                                       const TileDesc* __restrict__ tiles, uint32_t ntiles,
                                                       const uint64_t* __restrict__ splitters,
@@ -233,25 +241,33 @@ __global__ void __launch_bounds__(256) k_bucket_count(const uint8_t* __restrict_
     uint16_t* first = reinterpret_cast<uint16_t*>(smem + 4096 * 8);
     uint32_t* h = reinterpret_cast<uint32_t*>(smem + SPL_BYTES);
     uint8_t* sb = smem + SPL_BYTES + CNT_BYTES;
-    const int lane = threadIdx.x & 31;
     load_splitters(splitters, spl, first);
-    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        for (int i = threadIdx.x; i < NBK; i += blockDim.x) h[i] = 0;
-        const TileDesc td = tiles[t];
-        const BlockInfo bi = blocks[td.blk];
-        load_tile_bytes(S, bi, td.start - bi.off, td.len, sb);
-        __syncthreads();
-        for (uint32_t q0 = 0; q0 < td.len; q0 += blockDim.x) {
-            const uint32_t q = q0 + threadIdx.x;
-            const bool valid = q < td.len;
-            const uint32_t b = valid ? bucket_of(spl, first, pack8_smem(sb, q)) : (uint32_t)NBK;
-            const uint32_t peers = __match_any_sync(0xffffffffu, b);
-            if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[b], (uint32_t)__popc(peers));
+    for (int i = threadIdx.x; i < NBK; i += blockDim.x) h[i] = 0;
+    const uint32_t nspan = (ntiles + COUNT_SPAN - 1) / COUNT_SPAN;
+    for (uint32_t s = blockIdx.x; s < nspan; s += gridDim.x) {
+        const uint32_t t0 = s * COUNT_SPAN, t1 = min(ntiles, t0 + COUNT_SPAN);
+        uint32_t cur = tiles[t0].blk;
+        for (uint32_t t = t0; t < t1; ++t) {
+            const TileDesc td = tiles[t];
+            if (td.blk != cur) {  // CTA-uniform; the histogram is complete (synced after the last tile)
+                for (int i = threadIdx.x; i < NBK; i += blockDim.x) {
+                    const uint32_t c = h[i];
+                    h[i] = 0;
+                    if (c) atomicAdd(&counts[(size_t)cur * NBK + i], c);
+                }
+                cur = td.blk;
+            }
+            const BlockInfo bi = blocks[td.blk];
+            load_tile_bytes(S, bi, td.start - bi.off, td.len, sb);
+            __syncthreads();
+            for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x)
+                atomicAdd(&h[bucket_of(spl, first, pack8_smem(sb, q))], 1u);
+            __syncthreads();
         }
-        __syncthreads();
         for (int i = threadIdx.x; i < NBK; i += blockDim.x) {
             const uint32_t c = h[i];
-            if (c) atomicAdd(&counts[(size_t)td.blk * NBK + i], c);
+            h[i] = 0;
+            if (c) atomicAdd(&counts[(size_t)cur * NBK + i], c);
         }
         __syncthreads();
     }
@@ -302,10 +318,15 @@ __global__ void __launch_bounds__(256) k_bucket_stats(const uint32_t* __restrict
 // separate memory sector. Instead each block's consecutive fine buckets are
 // grouped into chunks of at most CHUNK_CAP rotations (greedy, one thread per
 // block); the scatter writes each tile's keys chunk by chunk in runs, and one
-// CTA per chunk then splits it by fine bucket in shared memory and sorts every
-// bucket by (K, i). A fine bucket larger than CHUNK_CAP is a chunk of its own
-// and goes to the overflow radix.
-constexpr uint32_t CHUNK_CAP = 3072;
+// CTA per chunk then sorts the whole chunk by (K, i) in shared memory and
+// names it. A chunk is a union of whole fine buckets, and a fine bucket is a
+// key interval, so a chunk holds every rotation of its key range: its first
+// rotation starts a group and its last ends one, and naming needs nothing
+// outside the chunk. A fine bucket larger than CHUNK_CAP is a chunk of its
+// own and goes to the overflow radix.
+constexpr int MS_NT = 256;                           // threads of the chunk sort
+constexpr int MS_IT = 13;                            // rotations per thread (odd: conflict-free strides)
+constexpr uint32_t CHUNK_CAP = MS_NT * MS_IT;        // 3328
 constexpr uint32_t MAXCH = 1024;  // chunks per block (blocks above (MAXCH - 2) * CHUNK_CAP / 2 go plain)
 
 struct ChunkTables {
@@ -331,17 +352,17 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
         __syncthreads();
         if (threadIdx.x == 0) {
             uint32_t nch = 0, nemit = 0, first = 0, len = 0;
-            auto close = [&](uint32_t last) {
+            auto close = [&]() {
                 if (nch < MAXCH) {
                     cb[nch] = st[first];
-                    if (len > 1) chunks[nemit++] = GroupDesc{bi.off + st[first], len, blk, first | (last << 16)};
+                    chunks[nemit++] = GroupDesc{bi.off + st[first], len, blk, 0u};
                 }
                 ++nch;
             };
             for (uint32_t b = 0; b < (uint32_t)NBK; ++b) {
                 const uint32_t sz = st[b + 1] - st[b];
                 if (sz > CHUNK_CAP) {
-                    if (len > 0) close(b);
+                    if (len > 0) close();
                     cm[b] = (uint16_t)min(nch, MAXCH - 1);
                     if (nch < MAXCH) cb[nch] = st[b];
                     ++nch;
@@ -351,7 +372,7 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
                     first = b + 1;
                     len = 0;
                 } else if (len + sz > CHUNK_CAP) {
-                    close(b);
+                    close();
                     first = b;
                     len = sz;
                     cm[b] = (uint16_t)min(nch, MAXCH - 1);
@@ -361,7 +382,7 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
                     cm[b] = (uint16_t)min(nch, MAXCH - 1);
                 }
             }
-            if (len > 0) close(NBK);
+            if (len > 0) close();
             if (nch > MAXCH) atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
             s_n[0] = nemit;
             s_n[1] = atomicAdd(&out.count[0], nemit);
@@ -402,8 +423,6 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
     uint32_t* stI = reinterpret_cast<uint32_t*>(stage + 4096 * 8);
     uint16_t* stC = reinterpret_cast<uint16_t*>(stage + CS_STAGE);
     __shared__ uint32_t scan_tmp[32];
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt = lanemask_lt();
     load_splitters(splitters, spl, first);
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         for (int i = threadIdx.x; i < (int)MAXCH; i += blockDim.x) lcount[i] = 0;
@@ -420,13 +439,11 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
             const uint32_t q = j * 256 + threadIdx.x;
             const bool valid = q < td.len;
             key[j] = valid ? pack8_smem(sb, q) : 0ull;
-            const uint32_t c = valid ? cmap[bucket_of(spl, first, key[j])] : MAXCH;
-            const uint32_t peers = __match_any_sync(0xffffffffu, c);
-            const int leader = __ffs(peers) - 1;
-            uint32_t base = 0;
-            if (valid && lane == leader) base = atomicAdd(&lcount[c], (uint32_t)__popc(peers));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            cs[j] = valid ? (c | ((base + __popc(peers & lt)) << 10)) : 0xffffffffu;
+            cs[j] = 0xffffffffu;
+            if (valid) {
+                const uint32_t c = cmap[bucket_of(spl, first, key[j])];
+                cs[j] = c | (atomicAdd(&lcount[c], 1u) << 10);
+            }
         }
         __syncthreads();
         // tile-local exclusive prefix over chunks and the global reservation
@@ -471,122 +488,123 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
     }
 }
 
-__device__ __forceinline__ bool pair_gt(uint64_t ak, uint32_t ai, uint64_t bk, uint32_t bi) {
-    return ak > bk || (ak == bk && ai > bi);
+__device__ __forceinline__ bool ki_less(uint64_t ak, uint32_t ai, uint64_t bk, uint32_t bi) {
+    return ak < bk || (ak == bk && ai < bi);
 }
 
-// Sorts (sk, si)[0..P) by (K, i), bitonic; NT threads cooperate.
-template <int NT>
-__device__ __forceinline__ void pair_bitonic(uint64_t* sk, uint32_t* si, uint32_t P, uint32_t t) {
-    for (uint32_t kk = 2; kk <= P; kk <<= 1) {
-        for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = t; i < P; i += NT) {
-                const uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t a = sk[i], b = sk[ixj];
-                    const uint32_t ai = si[i], bi = si[ixj];
-                    const bool up = (i & kk) == 0;
-                    if (pair_gt(a, ai, b, bi) == up) {
-                        sk[i] = b;
-                        sk[ixj] = a;
-                        si[i] = bi;
-                        si[ixj] = ai;
-                    }
+// Sorts sK/sI[0 .. CHUNK_CAP) by (K, i), ascending, with MS_NT threads: each
+// thread sorts its MS_IT consecutive entries in registers (odd-even
+// transposition), then log2(MS_NT) rounds merge pairs of sorted runs, each
+// thread producing MS_IT outputs from its merge-path split (binary search
+// on its output diagonal, then a sequential merge). All threads call; the
+// arrays hold CHUNK_CAP entries (pad with (~0, ~0), above every real pair).
+__device__ __forceinline__ void cta_merge_sort(uint64_t* sK, uint32_t* sI) {
+    const uint32_t t = threadIdx.x;
+    uint64_t k[MS_IT];
+    uint32_t v[MS_IT];
+#pragma unroll
+    for (int j = 0; j < MS_IT; ++j) {
+        k[j] = sK[t * MS_IT + j];
+        v[j] = sI[t * MS_IT + j];
+    }
+#pragma unroll
+    for (int r = 0; r < MS_IT; ++r) {
+#pragma unroll
+        for (int j = r & 1; j + 1 < MS_IT; j += 2) {
+            const bool sw = ki_less(k[j + 1], v[j + 1], k[j], v[j]);
+            const uint64_t a = sw ? k[j + 1] : k[j], b = sw ? k[j] : k[j + 1];
+            const uint32_t x = sw ? v[j + 1] : v[j], y = sw ? v[j] : v[j + 1];
+            k[j] = a;
+            k[j + 1] = b;
+            v[j] = x;
+            v[j + 1] = y;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < MS_IT; ++j) {
+        sK[t * MS_IT + j] = k[j];
+        sI[t * MS_IT + j] = v[j];
+    }
+    __syncthreads();
+    for (uint32_t m = 2; m <= (uint32_t)MS_NT; m <<= 1) {  // m threads per merged run of m * MS_IT
+        const uint32_t w = (m >> 1) * MS_IT;                // length of each input run
+        const uint32_t base = (t & ~(m - 1)) * MS_IT;
+        const uint32_t diag = (t & (m - 1)) * MS_IT;
+        const uint64_t* AK = sK + base;
+        const uint32_t* AI = sI + base;
+        const uint64_t* BK = AK + w;
+        const uint32_t* BI = AI + w;
+        uint32_t lo = diag > w ? diag - w : 0u, hi = diag < w ? diag : w;
+        while (lo < hi) {  // A entries among the first diag outputs (A first on ties)
+            const uint32_t mid = (lo + hi) >> 1;
+            if (!ki_less(BK[diag - 1 - mid], BI[diag - 1 - mid], AK[mid], AI[mid])) lo = mid + 1; else hi = mid;
+        }
+        uint32_t ia = lo, ib = diag - lo;
+        uint64_t ka = ia < w ? AK[ia] : 0ull, kb = ib < w ? BK[ib] : 0ull;
+        uint32_t va = ia < w ? AI[ia] : 0u, vb = ib < w ? BI[ib] : 0u;
+#pragma unroll
+        for (int j = 0; j < MS_IT; ++j) {
+            const bool take_a = ib >= w || (ia < w && !ki_less(kb, vb, ka, va));
+            k[j] = take_a ? ka : kb;
+            v[j] = take_a ? va : vb;
+            if (take_a) {
+                ++ia;
+                if (ia < w) {
+                    ka = AK[ia];
+                    va = AI[ia];
+                }
+            } else {
+                ++ib;
+                if (ib < w) {
+                    kb = BK[ib];
+                    vb = BI[ib];
                 }
             }
-            if constexpr (NT == 32) __syncwarp(); else __syncthreads();
         }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < MS_IT; ++j) {
+            sK[t * MS_IT + j] = k[j];
+            sI[t * MS_IT + j] = v[j];
+        }
+        __syncthreads();
     }
 }
 
-// One CTA per chunk: split by fine bucket in shared memory, sort every
-// bucket by (K, i) -- buckets up to 256 rotations by one warp each, larger
-// ones by the whole CTA -- and write the chunk back in order.
-constexpr size_t CHUNK_SORT_SMEM = 4096 * 12 + CHUNK_CAP * 12 + 4096 * 4;
+// One CTA per chunk: sort it by (K, i), write its SA, and name it (rank of
+// every rotation = block-local start of its group; groups of size > 1 go to
+// `bins` for the doubling rounds).
+constexpr size_t CHUNK_SORT_SMEM = (size_t)CHUNK_CAP * 12;
 
-__global__ void __launch_bounds__(256) k_chunk_sort(uint64_t* __restrict__ K, uint32_t* __restrict__ I,
-                                                    const uint32_t* __restrict__ starts,
-                                                    const uint64_t* __restrict__ spl_learned,
-                                                    const uint64_t* __restrict__ spl_flat,
-                                                    const uint32_t* __restrict__ route, Bins g) {
+__global__ void __launch_bounds__(MS_NT) k_chunk_sort_name(const uint64_t* __restrict__ K,
+                                                          uint32_t* __restrict__ SA,
+                                                          const BlockInfo* __restrict__ blocks, Bins chunks,
+                                                          uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* aK = reinterpret_cast<uint64_t*>(smem);                      // [4096] load buffer, then scratch
-    uint32_t* aI = reinterpret_cast<uint32_t*>(smem + 4096 * 8);
-    uint64_t* bK = reinterpret_cast<uint64_t*>(smem + 4096 * 12);          // [CHUNK_CAP] split by bucket
-    uint32_t* bI = reinterpret_cast<uint32_t*>(smem + 4096 * 12 + CHUNK_CAP * 8);
-    uint32_t* fend = reinterpret_cast<uint32_t*>(smem + 4096 * 12 + CHUNK_CAP * 12);  // [4096]
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t count = bin_count(g, 0);
+    uint64_t* sK = reinterpret_cast<uint64_t*>(smem);
+    uint32_t* sI = reinterpret_cast<uint32_t*>(smem + (size_t)CHUNK_CAP * 8);
+    __shared__ GroupDesc ebuf[MS_NT / 32][NCLS * EMIT_BUF];
+    if (ld_volatile(&ctrl[CTRL_ERR])) return;  // an earlier stage failed: the chunks are not permutations
+    WarpEmitter em;
+    em.init(ebuf[threadIdx.x >> 5]);
+    const uint32_t count = bin_count(chunks, 0);
     for (uint32_t c = blockIdx.x; c < count; c += gridDim.x) {
-        const GroupDesc gd = g.list[0][c];
-        const uint32_t f0 = gd.pad & 0xffffu, f1 = gd.pad >> 16;  // fine buckets [f0, f1)
-        const uint32_t nf = f1 - f0;
-        const uint32_t* st = starts + (size_t)gd.blk * NBK;
-        const uint64_t* spl = route[gd.blk] == 2u ? spl_flat : spl_learned;
-        const uint32_t base = st[f0];
-        for (uint32_t i = threadIdx.x; i < gd.len; i += blockDim.x) {
-            aK[i] = K[gd.start + i];
-            aI[i] = I[gd.start + i];
-        }
-        for (uint32_t f = threadIdx.x; f < nf; f += blockDim.x) fend[f] = st[f0 + f] - base;  // cursors at starts
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < gd.len; i += blockDim.x) {
-            const uint64_t k = aK[i];
-            uint32_t lo = f0, hi = f1 - 1;  // bucket = f0 + #{j in [f0, f1 - 1) : spl[j] <= k}
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (spl[mid] <= k) lo = mid + 1; else hi = mid;
-            }
-            const uint32_t pos = atomicAdd(&fend[lo - f0], 1u);
-            bK[pos] = k;
-            bI[pos] = aI[i];
-        }
-        __syncthreads();  // fend[f] is now the end of bucket f0 + f
-        for (uint32_t f = warp; f < nf; f += blockDim.x / 32) {
-            const uint32_t s0 = f == 0 ? 0u : fend[f - 1], s1 = fend[f];
-            const uint32_t m = s1 - s0;
-            if (m < 2 || m > 256) continue;
-            uint64_t* wk = aK + warp * 256;
-            uint32_t* wi = aI + warp * 256;
-            uint32_t P = 2;
-            while (P < m) P <<= 1;
-            for (uint32_t i = lane; i < P; i += 32) {
-                wk[i] = i < m ? bK[s0 + i] : ~0ull;
-                wi[i] = i < m ? bI[s0 + i] : ~0u;
-            }
-            __syncwarp();
-            pair_bitonic<32>(wk, wi, P, lane);
-            for (uint32_t i = lane; i < m; i += 32) {
-                bK[s0 + i] = wk[i];
-                bI[s0 + i] = wi[i];
-            }
-            __syncwarp();
+        const GroupDesc gd = chunks.list[0][c];
+        const BlockInfo bi = blocks[gd.blk];
+        const uint32_t len = min(gd.len, CHUNK_CAP);
+        for (uint32_t i = threadIdx.x; i < CHUNK_CAP; i += MS_NT) {
+            const bool in = i < len;
+            sK[i] = in ? K[gd.start + i] : ~0ull;
+            sI[i] = in ? SA[gd.start + i] : ~0u;
         }
         __syncthreads();
-        for (uint32_t f = 0; f < nf; ++f) {  // CTA-uniform: buckets of 257..CHUNK_CAP rotations
-            const uint32_t s0 = f == 0 ? 0u : fend[f - 1], s1 = fend[f];
-            const uint32_t m = s1 - s0;
-            if (m <= 256) continue;
-            uint32_t P = 512;
-            while (P < m) P <<= 1;
-            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-                aK[i] = i < m ? bK[s0 + i] : ~0ull;
-                aI[i] = i < m ? bI[s0 + i] : ~0u;
-            }
-            __syncthreads();
-            pair_bitonic<256>(aK, aI, P, threadIdx.x);
-            for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-                bK[s0 + i] = aK[i];
-                bI[s0 + i] = aI[i];
-            }
-            __syncthreads();
-        }
-        for (uint32_t i = threadIdx.x; i < gd.len; i += blockDim.x) {
-            K[gd.start + i] = bK[i];
-            I[gd.start + i] = bI[i];
-        }
+        cta_merge_sort(sK, sI);
+        for (uint32_t i = threadIdx.x; i < len; i += MS_NT) SA[gd.start + i] = sI[i];
+        name_tile<uint64_t, true>(sK, len, gd.start, gd.start, gd.start + len, sI, bi, gd.blk, rank, bins, bi.n > 8u,
+                                  em, &ctrl[CTRL_ERR]);
         __syncthreads();
     }
+    em.finish(bins, &ctrl[CTRL_ERR]);
 }
 
 __global__ void k_zero_rows_routed(uint32_t* __restrict__ counts, const uint32_t* __restrict__ route, uint32_t nb,
@@ -686,7 +704,8 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
                              (int)CHUNK_SCATTER_SMEM);
         cudaFuncSetAttribute((void*)k_chunk_scatter<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)CHUNK_SCATTER_SMEM);
-        cudaFuncSetAttribute((void*)k_chunk_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CHUNK_SORT_SMEM);
+        cudaFuncSetAttribute((void*)k_chunk_sort_name, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CHUNK_SORT_SMEM);
         return true;
     }();
     (void)attr;
@@ -697,8 +716,11 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
 
     // 1. count buckets per block, 2. per-block overflow statistics
     CKL(cudaMemsetAsync(p->bucket_count, 0, sizeof(uint32_t) * NBK * nb, st));
-    k_bucket_count<<<std::max(1, std::min<int>(nt, sms * 3)), 256, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles0, nt,
-                                                                                     p->splitters, p->bucket_count);
+    const auto count_grid = [&](uint32_t n_t) {
+        return std::max(1, std::min<int>((n_t + COUNT_SPAN - 1) / COUNT_SPAN, sms * 4));
+    };
+    k_bucket_count<<<count_grid(nt), 256, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles0, nt, p->splitters,
+                                                            p->bucket_count);
     k_bucket_stats<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, nb, p->bstats);
     CKL(cudaGetLastError());
     CKL(cudaMemcpyAsync(p->h_bstats, p->bstats, sizeof(unsigned long long) * 5 * nb, cudaMemcpyDeviceToHost, st));
@@ -747,8 +769,8 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
         CKL(cudaMemcpyAsync(p->route, p->h_route, sizeof(uint32_t) * nb, cudaMemcpyHostToDevice, st));
         CKL(cudaMemcpyAsync(p->tiles_aux, p->h_tiles_aux, sizeof(TileDesc) * ntc, cudaMemcpyHostToDevice, st));
         k_zero_rows_routed<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->route, nb, 2u);
-        k_bucket_count<<<std::max(1, std::min<int>(ntc, sms * 3)), 256, COUNT_SMEM, st>>>(
-            d_in, p->blocks, p->tiles_aux, ntc, p->splitters_flat, p->bucket_count);
+        k_bucket_count<<<count_grid(ntc), 256, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles_aux, ntc,
+                                                                 p->splitters_flat, p->bucket_count);
         k_bucket_stats<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, nb, p->bstats);
         CKL(cudaGetLastError());
         CKL(cudaMemcpyAsync(p->h_bstats, p->bstats, sizeof(unsigned long long) * 5 * nb, cudaMemcpyDeviceToHost, st));
@@ -786,7 +808,14 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
     const TileDesc* tilesL = p->tiles_aux + ntp;
     const TileDesc* tilesF = p->tiles_aux + ntp + ntl;
 
-    // 4a. plain-routed blocks: the first sort of the plain path, ending in buffer 0
+    p->sa = p->vals[0];
+    p->key2 = p->vals[1];
+    p->kA = reinterpret_cast<uint32_t*>(p->keys[1]);
+    p->vA = p->kA + p->cap_n;
+    p->kB = reinterpret_cast<uint32_t*>(p->keys[0]);
+    p->vB = p->kB + p->cap_n;
+
+    // 4a. plain-routed blocks: the first sort of the plain path, ending in buffer 0, and its naming
     const int rb = p->rbits, RADIX = 1 << rb;
     if (ntp) {
         const int P = (64 + rb - 1) / rb;
@@ -826,6 +855,8 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
             p->stats.radix_launches++;
             p->stats.radix_keys += plain_keys;
         }
+        CKL(launch_name_initial(p->keys[0], p->vals[0], p->blocks, tilesP, ntp, p->rank, bins_of(p, 0), ctrl, st));
+        p->stats.kernel_launches++;
     }
 
     // 4b. bucket-routed blocks: scan, scatter, per-bucket sorts
@@ -852,8 +883,13 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
         };
         scatter(tilesL, ntl, p->splitters);
         scatter(tilesF, ntf, p->splitters_flat);
-        k_chunk_sort<<<sms * 2, 256, CHUNK_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->bucket_count, p->splitters,
-                                                            p->splitters_flat, p->route, aux);
+        static const int sort_ctas = [] {
+            int per_sm = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_sort_name, MS_NT, CHUNK_SORT_SMEM);
+            return std::max(1, per_sm);
+        }();
+        k_chunk_sort_name<<<sms * sort_ctas, MS_NT, CHUNK_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks, aux,
+                                                                          p->rank, bins_of(p, 0), ctrl);
         CKL(cudaGetLastError());
         p->stats.kernel_launches += 2;
 
@@ -897,16 +933,15 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
             CKL(cudaGetLastError());
             p->stats.kernel_launches++;
         }
+        // overflow buckets are whole key ranges too: name them inside their own bounds
+        CKL(launch_name_segments(p->keys[0], p->vals[0], p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, p->rank,
+                                 bins_of(p, 0), ctrl, st));
+        p->stats.kernel_launches++;
     }
 
-    // 5. naming, doubling, L gather -- as on the plain path, from buffer 0
-    p->sa = p->vals[0];
-    p->key2 = p->vals[1];
-    p->kA = reinterpret_cast<uint32_t*>(p->keys[1]);
-    p->vA = p->kA + p->cap_n;
-    p->kB = reinterpret_cast<uint32_t*>(p->keys[0]);
-    p->vB = p->kB + p->cap_n;
-    if ((s = enqueue_naming(p, p->keys[0], st)) != BWT_OK) return s;
+    // 5. prefix doubling and the L gather, as on the plain path, from buffer 0
+    //    (every block is named: plain-routed ones after their radix, the
+    //    bucketed ones by the chunk sort and the overflow naming)
     if ((s = run_doubling_host_loop(p, st)) != BWT_OK) return s;
     CKL(launch_gather_L(d_in, p->sa, p->blocks, p->tiles0, p->ntiles0, d_L, d_primary, st));
     p->stats.kernel_launches++;
