@@ -181,11 +181,14 @@ namespace {
 constexpr int NBK = BWT_BUCKETS;
 constexpr int NSP = BWT_SPLITTERS;
 
-// Bucket of a key: #{j : spl[j] <= key}. first[c] = #{j : spl[j] < c << 56}
-// narrows the search to the splitters that share the key's top byte (the
+// Bucket of a key: #{j : spl[j] <= key}. first[c] = #{j : spl[j] < c << 52}
+// narrows the search to the splitters that share the key's top 12 bits (the
 // ones below all count, the ones above none).
+constexpr int IDX_BITS = 12;
+constexpr int IDX_CELLS = 1 << IDX_BITS;
+
 __device__ __forceinline__ uint32_t bucket_of(const uint64_t* spl, const uint16_t* first, uint64_t key) {
-    const uint32_t c = (uint32_t)(key >> 56);
+    const uint32_t c = (uint32_t)(key >> (64 - IDX_BITS));
     uint32_t lo = first[c], hi = first[c + 1];
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
@@ -194,12 +197,12 @@ __device__ __forceinline__ uint32_t bucket_of(const uint64_t* spl, const uint16_
     return lo;
 }
 
-// Loads the splitters into shared memory and builds the top-byte index.
+// Loads the splitters into shared memory and builds the top-12-bit index.
 __device__ __forceinline__ void load_splitters(const uint64_t* __restrict__ splitters, uint64_t* spl, uint16_t* first) {
     for (int i = threadIdx.x; i < NSP; i += blockDim.x) spl[i] = splitters[i];
     __syncthreads();
-    for (int c = threadIdx.x; c < 256; c += blockDim.x) {
-        const uint64_t x = (uint64_t)c << 56;
+    for (int c = threadIdx.x; c < IDX_CELLS; c += blockDim.x) {
+        const uint64_t x = (uint64_t)c << (64 - IDX_BITS);
         uint32_t lo = 0, hi = NSP;
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
@@ -207,7 +210,7 @@ __device__ __forceinline__ void load_splitters(const uint64_t* __restrict__ spli
         }
         first[c] = (uint16_t)lo;
     }
-    if (threadIdx.x == 0) first[256] = (uint16_t)NSP;
+    if (threadIdx.x == 0) first[IDX_CELLS] = (uint16_t)NSP;
     __syncthreads();
 }
 
@@ -221,21 +224,34 @@ __device__ __forceinline__ void load_tile_bytes(const uint8_t* S, BlockInfo bi, 
     }
 }
 
-constexpr size_t SPL_BYTES = 4096 * 8 + 528;  // splitters + top-byte index (257 u16, padded)
+constexpr size_t SPL_BYTES = 4096 * 8 + (IDX_CELLS + 8) * 2;  // splitters + top-12-bit index (padded)
 constexpr size_t CNT_BYTES = 4096 * 4;
 constexpr size_t TILE_BYTES = 4096 + 16;
 constexpr size_t COUNT_SMEM = SPL_BYTES + CNT_BYTES + TILE_BYTES;
 
-// A CTA counts COUNT_SPAN consecutive tiles into its shared histogram before
-// adding it to the block's row (one global atomic per non-empty bucket and
-// span instead of per tile); a span that crosses into the next block
-// flushes at the boundary.
-constexpr uint32_t COUNT_SPAN = 16;
+// Counts every rotation in two bucketings at once -- the learned splitters
+// and equal-width buckets (the top 12 key bits) -- and stores its learned
+// bucket in fb (u16 per rotation) for the scatter. The two histograms share
+// one shared-memory word per bucket (learned count in the low half, equal-
+// width count in the high half), so a CTA counts at most 65535 rotations
+// (`span` tiles) before it adds them to the block's rows: one global atomic
+// per non-empty bucket and span; a span that crosses into the next block
+// flushes at the boundary. counts: [2][block][4096] (learned rows, then
+// equal-width rows).
+__device__ __forceinline__ void flush_counts(uint32_t* h, uint32_t* __restrict__ counts, uint32_t nb, uint32_t blk) {
+    for (int i = threadIdx.x; i < NBK; i += blockDim.x) {
+        const uint32_t c = h[i];
+        h[i] = 0;
+        if (c & 0xffffu) atomicAdd(&counts[(size_t)blk * NBK + i], c & 0xffffu);
+        if (c >> 16) atomicAdd(&counts[((size_t)nb + blk) * NBK + i], c >> 16);
+    }
+}
 
 __global__ void __launch_bounds__(256) k_bucket_count(const uint8_t* __restrict__ S, const BlockInfo* __restrict__ blocks,
                                                       const TileDesc* __restrict__ tiles, uint32_t ntiles,
-                                                      const uint64_t* __restrict__ splitters,
-                                                      uint32_t* __restrict__ counts) {
+                                                      uint32_t span, const uint64_t* __restrict__ splitters,
+                                                      uint32_t nb, uint32_t* __restrict__ counts,
+                                                      uint16_t* __restrict__ fb) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* spl = reinterpret_cast<uint64_t*>(smem);
     uint16_t* first = reinterpret_cast<uint16_t*>(smem + 4096 * 8);
@@ -243,32 +259,29 @@ __global__ void __launch_bounds__(256) k_bucket_count(const uint8_t* __restrict_
     uint8_t* sb = smem + SPL_BYTES + CNT_BYTES;
     load_splitters(splitters, spl, first);
     for (int i = threadIdx.x; i < NBK; i += blockDim.x) h[i] = 0;
-    const uint32_t nspan = (ntiles + COUNT_SPAN - 1) / COUNT_SPAN;
+    const uint32_t nspan = (ntiles + span - 1) / span;
     for (uint32_t s = blockIdx.x; s < nspan; s += gridDim.x) {
-        const uint32_t t0 = s * COUNT_SPAN, t1 = min(ntiles, t0 + COUNT_SPAN);
+        const uint32_t t0 = s * span, t1 = min(ntiles, t0 + span);
         uint32_t cur = tiles[t0].blk;
         for (uint32_t t = t0; t < t1; ++t) {
             const TileDesc td = tiles[t];
             if (td.blk != cur) {  // CTA-uniform; the histogram is complete (synced after the last tile)
-                for (int i = threadIdx.x; i < NBK; i += blockDim.x) {
-                    const uint32_t c = h[i];
-                    h[i] = 0;
-                    if (c) atomicAdd(&counts[(size_t)cur * NBK + i], c);
-                }
+                flush_counts(h, counts, nb, cur);
                 cur = td.blk;
             }
             const BlockInfo bi = blocks[td.blk];
             load_tile_bytes(S, bi, td.start - bi.off, td.len, sb);
             __syncthreads();
-            for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x)
-                atomicAdd(&h[bucket_of(spl, first, pack8_smem(sb, q))], 1u);
+            for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) {
+                const uint64_t key = pack8_smem(sb, q);
+                const uint32_t b = bucket_of(spl, first, key);
+                fb[td.start + q] = (uint16_t)b;
+                atomicAdd(&h[b], 1u);
+                atomicAdd(&h[(uint32_t)(key >> 52)], 1u << 16);
+            }
             __syncthreads();
         }
-        for (int i = threadIdx.x; i < NBK; i += blockDim.x) {
-            const uint32_t c = h[i];
-            h[i] = 0;
-            if (c) atomicAdd(&counts[(size_t)cur * NBK + i], c);
-        }
+        flush_counts(h, counts, nb, cur);
         __syncthreads();
     }
 }
@@ -402,46 +415,47 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
     }
 }
 
-constexpr size_t CS_STAGE = 4096 * 12;  // staged keys and indexes of one tile (aliases its bytes)
-constexpr size_t CHUNK_SCATTER_SMEM = SPL_BYTES + 3 * MAXCH * 4 + CS_STAGE + 4096 * 2;
+constexpr size_t CS_STAGE = 4096 * 12;  // staged keys and indexes of one tile
+constexpr size_t CHUNK_SCATTER_SMEM = 3 * MAXCH * 4 + TILE_BYTES + CS_STAGE + 4096 * 2;
 
+// Scatters the tiles of bucketed blocks to their chunks: a rotation's bucket
+// is its stored learned bucket (fb) or, in blocks routed to equal-width
+// buckets, its top 12 key bits; its chunk comes from the block's chunk map.
+// The tile is staged in shared memory grouped by chunk, so each chunk's
+// share is written as one run at a slot range reserved with one atomic.
 template <int ITEMS>
 __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict__ S,
                                                        const BlockInfo* __restrict__ blocks,
                                                        const TileDesc* __restrict__ tiles, uint32_t ntiles,
-                                                       const uint64_t* __restrict__ splitters, ChunkTables ct,
+                                                       const uint16_t* __restrict__ fb,
+                                                       const uint32_t* __restrict__ route, ChunkTables ct,
                                                        uint64_t* __restrict__ K, uint32_t* __restrict__ I) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* spl = reinterpret_cast<uint64_t*>(smem);
-    uint16_t* first = reinterpret_cast<uint16_t*>(smem + 4096 * 8);
-    uint32_t* lcount = reinterpret_cast<uint32_t*>(smem + SPL_BYTES);
+    uint32_t* lcount = reinterpret_cast<uint32_t*>(smem);
     uint32_t* pre = lcount + MAXCH;
     uint32_t* gbase = pre + MAXCH;
-    unsigned char* stage = reinterpret_cast<unsigned char*>(gbase + MAXCH);
-    uint8_t* sb = stage;                                         // tile bytes (consumed before staging)
-    uint64_t* stK = reinterpret_cast<uint64_t*>(stage);          // staged keys
-    uint32_t* stI = reinterpret_cast<uint32_t*>(stage + 4096 * 8);
-    uint16_t* stC = reinterpret_cast<uint16_t*>(stage + CS_STAGE);
+    uint8_t* sb = reinterpret_cast<uint8_t*>(gbase + MAXCH);
+    uint64_t* stK = reinterpret_cast<uint64_t*>(sb + TILE_BYTES);
+    uint32_t* stI = reinterpret_cast<uint32_t*>(sb + TILE_BYTES + 4096 * 8);
+    uint16_t* stC = reinterpret_cast<uint16_t*>(sb + TILE_BYTES + CS_STAGE);
     __shared__ uint32_t scan_tmp[32];
-    load_splitters(splitters, spl, first);
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         for (int i = threadIdx.x; i < (int)MAXCH; i += blockDim.x) lcount[i] = 0;
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
         const uint32_t i0 = td.start - bi.off;
+        const bool flat = route[td.blk] == 2u;
         const uint16_t* cmap = ct.cmap + (size_t)td.blk * NBK;
         load_tile_bytes(S, bi, i0, td.len, sb);
         __syncthreads();
-        uint64_t key[ITEMS];
         uint32_t cs[ITEMS];  // chunk (low 10 bits) | slot within the tile's share of the chunk << 10
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const uint32_t q = j * 256 + threadIdx.x;
-            const bool valid = q < td.len;
-            key[j] = valid ? pack8_smem(sb, q) : 0ull;
             cs[j] = 0xffffffffu;
-            if (valid) {
-                const uint32_t c = cmap[bucket_of(spl, first, key[j])];
+            if (q < td.len) {
+                const uint32_t b = flat ? (uint32_t)(pack8_smem(sb, q) >> 52) : (uint32_t)fb[td.start + q];
+                const uint32_t c = cmap[b];
                 cs[j] = c | (atomicAdd(&lcount[c], 1u) << 10);
             }
         }
@@ -469,10 +483,11 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             if (cs[j] != 0xffffffffu) {
+                const uint32_t q = j * 256 + threadIdx.x;
                 const uint32_t c = cs[j] & (MAXCH - 1);
                 const uint32_t pos = pre[c] + (cs[j] >> 10);
-                stK[pos] = key[j];
-                stI[pos] = i0 + j * 256 + threadIdx.x;
+                stK[pos] = pack8_smem(sb, q);
+                stI[pos] = i0 + q;
                 stC[pos] = (uint16_t)c;
             }
         }
@@ -537,7 +552,9 @@ __device__ __forceinline__ void cta_merge_sort(uint64_t* sK, uint32_t* sI) {
         uint32_t lo = diag > w ? diag - w : 0u, hi = diag < w ? diag : w;
         while (lo < hi) {  // A entries among the first diag outputs (A first on ties)
             const uint32_t mid = (lo + hi) >> 1;
-            if (!ki_less(BK[diag - 1 - mid], BI[diag - 1 - mid], AK[mid], AI[mid])) lo = mid + 1; else hi = mid;
+            const uint64_t a = AK[mid], b = BK[diag - 1 - mid];
+            const bool a_first = a != b ? a < b : AI[mid] <= BI[diag - 1 - mid];
+            if (a_first) lo = mid + 1; else hi = mid;
         }
         uint32_t ia = lo, ib = diag - lo;
         uint64_t ka = ia < w ? AK[ia] : 0ull, kb = ib < w ? BK[ib] : 0ull;
@@ -607,11 +624,13 @@ __global__ void __launch_bounds__(MS_NT) k_chunk_sort_name(const uint64_t* __res
     em.finish(bins, &ctrl[CTRL_ERR]);
 }
 
-__global__ void k_zero_rows_routed(uint32_t* __restrict__ counts, const uint32_t* __restrict__ route, uint32_t nb,
-                                   uint32_t code) {
+// Blocks routed to equal-width buckets (route 2) take their equal-width row
+// as their bucket row.
+__global__ void k_select_rows(uint32_t* __restrict__ counts, const uint32_t* __restrict__ route, uint32_t nb) {
     for (uint32_t blk = blockIdx.x; blk < nb; blk += gridDim.x)
-        if (route[blk] == code)
-            for (int i = threadIdx.x; i < NBK; i += blockDim.x) counts[(size_t)blk * NBK + i] = 0;
+        if (route[blk] == 2u)
+            for (int i = threadIdx.x; i < NBK; i += blockDim.x)
+                counts[(size_t)blk * NBK + i] = counts[((size_t)nb + blk) * NBK + i];
 }
 
 // Per overflow segment: digit histograms of PI index passes then PK key passes.
@@ -673,12 +692,12 @@ int bits_needed(uint32_t max_value) {
 bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
     const size_t nbk = (size_t)p->cap_b * NBK;
     if (!p->splitters) CKL(cudaMalloc(&p->splitters, sizeof(uint64_t) * NSP));
-    if (!p->bucket_count) CKL(cudaMalloc(&p->bucket_count, sizeof(uint32_t) * nbk));
+    if (!p->bucket_count) CKL(cudaMalloc(&p->bucket_count, sizeof(uint32_t) * 2 * nbk));
     if (!p->bucket_cursor) CKL(cudaMalloc(&p->bucket_cursor, sizeof(uint32_t) * nbk));
     if (!p->chunk_map) CKL(cudaMalloc(&p->chunk_map, sizeof(uint16_t) * nbk));
     if (!p->chunk_base) CKL(cudaMalloc(&p->chunk_base, sizeof(uint32_t) * nbk));
     if (!p->route) CKL(cudaMalloc(&p->route, sizeof(uint32_t) * p->cap_b));
-    if (!p->bstats) CKL(cudaMalloc(&p->bstats, sizeof(unsigned long long) * 5 * p->cap_b));
+    if (!p->bstats) CKL(cudaMalloc(&p->bstats, sizeof(unsigned long long) * 10 * p->cap_b));
     if (!p->tiles_aux) CKL(cudaMalloc(&p->tiles_aux, sizeof(TileDesc) * p->cap_tiles0));
     if (!p->splitters_flat) {
         std::vector<uint64_t> flat(NSP);
@@ -687,7 +706,7 @@ bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
         CKL(cudaMemcpy(p->splitters_flat, flat.data(), sizeof(uint64_t) * NSP, cudaMemcpyHostToDevice));
     }
     if (!p->h_route) CKL(cudaMallocHost(&p->h_route, sizeof(uint32_t) * p->cap_b));
-    if (!p->h_bstats) CKL(cudaMallocHost(&p->h_bstats, sizeof(unsigned long long) * 5 * p->cap_b));
+    if (!p->h_bstats) CKL(cudaMallocHost(&p->h_bstats, sizeof(unsigned long long) * 10 * p->cap_b));
     if (!p->h_tiles_aux) CKL(cudaMallocHost(&p->h_tiles_aux, sizeof(TileDesc) * p->cap_tiles0));
     return BWT_OK;
 }
@@ -714,34 +733,49 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
     uint32_t* ctrl = p->ctrl;
     if ((s = reset_ctrl(p, st)) != BWT_OK) return s;
 
-    // 1. count buckets per block, 2. per-block overflow statistics
-    CKL(cudaMemsetAsync(p->bucket_count, 0, sizeof(uint32_t) * NBK * nb, st));
-    const auto count_grid = [&](uint32_t n_t) {
-        return std::max(1, std::min<int>((n_t + COUNT_SPAN - 1) / COUNT_SPAN, sms * 4));
-    };
-    k_bucket_count<<<count_grid(nt), 256, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles0, nt, p->splitters,
-                                                            p->bucket_count);
-    k_bucket_stats<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, nb, p->bstats);
+    // 1. count both bucketings per block and store every rotation's learned
+    //    bucket (in the u16 view of keys[1], free until the scatter has run),
+    // 2. per-block statistics of both
+    uint16_t* fb = reinterpret_cast<uint16_t*>(p->keys[1]);
+    CKL(cudaMemsetAsync(p->bucket_count, 0, sizeof(uint32_t) * 2 * NBK * nb, st));
+    {
+        const uint32_t span_max = 65535u / (uint32_t)p->tile;  // packed 16-bit counts per span
+        const uint32_t span = std::max(1u, std::min(span_max, nt / (uint32_t)(sms * 8)));
+        const int grid = std::max(1, std::min<int>((nt + span - 1) / span, sms * 3));
+        k_bucket_count<<<grid, 256, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles0, nt, span, p->splitters, nb,
+                                                      p->bucket_count, fb);
+    }
+    k_bucket_stats<<<std::min<uint32_t>(2 * nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, 2 * nb, p->bstats);
     CKL(cudaGetLastError());
-    CKL(cudaMemcpyAsync(p->h_bstats, p->bstats, sizeof(unsigned long long) * 5 * nb, cudaMemcpyDeviceToHost, st));
+    CKL(cudaMemcpyAsync(p->h_bstats, p->bstats, sizeof(unsigned long long) * 10 * nb, cudaMemcpyDeviceToHost, st));
     CKL(cudaStreamSynchronize(st));
-    p->stats.kernel_launches += 3;
+    p->stats.kernel_launches += 2;
 
     // 3. route each block: learned buckets (0) if their overflow holds at most a
     //    quarter of the block; else equal-width buckets (2) if those do; else
     //    the plain radix (1)
-    std::vector<uint32_t> cand;
-    for (uint32_t b = 0; b < nb; ++b) {
-        const unsigned long long* bs = p->h_bstats + 5 * b;
-        const bool too_big = (uint64_t)p->h_blocks[b].n * 2 > (uint64_t)(MAXCH - 2) * CHUNK_CAP;
-        const bool over = too_big || bs[0] * 4 > p->h_blocks[b].n;
-        p->h_route[b] = over ? 2u : 0u;
-        if (over) cand.push_back(b);
-        p->stats.max_bucket = std::max<uint32_t>(p->stats.max_bucket, (uint32_t)bs[2]);
-        p->stats.bucket_sq_sum += bs[3];
-        p->stats.buckets_nonempty += bs[4];
-    }
     const uint32_t T = (uint32_t)p->tile;
+    uint64_t plain_keys = 0;
+    for (uint32_t b = 0; b < nb; ++b) {
+        const unsigned long long* bl = p->h_bstats + 5 * b;         // learned
+        const unsigned long long* bf = p->h_bstats + 5 * (nb + b);  // equal-width
+        const uint64_t n = p->h_blocks[b].n;
+        const bool too_big = n * 2 > (uint64_t)(MAXCH - 2) * CHUNK_CAP;
+        const uint32_t r = too_big ? 1u : bl[0] * 4 <= n ? 0u : bf[0] * 4 <= n ? 2u : 1u;
+        p->h_route[b] = r;
+        p->stats.max_bucket = std::max<uint32_t>(p->stats.max_bucket, (uint32_t)bl[2]);
+        p->stats.bucket_sq_sum += bl[3];
+        p->stats.buckets_nonempty += bl[4];
+        if (r == 1u) {
+            plain_keys += n;
+            p->stats.blocks_routed_plain++;
+        } else {
+            const unsigned long long* bs = r == 2u ? bf : bl;
+            if (r == 2u) p->stats.blocks_routed_flat++;
+            p->stats.buckets_overflowed += bs[1];
+            p->stats.keys_overflowed += bs[0];
+        }
+    }
     auto build_tiles = [&](uint32_t code, uint32_t base, uint32_t* count) {
         uint32_t nt_ = 0;
         for (uint32_t b = 0; b < nb; ++b) {
@@ -763,36 +797,6 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
         }
         *count = nt_;
     };
-    if (!cand.empty()) {
-        uint32_t ntc = 0;
-        build_tiles(2u, 0, &ntc);
-        CKL(cudaMemcpyAsync(p->route, p->h_route, sizeof(uint32_t) * nb, cudaMemcpyHostToDevice, st));
-        CKL(cudaMemcpyAsync(p->tiles_aux, p->h_tiles_aux, sizeof(TileDesc) * ntc, cudaMemcpyHostToDevice, st));
-        k_zero_rows_routed<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->route, nb, 2u);
-        k_bucket_count<<<count_grid(ntc), 256, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles_aux, ntc,
-                                                                 p->splitters_flat, p->bucket_count);
-        k_bucket_stats<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, nb, p->bstats);
-        CKL(cudaGetLastError());
-        CKL(cudaMemcpyAsync(p->h_bstats, p->bstats, sizeof(unsigned long long) * 5 * nb, cudaMemcpyDeviceToHost, st));
-        CKL(cudaStreamSynchronize(st));
-        p->stats.kernel_launches += 3;
-        for (uint32_t b : cand)
-            if (p->h_bstats[5 * b] * 4 > p->h_blocks[b].n ||
-                (uint64_t)p->h_blocks[b].n * 2 > (uint64_t)(MAXCH - 2) * CHUNK_CAP)
-                p->h_route[b] = 1u;
-    }
-    uint64_t plain_keys = 0;
-    for (uint32_t b = 0; b < nb; ++b) {
-        const unsigned long long* bs = p->h_bstats + 5 * b;
-        if (p->h_route[b] == 1u) {
-            plain_keys += p->h_blocks[b].n;
-            p->stats.blocks_routed_plain++;
-        } else {
-            if (p->h_route[b] == 2u) p->stats.blocks_routed_flat++;
-            p->stats.buckets_overflowed += bs[1];
-            p->stats.keys_overflowed += bs[0];
-        }
-    }
     // sub-tables (first-tile indices relative to each sub-table)
     uint32_t ntp = 0, ntl = 0, ntf = 0;
     build_tiles(1u, 0, &ntp);
@@ -805,8 +809,6 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
     p->h_aux[1] = ntb;
     CKL(cudaMemcpyAsync(ctrl + CTRL_AUX0, p->h_aux, sizeof(uint32_t) * 2, cudaMemcpyHostToDevice, st));
     const TileDesc* tilesP = p->tiles_aux;
-    const TileDesc* tilesL = p->tiles_aux + ntp;
-    const TileDesc* tilesF = p->tiles_aux + ntp + ntl;
 
     p->sa = p->vals[0];
     p->key2 = p->vals[1];
@@ -815,7 +817,32 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
     p->kB = reinterpret_cast<uint32_t*>(p->keys[0]);
     p->vB = p->kB + p->cap_n;
 
-    // 4a. plain-routed blocks: the first sort of the plain path, ending in buffer 0, and its naming
+    // 4a. bucketed blocks: bucket starts, chunk plan and scatter (the scatter
+    //     consumes fb, so it runs before the plain passes reuse keys[1])
+    Bins aux = bins_of(p, 1);
+    CKL(cudaMemsetAsync(aux.count, 0, sizeof(uint32_t) * NCLS, st));
+    if (ntb) {
+        k_select_rows<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->route, nb);
+        CKL(launch_scan_rows(p->bucket_count, NBK, nullptr, 0, nb, nb, st));  // counts -> starts in place
+        ChunkTables ct{p->chunk_map, p->chunk_base, p->bucket_cursor};
+        k_chunk_plan<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->blocks, p->route, nb, ct, aux,
+                                                                    ctrl);
+        const TileDesc* tilesB = p->tiles_aux + ntp;
+        const int g = std::max(1, std::min<int>(ntb, sms * 3));
+        if (T <= 1024)
+            k_chunk_scatter<4><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, fb, p->route, ct,
+                                                                   p->keys[0], p->vals[0]);
+        else if (T <= 2048)
+            k_chunk_scatter<8><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, fb, p->route, ct,
+                                                                   p->keys[0], p->vals[0]);
+        else
+            k_chunk_scatter<16><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, fb, p->route, ct,
+                                                                    p->keys[0], p->vals[0]);
+        CKL(cudaGetLastError());
+        p->stats.kernel_launches += 4;
+    }
+
+    // 4b. plain-routed blocks: the first sort of the plain path, ending in buffer 0, and its naming
     const int rb = p->rbits, RADIX = 1 << rb;
     if (ntp) {
         const int P = (64 + rb - 1) / rb;
@@ -859,30 +886,8 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
         p->stats.kernel_launches++;
     }
 
-    // 4b. bucket-routed blocks: scan, scatter, per-bucket sorts
-    Bins aux = bins_of(p, 1);
-    CKL(cudaMemsetAsync(aux.count, 0, sizeof(uint32_t) * NCLS, st));
+    // 4c. bucketed blocks: chunk sorts with naming, then the overflow buckets
     if (ntb) {
-        CKL(launch_scan_rows(p->bucket_count, NBK, nullptr, 0, nb, nb, st));  // counts -> starts in place
-        ChunkTables ct{p->chunk_map, p->chunk_base, p->bucket_cursor};
-        k_chunk_plan<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->blocks, p->route, nb, ct, aux,
-                                                                    ctrl);
-        auto scatter = [&](const TileDesc* tl, uint32_t n_t, const uint64_t* spl) {
-            if (!n_t) return;
-            const int g = std::max(1, std::min<int>(n_t, sms * 2));
-            if (T <= 1024)
-                k_chunk_scatter<4><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tl, n_t, spl, ct, p->keys[0],
-                                                                       p->vals[0]);
-            else if (T <= 2048)
-                k_chunk_scatter<8><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tl, n_t, spl, ct, p->keys[0],
-                                                                       p->vals[0]);
-            else
-                k_chunk_scatter<16><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tl, n_t, spl, ct,
-                                                                        p->keys[0], p->vals[0]);
-            p->stats.kernel_launches++;
-        };
-        scatter(tilesL, ntl, p->splitters);
-        scatter(tilesF, ntf, p->splitters_flat);
         static const int sort_ctas = [] {
             int per_sm = 1;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_sort_name, MS_NT, CHUNK_SORT_SMEM);
@@ -891,9 +896,9 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
         k_chunk_sort_name<<<sms * sort_ctas, MS_NT, CHUNK_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks, aux,
                                                                           p->rank, bins_of(p, 0), ctrl);
         CKL(cudaGetLastError());
-        p->stats.kernel_launches += 2;
+        p->stats.kernel_launches++;
 
-        // 4c. overflow buckets: radix on the index, then on the key
+        // overflow buckets: radix on the index, then on the key
         const int PI = std::max(1, (bits_needed(p->max_n - 1) + 7) / 8), PK = 8, PT = PI + PK;
         CKL(launch_build_large_tiles(aux, p->tile, p->ltiles, p->cap_ltiles, ctrl, st));
         CKL(launch_zero_by_count(p->hist, aux.count + CLS_LARGE, (uint32_t)(PT * 256),
