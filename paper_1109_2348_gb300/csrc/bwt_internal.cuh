@@ -80,6 +80,21 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// Lanes of the warp whose label equals this lane's, for labels below
+// 2^BITS: one ballot per label bit, each lane keeping the lanes that agree
+// with it on that bit. All 32 lanes call. (The same set as match.any, at a
+// few cheap instructions per bit.)
+template <int BITS>
+__device__ __forceinline__ uint32_t match_label(uint32_t label) {
+    uint32_t m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+        const uint32_t bit = (label >> b) & 1u;
+        m &= __ballot_sync(0xffffffffu, bit) ^ (bit - 1u);
+    }
+    return m;
+}
+
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
     return *reinterpret_cast<const volatile uint32_t*>(p);
 }
@@ -98,6 +113,35 @@ __device__ __forceinline__ uint64_t pack8_smem(const uint8_t* sb, uint32_t idx) 
     const uint32_t lo = __funnelshift_r(w0, w1, sh);  // bytes idx .. idx+3, first byte lowest
     const uint32_t hi = __funnelshift_r(w1, w2, sh);  // bytes idx+4 .. idx+7
     return ((uint64_t)__byte_perm(lo, 0, 0x0123) << 32) | __byte_perm(hi, 0, 0x0123);
+}
+
+// Stages the bytes of rotations [i0, i0 + len) of block bi and the 7 bytes
+// that follow them (cyclically) in shared memory: byte q of that range lands
+// at sb[shift + q], and the return value is shift (0..15). A range that ends
+// at least 16 bytes before the block's end and starts no more than 15 bytes
+// after S is read with 16-byte loads from the aligned addresses covering it
+// (every load stays inside [S, end of the block)); other ranges are read byte
+// by byte with shift 0. sb must be 16-byte aligned and hold len + 48 bytes.
+// All `nthreads` threads call; the caller synchronises before reading sb.
+__device__ __forceinline__ uint32_t stage_tile_bytes(const uint8_t* __restrict__ S, BlockInfo bi, uint32_t i0,
+                                                     uint32_t len, uint8_t* sb, uint32_t tid, uint32_t nthreads) {
+    const uint32_t need = len + 7;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(S + bi.off + i0);
+    const uintptr_t a0 = a & ~(uintptr_t)15;
+    if ((uint64_t)i0 + need + 16 <= bi.n && a0 >= reinterpret_cast<uintptr_t>(S)) {
+        const uint32_t shift = (uint32_t)(a - a0);
+        const uint32_t nvec = (shift + need + 15) >> 4;
+        const uint4* src = reinterpret_cast<const uint4*>(a0);
+        uint4* dst = reinterpret_cast<uint4*>(sb);
+        for (uint32_t v = tid; v < nvec; v += nthreads) dst[v] = __ldg(src + v);
+        return shift;
+    }
+    for (uint32_t q = tid; q < need; q += nthreads) {
+        uint32_t pos = i0 + q;
+        if (pos >= bi.n) pos = bi.n >= 8 ? pos - bi.n : pos % bi.n;
+        sb[q] = S[bi.off + pos];
+    }
+    return 0;
 }
 
 // Number of valid entries of bin c (a count past the capacity means entries

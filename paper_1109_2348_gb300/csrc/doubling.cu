@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restri
             }
             for (int ps = 0; ps < passes; ++ps) {
                 const uint32_t d = valid ? ((k2 >> (ps * RBITS)) & (RADIX - 1)) : (uint32_t)RADIX;
-                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                const uint32_t peers = match_label<RBITS + 1>(d);
                 if (valid && lane == __ffs(peers) - 1) atomicAdd(&sh[ps * RADIX + d], (uint32_t)__popc(peers));
             }
         }

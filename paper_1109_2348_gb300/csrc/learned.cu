@@ -214,19 +214,9 @@ __device__ __forceinline__ void load_splitters(const uint64_t* __restrict__ spli
     __syncthreads();
 }
 
-// bytes of rotation positions [i0, i0 + len + 7) of block bi, wrapping
-__device__ __forceinline__ void load_tile_bytes(const uint8_t* S, BlockInfo bi, uint32_t i0, uint32_t len,
-                                                uint8_t* sb) {
-    for (uint32_t q = threadIdx.x; q < len + 7; q += blockDim.x) {
-        uint32_t pos = i0 + q;
-        if (pos >= bi.n) pos = bi.n >= 8 ? pos - bi.n : pos % bi.n;
-        sb[q] = S[bi.off + pos];
-    }
-}
-
 constexpr size_t SPL_BYTES = 4096 * 8 + (IDX_CELLS + 8) * 2;  // splitters + top-12-bit index (padded)
 constexpr size_t CNT_BYTES = 4096 * 4;
-constexpr size_t TILE_BYTES = 4096 + 16;
+constexpr size_t TILE_BYTES = 4096 + 48;
 constexpr size_t COUNT_SMEM = SPL_BYTES + CNT_BYTES + TILE_BYTES;
 
 // Counts every rotation in two bucketings at once -- the learned splitters
@@ -270,10 +260,10 @@ __global__ void __launch_bounds__(256) k_bucket_count(const uint8_t* __restrict_
                 cur = td.blk;
             }
             const BlockInfo bi = blocks[td.blk];
-            load_tile_bytes(S, bi, td.start - bi.off, td.len, sb);
+            const uint32_t shift = stage_tile_bytes(S, bi, td.start - bi.off, td.len, sb, threadIdx.x, blockDim.x);
             __syncthreads();
             for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) {
-                const uint64_t key = pack8_smem(sb, q);
+                const uint64_t key = pack8_smem(sb, shift + q);
                 const uint32_t b = bucket_of(spl, first, key);
                 fb[td.start + q] = (uint16_t)b;
                 atomicAdd(&h[b], 1u);
@@ -415,91 +405,108 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
     }
 }
 
-constexpr size_t CS_STAGE = 4096 * 12;  // staged keys and indexes of one tile
-constexpr size_t CHUNK_SCATTER_SMEM = 3 * MAXCH * 4 + TILE_BYTES + CS_STAGE + 4096 * 2;
+// Scatters the tiles of bucketed blocks to their chunks. A CTA takes `span`
+// consecutive tiles (reloading the block's chunk map and chunk starts into
+// shared memory when the block changes). A rotation's bucket is its stored
+// learned bucket (fb) or, in blocks routed to equal-width buckets, its top 12
+// key bits. Each tile is ranked by chunk in shared memory (tile-local
+// positions and chunks only, 4 bytes a rotation; keys are re-packed from the
+// staged bytes on the way out), so each chunk's share of the tile is written
+// as one run, at a slot range reserved with one atomic per tile and chunk.
+constexpr size_t CHUNK_SCATTER_SMEM = NBK * 2 + 4 * MAXCH * 4 + TILE_BYTES + 4096 * 4;
 
-// Scatters the tiles of bucketed blocks to their chunks: a rotation's bucket
-// is its stored learned bucket (fb) or, in blocks routed to equal-width
-// buckets, its top 12 key bits; its chunk comes from the block's chunk map.
-// The tile is staged in shared memory grouped by chunk, so each chunk's
-// share is written as one run at a slot range reserved with one atomic.
 template <int ITEMS>
 __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict__ S,
                                                        const BlockInfo* __restrict__ blocks,
                                                        const TileDesc* __restrict__ tiles, uint32_t ntiles,
-                                                       const uint16_t* __restrict__ fb,
+                                                       uint32_t span, const uint16_t* __restrict__ fb,
                                                        const uint32_t* __restrict__ route, ChunkTables ct,
                                                        uint64_t* __restrict__ K, uint32_t* __restrict__ I) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* lcount = reinterpret_cast<uint32_t*>(smem);
-    uint32_t* pre = lcount + MAXCH;
-    uint32_t* gbase = pre + MAXCH;
-    uint8_t* sb = reinterpret_cast<uint8_t*>(gbase + MAXCH);
-    uint64_t* stK = reinterpret_cast<uint64_t*>(sb + TILE_BYTES);
-    uint32_t* stI = reinterpret_cast<uint32_t*>(sb + TILE_BYTES + 4096 * 8);
-    uint16_t* stC = reinterpret_cast<uint16_t*>(sb + TILE_BYTES + CS_STAGE);
+    uint8_t* sb = smem;                                                  // [TILE_BYTES], 16-aligned
+    uint16_t* cm = reinterpret_cast<uint16_t*>(smem + TILE_BYTES);       // [NBK] chunk of each bucket
+    uint32_t* cb = reinterpret_cast<uint32_t*>(cm + NBK);                // [MAXCH] chunk starts (block-relative)
+    uint32_t* lcount = cb + MAXCH;                                       // [MAXCH] tile's rotations per chunk
+    uint32_t* pre = lcount + MAXCH;                                      // [MAXCH] tile-local chunk offsets
+    uint32_t* dbase = pre + MAXCH;                                       // [MAXCH] destination of pre[c]
+    uint16_t* stQ = reinterpret_cast<uint16_t*>(dbase + MAXCH);          // [4096] tile position by rank
+    uint16_t* stC = stQ + 4096;                                          // [4096] its chunk
     __shared__ uint32_t scan_tmp[32];
-    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        for (int i = threadIdx.x; i < (int)MAXCH; i += blockDim.x) lcount[i] = 0;
-        const TileDesc td = tiles[t];
-        const BlockInfo bi = blocks[td.blk];
-        const uint32_t i0 = td.start - bi.off;
-        const bool flat = route[td.blk] == 2u;
-        const uint16_t* cmap = ct.cmap + (size_t)td.blk * NBK;
-        load_tile_bytes(S, bi, i0, td.len, sb);
-        __syncthreads();
-        uint32_t cs[ITEMS];  // chunk (low 10 bits) | slot within the tile's share of the chunk << 10
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const uint32_t q = j * 256 + threadIdx.x;
-            cs[j] = 0xffffffffu;
-            if (q < td.len) {
-                const uint32_t b = flat ? (uint32_t)(pack8_smem(sb, q) >> 52) : (uint32_t)fb[td.start + q];
-                const uint32_t c = cmap[b];
-                cs[j] = c | (atomicAdd(&lcount[c], 1u) << 10);
+    const uint32_t nspan = (ntiles + span - 1) / span;
+    for (uint32_t s = blockIdx.x; s < nspan; s += gridDim.x) {
+        const uint32_t t0 = s * span, t1 = min(ntiles, t0 + span);
+        uint32_t cur = 0xffffffffu;
+        for (uint32_t t = t0; t < t1; ++t) {
+            const TileDesc td = tiles[t];
+            const BlockInfo bi = blocks[td.blk];
+            const uint32_t i0 = td.start - bi.off;
+            if (td.blk != cur) {  // CTA-uniform
+                cur = td.blk;
+                for (int i = threadIdx.x; i < NBK; i += blockDim.x) cm[i] = ct.cmap[(size_t)cur * NBK + i];
+                for (int i = threadIdx.x; i < (int)MAXCH; i += blockDim.x) cb[i] = ct.cbase[(size_t)cur * MAXCH + i];
             }
-        }
-        __syncthreads();
-        // tile-local exclusive prefix over chunks and the global reservation
-        {
-            constexpr int PER = MAXCH / 256;
-            uint32_t v[PER], sum = 0;
+            for (int i = threadIdx.x; i < (int)MAXCH; i += blockDim.x) lcount[i] = 0;
+            const bool flat = route[td.blk] == 2u;
+            uint32_t bk[ITEMS];
+            if (!flat) {
 #pragma unroll
-            for (int i = 0; i < PER; ++i) {
-                v[i] = lcount[threadIdx.x * PER + i];
-                sum += v[i];
+                for (int j = 0; j < ITEMS; ++j) {
+                    const uint32_t q = j * 256 + threadIdx.x;
+                    bk[j] = q < td.len ? (uint32_t)fb[td.start + q] : 0u;
+                }
             }
-            uint32_t total;
-            uint32_t ex = block_exclusive_scan<256>(sum, scan_tmp, &total);
+            const uint32_t shift = stage_tile_bytes(S, bi, i0, td.len, sb, threadIdx.x, 256);
+            __syncthreads();
+            uint32_t cs[ITEMS];  // chunk (low 10 bits) | slot within the tile's share of the chunk << 10
 #pragma unroll
-            for (int i = 0; i < PER; ++i) {
-                const uint32_t c = threadIdx.x * PER + i;
-                pre[c] = ex;
-                ex += v[i];
-                if (v[i]) gbase[c] = atomicAdd(&ct.ccur[(size_t)td.blk * MAXCH + c], v[i]);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if (cs[j] != 0xffffffffu) {
+            for (int j = 0; j < ITEMS; ++j) {
                 const uint32_t q = j * 256 + threadIdx.x;
-                const uint32_t c = cs[j] & (MAXCH - 1);
-                const uint32_t pos = pre[c] + (cs[j] >> 10);
-                stK[pos] = pack8_smem(sb, q);
-                stI[pos] = i0 + q;
-                stC[pos] = (uint16_t)c;
+                cs[j] = 0xffffffffu;
+                if (q < td.len) {
+                    const uint32_t b = flat ? (uint32_t)(pack8_smem(sb, shift + q) >> 52) : bk[j];
+                    const uint32_t c = cm[b];
+                    cs[j] = c | (atomicAdd(&lcount[c], 1u) << 10);
+                }
             }
+            __syncthreads();
+            // tile-local exclusive prefix over chunks and the global reservation
+            {
+                constexpr int PER = MAXCH / 256;
+                uint32_t v[PER], sum = 0;
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    v[i] = lcount[threadIdx.x * PER + i];
+                    sum += v[i];
+                }
+                uint32_t total;
+                uint32_t ex = block_exclusive_scan<256>(sum, scan_tmp, &total);
+#pragma unroll
+                for (int i = 0; i < PER; ++i) {
+                    const uint32_t c = threadIdx.x * PER + i;
+                    pre[c] = ex;
+                    if (v[i]) dbase[c] = bi.off + cb[c] + atomicAdd(&ct.ccur[(size_t)td.blk * MAXCH + c], v[i]);
+                    ex += v[i];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                if (cs[j] != 0xffffffffu) {
+                    const uint32_t c = cs[j] & (MAXCH - 1);
+                    const uint32_t pos = pre[c] + (cs[j] >> 10);
+                    stQ[pos] = (uint16_t)(j * 256 + threadIdx.x);
+                    stC[pos] = (uint16_t)c;
+                }
+            }
+            __syncthreads();
+            for (uint32_t r = threadIdx.x; r < td.len; r += blockDim.x) {
+                const uint32_t q = stQ[r], c = stC[r];
+                const uint32_t dst = dbase[c] + (r - pre[c]);
+                K[dst] = pack8_smem(sb, shift + q);
+                I[dst] = i0 + q;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        const uint32_t* cbase = ct.cbase + (size_t)td.blk * MAXCH;
-        for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) {
-            const uint32_t c = stC[q];
-            const uint32_t dst = bi.off + cbase[c] + gbase[c] + (q - pre[c]);
-            K[dst] = stK[q];
-            I[dst] = stI[q];
-        }
-        __syncthreads();
     }
 }
 
@@ -655,7 +662,7 @@ __global__ void __launch_bounds__(256) k_seg_hist_u64(const uint64_t* __restrict
             for (int ps = 0; ps < P; ++ps) {
                 uint32_t d = 256;
                 if (valid) d = ps < PI ? (v >> (8 * ps)) & 255u : (uint32_t)((k >> (8 * (ps - PI))) & 255u);
-                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                const uint32_t peers = match_label<9>(d);
                 if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[ps * 256 + d], (uint32_t)__popc(peers));
             }
         }
@@ -828,16 +835,17 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
         k_chunk_plan<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->blocks, p->route, nb, ct, aux,
                                                                     ctrl);
         const TileDesc* tilesB = p->tiles_aux + ntp;
-        const int g = std::max(1, std::min<int>(ntb, sms * 3));
+        const uint32_t span = std::max(1u, std::min(16u, ntb / (uint32_t)(sms * 16)));
+        const int g = std::max(1, std::min<int>((ntb + span - 1) / span, sms * 5));
         if (T <= 1024)
-            k_chunk_scatter<4><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, fb, p->route, ct,
-                                                                   p->keys[0], p->vals[0]);
+            k_chunk_scatter<4><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, span, fb, p->route,
+                                                                   ct, p->keys[0], p->vals[0]);
         else if (T <= 2048)
-            k_chunk_scatter<8><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, fb, p->route, ct,
-                                                                   p->keys[0], p->vals[0]);
+            k_chunk_scatter<8><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, span, fb, p->route,
+                                                                   ct, p->keys[0], p->vals[0]);
         else
-            k_chunk_scatter<16><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, fb, p->route, ct,
-                                                                    p->keys[0], p->vals[0]);
+            k_chunk_scatter<16><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, span, fb,
+                                                                    p->route, ct, p->keys[0], p->vals[0]);
         CKL(cudaGetLastError());
         p->stats.kernel_launches += 4;
     }

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(NA_THREADS, 1) k_bwt_block_noalloc(const uint8
             for (uint32_t c0 = 0; c0 < n; c0 += NA_THREADS) {
                 const uint32_t i = c0 + tid;
                 const uint32_t d = i < n ? (sk[i] >> shift) & 255u : 256u;
-                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                const uint32_t peers = bwt::match_label<9>(d);
                 if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&base[d], (uint32_t)__popc(peers));
             }
             __syncthreads();
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(NA_THREADS, 1) k_bwt_block_noalloc(const uint8
                 const uint32_t key = valid ? sk[i] : 0u;
                 const uint32_t val = valid ? sv[i] : 0u;
                 const uint32_t d = valid ? (key >> shift) & 255u : 256u;
-                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                const uint32_t peers = bwt::match_label<9>(d);
                 const uint32_t below = __popc(peers & lt);
                 if (valid && lane == __ffs(peers) - 1) whist[warp][d] = (uint16_t)__popc(peers);
                 __syncthreads();

@@ -7,7 +7,7 @@
 // never straddle segments, so one launch sorts every segment of a batch.
 //
 // One pass = one launch. A CTA takes the next tile index from an atomic
-// counter, ranks its keys by digit with warp-level __match_any_sync (stable:
+// counter, ranks its keys by digit with warp-level peer masks (stable:
 // warp-striped order, warps in order), publishes its per-digit counts, looks
 // back over the preceding tiles of its segment for the exclusive prefix
 // (decoupled look-back; each wait is bounded and sets ERR_TIMEOUT when it
@@ -30,13 +30,22 @@ struct OsThreads {
     static constexpr int value = 256;
 };
 
+// Resident CTAs per SM the register budget is sized for: a pass is bound by
+// the latency of each tile's chain of phases, so more CTAs in flight beat
+// more registers (measured on 64 x 900,000 keys: 3 CTAs of <= 80 registers
+// ran a u64 pass 16% faster than 2 of 128).
+template <int TILE>
+struct OsMinBlocks {
+    static constexpr int value = TILE >= 4096 ? 3 : TILE >= 2048 ? 5 : 6;
+};
+
 template <typename KeyT, int RBITS, int TILE, bool FROM_S>
 struct OneSweepLayout {
     static constexpr int RADIX = 1 << RBITS;
     static constexpr int WARPS = OsThreads<TILE>::value / 32;
     static constexpr size_t WHIST = (size_t)WARPS * RADIX * 2;
     static constexpr size_t STAGE = (size_t)TILE * (sizeof(KeyT) + 4);
-    static constexpr size_t BYTES = FROM_S ? (size_t)TILE + 16 : 0;  // tile + 7 halo bytes + word over-read
+    static constexpr size_t BYTES = FROM_S ? (size_t)TILE + 48 : 0;  // tile + 7 halo bytes + alignment slack
     static constexpr size_t U0 = WHIST > STAGE ? WHIST : STAGE;
     static constexpr size_t U = ((U0 > BYTES ? U0 : BYTES) + 15) & ~(size_t)15;
     static constexpr size_t TOTAL = U + 2 * RADIX * 4 + 32 * 4 + 16;
@@ -46,7 +55,7 @@ struct OneSweepLayout {
 // key; used to put overflow buckets of the learned bucketing in index order
 // before their key passes.
 template <typename KeyT, int RBITS, int TILE, bool FROM_S, bool VDIG = false>
-__global__ void __launch_bounds__(OsThreads<TILE>::value) k_onesweep(OneSweepParams p) {
+__global__ void __launch_bounds__(OsThreads<TILE>::value, OsMinBlocks<TILE>::value) k_onesweep(OneSweepParams p) {
     using Lay = OneSweepLayout<KeyT, RBITS, TILE, FROM_S>;
     constexpr int OS_THREADS = OsThreads<TILE>::value;
     constexpr int OS_WARPS = OS_THREADS / 32;
@@ -85,39 +94,29 @@ __global__ void __launch_bounds__(OsThreads<TILE>::value) k_onesweep(OneSweepPar
 
         // ---- load the tile (warp-striped: item j of lane l of warp w is
         //      tile index w*WKEYS + j*32 + l)
+        //      Values are read only when the tile is staged (fewer live
+        //      registers through ranking and look-back), except with VDIG,
+        //      where they carry the digit.
         KeyT key[ITEMS];
-        uint32_t val[ITEMS];
+        uint32_t val[VDIG ? ITEMS : 1];
+        uint32_t i0 = 0;  // FROM_S: block-relative index of the tile's first rotation (its value)
         if constexpr (FROM_S) {
             const BlockInfo bi = p.blocks[td.blk];
-            const uint32_t i0 = td.start - bi.off;
-            const uint8_t* Sb = p.S + bi.off;
-            for (uint32_t q = tid; q < td.len + 7; q += OS_THREADS) {
-                uint32_t pos = i0 + q;
-                if (pos >= bi.n) pos = bi.n >= 8 ? pos - bi.n : pos % bi.n;
-                sbytes[q] = Sb[pos];
-            }
+            i0 = td.start - bi.off;
+            const uint32_t shift = stage_tile_bytes(p.S, bi, i0, td.len, sbytes, tid, OS_THREADS);
             __syncthreads();
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) {
                 const uint32_t idx = warp * WKEYS + j * 32 + lane;
-                key[j] = 0;
-                val[j] = 0;
-                if (idx < td.len) {
-                    key[j] = (KeyT)pack8_smem(sbytes, idx);
-                    val[j] = i0 + idx;
-                }
+                key[j] = idx < td.len ? (KeyT)pack8_smem(sbytes, shift + idx) : (KeyT)0;
             }
             __syncthreads();
         } else {
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) {
                 const uint32_t idx = warp * WKEYS + j * 32 + lane;
-                key[j] = 0;
-                val[j] = 0;
-                if (idx < td.len) {
-                    key[j] = kin[td.start + idx];
-                    val[j] = p.vin[td.start + idx];
-                }
+                key[j] = idx < td.len ? kin[td.start + idx] : (KeyT)0;
+                if constexpr (VDIG) val[j] = idx < td.len ? p.vin[td.start + idx] : 0u;
             }
         }
 
@@ -138,7 +137,7 @@ __global__ void __launch_bounds__(OsThreads<TILE>::value) k_onesweep(OneSweepPar
                 if constexpr (VDIG) d = (val[j] >> p.shift) & (uint32_t)(RADIX - 1);
                 else d = (uint32_t)((key[j] >> p.shift) & (KeyT)(RADIX - 1));
             }
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t peers = match_label<RBITS + 1>(d);
             const int leader = __ffs(peers) - 1;
             uint32_t base = 0;
             if (valid && lane == leader) {
@@ -228,8 +227,13 @@ __global__ void __launch_bounds__(OsThreads<TILE>::value) k_onesweep(OneSweepPar
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             if (rkdg[j] != 0xffffffffu) {
+                const uint32_t idx = warp * WKEYS + j * 32 + lane;
+                uint32_t v;
+                if constexpr (VDIG) v = val[j];
+                else if constexpr (FROM_S) v = i0 + idx;
+                else v = p.vin[td.start + idx];
                 skeys[rkdg[j]] = key[j];
-                svals[rkdg[j]] = val[j];
+                svals[rkdg[j]] = v;
             }
         }
         __syncthreads();
@@ -297,20 +301,16 @@ __global__ void __launch_bounds__(256) k_hist_keys11(const uint8_t* __restrict__
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
         const uint32_t i0 = td.start - bi.off;
-        for (uint32_t q = threadIdx.x; q < td.len + 7; q += 256) {
-            uint32_t pos = i0 + q;
-            if (pos >= bi.n) pos = bi.n >= 8 ? pos - bi.n : pos % bi.n;
-            sbytes[q] = S[bi.off + pos];
-        }
+        const uint32_t shift = stage_tile_bytes(S, bi, i0, td.len, sbytes, threadIdx.x, 256);
         __syncthreads();
         for (uint32_t q0 = 0; q0 < td.len; q0 += 256) {
             const uint32_t q = q0 + threadIdx.x;
             const bool valid = q < td.len;
-            const uint64_t k = valid ? pack8_smem(sbytes, q) : 0ull;
+            const uint64_t k = valid ? pack8_smem(sbytes, shift + q) : 0ull;
 #pragma unroll
             for (int ps = 0; ps < PASSES; ++ps) {
                 const uint32_t d = valid ? (uint32_t)((k >> (11 * ps)) & (RADIX - 1)) : (uint32_t)RADIX;
-                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                const uint32_t peers = match_label<12>(d);
                 if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[ps * RADIX + d], (uint32_t)__popc(peers));
             }
         }
@@ -456,10 +456,10 @@ cudaError_t launch_hist_bytes(const uint8_t* S, const BlockInfo* blocks, const T
 cudaError_t launch_hist_keys11(const uint8_t* S, const BlockInfo* blocks, const TileDesc* tiles, uint32_t num_tiles,
                                int tile, uint32_t* hist, cudaStream_t st) {
     if (num_tiles == 0) return cudaSuccess;
-    const size_t smem = 6 * 2048 * 4 + (size_t)tile + 16;
+    const size_t smem = 6 * 2048 * 4 + (size_t)tile + 48;
     static bool attr = [] {
         cudaFuncSetAttribute((void*)k_hist_keys11<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             6 * 2048 * 4 + 4096 + 16);
+                             6 * 2048 * 4 + 4096 + 48);
         return true;
     }();
     (void)attr;
