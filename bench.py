@@ -181,6 +181,21 @@ def run_cpu_oracle(w, threads: int, repeats: int = 1):
     return buf.size / dt / 1e6, dt
 
 
+# DRAM bytes (read + write) per key of one u64 onesweep pass as ncu counted them
+# for the current kernel on the full mixed3-64x900000 pass
+# (profiles/launches_mixed3-64x900000_graph.md); None
+# when the kernel has changed since.
+ONESWEEP_DRAM_BYTES_PER_KEY = 23.48
+
+
+def add_first_sort(acc, st, n):
+    """Accumulates the first sort's passes of one call (BWT_F_TIMING stats)."""
+    acc["ms"] += st["first_ms"]
+    acc["bytes"] += st["first_bytes"]
+    acc["launches"] += st["first_launches"]
+    acc["keys"] += n * st["first_launches"]
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -268,7 +283,7 @@ def ours(args):
     sampler.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches = 0
-    radix = {"ms": 0.0, "bytes": 0.0, "launches": 0}
+    radix = {"ms": 0.0, "bytes": 0.0, "launches": 0, "keys": 0.0}
     stats = None
     for i in range(args.steps):
         flush.zero_()
@@ -278,9 +293,7 @@ def ours(args):
         stats = plan.stats()
         launches += stats["kernel_launches"]
         if tplan is None:
-            radix["ms"] += stats["radix_ms"]
-            radix["bytes"] += stats["radix_bytes"]
-            radix["launches"] += stats["radix_launches"]
+            add_first_sort(radix, stats, n)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -335,10 +348,7 @@ def ours(args):
             b.record(stream)
             b.synchronize()
             pms.append(a.elapsed_time(b))
-            ts = pplan.stats()
-            radix["ms"] += ts["radix_ms"]
-            radix["bytes"] += ts["radix_bytes"]
-            radix["launches"] += ts["radix_launches"]
+            add_first_sort(radix, pplan.stats(), n)
         pplan.close()
         plain_cmp = {"value": round(n * args.steps / (sum(pms) / 1e3) / 1e6, 3), "unit": "MB/s",
                      "mode": "plain (host-driven rounds, events around each radix launch)",
@@ -346,11 +356,19 @@ def ours(args):
     peak, peak_kind = measured_peaks()
     roof = None
     if radix["ms"] > 0:
+        # the first sort's u64 onesweep passes: algorithmic bytes (13 per key for
+        # the pass that packs the keys from the bytes, 24 for the others) over
+        # their CUDA-event time; traffic = the DRAM bytes per key ncu measured for
+        # the current kernel, times the keys of one launch
         achieved = radix["bytes"] / (radix["ms"] / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_onesweep (segmented onesweep radix pass)",
+        per_launch_keys = radix["keys"] / max(1, radix["launches"])
+        traffic = None if ONESWEEP_DRAM_BYTES_PER_KEY is None else \
+            round(ONESWEEP_DRAM_BYTES_PER_KEY * per_launch_keys)
+        roof = {"bound": "hbm", "kernel": "k_onesweep<u64, 8, 4096> (first-sort radix pass)",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind + " hbm_gbs",
-                "traffic": None, "launches_timed": radix["launches"],
+                "traffic": traffic, "algorithmic_bytes_per_launch": round(radix["bytes"] / max(1, radix["launches"])),
+                "launches_timed": radix["launches"],
                 "avg_launch_ms": round(radix["ms"] / max(1, radix["launches"]), 4)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

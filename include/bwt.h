@@ -90,6 +90,9 @@ typedef struct {
     uint64_t buckets_nonempty;  /* learned bucketing: non-empty buckets over all blocks */
     uint32_t round_radix_bits;  /* digit width of the doubling rounds' radix */
     uint32_t pad2_;
+    uint64_t first_launches;    /* the first sort's u64 passes alone (a subset of radix_launches) */
+    double first_ms;            /* their summed device time (only with BWT_F_TIMING) */
+    double first_bytes;         /* their algorithmic HBM bytes (13 per key for the first pass, 24 after) */
 } bwt_stats;
 
 /* Create a plan on CUDA device `device` (made current for the call). The plan

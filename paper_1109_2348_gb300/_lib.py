@@ -57,6 +57,9 @@ class Stats(ctypes.Structure):
         ("buckets_nonempty", ctypes.c_uint64),
         ("round_radix_bits", ctypes.c_uint32),
         ("pad2_", ctypes.c_uint32),
+        ("first_launches", ctypes.c_uint64),
+        ("first_ms", ctypes.c_double),
+        ("first_bytes", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:

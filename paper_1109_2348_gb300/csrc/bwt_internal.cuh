@@ -320,8 +320,19 @@ __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t
                                           uint32_t carry_end, const uint32_t* __restrict__ SA, BlockInfo bi,
                                           uint32_t blk, uint32_t* __restrict__ rank, const Bins& bins, bool emit_ok,
                                           WarpEmitter& em, uint32_t* err) {
-    for (uint32_t q0 = 0; q0 < len; q0 += blockDim.x) {
-        const uint32_t q = q0 + threadIdx.x;
+    // 256 threads, len <= 4096: at most 16 elements a thread. The tile's SA
+    // entries are read up front (independent loads, all in flight at once).
+    constexpr int MAXIT = 16;
+    uint32_t sav[MAXIT];
+#pragma unroll
+    for (int it = 0; it < MAXIT; ++it) {
+        const uint32_t q = it * 256u + threadIdx.x;
+        sav[it] = q < len ? (SA_LOCAL ? SA[q] : SA[tstart + q]) : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < MAXIT; ++it) {
+        const uint32_t q = it * 256u + threadIdx.x;
+        if (it * 256u >= len) break;  // CTA-uniform
         const bool valid = q < len;
         bool want = false;
         uint32_t glen = 0;
@@ -331,7 +342,7 @@ __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t
             const bool differs_prev = q > 0 && sk[q - 1] != key;
             const uint32_t lb = differs_prev ? q : (q == 0 ? 0u : smem_lower_bound<KeyT>(sk, q, key));
             const uint32_t gs = lb == 0 ? carry_start : tstart + lb;
-            const uint32_t sa = SA_LOCAL ? SA[q] : SA[k];
+            const uint32_t sa = sav[it];
             if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
             if (gs == k && emit_ok) {
                 uint32_t ub;

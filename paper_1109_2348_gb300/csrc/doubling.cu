@@ -29,60 +29,84 @@ namespace bwt {
 
 namespace {
 
-// First index f in [lo, k] with K[f] == key, given K sorted non-decreasingly
-// on [lo, k] and K[k] == key: exponential search backward, then bisection.
+// The run of keys equal to K[k] inside a sorted range, found by one warp:
+// each round probes 32 positions at once (first exponentially spaced, then
+// evenly inside the bracket left), so a run of length r costs about
+// 1 + log32(r) dependent global reads instead of 2 log2(r). All 32 lanes
+// call and all return the result.
+
+// First index f in [lo, k] with K[f] == key (K sorted on [lo, k], K[k] == key).
 template <typename KeyT>
-__device__ __forceinline__ uint32_t first_equal(const KeyT* __restrict__ K, uint32_t lo, uint32_t k, KeyT key) {
-    uint32_t hi_eq = k;
-    int64_t below = -1;
-    uint32_t step = 1;
-    for (;;) {
-        if ((uint64_t)(k - lo) < step) {
-            below = (int64_t)lo - 1;
-            break;
-        }
-        const uint32_t c = k - step;
-        if (K[c] != key) {
-            below = c;
-            break;
-        }
-        hi_eq = c;
-        step <<= 1;
+__device__ __forceinline__ uint32_t warp_run_start(const KeyT* __restrict__ K, uint32_t lo, uint32_t k, KeyT key) {
+    const uint32_t lane = threadIdx.x & 31;
+    int64_t a = (int64_t)lo - 1, b = k;  // K[a] != key (or a < lo), K[b] == key
+    {
+        const int64_t p = (int64_t)k - (int64_t)(1ull << lane);  // decreasing with the lane
+        const bool eq = p > a && K[p] == key;
+        const uint32_t m = __popc(__ballot_sync(0xffffffffu, eq));  // equal probes: lanes 0 .. m-1
+        if (m > 0) b = (int64_t)k - (int64_t)(1ull << (m - 1));
+        if (m < 32) a = max(a, (int64_t)k - (int64_t)(1ull << m));
     }
-    uint32_t a = (uint32_t)(below + 1), b = hi_eq;
-    while (a < b) {
-        const uint32_t mid = a + ((b - a) >> 1);
-        if (K[mid] == key) b = mid; else a = mid + 1;
+    while (b - a > 1) {
+        const int64_t span = b - a;
+        const int64_t p = a + 1 + (span - 1) * (int64_t)lane / 32;  // increasing, inside (a, b)
+        const uint32_t eqm = __ballot_sync(0xffffffffu, K[p] == key);  // equal probes: a suffix of lanes
+        if (eqm == 0u) {
+            a = a + 1 + (span - 1) * 31 / 32;
+        } else {
+            const int l = __ffs(eqm) - 1;
+            const int64_t nb = a + 1 + (span - 1) * l / 32;
+            if (l > 0) a = a + 1 + (span - 1) * (l - 1) / 32;
+            b = nb;
+        }
     }
-    return a;
+    return (uint32_t)b;
 }
 
-// First index e in (k, hi] with e == hi or K[e] != key, given K[k] == key and
-// K sorted on [k, hi).
+// First index e in (k, hi] with e == hi or K[e] != key (K sorted on [k, hi),
+// K[k] == key).
 template <typename KeyT>
-__device__ __forceinline__ uint32_t end_equal(const KeyT* __restrict__ K, uint32_t k, uint32_t hi, KeyT key) {
-    uint32_t lo_eq = k;
-    uint32_t above = hi;
-    uint32_t step = 1;
-    for (;;) {
-        if ((uint64_t)(hi - 1 - k) < step) {
-            above = hi;
-            break;
-        }
-        const uint32_t c = k + step;
-        if (K[c] != key) {
-            above = c;
-            break;
-        }
-        lo_eq = c;
-        step <<= 1;
+__device__ __forceinline__ uint32_t warp_run_end(const KeyT* __restrict__ K, uint32_t k, uint32_t hi, KeyT key) {
+    const uint32_t lane = threadIdx.x & 31;
+    int64_t a = k, b = hi;  // K[a] == key; b == hi or K[b] != key
+    {
+        const int64_t p = (int64_t)k + (int64_t)(1ull << lane);  // increasing with the lane
+        const bool eq = p < b && K[p] == key;
+        const uint32_t m = __popc(__ballot_sync(0xffffffffu, eq));  // equal probes: lanes 0 .. m-1
+        if (m > 0) a = (int64_t)k + (int64_t)(1ull << (m - 1));
+        if (m < 32) b = min(b, (int64_t)k + (int64_t)(1ull << m));
     }
-    uint32_t a = lo_eq + 1, b = above;
-    while (a < b) {
-        const uint32_t mid = a + ((b - a) >> 1);
-        if (K[mid] != key) b = mid; else a = mid + 1;
+    while (b - a > 1) {
+        const int64_t span = b - a;
+        const int64_t p = a + 1 + (span - 1) * (int64_t)lane / 32;  // increasing, inside (a, b)
+        const uint32_t eqm = __ballot_sync(0xffffffffu, K[p] == key);  // equal probes: a prefix of lanes
+        const int m = __popc(eqm);
+        if (m == 0) {
+            b = a + 1;
+        } else {
+            const int64_t na = a + 1 + (span - 1) * (m - 1) / 32;
+            if (m < 32) b = a + 1 + (span - 1) * m / 32;
+            a = na;
+        }
     }
-    return a;
+    return (uint32_t)b;
+}
+
+// Carries of a sorted tile [start, start + len) inside the sorted range
+// [lo, hi): the start of the run holding its first key and the end of the
+// run holding its last key. Warp 0 calls (all lanes); lane 0 writes them.
+template <typename KeyT>
+__device__ __forceinline__ void tile_carries(const KeyT* __restrict__ K, uint32_t lo, uint32_t hi, uint32_t start,
+                                             uint32_t len, uint32_t* s_carry) {
+    const uint32_t last = start + len - 1;
+    const KeyT k0 = K[start], k1 = K[last];
+    uint32_t c0 = start, c1 = last + 1;
+    if (start > lo && K[start - 1] == k0) c0 = warp_run_start<KeyT>(K, lo, start, k0);
+    if (last + 1 < hi && K[last + 1] == k1) c1 = warp_run_end<KeyT>(K, last, hi, k1);
+    if ((threadIdx.x & 31) == 0) {
+        s_carry[0] = c0;
+        s_carry[1] = c1;
+    }
 }
 
 // ---- first naming ------------------------------------------------------------
@@ -107,16 +131,12 @@ __global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict
         const BlockInfo bi = blocks[td.blk];
         const uint32_t lo = seg_bounds ? td.segStart : bi.off;
         const uint32_t hi = seg_bounds ? td.segStart + td.pad0 : bi.off + bi.n;
-        for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) sk[q] = K[td.start + q];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const uint32_t last = td.start + td.len - 1;
-            s_carry[0] = (td.start == lo || K[td.start - 1] != sk[0]) ? td.start
-                                                                      : first_equal<uint64_t>(K, lo, td.start, sk[0]);
-            s_carry[1] = (last + 1 == hi || K[last + 1] != sk[td.len - 1])
-                             ? last + 1
-                             : end_equal<uint64_t>(K, last, hi, sk[td.len - 1]);
+#pragma unroll
+        for (int it = 0; it < 16; ++it) {  // tiles hold at most 4096 keys
+            const uint32_t q = it * 256u + threadIdx.x;
+            if (q < td.len) sk[q] = K[td.start + q];
         }
+        if (threadIdx.x < 32) tile_carries<uint64_t>(K, lo, hi, td.start, td.len, s_carry);
         __syncthreads();
         name_tile<uint64_t>(sk, td.len, td.start, s_carry[0], s_carry[1], SA, bi, td.blk, rank, bins, bi.n > 8u, em,
                             &ctrl[CTRL_ERR]);
@@ -246,7 +266,7 @@ __global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restri
             }
             for (int ps = 0; ps < passes; ++ps) {
                 const uint32_t d = valid ? ((k2 >> (ps * RBITS)) & (RADIX - 1)) : (uint32_t)RADIX;
-                const uint32_t peers = match_label<RBITS + 1>(d);
+                const uint32_t peers = __match_any_sync(0xffffffffu, d);
                 if (valid && lane == __ffs(peers) - 1) atomicAdd(&sh[ps * RADIX + d], (uint32_t)__popc(peers));
             }
         }
@@ -508,17 +528,12 @@ __global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
         const uint32_t lo = td.segStart, hi = td.segStart + td.pad0;
-        for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) sk[q] = key2[td.start + q];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const uint32_t last = td.start + td.len - 1;
-            s_carry[0] = (td.start == lo || key2[td.start - 1] != sk[0])
-                             ? td.start
-                             : first_equal<uint32_t>(key2, lo, td.start, sk[0]);
-            s_carry[1] = (last + 1 == hi || key2[last + 1] != sk[td.len - 1])
-                             ? last + 1
-                             : end_equal<uint32_t>(key2, last, hi, sk[td.len - 1]);
+#pragma unroll
+        for (int it = 0; it < 16; ++it) {  // tiles hold at most 4096 keys
+            const uint32_t q = it * 256u + threadIdx.x;
+            if (q < td.len) sk[q] = key2[td.start + q];
         }
+        if (threadIdx.x < 32) tile_carries<uint32_t>(key2, lo, hi, td.start, td.len, s_carry);
         __syncthreads();
         name_tile<uint32_t>(sk, td.len, td.start, s_carry[0], s_carry[1], SA, bi, td.blk, rank, next,
                             new_depth < bi.n, em, &ctrl[CTRL_ERR]);

@@ -329,7 +329,7 @@ Bins bwt::bins_of(bwt_plan* p, int par) {
 // Records an event pair around a radix launch when timing is on.
 static cudaError_t timed_onesweep(bwt_plan* p, int key_bytes, bool from_s, const OneSweepParams& a,
                                   double bytes_per_key, uint64_t keys_host, int ctrl_keys_word, cudaStream_t st,
-                                  int radix_bits = 0) {
+                                  int radix_bits = 0, bool first_sort = false) {
     const bool timing = !p->events.empty() && !p->capturing && p->ev_used + 2 <= p->events.size();
     if (timing) cudaEventRecord(p->events[p->ev_used], st);
     cudaError_t e = launch_onesweep(key_bytes, from_s, radix_bits ? radix_bits : p->rbits, p->tile, a, 0, st);
@@ -337,6 +337,7 @@ static cudaError_t timed_onesweep(bwt_plan* p, int key_bytes, bool from_s, const
         cudaEventRecord(p->events[p->ev_used + 1], st);
         EvMeta m;
         m.bytes_per_key = bytes_per_key;
+        m.first_sort = first_sort;
         m.keys_host = keys_host;
         m.ctrl_word = ctrl_keys_word;
         p->ev_meta.push_back(m);
@@ -391,7 +392,7 @@ bwt_status bwt::enqueue_initial_sort(bwt_plan* p, const uint8_t* d_in, cudaStrea
         a.tile_counter = ctrl + CTRL_TILE_CTR + ps;
         a.ctrl = ctrl;
         a.shift = ps * rb;
-        CK(timed_onesweep(p, 8, ps == 0, a, ps == 0 ? 13.0 : 24.0, p->total, -1, st));
+        CK(timed_onesweep(p, 8, ps == 0, a, ps == 0 ? 13.0 : 24.0, p->total, -1, st, 0, true));
     }
     p->sa = p->vals[(P - 1) & 1];
     p->key2 = p->vals[P & 1];
@@ -492,6 +493,11 @@ void bwt::collect_timing(bwt_plan* p) {
         const uint64_t keys = m.keys_host ? m.keys_host : m.keys_dev;
         p->stats.radix_ms += ms;
         p->radix_bytes += m.bytes_per_key * (double)keys;
+        if (m.first_sort) {
+            p->stats.first_launches++;
+            p->stats.first_ms += ms;
+            p->stats.first_bytes += m.bytes_per_key * (double)keys;
+        }
     }
     p->ev_meta.clear();
     p->ev_used = 0;

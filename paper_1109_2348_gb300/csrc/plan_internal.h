@@ -15,6 +15,7 @@ namespace bwt {
 
 struct EvMeta {
     double bytes_per_key;
+    bool first_sort;     // a pass of the first sort (also reported on its own)
     uint64_t keys_host;  // keys moved, when the host knows it
     int ctrl_word;       // else: the ctrl word holding it (read after the round), -1 if none
     uint64_t keys_dev = 0;

@@ -94,11 +94,12 @@ __global__ void __launch_bounds__(OsThreads<TILE>::value, OsMinBlocks<TILE>::val
 
         // ---- load the tile (warp-striped: item j of lane l of warp w is
         //      tile index w*WKEYS + j*32 + l)
-        //      Values are read only when the tile is staged (fewer live
-        //      registers through ranking and look-back), except with VDIG,
-        //      where they carry the digit.
+        //      With u64 keys the values are read only when the tile is staged
+        //      (fewer live registers through ranking and look-back), unless
+        //      they carry the digit (VDIG); u32-key tiles load them up front.
+        constexpr bool EARLY_VALS = VDIG || sizeof(KeyT) == 4;
         KeyT key[ITEMS];
-        uint32_t val[VDIG ? ITEMS : 1];
+        uint32_t val[EARLY_VALS ? ITEMS : 1];
         uint32_t i0 = 0;  // FROM_S: block-relative index of the tile's first rotation (its value)
         if constexpr (FROM_S) {
             const BlockInfo bi = p.blocks[td.blk];
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(OsThreads<TILE>::value, OsMinBlocks<TILE>::val
             for (int j = 0; j < ITEMS; ++j) {
                 const uint32_t idx = warp * WKEYS + j * 32 + lane;
                 key[j] = idx < td.len ? kin[td.start + idx] : (KeyT)0;
-                if constexpr (VDIG) val[j] = idx < td.len ? p.vin[td.start + idx] : 0u;
+                if constexpr (EARLY_VALS) val[j] = idx < td.len ? p.vin[td.start + idx] : 0u;
             }
         }
 
@@ -137,7 +138,12 @@ __global__ void __launch_bounds__(OsThreads<TILE>::value, OsMinBlocks<TILE>::val
                 if constexpr (VDIG) d = (val[j] >> p.shift) & (uint32_t)(RADIX - 1);
                 else d = (uint32_t)((key[j] >> p.shift) & (KeyT)(RADIX - 1));
             }
-            const uint32_t peers = match_label<RBITS + 1>(d);
+            // peer masks: one ballot per digit bit for u64 passes (the first
+            // sort: many distinct digits per warp), match.any for u32 passes
+            // (doubling rounds: repetitive rank digits, where it measured faster)
+            uint32_t peers;
+            if constexpr (sizeof(KeyT) == 8) peers = match_label<RBITS + 1>(d);
+            else peers = __match_any_sync(0xffffffffu, d);
             const int leader = __ffs(peers) - 1;
             uint32_t base = 0;
             if (valid && lane == leader) {
@@ -229,8 +235,8 @@ __global__ void __launch_bounds__(OsThreads<TILE>::value, OsMinBlocks<TILE>::val
             if (rkdg[j] != 0xffffffffu) {
                 const uint32_t idx = warp * WKEYS + j * 32 + lane;
                 uint32_t v;
-                if constexpr (VDIG) v = val[j];
-                else if constexpr (FROM_S) v = i0 + idx;
+                if constexpr (FROM_S) v = i0 + idx;
+                else if constexpr (EARLY_VALS) v = val[j];
                 else v = p.vin[td.start + idx];
                 skeys[rkdg[j]] = key[j];
                 svals[rkdg[j]] = v;
