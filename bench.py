@@ -38,7 +38,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--blocks", type=int, default=0, help="use only the first N blocks of the workload")
-    ap.add_argument("--mode", choices=["host", "graph", "perblock", "learned"], default="graph")
+    ap.add_argument("--mode", choices=["host", "graph", "perblock", "learned", "learned-host"], default="graph",
+                    help="learned = learned bucketing + the batched graph launch; learned-host drives its rounds "
+                         "from the host")
     ap.add_argument("--radix-bits", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--model", default=None, help="model file for --mode learned (trained in-process if absent)")
@@ -235,10 +237,11 @@ def ours(args):
     w = rank_workload(args.config, args.blocks, rank, world)
     buf, off = w.generate()
     n = buf.size
-    flags = {"host": F_TIMING, "graph": F_GRAPH, "perblock": F_PER_BLOCK_LAUNCH, "learned": F_LEARNED}[args.mode]
+    flags = {"host": F_TIMING, "graph": F_GRAPH, "perblock": F_PER_BLOCK_LAUNCH, "learned": F_LEARNED | F_GRAPH,
+             "learned-host": F_LEARNED}[args.mode]
     sizes = np.diff(off.astype(np.int64))
     model_info = None
-    if args.mode == "learned" and not args.model:
+    if args.mode.startswith("learned") and not args.model:
         import tempfile
         from paper_1109_2348_gb300 import model as mdl
         t0 = time.perf_counter()
@@ -299,7 +302,7 @@ def ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     learned_stats = {k: stats[k] for k in ("blocks_routed_plain", "buckets_overflowed", "keys_overflowed",
                                            "max_bucket", "bucket_sq_sum", "buckets_nonempty")} \
-        if args.mode == "learned" else None
+        if args.mode.startswith("learned") else None
     t_ms = reduce_max(float(np.sum(step_ms)), world, dev)
     value = job_value(n, world, args.steps, t_ms)
 

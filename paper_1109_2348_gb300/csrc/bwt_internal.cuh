@@ -320,14 +320,17 @@ __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t
                                           uint32_t carry_end, const uint32_t* __restrict__ SA, BlockInfo bi,
                                           uint32_t blk, uint32_t* __restrict__ rank, const Bins& bins, bool emit_ok,
                                           WarpEmitter& em, uint32_t* err) {
-    // 256 threads, len <= 4096: at most 16 elements a thread. The tile's SA
-    // entries are read up front (independent loads, all in flight at once).
+    // 256 threads, len <= 4096: at most 16 elements a thread. A global SA's
+    // entries for the tile are read up front (independent loads, all in
+    // flight at once); a shared-memory SA is read in place.
     constexpr int MAXIT = 16;
-    uint32_t sav[MAXIT];
+    uint32_t sav[SA_LOCAL ? 1 : MAXIT];
+    if constexpr (!SA_LOCAL) {
 #pragma unroll
-    for (int it = 0; it < MAXIT; ++it) {
-        const uint32_t q = it * 256u + threadIdx.x;
-        sav[it] = q < len ? (SA_LOCAL ? SA[q] : SA[tstart + q]) : 0u;
+        for (int it = 0; it < MAXIT; ++it) {
+            const uint32_t q = it * 256u + threadIdx.x;
+            sav[it] = q < len ? SA[tstart + q] : 0u;
+        }
     }
 #pragma unroll
     for (int it = 0; it < MAXIT; ++it) {
@@ -342,7 +345,9 @@ __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t
             const bool differs_prev = q > 0 && sk[q - 1] != key;
             const uint32_t lb = differs_prev ? q : (q == 0 ? 0u : smem_lower_bound<KeyT>(sk, q, key));
             const uint32_t gs = lb == 0 ? carry_start : tstart + lb;
-            const uint32_t sa = sav[it];
+            uint32_t sa;
+            if constexpr (SA_LOCAL) sa = SA[q];
+            else sa = sav[it];
             if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
             if (gs == k && emit_ok) {
                 uint32_t ub;

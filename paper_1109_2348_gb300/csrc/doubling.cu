@@ -575,10 +575,11 @@ cudaError_t launch_name_initial(const uint64_t* K, const uint32_t* SA, const Blo
     return cudaGetLastError();
 }
 
-cudaError_t launch_name_segments(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks,
-                                 const TileDesc* tiles, const uint32_t* num_tiles_dev, uint32_t* rank, Bins bins,
-                                 uint32_t* ctrl, cudaStream_t st) {
-    k_name_initial<<<num_sms() * 4, 256, 0, st>>>(K, SA, blocks, tiles, 0u, num_tiles_dev, true, rank, bins, ctrl);
+cudaError_t launch_name_tiles(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks, const TileDesc* tiles,
+                              const uint32_t* num_tiles_dev, bool seg_bounds, uint32_t* rank, Bins bins,
+                              uint32_t* ctrl, cudaStream_t st) {
+    k_name_initial<<<num_sms() * 4, 256, 0, st>>>(K, SA, blocks, tiles, 0u, num_tiles_dev, seg_bounds, rank, bins,
+                                                  ctrl);
     return cudaGetLastError();
 }
 

@@ -1,7 +1,8 @@
 // BWT_F_GRAPH: the whole batch as one CUDA graph, replayed when the block
 // layout and buffers repeat.
 //
-// Graph = reset -> first sort + naming -> set loop condition ->
+// Graph = reset -> first stage (plain: first sort + naming; with
+//         BWT_F_LEARNED: the learned first stage) -> set loop condition ->
 //         WHILE(cond) { round on bins[0]; round on bins[1]; set cond } ->
 //         L gather.
 // The body holds two rounds so the double-buffered group bins alternate
@@ -35,12 +36,18 @@ using namespace bwt;
 static std::vector<uint64_t> graph_key_of(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary) {
     std::vector<uint64_t> k = {(uint64_t)(uintptr_t)d_in, (uint64_t)(uintptr_t)d_L, (uint64_t)(uintptr_t)d_primary,
                                (uint64_t)p->rbits, (uint64_t)p->tile, (uint64_t)p->spin_limit,
-                               (uint64_t)p->withhold, (uint64_t)p->nb};
+                               (uint64_t)p->withhold, (uint64_t)p->nb, (uint64_t)p->round_bits};
     k.insert(k.end(), p->h_off, p->h_off + p->nb + 1);
     return k;
 }
 
 bwt_status bwt::run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st) {
+    const bool learned = (p->desc.flags & BWT_F_LEARNED) != 0;
+    if (learned) {
+        if (!p->have_model) return BWT_ENOMODEL;
+        bwt_status s = ensure_learned_buffers(p);  // allocations happen before any capture
+        if (s != BWT_OK) return s;
+    }
     std::vector<uint64_t> key = graph_key_of(p, d_in, d_L, d_primary);
     if (p->graph_exec && key == p->graph_key) {
         cudaError_t e = cudaGraphLaunch(p->graph_exec, st);
@@ -74,7 +81,8 @@ bwt_status bwt::run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_
     k0 = p->stats.kernel_launches;
     r0 = p->stats.radix_launches;
     CKS(reset_ctrl(p, cs));
-    CKS(enqueue_initial_sort(p, d_in, cs));
+    if (learned) CKS(enqueue_learned(p, d_in, cs));
+    else CKS(enqueue_initial_sort(p, d_in, cs));
     CKG(launch_set_cond_initial(p->ctrl, p->max_n, cond, cs));
     p->stats.kernel_launches++;
     k1 = p->stats.kernel_launches;

@@ -41,14 +41,17 @@ size_t onesweep_smem(int key_bytes, bool from_s, int radix_bits, int tile);
 
 // Byte histogram of every block (d = 8: every pass of the first sort has the
 // block's byte histogram as its digit histogram, because the pass-p digit of
-// rotation i is S[(i + 7 - p) mod n]). hist: [block][256], zeroed.
+// rotation i is S[(i + 7 - p) mod n]). hist: [block][256], zeroed. With
+// num_tiles_dev the tile count is read on the device (num_tiles ignored).
 cudaError_t launch_hist_bytes(const uint8_t* S, const BlockInfo* blocks, const TileDesc* tiles,
-                              uint32_t num_tiles, uint32_t* hist, cudaStream_t st);
+                              uint32_t num_tiles, uint32_t* hist, cudaStream_t st,
+                              const uint32_t* num_tiles_dev = nullptr);
 
 // Per-pass digit histograms of the u64 rotation prefixes for radix_bits = 11:
 // hist: [block][passes][2048], zeroed.
 cudaError_t launch_hist_keys11(const uint8_t* S, const BlockInfo* blocks, const TileDesc* tiles,
-                               uint32_t num_tiles, int tile, uint32_t* hist, cudaStream_t st);
+                               uint32_t num_tiles, int tile, uint32_t* hist, cudaStream_t st,
+                               const uint32_t* num_tiles_dev = nullptr);
 
 // Exclusive scan of every row of `radix` counts, in place; rows = *num_rows_dev
 // * rows_mult (or rows_host if num_rows_dev is null), at most max_rows.
@@ -68,12 +71,13 @@ cudaError_t launch_name_initial(const uint64_t* K, const uint32_t* SA, const Blo
                                 const TileDesc* tiles, uint32_t num_tiles, uint32_t* rank, Bins bins,
                                 uint32_t* ctrl, cudaStream_t st);
 
-// The same over tiles of segments that are whole ranges of groups (tiles
-// from launch_build_large_tiles; count on the device): carries stay inside
-// each tile's segment, so keys outside the segments are never read.
-cudaError_t launch_name_segments(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks,
-                                 const TileDesc* tiles, const uint32_t* num_tiles_dev, uint32_t* rank, Bins bins,
-                                 uint32_t* ctrl, cudaStream_t st);
+// The same with the tile count on the device. seg_bounds: every tile's
+// segment [segStart, segStart + pad0) is a whole range of groups (tiles from
+// launch_build_large_tiles), so the carries stay inside it and keys outside
+// the segments are never read; else the carries search the tile's block.
+cudaError_t launch_name_tiles(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks, const TileDesc* tiles,
+                              const uint32_t* num_tiles_dev, bool seg_bounds, uint32_t* rank, Bins bins,
+                              uint32_t* ctrl, cudaStream_t st);
 
 // Round with prefix length h = *depth: key2[k] = rank[(SA[k] + h) mod n] for
 // every element of the micro, tiny, small and medium groups in `cur`.

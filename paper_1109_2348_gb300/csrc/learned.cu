@@ -405,8 +405,8 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
     }
 }
 
-// Scatters the tiles of bucketed blocks to their chunks. A CTA takes `span`
-// consecutive tiles (reloading the block's chunk map and chunk starts into
+// Scatters the tiles of bucketed blocks to their chunks. A CTA takes runs of
+// consecutive tiles (up to 16, fewer when there are few tiles per CTA) (reloading the block's chunk map and chunk starts into
 // shared memory when the block changes). A rotation's bucket is its stored
 // learned bucket (fb) or, in blocks routed to equal-width buckets, its top 12
 // key bits. Each tile is ranked by chunk in shared memory (tile-local
@@ -418,8 +418,9 @@ constexpr size_t CHUNK_SCATTER_SMEM = NBK * 2 + 4 * MAXCH * 4 + TILE_BYTES + 409
 template <int ITEMS>
 __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict__ S,
                                                        const BlockInfo* __restrict__ blocks,
-                                                       const TileDesc* __restrict__ tiles, uint32_t ntiles,
-                                                       uint32_t span, const uint16_t* __restrict__ fb,
+                                                       const TileDesc* __restrict__ tiles,
+                                                       const uint32_t* __restrict__ ntiles_dev,
+                                                       const uint16_t* __restrict__ fb,
                                                        const uint32_t* __restrict__ route, ChunkTables ct,
                                                        uint64_t* __restrict__ K, uint32_t* __restrict__ I) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -432,6 +433,8 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
     uint16_t* stQ = reinterpret_cast<uint16_t*>(dbase + MAXCH);          // [4096] tile position by rank
     uint16_t* stC = stQ + 4096;                                          // [4096] its chunk
     __shared__ uint32_t scan_tmp[32];
+    const uint32_t ntiles = *ntiles_dev;
+    const uint32_t span = max(1u, min(16u, ntiles / (gridDim.x * 4u)));
     const uint32_t nspan = (ntiles + span - 1) / span;
     for (uint32_t s = blockIdx.x; s < nspan; s += gridDim.x) {
         const uint32_t t0 = s * span, t1 = min(ntiles, t0 + span);
@@ -600,7 +603,7 @@ __device__ __forceinline__ void cta_merge_sort(uint64_t* sK, uint32_t* sI) {
 // `bins` for the doubling rounds).
 constexpr size_t CHUNK_SORT_SMEM = (size_t)CHUNK_CAP * 12;
 
-__global__ void __launch_bounds__(MS_NT) k_chunk_sort_name(const uint64_t* __restrict__ K,
+__global__ void __launch_bounds__(MS_NT, 4) k_chunk_sort_name(const uint64_t* __restrict__ K,
                                                           uint32_t* __restrict__ SA,
                                                           const BlockInfo* __restrict__ blocks, Bins chunks,
                                                           uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl) {
@@ -638,6 +641,63 @@ __global__ void k_select_rows(uint32_t* __restrict__ counts, const uint32_t* __r
         if (route[blk] == 2u)
             for (int i = threadIdx.x; i < NBK; i += blockDim.x)
                 counts[(size_t)blk * NBK + i] = counts[((size_t)nb + blk) * NBK + i];
+}
+
+// Routes every block and numbers its tiles in its route's tile table, in one
+// CTA: route 0 (learned buckets) if the learned over-capacity buckets hold at
+// most a quarter of the block, else 2 (equal-width buckets) if those do, else
+// 1 (plain radix); blocks too large for the chunk tables go plain. first:
+// [2][block] first tile of the block in the plain table and in the bucketed
+// table; the two table sizes go to ctrl[CTRL_AUX0] and ctrl[CTRL_AUX1].
+__global__ void __launch_bounds__(1024) k_route_scan(const unsigned long long* __restrict__ bstats,
+                                                     const BlockInfo* __restrict__ blocks, uint32_t nb, uint32_t tile,
+                                                     uint32_t* __restrict__ route, uint32_t* __restrict__ first,
+                                                     uint32_t* ctrl) {
+    __shared__ uint32_t tmp[32];
+    uint32_t run_p = 0, run_b = 0;
+    for (uint32_t base = 0; base < nb; base += 1024) {
+        const uint32_t b = base + threadIdx.x;
+        uint32_t np = 0, nbk = 0;
+        if (b < nb) {
+            const uint64_t n = blocks[b].n;
+            const unsigned long long* bl = bstats + 5 * (size_t)b;
+            const unsigned long long* bf = bstats + 5 * ((size_t)nb + b);
+            const bool too_big = n * 2 > (uint64_t)(MAXCH - 2) * CHUNK_CAP;
+            const uint32_t r = too_big ? 1u : bl[0] * 4 <= n ? 0u : bf[0] * 4 <= n ? 2u : 1u;
+            route[b] = r;
+            const uint32_t nt = (uint32_t)((n + tile - 1) / tile);
+            if (r == 1u) np = nt; else nbk = nt;
+        }
+        uint32_t tot_p, tot_b;
+        const uint32_t ep = block_exclusive_scan<1024>(np, tmp, &tot_p);
+        const uint32_t eb = block_exclusive_scan<1024>(nbk, tmp, &tot_b);
+        if (b < nb) {
+            first[b] = run_p + ep;
+            first[nb + b] = run_b + eb;
+        }
+        run_p += tot_p;
+        run_b += tot_b;
+    }
+    if (threadIdx.x == 0) {
+        ctrl[CTRL_AUX0] = run_p;
+        ctrl[CTRL_AUX1] = run_b;
+    }
+}
+
+// Copies every first-sort tile into its block's route table (plain, or
+// bucketed), with its first-tile index relative to that table.
+__global__ void k_route_tiles(const TileDesc* __restrict__ tiles0, uint32_t ntiles0, uint32_t nb,
+                              const uint32_t* __restrict__ route, const uint32_t* __restrict__ first,
+                              TileDesc* __restrict__ tiles_p, TileDesc* __restrict__ tiles_b) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles0; t += gridDim.x * blockDim.x) {
+        TileDesc td = tiles0[t];
+        const uint32_t b = td.blk;
+        const bool plain = route[b] == 1u;
+        const uint32_t f = plain ? first[b] : first[nb + b];
+        const uint32_t dst = f + (t - td.firstTile);
+        td.firstTile = f;
+        (plain ? tiles_p : tiles_b)[dst] = td;
+    }
 }
 
 // Per overflow segment: digit histograms of PI index passes then PK key passes.
@@ -704,8 +764,9 @@ bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
     if (!p->chunk_map) CKL(cudaMalloc(&p->chunk_map, sizeof(uint16_t) * nbk));
     if (!p->chunk_base) CKL(cudaMalloc(&p->chunk_base, sizeof(uint32_t) * nbk));
     if (!p->route) CKL(cudaMalloc(&p->route, sizeof(uint32_t) * p->cap_b));
+    if (!p->route_first) CKL(cudaMalloc(&p->route_first, sizeof(uint32_t) * 2 * p->cap_b));
     if (!p->bstats) CKL(cudaMalloc(&p->bstats, sizeof(unsigned long long) * 10 * p->cap_b));
-    if (!p->tiles_aux) CKL(cudaMalloc(&p->tiles_aux, sizeof(TileDesc) * p->cap_tiles0));
+    if (!p->tiles_aux) CKL(cudaMalloc(&p->tiles_aux, sizeof(TileDesc) * 2 * (size_t)p->cap_tiles0));
     if (!p->splitters_flat) {
         std::vector<uint64_t> flat(NSP);
         for (int j = 0; j < NSP; ++j) flat[j] = (uint64_t)(j + 1) << 52;  // bucket = top 12 key bits
@@ -714,109 +775,24 @@ bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
     }
     if (!p->h_route) CKL(cudaMallocHost(&p->h_route, sizeof(uint32_t) * p->cap_b));
     if (!p->h_bstats) CKL(cudaMallocHost(&p->h_bstats, sizeof(unsigned long long) * 10 * p->cap_b));
-    if (!p->h_tiles_aux) CKL(cudaMallocHost(&p->h_tiles_aux, sizeof(TileDesc) * p->cap_tiles0));
+    // kernel attributes and occupancy: set up here, outside any stream capture
+    static const int sort_ctas = [] {
+        cudaFuncSetAttribute((void*)k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COUNT_SMEM);
+        cudaFuncSetAttribute((void*)k_chunk_sort_name, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CHUNK_SORT_SMEM);
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_sort_name, MS_NT, CHUNK_SORT_SMEM);
+        return std::max(1, per_sm);
+    }();
+    p->chunk_sort_ctas = sort_ctas;
     return BWT_OK;
 }
 
-bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st) {
-    if (!p->have_model) return BWT_ENOMODEL;
-    bwt_status s;
-    if ((s = ensure_learned_buffers(p)) != BWT_OK) return s;
-    static bool attr = [] {
-        cudaFuncSetAttribute((void*)k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COUNT_SMEM);
-        cudaFuncSetAttribute((void*)k_chunk_scatter<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)CHUNK_SCATTER_SMEM);
-        cudaFuncSetAttribute((void*)k_chunk_scatter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)CHUNK_SCATTER_SMEM);
-        cudaFuncSetAttribute((void*)k_chunk_scatter<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)CHUNK_SCATTER_SMEM);
-        cudaFuncSetAttribute((void*)k_chunk_sort_name, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)CHUNK_SORT_SMEM);
-        return true;
-    }();
-    (void)attr;
+bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t st) {
     const uint32_t nb = p->nb, nt = p->ntiles0;
     const int sms = num_sms();
     uint32_t* ctrl = p->ctrl;
-    if ((s = reset_ctrl(p, st)) != BWT_OK) return s;
-
-    // 1. count both bucketings per block and store every rotation's learned
-    //    bucket (in the u16 view of keys[1], free until the scatter has run),
-    // 2. per-block statistics of both
-    uint16_t* fb = reinterpret_cast<uint16_t*>(p->keys[1]);
-    CKL(cudaMemsetAsync(p->bucket_count, 0, sizeof(uint32_t) * 2 * NBK * nb, st));
-    {
-        const uint32_t span_max = 65535u / (uint32_t)p->tile;  // packed 16-bit counts per span
-        const uint32_t span = std::max(1u, std::min(span_max, nt / (uint32_t)(sms * 8)));
-        const int grid = std::max(1, std::min<int>((nt + span - 1) / span, sms * 3));
-        k_bucket_count<<<grid, 256, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles0, nt, span, p->splitters, nb,
-                                                      p->bucket_count, fb);
-    }
-    k_bucket_stats<<<std::min<uint32_t>(2 * nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, 2 * nb, p->bstats);
-    CKL(cudaGetLastError());
-    CKL(cudaMemcpyAsync(p->h_bstats, p->bstats, sizeof(unsigned long long) * 10 * nb, cudaMemcpyDeviceToHost, st));
-    CKL(cudaStreamSynchronize(st));
-    p->stats.kernel_launches += 2;
-
-    // 3. route each block: learned buckets (0) if their overflow holds at most a
-    //    quarter of the block; else equal-width buckets (2) if those do; else
-    //    the plain radix (1)
     const uint32_t T = (uint32_t)p->tile;
-    uint64_t plain_keys = 0;
-    for (uint32_t b = 0; b < nb; ++b) {
-        const unsigned long long* bl = p->h_bstats + 5 * b;         // learned
-        const unsigned long long* bf = p->h_bstats + 5 * (nb + b);  // equal-width
-        const uint64_t n = p->h_blocks[b].n;
-        const bool too_big = n * 2 > (uint64_t)(MAXCH - 2) * CHUNK_CAP;
-        const uint32_t r = too_big ? 1u : bl[0] * 4 <= n ? 0u : bf[0] * 4 <= n ? 2u : 1u;
-        p->h_route[b] = r;
-        p->stats.max_bucket = std::max<uint32_t>(p->stats.max_bucket, (uint32_t)bl[2]);
-        p->stats.bucket_sq_sum += bl[3];
-        p->stats.buckets_nonempty += bl[4];
-        if (r == 1u) {
-            plain_keys += n;
-            p->stats.blocks_routed_plain++;
-        } else {
-            const unsigned long long* bs = r == 2u ? bf : bl;
-            if (r == 2u) p->stats.blocks_routed_flat++;
-            p->stats.buckets_overflowed += bs[1];
-            p->stats.keys_overflowed += bs[0];
-        }
-    }
-    auto build_tiles = [&](uint32_t code, uint32_t base, uint32_t* count) {
-        uint32_t nt_ = 0;
-        for (uint32_t b = 0; b < nb; ++b) {
-            if (p->h_route[b] != code) continue;
-            const BlockInfo bi = p->h_blocks[b];
-            const uint32_t first = nt_;
-            for (uint32_t o = 0; o < bi.n; o += T) {
-                TileDesc td;
-                td.start = bi.off + o;
-                td.len = std::min(T, bi.n - o);
-                td.seg = b;
-                td.firstTile = first;
-                td.segStart = bi.off;
-                td.blk = b;
-                td.pad0 = bi.n;
-                td.pad1 = 0;
-                p->h_tiles_aux[base + nt_++] = td;
-            }
-        }
-        *count = nt_;
-    };
-    // sub-tables (first-tile indices relative to each sub-table)
-    uint32_t ntp = 0, ntl = 0, ntf = 0;
-    build_tiles(1u, 0, &ntp);
-    build_tiles(0u, ntp, &ntl);
-    build_tiles(2u, ntp + ntl, &ntf);
-    const uint32_t ntb = ntl + ntf;
-    CKL(cudaMemcpyAsync(p->route, p->h_route, sizeof(uint32_t) * nb, cudaMemcpyHostToDevice, st));
-    CKL(cudaMemcpyAsync(p->tiles_aux, p->h_tiles_aux, sizeof(TileDesc) * (ntp + ntb), cudaMemcpyHostToDevice, st));
-    p->h_aux[0] = ntp;
-    p->h_aux[1] = ntb;
-    CKL(cudaMemcpyAsync(ctrl + CTRL_AUX0, p->h_aux, sizeof(uint32_t) * 2, cudaMemcpyHostToDevice, st));
-    const TileDesc* tilesP = p->tiles_aux;
-
     p->sa = p->vals[0];
     p->key2 = p->vals[1];
     p->kA = reinterpret_cast<uint32_t*>(p->keys[1]);
@@ -824,51 +800,79 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
     p->kB = reinterpret_cast<uint32_t*>(p->keys[0]);
     p->vB = p->kB + p->cap_n;
 
+    // 1. count both bucketings per block and store every rotation's learned
+    //    bucket (in the u16 view of keys[1], free until the scatter has run),
+    // 2. per-block statistics of both, 3. route every block and split the
+    //    tile table by route -- all on the device
+    uint16_t* fb = reinterpret_cast<uint16_t*>(p->keys[1]);
+    CKL(cudaMemsetAsync(p->bucket_count, 0, sizeof(uint32_t) * 2 * NBK * nb, st));
+    {
+        const uint32_t span_max = 65535u / T;  // packed 16-bit counts per span
+        const uint32_t span = std::max(1u, std::min(span_max, nt / (uint32_t)(sms * 8)));
+        const int grid = std::max(1, std::min<int>((nt + span - 1) / span, sms * 3));
+        k_bucket_count<<<grid, 256, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles0, nt, span, p->splitters, nb,
+                                                      p->bucket_count, fb);
+    }
+    k_bucket_stats<<<std::min<uint32_t>(2 * nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, 2 * nb, p->bstats);
+    k_route_scan<<<1, 1024, 0, st>>>(p->bstats, p->blocks, nb, T, p->route, p->route_first, ctrl);
+    TileDesc* tilesP = p->tiles_aux;
+    TileDesc* tilesB = p->tiles_aux + p->cap_tiles0;
+    k_route_tiles<<<std::max(1, std::min<int>((nt + 255) / 256, sms * 4)), 256, 0, st>>>(
+        p->tiles0, nt, nb, p->route, p->route_first, tilesP, tilesB);
+    CKL(cudaGetLastError());
+    // for the statistics, read after the call
+    CKL(cudaMemcpyAsync(p->h_bstats, p->bstats, sizeof(unsigned long long) * 10 * nb, cudaMemcpyDeviceToHost, st));
+    CKL(cudaMemcpyAsync(p->h_route, p->route, sizeof(uint32_t) * nb, cudaMemcpyDeviceToHost, st));
+    p->stats.kernel_launches += 4;
+    const uint32_t* ntp = ctrl + CTRL_AUX0;
+    const uint32_t* ntb = ctrl + CTRL_AUX1;
+
     // 4a. bucketed blocks: bucket starts, chunk plan and scatter (the scatter
     //     consumes fb, so it runs before the plain passes reuse keys[1])
     Bins aux = bins_of(p, 1);
     CKL(cudaMemsetAsync(aux.count, 0, sizeof(uint32_t) * NCLS, st));
-    if (ntb) {
-        k_select_rows<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->route, nb);
-        CKL(launch_scan_rows(p->bucket_count, NBK, nullptr, 0, nb, nb, st));  // counts -> starts in place
-        ChunkTables ct{p->chunk_map, p->chunk_base, p->bucket_cursor};
-        k_chunk_plan<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->blocks, p->route, nb, ct, aux,
-                                                                    ctrl);
-        const TileDesc* tilesB = p->tiles_aux + ntp;
-        const uint32_t span = std::max(1u, std::min(16u, ntb / (uint32_t)(sms * 16)));
-        const int g = std::max(1, std::min<int>((ntb + span - 1) / span, sms * 5));
+    k_select_rows<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->route, nb);
+    CKL(launch_scan_rows(p->bucket_count, NBK, nullptr, 0, nb, nb, st));  // counts -> starts in place
+    ChunkTables ct{p->chunk_map, p->chunk_base, p->bucket_cursor};
+    k_chunk_plan<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->blocks, p->route, nb, ct, aux,
+                                                                ctrl);
+    {
+        const int g = sms * 4;
         if (T <= 1024)
-            k_chunk_scatter<4><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, span, fb, p->route,
-                                                                   ct, p->keys[0], p->vals[0]);
+            k_chunk_scatter<4><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, fb, p->route, ct,
+                                                                   p->keys[0], p->vals[0]);
         else if (T <= 2048)
-            k_chunk_scatter<8><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, span, fb, p->route,
-                                                                   ct, p->keys[0], p->vals[0]);
+            k_chunk_scatter<8><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, fb, p->route, ct,
+                                                                   p->keys[0], p->vals[0]);
         else
-            k_chunk_scatter<16><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, span, fb,
-                                                                    p->route, ct, p->keys[0], p->vals[0]);
-        CKL(cudaGetLastError());
-        p->stats.kernel_launches += 4;
+            k_chunk_scatter<16><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, fb, p->route, ct,
+                                                                    p->keys[0], p->vals[0]);
     }
+    CKL(cudaGetLastError());
+    p->stats.kernel_launches += 4;
 
-    // 4b. plain-routed blocks: the first sort of the plain path, ending in buffer 0, and its naming
+    // 4b. plain-routed blocks: the first sort of the plain path, ending in
+    //     buffer 0, and its naming (with no plain-routed block every kernel
+    //     here finds zero tiles and returns)
     const int rb = p->rbits, RADIX = 1 << rb;
-    if (ntp) {
+    const uint32_t status_cap = (uint32_t)std::min<uint64_t>(p->cap_status, 0xffffffffu);
+    {
         const int P = (64 + rb - 1) / rb;
         uint32_t seg_stride;
         if (rb == 8) {
             CKL(cudaMemsetAsync(p->hist, 0, sizeof(uint32_t) * 256 * nb, st));
-            CKL(launch_hist_bytes(d_in, p->blocks, tilesP, ntp, p->hist, st));
+            CKL(launch_hist_bytes(d_in, p->blocks, tilesP, 0, p->hist, st, ntp));
             CKL(launch_scan_rows(p->hist, 256, nullptr, 0, nb, nb, st));
             seg_stride = 256;
         } else {
             CKL(cudaMemsetAsync(p->hist, 0, sizeof(uint32_t) * 6 * 2048 * nb, st));
-            CKL(launch_hist_keys11(d_in, p->blocks, tilesP, ntp, p->tile, p->hist, st));
+            CKL(launch_hist_keys11(d_in, p->blocks, tilesP, 0, p->tile, p->hist, st, ntp));
             CKL(launch_scan_rows(p->hist, 2048, nullptr, 0, nb * 6, nb * 6, st));
             seg_stride = 6 * 2048;
         }
         p->stats.kernel_launches += 2;
         for (int ps = 0; ps < P; ++ps) {
-            CKL(cudaMemsetAsync(p->status, 0, sizeof(uint32_t) * (size_t)ntp * RADIX, st));
+            CKL(launch_zero_by_count(p->status, ntp, (uint32_t)RADIX, status_cap, st));
             OneSweepParams a{};
             const int out = (P - 1 - ps) & 1, in = (P - ps) & 1;
             a.kin = ps == 0 ? nullptr : p->keys[in];
@@ -878,7 +882,7 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
             a.S = d_in;
             a.blocks = p->blocks;
             a.tiles = tilesP;
-            a.num_tiles = ctrl + CTRL_AUX0;
+            a.num_tiles = ntp;
             a.seg_base = p->hist + (rb == 8 ? 0 : ps * 2048);
             a.seg_base_stride = seg_stride;
             a.status = p->status;
@@ -886,75 +890,96 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
             a.ctrl = ctrl;
             a.shift = ps * rb;
             CKL(launch_onesweep(8, ps == 0, rb, p->tile, a, 0, st));
-            p->stats.kernel_launches++;
+            p->stats.kernel_launches += 2;
             p->stats.radix_launches++;
-            p->stats.radix_keys += plain_keys;
         }
-        CKL(launch_name_initial(p->keys[0], p->vals[0], p->blocks, tilesP, ntp, p->rank, bins_of(p, 0), ctrl, st));
+        CKL(launch_name_tiles(p->keys[0], p->vals[0], p->blocks, tilesP, ntp, false, p->rank, bins_of(p, 0), ctrl,
+                              st));
         p->stats.kernel_launches++;
     }
 
     // 4c. bucketed blocks: chunk sorts with naming, then the overflow buckets
-    if (ntb) {
-        static const int sort_ctas = [] {
-            int per_sm = 1;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_sort_name, MS_NT, CHUNK_SORT_SMEM);
-            return std::max(1, per_sm);
-        }();
-        k_chunk_sort_name<<<sms * sort_ctas, MS_NT, CHUNK_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks, aux,
-                                                                          p->rank, bins_of(p, 0), ctrl);
-        CKL(cudaGetLastError());
-        p->stats.kernel_launches++;
+    k_chunk_sort_name<<<sms * p->chunk_sort_ctas, MS_NT, CHUNK_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks,
+                                                                                  aux, p->rank, bins_of(p, 0), ctrl);
+    CKL(cudaGetLastError());
+    p->stats.kernel_launches++;
 
-        // overflow buckets: radix on the index, then on the key
-        const int PI = std::max(1, (bits_needed(p->max_n - 1) + 7) / 8), PK = 8, PT = PI + PK;
-        CKL(launch_build_large_tiles(aux, p->tile, p->ltiles, p->cap_ltiles, ctrl, st));
-        CKL(launch_zero_by_count(p->hist, aux.count + CLS_LARGE, (uint32_t)(PT * 256),
-                                 (uint32_t)std::min<uint64_t>(p->cap_hist, 0xffffffffu), st));
-        k_seg_hist_u64<<<sms * 4, 256, PT * 256 * 4, st>>>(p->keys[0], p->vals[0], p->ltiles, ctrl + CTRL_NUM_LTILES,
-                                                           p->hist, PI, PK);
+    // overflow buckets: radix on the index, then on the key
+    const int PI = std::max(1, (bits_needed(p->max_n - 1) + 7) / 8), PK = 8, PT = PI + PK;
+    CKL(launch_build_large_tiles(aux, p->tile, p->ltiles, p->cap_ltiles, ctrl, st));
+    CKL(launch_zero_by_count(p->hist, aux.count + CLS_LARGE, (uint32_t)(PT * 256),
+                             (uint32_t)std::min<uint64_t>(p->cap_hist, 0xffffffffu), st));
+    k_seg_hist_u64<<<sms * 4, 256, PT * 256 * 4, st>>>(p->keys[0], p->vals[0], p->ltiles, ctrl + CTRL_NUM_LTILES,
+                                                       p->hist, PI, PK);
+    CKL(cudaGetLastError());
+    CKL(launch_scan_rows(p->hist, 256, aux.count + CLS_LARGE, (uint32_t)PT, 0, (uint32_t)(p->cap_hist / 256), st));
+    p->stats.kernel_launches += 4;
+    for (int ps = 0; ps < PT; ++ps) {
+        CKL(launch_zero_by_count(p->status, ctrl + CTRL_NUM_LTILES, 256u, status_cap, st));
+        CKL(cudaMemsetAsync(ctrl + CTRL_TILE_CTR + 16 + ps, 0, 4, st));
+        OneSweepParams a{};
+        a.kin = p->keys[ps & 1];
+        a.vin = p->vals[ps & 1];
+        a.kout = p->keys[(ps + 1) & 1];
+        a.vout = p->vals[(ps + 1) & 1];
+        a.blocks = p->blocks;
+        a.tiles = p->ltiles;
+        a.num_tiles = ctrl + CTRL_NUM_LTILES;
+        a.seg_base = p->hist + ps * 256;
+        a.seg_base_stride = (uint32_t)(PT * 256);
+        a.status = p->status;
+        a.tile_counter = ctrl + CTRL_TILE_CTR + 16 + ps;
+        a.ctrl = ctrl;
+        a.shift = ps < PI ? 8 * ps : 8 * (ps - PI);
+        CKL(launch_onesweep(ps < PI ? -8 : 8, false, 8, p->tile, a, 0, st));
+        p->stats.kernel_launches += 2;
+        p->stats.radix_launches++;
+    }
+    if (PT & 1) {
+        k_copy_tiles<<<sms * 4, 256, 0, st>>>(p->keys[1], p->vals[1], p->keys[0], p->vals[0], p->ltiles,
+                                              ctrl + CTRL_NUM_LTILES);
         CKL(cudaGetLastError());
-        CKL(launch_scan_rows(p->hist, 256, aux.count + CLS_LARGE, (uint32_t)PT, 0, (uint32_t)(p->cap_hist / 256),
-                             st));
-        p->stats.kernel_launches += 4;
-        for (int ps = 0; ps < PT; ++ps) {
-            CKL(launch_zero_by_count(p->status, ctrl + CTRL_NUM_LTILES, 256u,
-                                     (uint32_t)std::min<uint64_t>(p->cap_status, 0xffffffffu), st));
-            CKL(cudaMemsetAsync(ctrl + CTRL_TILE_CTR + 16 + ps, 0, 4, st));
-            OneSweepParams a{};
-            a.kin = p->keys[ps & 1];
-            a.vin = p->vals[ps & 1];
-            a.kout = p->keys[(ps + 1) & 1];
-            a.vout = p->vals[(ps + 1) & 1];
-            a.blocks = p->blocks;
-            a.tiles = p->ltiles;
-            a.num_tiles = ctrl + CTRL_NUM_LTILES;
-            a.seg_base = p->hist + ps * 256;
-            a.seg_base_stride = (uint32_t)(PT * 256);
-            a.status = p->status;
-            a.tile_counter = ctrl + CTRL_TILE_CTR + 16 + ps;
-            a.ctrl = ctrl;
-            a.shift = ps < PI ? 8 * ps : 8 * (ps - PI);
-            CKL(launch_onesweep(ps < PI ? -8 : 8, false, 8, p->tile, a, 0, st));
-            p->stats.kernel_launches += 2;
-            p->stats.radix_launches++;
-            p->stats.radix_keys += p->stats.keys_overflowed;
-        }
-        if (PT & 1) {
-            k_copy_tiles<<<sms * 4, 256, 0, st>>>(p->keys[1], p->vals[1], p->keys[0], p->vals[0], p->ltiles,
-                                                  ctrl + CTRL_NUM_LTILES);
-            CKL(cudaGetLastError());
-            p->stats.kernel_launches++;
-        }
-        // overflow buckets are whole key ranges too: name them inside their own bounds
-        CKL(launch_name_segments(p->keys[0], p->vals[0], p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, p->rank,
-                                 bins_of(p, 0), ctrl, st));
         p->stats.kernel_launches++;
     }
+    // overflow buckets are whole key ranges too: name them inside their own bounds
+    CKL(launch_name_tiles(p->keys[0], p->vals[0], p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, true, p->rank,
+                          bins_of(p, 0), ctrl, st));
+    p->stats.kernel_launches++;
+    p->learned_overflow_passes = (uint32_t)PT;
+    return BWT_OK;
+}
 
-    // 5. prefix doubling and the L gather, as on the plain path, from buffer 0
-    //    (every block is named: plain-routed ones after their radix, the
-    //    bucketed ones by the chunk sort and the overflow naming)
+void bwt::learned_stats(bwt_plan* p) {
+    const uint32_t nb = p->nb;
+    const int P = (64 + p->rbits - 1) / p->rbits;
+    for (uint32_t b = 0; b < nb; ++b) {
+        const unsigned long long* bl = p->h_bstats + 5 * (size_t)b;
+        const unsigned long long* bf = p->h_bstats + 5 * ((size_t)nb + b);
+        const uint32_t r = p->h_route[b];
+        p->stats.max_bucket = std::max<uint32_t>(p->stats.max_bucket, (uint32_t)bl[2]);
+        p->stats.bucket_sq_sum += bl[3];
+        p->stats.buckets_nonempty += bl[4];
+        if (r == 1u) {
+            p->stats.blocks_routed_plain++;
+            p->stats.radix_keys += (uint64_t)P * p->h_blocks[b].n;
+        } else {
+            const unsigned long long* bs = r == 2u ? bf : bl;
+            if (r == 2u) p->stats.blocks_routed_flat++;
+            p->stats.buckets_overflowed += bs[1];
+            p->stats.keys_overflowed += bs[0];
+        }
+    }
+    p->stats.radix_keys += (uint64_t)p->learned_overflow_passes * p->stats.keys_overflowed;
+}
+
+// Host-driven learned mode: the learned first stage, then doubling rounds
+// driven from the host, then the L gather.
+bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st) {
+    if (!p->have_model) return BWT_ENOMODEL;
+    bwt_status s;
+    if ((s = ensure_learned_buffers(p)) != BWT_OK) return s;
+    if ((s = reset_ctrl(p, st)) != BWT_OK) return s;
+    if ((s = enqueue_learned(p, d_in, st)) != BWT_OK) return s;
     if ((s = run_doubling_host_loop(p, st)) != BWT_OK) return s;
     CKL(launch_gather_L(d_in, p->sa, p->blocks, p->tiles0, p->ntiles0, d_L, d_primary, st));
     p->stats.kernel_launches++;

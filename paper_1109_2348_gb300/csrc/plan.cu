@@ -115,9 +115,9 @@ void bwt::free_plan_memory(bwt_plan* p) {
     F(p->tiles0); F(p->ltiles); F(p->blocks); F(p->hist); F(p->status); F(p->ctrl);
     for (int s = 0; s < 2; ++s)
         for (int c = 0; c < NCLS; ++c) F(p->bins[s][c]);
-    F(p->splitters); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->bstats); F(p->tiles_aux);
+    F(p->splitters); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->route_first); F(p->bstats); F(p->tiles_aux);
     FH(p->h_ctrl); FH(p->h_tiles); FH(p->h_blocks); FH(p->h_off);
-    FH(p->h_route); FH(p->h_bstats); FH(p->h_tiles_aux);
+    FH(p->h_route); FH(p->h_bstats);
     for (auto& e : p->events) cudaEventDestroy(e);
     p->events.clear();
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
@@ -597,19 +597,22 @@ extern "C" bwt_status bwt_forward_batch(bwt_plan* p, const uint8_t* d_in, const 
     p->stats.radix_bits = (uint32_t)p->rbits;
     p->stats.round_radix_bits = (uint32_t)(p->round_bits ? p->round_bits : 8);
     p->stats.tile_keys = (uint32_t)p->tile;
-    if (p->desc.flags & BWT_F_PER_BLOCK_LAUNCH) {
+    const bool per_block = (p->desc.flags & BWT_F_PER_BLOCK_LAUNCH) != 0;
+    const bool graph = !per_block && (p->desc.flags & BWT_F_GRAPH);
+    const bool learned = !per_block && (p->desc.flags & BWT_F_LEARNED);
+    if (per_block) {
         s = run_per_block(p, d_in, d_L, d_primary, st);
-    } else if (p->desc.flags & BWT_F_LEARNED) {
+    } else if (graph) {
+        s = run_graph(p, d_in, d_L, d_primary, st);  // plain or learned first stage
+    } else if (learned) {
         s = run_learned(p, d_in, d_L, d_primary, st);
-    } else if (p->desc.flags & BWT_F_GRAPH) {
-        s = run_graph(p, d_in, d_L, d_primary, st);
     } else {
         s = run_plain_host_loop(p, d_in, d_L, d_primary, st);
     }
     if (s == BWT_OK) s = finish_status(p, st);
     else cudaStreamSynchronize(st);
-    if ((p->desc.flags & BWT_F_GRAPH) && !(p->desc.flags & (BWT_F_PER_BLOCK_LAUNCH | BWT_F_LEARNED)))
-        graph_stats(p);
+    if (graph) graph_stats(p);
+    if (learned && s != BWT_ENOMODEL && p->h_bstats) learned_stats(p);
     if (!p->events.empty()) collect_timing(p);
     const uint64_t act = (uint64_t)p->h_ctrl[CTRL_ACTIVE] | ((uint64_t)p->h_ctrl[CTRL_ACTIVE + 1] << 32);
     p->stats.active_elements = act;

@@ -55,19 +55,20 @@ struct bwt_plan {
     // learned bucketing (allocated when a model is installed)
     uint64_t* splitters = nullptr;      // [BWT_SPLITTERS] sorted
     uint64_t* splitters_flat = nullptr; // [BWT_SPLITTERS] equal-width fallback (top 12 key bits)
-    uint32_t* bucket_count = nullptr;   // [block][BWT_BUCKETS] counts, then starts
+    uint32_t* bucket_count = nullptr;   // [2][block][BWT_BUCKETS] counts (learned, equal-width), then starts
     uint32_t* bucket_cursor = nullptr;  // [block][BWT_BUCKETS] slots taken so far (per chunk)
     uint16_t* chunk_map = nullptr;      // [block][BWT_BUCKETS] chunk of each bucket
     uint32_t* chunk_base = nullptr;     // [block][BWT_BUCKETS] block-relative start of each chunk
-    uint32_t* route = nullptr;          // [block] 0 = buckets, 1 = plain radix
-    unsigned long long* bstats = nullptr;  // [block][5] overflow keys, overflow buckets, largest bucket,
+    uint32_t* route = nullptr;          // [block] 0 = learned buckets, 1 = plain radix, 2 = equal-width buckets
+    uint32_t* route_first = nullptr;    // [2][block] first tile of each block in its route's tile table
+    unsigned long long* bstats = nullptr;  // [2][block][5] overflow keys, overflow buckets, largest bucket,
                                            // sum of squared sizes, non-empty buckets
-    bwt::TileDesc* tiles_aux = nullptr; // sub-tables of plain-routed and bucketed blocks
+    bwt::TileDesc* tiles_aux = nullptr; // [2][tiles0]: tiles of plain-routed blocks, then of bucketed ones
     uint32_t* h_route = nullptr;
     unsigned long long* h_bstats = nullptr;
-    bwt::TileDesc* h_tiles_aux = nullptr;
-    uint32_t h_aux[4] = {0, 0, 0, 0};
     bool have_model = false;
+    int chunk_sort_ctas = 1;            // resident chunk-sort CTAs per SM
+    uint32_t learned_overflow_passes = 0;  // radix passes over the overflow buckets (index + key)
 
     // pinned host staging
     uint32_t* h_ctrl = nullptr;
@@ -119,6 +120,13 @@ bwt_status run_doubling_host_loop(bwt_plan* p, cudaStream_t st);
 bwt_status run_per_block(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st);
 bwt_status run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st);
 bwt_status run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st);
+// Learned first stage (bucket count, device-side routing, scatter, chunk sorts
+// with naming, overflow radix, plain radix of plain-routed blocks) with no
+// host synchronisation, so it can be captured; ctrl must have been reset.
+bwt_status enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t st);
+// After the call has synchronised: routing and bucket statistics from the
+// per-block counters the learned stage copied to the host.
+void learned_stats(bwt_plan* p);
 bwt_status load_model(bwt_plan* p, const char* path);
 void graph_stats(bwt_plan* p);
 bwt_status ensure_learned_buffers(bwt_plan* p);

@@ -264,8 +264,10 @@ __global__ void __launch_bounds__(OsThreads<TILE>::value, OsMinBlocks<TILE>::val
 // do not serialise on one shared-memory counter.
 __global__ void __launch_bounds__(256) k_hist_bytes(const uint8_t* __restrict__ S, const BlockInfo* __restrict__ blocks,
                                                     const TileDesc* __restrict__ tiles, uint32_t num_tiles,
+                                                    const uint32_t* __restrict__ num_tiles_dev,
                                                     uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[256];
+    if (num_tiles_dev) num_tiles = *num_tiles_dev;
     for (uint32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
         h[threadIdx.x] = 0;
         __syncthreads();
@@ -296,8 +298,10 @@ __global__ void __launch_bounds__(256) k_hist_bytes(const uint8_t* __restrict__ 
 template <int TILE>
 __global__ void __launch_bounds__(256) k_hist_keys11(const uint8_t* __restrict__ S, const BlockInfo* __restrict__ blocks,
                                                      const TileDesc* __restrict__ tiles, uint32_t num_tiles,
+                                                     const uint32_t* __restrict__ num_tiles_dev,
                                                      uint32_t* __restrict__ hist) {
     constexpr int RADIX = 2048, PASSES = 6;
+    if (num_tiles_dev) num_tiles = *num_tiles_dev;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* h = reinterpret_cast<uint32_t*>(smem);
     uint8_t* sbytes = smem + PASSES * RADIX * 4;
@@ -452,16 +456,16 @@ cudaError_t launch_onesweep(int key_bytes, bool from_s, int radix_bits, int tile
 }
 
 cudaError_t launch_hist_bytes(const uint8_t* S, const BlockInfo* blocks, const TileDesc* tiles, uint32_t num_tiles,
-                              uint32_t* hist, cudaStream_t st) {
-    if (num_tiles == 0) return cudaSuccess;
-    const int grid = (int)std::min<uint32_t>(num_tiles, (uint32_t)num_sms() * 8);
-    k_hist_bytes<<<grid, 256, 0, st>>>(S, blocks, tiles, num_tiles, hist);
+                              uint32_t* hist, cudaStream_t st, const uint32_t* num_tiles_dev) {
+    if (num_tiles == 0 && !num_tiles_dev) return cudaSuccess;
+    const int grid = num_tiles_dev ? num_sms() * 8 : (int)std::min<uint32_t>(num_tiles, (uint32_t)num_sms() * 8);
+    k_hist_bytes<<<grid, 256, 0, st>>>(S, blocks, tiles, num_tiles, num_tiles_dev, hist);
     return cudaGetLastError();
 }
 
 cudaError_t launch_hist_keys11(const uint8_t* S, const BlockInfo* blocks, const TileDesc* tiles, uint32_t num_tiles,
-                               int tile, uint32_t* hist, cudaStream_t st) {
-    if (num_tiles == 0) return cudaSuccess;
+                               int tile, uint32_t* hist, cudaStream_t st, const uint32_t* num_tiles_dev) {
+    if (num_tiles == 0 && !num_tiles_dev) return cudaSuccess;
     const size_t smem = 6 * 2048 * 4 + (size_t)tile + 48;
     static bool attr = [] {
         cudaFuncSetAttribute((void*)k_hist_keys11<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -469,8 +473,8 @@ cudaError_t launch_hist_keys11(const uint8_t* S, const BlockInfo* blocks, const 
         return true;
     }();
     (void)attr;
-    const int grid = (int)std::min<uint32_t>(num_tiles, (uint32_t)num_sms() * 4);
-    k_hist_keys11<4096><<<grid, 256, smem, st>>>(S, blocks, tiles, num_tiles, hist);
+    const int grid = num_tiles_dev ? num_sms() * 4 : (int)std::min<uint32_t>(num_tiles, (uint32_t)num_sms() * 4);
+    k_hist_keys11<4096><<<grid, 256, smem, st>>>(S, blocks, tiles, num_tiles, num_tiles_dev, hist);
     return cudaGetLastError();
 }
 

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1109_2348_gb300 import F_LEARNED, Plan, _lib, datagen, model
+from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, Plan, _lib, datagen, model
 
 from gpu_util import assert_matches_oracle, gpu_bwt
 
@@ -124,10 +124,11 @@ def test_training_samples_come_from_the_plain_sort():
         assert abs(t[s] - k / n) < 1e-6
 
 
-def _learned_run(buf, off, splitters, **kw):
+def _learned_run(buf, off, splitters, graph=False, **kw):
     import torch
     sizes = np.diff(off.astype(np.int64))
-    with Plan(max_blocks=off.size - 1, max_total_bytes=buf.size, max_block_bytes=int(sizes.max()), flags=F_LEARNED,
+    flags = F_LEARNED | (F_GRAPH if graph else 0)
+    with Plan(max_blocks=off.size - 1, max_total_bytes=buf.size, max_block_bytes=int(sizes.max()), flags=flags,
               **kw) as plan:
         model.install(plan, splitters)
         d_in = torch.from_numpy(buf).cuda()
@@ -146,15 +147,43 @@ def test_learned_equals_oracle_on_held_out_blocks(small_model):
     assert st["blocks_routed_flat"] >= 1 and st["blocks_routed_plain"] == 0, st
 
 
+@pytest.mark.parametrize("graph", [False, True])
 @pytest.mark.parametrize("which", ["model", "equal_width"])
-def test_learned_path_exact_for_any_splitters(small_model, which):
+def test_learned_path_exact_for_any_splitters(small_model, which, graph):
     spl = small_model.splitters if which == "model" else model.equal_width_splitters()
     w = datagen.Workload("t", [datagen.CONST, datagen.PERIOD7, datagen.FIBONACCI, datagen.RUNS16, datagen.UNIFORM,
                                datagen.MARKOV3_Z96, datagen.MARKOV2_Z64],
                          [1, 2, 3, 4, 5, 6, 7], [30_000, 20_001, 25_000, 40_000, 3, 60_000, 7_777])
     buf, off = w.generate()
-    L, prim, _ = _learned_run(buf, off, spl)
-    assert_matches_oracle(buf, off, L, prim, which)
+    L, prim, st = _learned_run(buf, off, spl, graph=graph)
+    assert_matches_oracle(buf, off, L, prim, f"{which} graph={graph}")
+    assert st["blocks_routed_plain"] >= 1, st  # the constant block overflows every bucketing
+
+
+def test_learned_graph_equals_oracle_and_replays(small_model):
+    """Learned + batched: the learned stage (device-side routing included) and
+    the doubling loop captured as one CUDA graph. The first call captures, the
+    second replays; both are exact and route every block as the host-driven
+    learned mode does."""
+    import torch
+    w = datagen.learned_eval(num_blocks=20, n=150_000)
+    buf, off = w.generate()
+    with Plan(max_blocks=20, max_total_bytes=buf.size, max_block_bytes=150_000, flags=F_LEARNED | F_GRAPH) as plan:
+        model.install(plan, small_model.splitters)
+        d_in = torch.from_numpy(buf).cuda()
+        L = torch.empty_like(d_in)
+        prim = torch.empty(20, dtype=torch.int32, device="cuda")
+        for it in range(2):  # the same buffers: the second call replays the graph
+            L.zero_()
+            plan.forward_into(d_in, off, L, prim)
+            torch.cuda.synchronize()
+            st = plan.stats()
+            assert_matches_oracle(buf, off, L.cpu().numpy(), prim.cpu().numpy(), f"learned graph call {it}")
+            assert st["graph_replayed"] == it, st
+    _, _, st_host = _learned_run(buf, off, small_model.splitters)
+    for k in ("blocks_routed_flat", "blocks_routed_plain", "buckets_overflowed", "keys_overflowed", "bucket_sq_sum",
+              "buckets_nonempty", "radix_keys"):
+        assert st[k] == st_host[k], (k, st, st_host)
 
 
 def test_learned_with_radix_variants(small_model):
