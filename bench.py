@@ -2,11 +2,14 @@
 
 Default workload: 64 blocks x 900,000 bytes (the bzip2 -9 block size) from
 three seeded sources (uniform bytes, order-3 Markov text-like, geometric
-runs), sorted in one batched call with inputs resident in HBM. Prints one
-JSON line (rank 0). Metric: input MB/s (10^6 bytes of blocks per second).
+runs), sorted by the learned bucketing in one batched, graph-captured call
+with inputs resident in HBM; the plain batched path on the same batch is
+timed beside it ("plain"). Prints one JSON line (rank 0). Metric: input MB/s
+(10^6 bytes of blocks per second).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1..5]
-                  [--mode host|graph|perblock|learned] [--impl ours|reference]
+                  [--mode learned|graph|host|perblock|learned-host]
+                  [--impl ours|reference]
 
 --impl reference times the CPU oracle (the only other place this script runs
 it) on a bounded sample of the same workload.
@@ -38,7 +41,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--blocks", type=int, default=0, help="use only the first N blocks of the workload")
-    ap.add_argument("--mode", choices=["host", "graph", "perblock", "learned", "learned-host"], default="graph",
+    ap.add_argument("--mode", choices=["host", "graph", "perblock", "learned", "learned-host"], default="learned",
                     help="learned = learned bucketing + the batched graph launch; learned-host drives its rounds "
                          "from the host")
     ap.add_argument("--radix-bits", type=int, default=0)
@@ -183,6 +186,25 @@ def run_cpu_oracle(w, threads: int, repeats: int = 1):
     return buf.size / dt / 1e6, dt
 
 
+def timed_cpu_baseline(w, cores: int, target_s: float = 12.0):
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    workload sized to about target_s seconds: blocks taken round-robin over
+    the workload's sources (the whole workload, repeated, if it is smaller)."""
+    probe = cpu_sample(w, cores)
+    _, dt = run_cpu_oracle(probe, cores)
+    per_byte = dt / probe.total_bytes
+    want = int(target_s / per_byte)
+    if want >= w.total_bytes:
+        sample, repeats = w, max(1, int(round(want / w.total_bytes)))
+    else:
+        k = max(cores, min(w.num_blocks, int(w.num_blocks * want / w.total_bytes)))
+        sample, repeats = cpu_sample(w, k), 1
+    mbs, dt = run_cpu_oracle(sample, cores, repeats)
+    return {"value": round(mbs, 3), "unit": "MB/s", "cores": cores, "kind": "oracle",
+            "sample": f"{sample.num_blocks} blocks ({sample.total_bytes} bytes) of {w.name}, {repeats} pass(es), "
+                      f"{dt * repeats:.1f} s"}
+
+
 # DRAM bytes (read + write) per key of one u64 onesweep pass as ncu counted them
 # for the current kernel on the full mixed3-64x900000 pass
 # (profiles/launches_mixed3-64x900000_graph.md); None
@@ -226,7 +248,7 @@ def reference_arm(args):
 
 def ours(args):
     import torch
-    from paper_1109_2348_gb300 import F_GRAPH, F_PER_BLOCK_LAUNCH, F_TIMING, F_LEARNED, Plan
+    from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, F_PER_BLOCK_LAUNCH, F_TIMING, Plan
 
     rank, world, local = dist_env()
     if world > 1:
@@ -237,11 +259,12 @@ def ours(args):
     w = rank_workload(args.config, args.blocks, rank, world)
     buf, off = w.generate()
     n = buf.size
+    learned = args.mode.startswith("learned")
     flags = {"host": F_TIMING, "graph": F_GRAPH, "perblock": F_PER_BLOCK_LAUNCH, "learned": F_LEARNED | F_GRAPH,
              "learned-host": F_LEARNED}[args.mode]
     sizes = np.diff(off.astype(np.int64))
     model_info = None
-    if args.mode.startswith("learned") and not args.model:
+    if learned and not args.model:
         import tempfile
         from paper_1109_2348_gb300 import model as mdl
         t0 = time.perf_counter()
@@ -251,9 +274,13 @@ def ours(args):
         model_info = {"trained_s": round(time.perf_counter() - t0, 2), "samples": args.train_samples,
                       "epochs": args.train_epochs, "final_loss": float(trained.epoch_loss[-1]),
                       "train_blocks": "100 x 900000 order-3 Markov, seeds 5000..5099"}
-    plan = Plan(max_blocks=w.num_blocks, max_total_bytes=n, max_block_bytes=int(sizes.max()),
-                radix_bits=args.radix_bits, tile_keys=args.tile, flags=flags, model_path=args.model,
-                device=local)
+
+    def make_plan(fl, rb=None, tk=None):
+        return Plan(max_blocks=w.num_blocks, max_total_bytes=n, max_block_bytes=int(sizes.max()),
+                    radix_bits=args.radix_bits if rb is None else rb, tile_keys=args.tile if tk is None else tk,
+                    flags=fl, model_path=args.model if fl & F_LEARNED else None, device=local)
+
+    plan = make_plan(flags)
     pinned = torch.from_numpy(buf).pin_memory()
     d_in = pinned.to(dev)
     d_L = torch.empty_like(d_in)
@@ -267,42 +294,42 @@ def ours(args):
         cache = args.autotune_cache or os.path.join(tempfile.mkdtemp(), "autotune.jsonl")
         rb, tk, ms = plan.autotune(d_in, off, d_L, d_p, cache_path=cache, repeats=3, stream=stream)
         tuned = {"radix_bits": rb, "tile_keys": tk, "ms": round(ms, 4)}
-    for _ in range(max(3, args.warmup)):
-        plan.forward_into(d_in, off, d_L, d_p, stream)
-    torch.cuda.synchronize()
+    rb_used = tuned["radix_bits"] if tuned else args.radix_bits
+    tk_used = tuned["tile_keys"] if tuned else args.tile
 
-    # a separate timing pass for the dominant kernel (events around each radix
-    # launch); the headline steps below run the plan's own mode
-    tplan = None
-    if args.mode != "host":
-        tb = tuned["radix_bits"] if tuned else args.radix_bits
-        tt = tuned["tile_keys"] if tuned else args.tile
-        tplan = (tb, tt)  # created after the headline steps, so only one plan's scratch is resident
+    def warm(pl, outs):
+        for _ in range(max(3, args.warmup)):
+            pl.forward_into(d_in, off, outs[0], outs[1], stream)
+        torch.cuda.synchronize()
 
+    def timed_steps(pl, radix=None):
+        """K steps, L2 flushed before each, CUDA events on the launch stream."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        launches, st = 0, None
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            pl.forward_into(d_in, off, d_L, d_p, stream)
+            ev[i][1].record(stream)
+            st = pl.stats()
+            launches += st["kernel_launches"]
+            if radix is not None:
+                add_first_sort(radix, st, n)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], st, launches
+
+    warm(plan, (d_L, d_p))
+    radix = {"ms": 0.0, "bytes": 0.0, "launches": 0, "keys": 0.0}
     sampler = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches = 0
-    radix = {"ms": 0.0, "bytes": 0.0, "launches": 0, "keys": 0.0}
-    stats = None
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        plan.forward_into(d_in, off, d_L, d_p, stream)
-        ev[i][1].record(stream)
-        stats = plan.stats()
-        launches += stats["kernel_launches"]
-        if tplan is None:
-            add_first_sort(radix, stats, n)
-    torch.cuda.synchronize()
+    step_ms, stats, launches = timed_steps(plan, radix if args.mode == "host" else None)
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    learned_stats = {k: stats[k] for k in ("blocks_routed_plain", "buckets_overflowed", "keys_overflowed",
-                                           "max_bucket", "bucket_sq_sum", "buckets_nonempty")} \
-        if args.mode.startswith("learned") else None
+    learned_stats = {k: stats[k] for k in ("blocks_routed_plain", "blocks_routed_flat", "buckets_overflowed",
+                                           "keys_overflowed", "max_bucket", "bucket_sq_sum", "buckets_nonempty")} \
+        if learned else None
     t_ms = reduce_max(float(np.sum(step_ms)), world, dev)
     value = job_value(n, world, args.steps, t_ms)
 
@@ -316,46 +343,67 @@ def ours(args):
 
     e2e = None
     if not args.no_e2e:
-        h_L = torch.empty(n, dtype=torch.uint8).pin_memory()
-        h_p = torch.empty(w.num_blocks, dtype=torch.int32).pin_memory()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # End to end through the public call, two buffer sets in flight: step
+        # k+1's host->device copy and step k-1's device->host copy run on the
+        # copy engines while step k sorts; every step's copies are inside the
+        # timed region.
+        plan2 = make_plan(flags, rb_used, tk_used)
+        sets = []
+        for pl in (plan, plan2):
+            sets.append({"plan": pl, "in": torch.empty_like(d_in), "L": torch.empty_like(d_in),
+                         "p": torch.empty_like(d_p), "hL": torch.empty(n, dtype=torch.uint8).pin_memory(),
+                         "hp": torch.empty(w.num_blocks, dtype=torch.int32).pin_memory(),
+                         "st": torch.cuda.Stream(device=dev)})
+        for st_ in sets:  # capture / warm each set's own buffers
+            st_["in"].copy_(d_in)
+            for _ in range(2):
+                st_["plan"].forward_into(st_["in"], off, st_["L"], st_["p"], st_["st"])
         torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
-            d_in.copy_(pinned, non_blocking=True)
-            plan.forward_into(d_in, off, d_L, d_p, stream)
-            h_L.copy_(d_L, non_blocking=True)
-            h_p.copy_(d_p, non_blocking=True)
+        for st_ in sets:
+            st_["st"].wait_event(e0)
+        with torch.cuda.stream(sets[0]["st"]):
+            sets[0]["in"].copy_(pinned, non_blocking=True)
+        for i in range(args.steps):
+            cur, nxt = sets[i % 2], sets[(i + 1) % 2]
+            if i + 1 < args.steps:
+                with torch.cuda.stream(nxt["st"]):
+                    nxt["in"].copy_(pinned, non_blocking=True)
+            cur["plan"].forward_into(cur["in"], off, cur["L"], cur["p"], cur["st"])
+            with torch.cuda.stream(cur["st"]):
+                cur["hL"].copy_(cur["L"], non_blocking=True)
+                cur["hp"].copy_(cur["p"], non_blocking=True)
+        for st_ in sets:
+            stream.wait_stream(st_["st"])
         e1.record(stream)
         torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1)
-        e2e = {"value": round(n * args.steps / (e_ms / 1e3) / 1e6, 3), "unit": "MB/s",
-               "h2d_bytes_per_step": int(n + off.nbytes), "d2h_bytes_per_step": int(n + 4 * w.num_blocks)}
+        e_ms = reduce_max(e0.elapsed_time(e1), world, dev)
+        assert np.array_equal(sets[(args.steps - 1) % 2]["hL"].numpy(), d_L.cpu().numpy())
+        e2e = {"value": round(n * world * args.steps / (e_ms / 1e3) / 1e6, 3), "unit": "MB/s",
+               "h2d_bytes_per_step": int(n + off.nbytes), "d2h_bytes_per_step": int(n + 4 * w.num_blocks),
+               "pipelined": "2 buffer sets: copies of steps k-1 and k+1 overlap step k"}
+        plan2.close()
+        del sets
 
+    plan.close()
     plain_cmp = None
-    if args.compare_plain or tplan is not None:
-        # the plain path on the same batch: host-driven mode with CUDA events around
-        # every radix launch (the roofline's timing) and the step time for comparison
-        plan.close()
-        tb, tt = tplan if tplan is not None else (args.radix_bits, args.tile)
-        pplan = Plan(max_blocks=w.num_blocks, max_total_bytes=n, max_block_bytes=int(sizes.max()),
-                     radix_bits=tb, tile_keys=tt, flags=F_TIMING, device=local)
-        for _ in range(2):
-            pplan.forward_into(d_in, off, d_L, d_p, stream)
-        pms = []
-        for i in range(args.steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            pplan.forward_into(d_in, off, d_L, d_p, stream)
-            b.record(stream)
-            b.synchronize()
-            pms.append(a.elapsed_time(b))
-            add_first_sort(radix, pplan.stats(), n)
-        pplan.close()
-        plain_cmp = {"value": round(n * args.steps / (sum(pms) / 1e3) / 1e6, 3), "unit": "MB/s",
-                     "mode": "plain (host-driven rounds, events around each radix launch)",
-                     "ms_per_step": round(sum(pms) / args.steps, 4)}
+    if learned or args.compare_plain:
+        # the plain path on the same batch, batched the same way (graph)
+        pg = make_plan(F_GRAPH, rb_used, tk_used)
+        warm(pg, (d_L, d_p))
+        pms, _, _ = timed_steps(pg)
+        pg.close()
+        p_ms = reduce_max(float(np.sum(pms)), world, dev)
+        plain_cmp = {"value": round(job_value(n, world, args.steps, p_ms), 3), "unit": "MB/s",
+                     "mode": "plain radix, batched (graph)", "ms_per_step": round(p_ms / args.steps, 4)}
+    if args.mode != "host":
+        # the roofline's timing: the same batch in host-driven mode with CUDA
+        # events around every radix launch of the first sort
+        th = make_plan(F_TIMING, rb_used, tk_used)
+        warm(th, (d_L, d_p))
+        timed_steps(th, radix)
+        th.close()
     peak, peak_kind = measured_peaks()
     roof = None
     if radix["ms"] > 0:
@@ -375,11 +423,7 @@ def ours(args):
                 "avg_launch_ms": round(radix["ms"] / max(1, radix["launches"]), 4)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cores = os.cpu_count() or 1
-        sample = cpu_sample(w, cores)
-        mbs, dt = run_cpu_oracle(sample, cores)
-        cpu = {"value": round(mbs, 3), "unit": "MB/s", "cores": cores, "kind": "oracle",
-               "sample": f"{sample.num_blocks} blocks ({sample.total_bytes} bytes) of {w.name}, {dt:.1f} s"}
+        cpu = timed_cpu_baseline(w, os.cpu_count() or 1)
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "MB/s", "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": round(t_ms / args.steps, 4),
@@ -400,7 +444,6 @@ def ours(args):
         if model_info:
             line["config"]["model"] = model_info
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
