@@ -41,9 +41,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--blocks", type=int, default=0, help="use only the first N blocks of the workload")
-    ap.add_argument("--mode", choices=["host", "graph", "perblock", "learned", "learned-host"], default="learned",
+    ap.add_argument("--mode", choices=["host", "graph", "perblock", "learned", "learned-host", "inverse"],
+                    default="learned",
                     help="learned = learned bucketing + the batched graph launch; learned-host drives its rounds "
-                         "from the host")
+                         "from the host; inverse times the GPU inverse transform of the workload's BWT")
     ap.add_argument("--radix-bits", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--model", default=None, help="model file for --mode learned (trained in-process if absent)")
@@ -448,10 +449,104 @@ def ours(args):
         torch.distributed.destroy_process_group()
 
 
+def inverse_bench(args):
+    """The GPU inverse (bwt_inverse_batch) of the workload's BWT: output MB/s,
+    every step's result compared with the input."""
+    import torch
+    from paper_1109_2348_gb300 import Plan
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = rank_workload(args.config, args.blocks, rank, world)
+    buf, off = w.generate()
+    n = buf.size
+    sizes = np.diff(off.astype(np.int64))
+    plan = Plan(max_blocks=w.num_blocks, max_total_bytes=n, max_block_bytes=int(sizes.max()), device=local)
+    d_in = torch.from_numpy(buf).to(dev)
+    d_L, d_p = plan.forward(d_in, off)
+    d_out = torch.empty_like(d_in)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        plan.inverse_into(d_L, off, d_p, d_out, stream)
+    torch.cuda.synchronize()
+    assert torch.equal(d_out, d_in), "the GPU inverse does not give the input back"
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        plan.inverse_into(d_L, off, d_p, d_out, stream)
+        ev[i][1].record(stream)
+        launches += plan.stats()["kernel_launches"]
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    assert torch.equal(d_out, d_in)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = reduce_max(float(np.sum(step_ms)), world, dev)
+    e2e = None
+    if not args.no_e2e:
+        hL = d_L.cpu().pin_memory()
+        hp = d_p.cpu().pin_memory()
+        ho = torch.empty(n, dtype=torch.uint8).pin_memory()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            d_L.copy_(hL, non_blocking=True)
+            d_p.copy_(hp, non_blocking=True)
+            plan.inverse_into(d_L, off, d_p, d_out, stream)
+            ho.copy_(d_out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = reduce_max(e0.elapsed_time(e1), world, dev)
+        e2e = {"value": round(n * world * args.steps / (e_ms / 1e3) / 1e6, 3), "unit": "MB/s",
+               "h2d_bytes_per_step": int(n + 4 * w.num_blocks + off.nbytes), "d2h_bytes_per_step": int(n)}
+    plan.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        L_h, p_h = d_L.cpu().numpy(), d_p.cpu().numpy()
+        t0 = time.perf_counter()
+        done = 0
+        b = 0
+        while time.perf_counter() - t0 < 10.0 and b < w.num_blocks:
+            s0, e0_ = int(off[b]), int(off[b + 1])
+            oracle.inverse_bwt(L_h[s0:e0_], int(p_h[b]))
+            done += e0_ - s0
+            b += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(done / dt / 1e6, 3), "unit": "MB/s", "cores": 1, "kind": "oracle",
+               "sample": f"{b} blocks ({done} bytes) of {w.name}, inverse LF walk, one thread, {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": "BWT inverse output MB/s on 1 GB300, bit-exact", "value": round(
+                    job_value(n, world, args.steps, t_ms), 3), "unit": "MB/s", "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded generators, no dataset)",
+                "config": {"workload": w.name, "blocks": w.num_blocks, "bytes": n, "mode": "inverse",
+                           "l2": "256 MB flush before every timed step"},
+                "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "roofline": None, "cpu_baseline": cpu,
+                "step_ms": [round(x, 3) for x in step_ms]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.mode == "inverse":
+        inverse_bench(args)
     else:
         ours(args)
 

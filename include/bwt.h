@@ -126,6 +126,22 @@ bwt_status bwt_forward_batch(bwt_plan* plan, const uint8_t* d_in, const uint64_t
  * outside [0, n). */
 bwt_status bwt_inverse_check(const uint8_t* L, uint64_t n, int32_t primary, const uint8_t* original);
 
+/* Inverse BWT of a batch on the device (Section 3.1: a block is recovered
+ * from its L column and primary index alone).
+ *   d_L         device, uint8[offsets[num_blocks]]: the L columns, concatenated.
+ *   offsets     as in bwt_forward_batch (host or device memory).
+ *   d_primary   device, int32[num_blocks]: the primary index of every block.
+ *   d_out       device, uint8[offsets[num_blocks]]: receives the blocks.
+ *   stream      cudaStream_t to run on (NULL = the legacy default stream).
+ * Uses the plan's scratch plus about 1.5 bytes per byte of max_total_bytes
+ * allocated on the first call. Returns BWT_EINVAL for bad arguments and for a primary
+ * outside [0, n) (found on the device; that block's output is undefined).
+ * The call synchronises `stream` before it returns. d_out must not alias
+ * d_L. For any L that is a permutation of some block's bytes the result is
+ * the block whose BWT (with this primary) is L. */
+bwt_status bwt_inverse_batch(bwt_plan* plan, const uint8_t* d_L, const uint64_t* offsets, uint32_t num_blocks,
+                             const int32_t* d_primary, uint8_t* d_out, void* stream);
+
 /* Free the plan and all its device and host memory. NULL is accepted. */
 bwt_status bwt_plan_destroy(bwt_plan* plan);
 

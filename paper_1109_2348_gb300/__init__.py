@@ -86,6 +86,26 @@ class Plan:
         self.forward_into(d_in, offsets, L, prim, stream)
         return L, prim
 
+    def inverse_into(self, d_L, offsets, d_primary, d_out, stream=None, raise_on_error: bool = True) -> int:
+        """bwt_inverse_batch on caller-owned buffers (offsets as for forward_into)."""
+        if isinstance(offsets, np.ndarray):
+            off = np.ascontiguousarray(offsets, dtype=np.uint64)
+            off_ptr, nb = off.ctypes.data, off.size - 1
+        else:
+            off_ptr, nb = _ptr(offsets), offsets.numel() - 1
+        st = self.lib.bwt_inverse_batch(self.handle, _ptr(d_L), off_ptr, nb, _ptr(d_primary), _ptr(d_out),
+                                        _stream_handle(stream))
+        if raise_on_error:
+            check(st, "bwt_inverse_batch")
+        return st
+
+    def inverse(self, d_L, offsets, d_primary, stream=None):
+        """Returns the blocks (uint8 CUDA tensor) whose BWT is (d_L, d_primary)."""
+        import torch
+        out = torch.empty_like(d_L)
+        self.inverse_into(d_L, offsets, d_primary, out, stream)
+        return out
+
     def stats(self) -> dict:
         s = Stats()
         check(self.lib.bwt_plan_stats(self.handle, ctypes.byref(s)), "bwt_plan_stats")

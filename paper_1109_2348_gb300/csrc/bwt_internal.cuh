@@ -38,6 +38,7 @@ constexpr uint32_t ST_VALUE = (1u << 30) - 1;
 // Device error bits (ctrl[CTRL_ERR]).
 constexpr uint32_t ERR_TIMEOUT = 1u;
 constexpr uint32_t ERR_CAPACITY = 2u;
+constexpr uint32_t ERR_INPUT = 4u;  // device-checked input out of range (the inverse's primary index)
 
 // Group size classes of a doubling round.
 constexpr int NCLS = 5;

@@ -115,9 +115,9 @@ void bwt::free_plan_memory(bwt_plan* p) {
     F(p->tiles0); F(p->ltiles); F(p->blocks); F(p->hist); F(p->status); F(p->ctrl);
     for (int s = 0; s < 2; ++s)
         for (int c = 0; c < NCLS; ++c) F(p->bins[s][c]);
-    F(p->splitters); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->route_first); F(p->bstats); F(p->tiles_aux);
+    F(p->splitters); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->route_first); F(p->bstats); F(p->tiles_aux); F(p->inv_slots); F(p->inv_items);
     FH(p->h_ctrl); FH(p->h_tiles); FH(p->h_blocks); FH(p->h_off);
-    FH(p->h_route); FH(p->h_bstats);
+    FH(p->h_route); FH(p->h_bstats); FH(p->h_inv_items);
     for (auto& e : p->events) cudaEventDestroy(e);
     p->events.clear();
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
@@ -185,6 +185,7 @@ extern "C" bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt
     A(host_alloc(&p->h_tiles, p->cap_tiles0));
     A(host_alloc(&p->h_blocks, B));
     A(host_alloc(&p->h_off, (size_t)B + 1));
+    A(host_alloc(&p->h_inv_items, 2 * ((size_t)B + 1)));
     p->device_bytes = total;
     if (s == BWT_OK && (desc->flags & BWT_F_TIMING)) {
         p->events.resize(512);
@@ -479,6 +480,7 @@ bwt_status bwt::finish_status(bwt_plan* p, cudaStream_t st) {
     const uint32_t err = p->h_ctrl[CTRL_ERR];
     if (err & ERR_TIMEOUT) return BWT_ETIMEOUT;
     if (err & ERR_CAPACITY) return BWT_ECAPACITY;
+    if (err & ERR_INPUT) return BWT_EINVAL;
     return BWT_OK;
 }
 

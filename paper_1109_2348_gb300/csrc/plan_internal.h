@@ -70,6 +70,11 @@ struct bwt_plan {
     int chunk_sort_ctas = 1;            // resident chunk-sort CTAs per SM
     uint32_t learned_overflow_passes = 0;  // radix passes over the overflow buckets (index + key)
 
+    // GPU inverse (allocated on first use)
+    uint32_t* inv_slots = nullptr;     // [6][cap_n / 16 + 3 cap_b + 4] sample walks and pointer jumping
+    uint32_t* inv_items = nullptr;     // [2][cap_b + 1] prefixes of work items and of samples per block
+    uint32_t* h_inv_items = nullptr;   // pinned staging
+
     // pinned host staging
     uint32_t* h_ctrl = nullptr;
     bwt::TileDesc* h_tiles = nullptr;

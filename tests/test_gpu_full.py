@@ -3,7 +3,8 @@ configuration bench.py times. Workloads 1-4 are compared with the oracle
 byte for byte in full (the oracle runs on all host cores). Workload 5 (1.08
 GB) is checked block by block with the host inverse transform and the
 permutation invariant, and byte for byte against the oracle on a sample of 32
-blocks (the oracle would need over a minute for all 1,200)."""
+blocks (the oracle would need over a minute for all 1,200), and the GPU
+inverse of the whole output must give the input back."""
 import numpy as np
 import pytest
 
@@ -66,6 +67,12 @@ def test_workload5_learned_1200x900k(trained_model_path):
         s, e = int(off[b]), int(off[b + 1])
         assert np.array_equal(np.bincount(L[s:e], minlength=256), np.bincount(buf[s:e], minlength=256))
         assert bwt_inverse_check(L[s:e], int(prim[b]), buf[s:e]) == 0, b
+    # the GPU inverse of the whole output gives the input back
+    import torch
+    with Plan(max_blocks=w.num_blocks, max_total_bytes=buf.size, max_block_bytes=900_000) as inv:
+        back = inv.inverse(torch.from_numpy(L).cuda(), off, torch.from_numpy(prim).cuda())
+        torch.cuda.synchronize()
+        assert np.array_equal(back.cpu().numpy(), buf)
     sample = list(range(0, 1200, 38))[:32]
     sub = w.subset(sample)
     sbuf, soff = sub.generate()
