@@ -142,6 +142,32 @@ bwt_status bwt_inverse_check(const uint8_t* L, uint64_t n, int32_t primary, cons
 bwt_status bwt_inverse_batch(bwt_plan* plan, const uint8_t* d_L, const uint64_t* offsets, uint32_t num_blocks,
                              const int32_t* d_primary, uint8_t* d_out, void* stream);
 
+/* ---- the stages after the block sort (Sections 3.2-3.4) ---------------
+ * They take a plan for its scratch and its batch checks (offsets as in
+ * bwt_forward_batch, host or device memory); they run on `stream` and
+ * synchronise it before returning. */
+
+/* Run-length encoding of a batch (Section 3.2, Fig. 1): every block becomes
+ * its maximal runs, in order; runs never cross blocks.
+ *   d_in       device, uint8[offsets[num_blocks]]: the blocks.
+ *   d_chars    device, uint8[offsets[num_blocks]] (room for one run a byte):
+ *              the byte of every run, block after block.
+ *   d_lens     device, uint32[offsets[num_blocks]]: every run's length.
+ *   d_run_off  device, uint64[num_blocks + 1]: block b's runs are
+ *              [d_run_off[b], d_run_off[b + 1]); d_run_off[num_blocks] is the
+ *              number of runs. */
+bwt_status bwt_rle_encode(bwt_plan* plan, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
+                          uint8_t* d_chars, uint32_t* d_lens, uint64_t* d_run_off, void* stream);
+
+/* Run-length decoding (Section 3.2, Fig. 2), the inverse of bwt_rle_encode:
+ * d_chars, d_lens and d_run_off as it writes them; `offsets` gives the
+ * decoded blocks' layout; d_out (device, uint8[offsets[num_blocks]])
+ * receives the blocks. Returns BWT_EINVAL if a length is zero or a block's
+ * runs do not add up to its size (checked on the device; d_out is then
+ * undefined). */
+bwt_status bwt_rle_decode(bwt_plan* plan, const uint8_t* d_chars, const uint32_t* d_lens, const uint64_t* d_run_off,
+                          const uint64_t* offsets, uint32_t num_blocks, uint8_t* d_out, void* stream);
+
 /* Free the plan and all its device and host memory. NULL is accepted. */
 bwt_status bwt_plan_destroy(bwt_plan* plan);
 

@@ -106,6 +106,49 @@ class Plan:
         self.inverse_into(d_L, offsets, d_primary, out, stream)
         return out
 
+    @staticmethod
+    def _offsets(offsets):
+        if isinstance(offsets, np.ndarray):
+            off = np.ascontiguousarray(offsets, dtype=np.uint64)
+            return off, off.ctypes.data, off.size - 1
+        return offsets, _ptr(offsets), offsets.numel() - 1
+
+    def rle_encode_into(self, d_in, offsets, d_chars, d_lens, d_run_off, stream=None, raise_on_error=True) -> int:
+        """bwt_rle_encode on caller-owned buffers (d_chars, d_lens sized like d_in)."""
+        keep, off_ptr, nb = self._offsets(offsets)
+        st = self.lib.bwt_rle_encode(self.handle, _ptr(d_in), off_ptr, nb, _ptr(d_chars), _ptr(d_lens),
+                                     _ptr(d_run_off), _stream_handle(stream))
+        if raise_on_error:
+            check(st, "bwt_rle_encode")
+        return st
+
+    def rle_encode(self, d_in, offsets, stream=None):
+        """(chars uint8, lens int32 (uint32 values), run_off int64 (uint64 values)) CUDA tensors,
+        trimmed to the number of runs."""
+        import torch
+        nb = (offsets.size if isinstance(offsets, np.ndarray) else offsets.numel()) - 1
+        chars = torch.empty_like(d_in)
+        lens = torch.empty(d_in.numel(), dtype=torch.int32, device=d_in.device)
+        run_off = torch.empty(nb + 1, dtype=torch.int64, device=d_in.device)
+        self.rle_encode_into(d_in, offsets, chars, lens, run_off, stream)
+        R = int(run_off[nb].item())
+        return chars[:R], lens[:R], run_off
+
+    def rle_decode_into(self, d_chars, d_lens, d_run_off, offsets, d_out, stream=None, raise_on_error=True) -> int:
+        keep, off_ptr, nb = self._offsets(offsets)
+        st = self.lib.bwt_rle_decode(self.handle, _ptr(d_chars), _ptr(d_lens), _ptr(d_run_off), off_ptr, nb,
+                                     _ptr(d_out), _stream_handle(stream))
+        if raise_on_error:
+            check(st, "bwt_rle_decode")
+        return st
+
+    def rle_decode(self, d_chars, d_lens, d_run_off, offsets, stream=None):
+        import torch
+        total = int(offsets[-1]) if isinstance(offsets, np.ndarray) else int(offsets[-1].item())
+        out = torch.empty(total, dtype=torch.uint8, device=d_chars.device)
+        self.rle_decode_into(d_chars, d_lens, d_run_off, offsets, out, stream)
+        return out
+
     def stats(self) -> dict:
         s = Stats()
         check(self.lib.bwt_plan_stats(self.handle, ctypes.byref(s)), "bwt_plan_stats")

@@ -145,6 +145,69 @@ __device__ __forceinline__ uint32_t stage_tile_bytes(const uint8_t* __restrict__
     return 0;
 }
 
+// ---- single-pass scan of one 64-bit count per tile -------------------------
+//
+// Decoupled look-back: tile t publishes its own total (AGG) at once and its
+// inclusive prefix (INC) when known; a later tile adds up predecessors'
+// words until it meets an INC. Tiles must be started in scan order (a tile
+// counter), so every predecessor is in flight or done. The scan restarts at
+// segment starts: `first` is the first tile of t's segment. A status word is
+// the value in bits 0..61 and the flag in bits 62..63; words start at zero.
+constexpr uint64_t LB_AGG = 1ull << 62;
+constexpr uint64_t LB_INC = 2ull << 62;
+constexpr uint64_t LB_VAL = LB_AGG - 1;
+
+__device__ __forceinline__ uint64_t ld_volatile64(const uint64_t* p) {
+    return *reinterpret_cast<const volatile uint64_t*>(p);
+}
+
+__device__ __forceinline__ void st_volatile64(uint64_t* p, uint64_t v) {
+    *reinterpret_cast<volatile uint64_t*>(p) = v;
+}
+
+// All 32 lanes of one warp call; returns the exclusive prefix of tile t in
+// every lane. A wait that runs past spin_limit polls sets ERR_TIMEOUT in *err
+// and counts the word as an inclusive zero (the result is then wrong but in
+// range: callers bound every index they derive from it).
+__device__ __forceinline__ uint64_t lookback_u64(uint64_t* status, uint32_t t, uint32_t first, uint64_t agg,
+                                                 uint32_t spin_limit, uint32_t* err) {
+    const uint32_t lane = threadIdx.x & 31;
+    if (t == first) {
+        if (lane == 0) st_volatile64(status + t, LB_INC | agg);
+        return 0;
+    }
+    if (lane == 0) st_volatile64(status + t, LB_AGG | agg);
+    uint64_t excl = 0;
+    uint32_t end = t;  // predecessors end - 1, end - 2, ... still to add
+    for (;;) {
+        const int64_t q = (int64_t)end - 1 - lane;
+        uint64_t v = LB_INC;  // before the segment: an inclusive zero
+        if (q >= (int64_t)first) {
+            v = ld_volatile64(status + q);
+            uint32_t it = 0;
+            while ((v & (LB_AGG | LB_INC)) == 0ull) {
+                if (++it > spin_limit) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    v = LB_INC;
+                    break;
+                }
+                if (it > 32) __nanosleep(64);
+                v = ld_volatile64(status + q);
+            }
+        }
+        const uint32_t inc = __ballot_sync(0xffffffffu, (v & LB_INC) != 0ull);
+        const int stop = inc ? __ffs(inc) - 1 : 31;  // nearest inclusive word, or the whole window
+        uint64_t x = lane <= (uint32_t)stop ? (v & LB_VAL) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        excl += x;
+        if (inc) break;
+        end -= 32;
+    }
+    if (lane == 0) st_volatile64(status + t, LB_INC | ((excl + agg) & LB_VAL));
+    return excl;
+}
+
 // Number of valid entries of bin c (a count past the capacity means entries
 // were dropped and ERR_CAPACITY is set).
 __device__ __forceinline__ uint32_t bin_count(const Bins& b, int c) {

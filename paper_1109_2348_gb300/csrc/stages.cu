@@ -1,0 +1,274 @@
+// Run-length encoding and decoding of a batch (Section 3.2, Fig. 1 and
+// Fig. 2 of the paper; the method of Fang et al. it describes).
+//
+// Encode: a byte ends a run if the next byte differs or starts another block
+// (runs never cross blocks); an exclusive prefix sum of these flags gives
+// every run its output slot; the run's byte and its end index (global, one
+// past the last byte) go to that slot; a run's length is the difference of
+// consecutive end indices. Decode: the inclusive prefix sum of the lengths
+// gives every run's end; flags at the last byte of every run, prefix-summed
+// over the output, give every output byte its run; the byte is copied.
+//
+// GB300 layout: the prefix sums are single passes over 4,096-element tiles
+// (256 threads x 16) with decoupled look-back between tiles, so each of the
+// two steps reads and writes every element once; tiles start in order from
+// a tile counter.
+#include <algorithm>
+#include <cstring>
+
+#include "bwt.h"
+#include "kernels.h"
+#include "plan_internal.h"
+
+using namespace bwt;
+
+#define CKS(call)                                              \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return record_cuda(_e, #call);  \
+    } while (0)
+
+namespace {
+
+constexpr int RT = 256;                 // threads per tile
+constexpr int RI = 16;                  // elements per thread
+constexpr uint32_t RTILE = RT * RI;     // 4096
+
+// Block holding global position i (blocks are contiguous and cover the batch).
+__device__ __forceinline__ uint32_t block_at(const BlockInfo* blocks, uint32_t nb, uint32_t i) {
+    uint32_t lo = 0, hi = nb;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (blocks[mid].off <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t next_tile(uint32_t* s_tile, uint32_t* counter) {
+    if (threadIdx.x == 0) *s_tile = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t t = *s_tile;
+    __syncthreads();
+    return t;
+}
+
+// Encode steps 1-3: run-end flags, their prefix sum, and the scatter of
+// (byte, end index) to the run's slot. run_off[b] = the first run of block b
+// (run_off[nb] = the number of runs).
+__global__ void __launch_bounds__(RT) k_rle_encode(const uint8_t* __restrict__ S, uint32_t N,
+                                                   const BlockInfo* __restrict__ blocks, uint32_t nb,
+                                                   uint8_t* __restrict__ chars, uint32_t* __restrict__ ends,
+                                                   uint64_t* __restrict__ run_off, uint64_t* __restrict__ status,
+                                                   uint32_t* __restrict__ counter, uint32_t* ctrl) {
+    __shared__ __align__(16) uint8_t sb[RTILE + 16];
+    __shared__ uint32_t s_tile, scan_tmp[32];
+    __shared__ uint64_t s_excl;
+    const uint32_t ntiles = (N + RTILE - 1) / RTILE;
+    const uint32_t spin = ctrl[CTRL_SPIN];
+    for (;;) {
+        const uint32_t t = next_tile(&s_tile, counter);
+        if (t >= ntiles) break;
+        const uint32_t t0 = t * RTILE, len = min(RTILE, N - t0);
+        for (uint32_t q = threadIdx.x; q < len + 1 && t0 + q < N; q += RT) sb[q] = S[t0 + q];
+        __syncthreads();
+        const uint32_t q0 = threadIdx.x * RI, i0 = t0 + q0;
+        uint32_t flags = 0;  // bit j: element q0 + j ends a run
+        uint32_t b = i0 < N ? block_at(blocks, nb, i0) : 0u;
+        {
+            uint32_t bend = i0 < N ? blocks[b].off + blocks[b].n : 0u, bb = b;
+#pragma unroll
+            for (int j = 0; j < RI; ++j) {
+                const uint32_t i = i0 + j;
+                if (i >= N) break;
+                while (i >= bend) {
+                    ++bb;
+                    bend = blocks[bb].off + blocks[bb].n;
+                }
+                const bool end = i + 1 == N || i + 1 == bend || sb[q0 + j + 1] != sb[q0 + j];
+                flags |= (uint32_t)end << j;
+            }
+        }
+        uint32_t total;
+        const uint32_t pre = block_exclusive_scan<RT>(__popc(flags), scan_tmp, &total);
+        if (threadIdx.x < 32) {
+            const uint64_t e = lookback_u64(status, t, 0, total, spin, &ctrl[CTRL_ERR]);
+            if (threadIdx.x == 0) s_excl = e;
+        }
+        __syncthreads();
+        uint64_t k = s_excl + pre;
+#pragma unroll
+        for (int j = 0; j < RI; ++j) {
+            const uint32_t i = i0 + j;
+            if (i >= N) break;
+            while (b + 1 < nb && blocks[b + 1].off <= i) ++b;
+            if (blocks[b].off == i) run_off[b] = k;  // runs before the block's first byte
+            if ((flags >> j) & 1u) {
+                if (k < N) {
+                    chars[k] = sb[q0 + j];
+                    ends[k] = i + 1;
+                }
+                ++k;
+            }
+            if (i + 1 == N) run_off[nb] = k;
+        }
+        __syncthreads();
+    }
+}
+
+// Encode step 4: run lengths from consecutive end indices.
+__global__ void k_rle_lengths(const uint32_t* __restrict__ ends, const uint64_t* __restrict__ run_off, uint32_t nb,
+                              uint32_t* __restrict__ lens) {
+    const uint64_t R = run_off[nb];
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < R; k += (uint64_t)gridDim.x * blockDim.x)
+        lens[k] = ends[k] - (k ? ends[k - 1] : 0u);
+}
+
+// Decode step 1: B[k] = end of run k (inclusive prefix sum of the lengths,
+// global). A zero length is an input error.
+__global__ void __launch_bounds__(RT) k_rle_scan(const uint32_t* __restrict__ lens, const uint64_t* __restrict__ run_off,
+                                                 uint32_t nb, uint32_t N, uint32_t* __restrict__ B,
+                                                 uint64_t* __restrict__ status,
+                                                 uint32_t* __restrict__ counter, uint32_t* ctrl) {
+    __shared__ uint32_t s_tile, scan_tmp[32];
+    __shared__ uint64_t s_excl;
+    const uint64_t R = min(run_off[nb], (uint64_t)N);  // a run holds at least one byte
+    const uint32_t ntiles = (uint32_t)((R + RTILE - 1) / RTILE);
+    const uint32_t spin = ctrl[CTRL_SPIN];
+    for (;;) {
+        const uint32_t t = next_tile(&s_tile, counter);
+        if (t >= ntiles) break;
+        const uint64_t k0 = (uint64_t)t * RTILE + threadIdx.x * RI;
+        uint32_t v[RI], sum = 0;
+#pragma unroll
+        for (int j = 0; j < RI; ++j) {
+            v[j] = k0 + j < R ? lens[k0 + j] : 0u;
+            if (k0 + j < R && v[j] == 0u) atomicOr(&ctrl[CTRL_ERR], ERR_INPUT);
+            sum += v[j];
+        }
+        uint32_t total;
+        const uint32_t pre = block_exclusive_scan<RT>(sum, scan_tmp, &total);
+        if (threadIdx.x < 32) {
+            const uint64_t e = lookback_u64(status, t, 0, total, spin, &ctrl[CTRL_ERR]);
+            if (threadIdx.x == 0) s_excl = e;
+        }
+        __syncthreads();
+        uint64_t acc = s_excl + pre;
+#pragma unroll
+        for (int j = 0; j < RI; ++j) {
+            acc += v[j];
+            if (k0 + j < R) B[k0 + j] = (uint32_t)acc;
+        }
+        __syncthreads();
+    }
+}
+
+// Decode check: every block's runs end exactly at the block's end.
+__global__ void k_rle_check(const uint32_t* __restrict__ B, const uint64_t* __restrict__ run_off,
+                            const BlockInfo* __restrict__ blocks, uint32_t nb, uint32_t cap, uint32_t* ctrl) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        const uint64_t r0 = run_off[b], r1 = run_off[b + 1];
+        const bool ok = (b > 0 || r0 == 0) && r1 > r0 && r1 <= cap && B[r1 - 1] == blocks[b].off + blocks[b].n;
+        if (!ok) atomicOr(&ctrl[CTRL_ERR], ERR_INPUT);
+    }
+}
+
+// Decode steps 2-4 for one output tile: flags at the last byte of every run
+// that ends in the tile, their exclusive prefix sum = the run of every byte
+// (after the runs that end before the tile), and the copy of the run's byte.
+__global__ void __launch_bounds__(RT) k_rle_expand(const uint8_t* __restrict__ chars, const uint32_t* __restrict__ B,
+                                                   const uint64_t* __restrict__ run_off, uint32_t nb, uint32_t N,
+                                                   uint8_t* __restrict__ out) {
+    __shared__ uint8_t sflag[RTILE];
+    __shared__ uint32_t s_k0, scan_tmp[32];
+    const uint64_t R = min(run_off[nb], (uint64_t)N);
+    if (R == 0) return;  // no runs: the check has flagged the input
+    const uint32_t ntiles = (N + RTILE - 1) / RTILE;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint32_t t0 = t * RTILE, len = min(RTILE, N - t0);
+        for (uint32_t q = threadIdx.x; q < RTILE; q += RT) sflag[q] = 0;
+        if (threadIdx.x == 0) {  // first run ending after t0: runs before it end at or before t0
+            uint64_t lo = 0, hi = R;
+            while (lo < hi) {
+                const uint64_t mid = (lo + hi) >> 1;
+                if (B[mid] <= t0) lo = mid + 1; else hi = mid;
+            }
+            s_k0 = (uint32_t)lo;
+        }
+        __syncthreads();
+        const uint32_t k0 = s_k0;
+        for (uint32_t x = threadIdx.x; x < len; x += RT) {  // at most len runs end inside the tile
+            const uint64_t k = (uint64_t)k0 + x;
+            if (k >= R) break;
+            const uint32_t e = B[k];
+            if (e - 1 - t0 >= len) break;  // ends after the tile (B increases)
+            sflag[e - 1 - t0] = 1;
+        }
+        __syncthreads();
+        const uint32_t q0 = threadIdx.x * RI;
+        uint32_t f[RI], cnt = 0;
+#pragma unroll
+        for (int j = 0; j < RI; ++j) {
+            f[j] = q0 + j < len ? sflag[q0 + j] : 0u;
+            cnt += f[j];
+        }
+        uint32_t total;
+        uint32_t r = block_exclusive_scan<RT>(cnt, scan_tmp, &total);
+#pragma unroll
+        for (int j = 0; j < RI; ++j) {
+            if (q0 + j >= len) break;
+            const uint64_t k = min((uint64_t)k0 + r, R - 1);
+            out[t0 + q0 + j] = chars[k];
+            r += f[j];
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+extern "C" bwt_status bwt_rle_encode(bwt_plan* p, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
+                                     uint8_t* d_chars, uint32_t* d_lens, uint64_t* d_run_off, void* stream) {
+    if (!p || !d_in || !offsets || !d_chars || !d_lens || !d_run_off) return BWT_EINVAL;
+    if (cudaSetDevice(p->device) != cudaSuccess) return BWT_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::memset(&p->stats, 0, sizeof(p->stats));
+    bwt_status s = prepare_batch(p, offsets, num_blocks, st);
+    if (s != BWT_OK) return p->last = s;
+    if ((s = reset_ctrl(p, st)) != BWT_OK) return p->last = s;
+    const uint32_t N = p->total, nt = (N + RTILE - 1) / RTILE;
+    uint64_t* status = reinterpret_cast<uint64_t*>(p->status);
+    CKS(cudaMemsetAsync(status, 0, sizeof(uint64_t) * nt, st));
+    uint32_t* ends = p->vals[0];
+    const int sms = num_sms();
+    k_rle_encode<<<std::max(1, std::min<int>(nt, sms * 8)), RT, 0, st>>>(
+        d_in, N, p->blocks, p->nb, d_chars, ends, d_run_off, status, p->ctrl + CTRL_TILE_CTR, p->ctrl);
+    k_rle_lengths<<<sms * 8, 256, 0, st>>>(ends, d_run_off, p->nb, d_lens);
+    CKS(cudaGetLastError());
+    p->stats.kernel_launches = 3;
+    return p->last = finish_status(p, st);
+}
+
+extern "C" bwt_status bwt_rle_decode(bwt_plan* p, const uint8_t* d_chars, const uint32_t* d_lens,
+                                     const uint64_t* d_run_off, const uint64_t* offsets, uint32_t num_blocks,
+                                     uint8_t* d_out, void* stream) {
+    if (!p || !d_chars || !d_lens || !d_run_off || !offsets || !d_out) return BWT_EINVAL;
+    if (cudaSetDevice(p->device) != cudaSuccess) return BWT_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::memset(&p->stats, 0, sizeof(p->stats));
+    bwt_status s = prepare_batch(p, offsets, num_blocks, st);
+    if (s != BWT_OK) return p->last = s;
+    if ((s = reset_ctrl(p, st)) != BWT_OK) return p->last = s;
+    const uint32_t N = p->total, nt = (N + RTILE - 1) / RTILE;  // runs <= N, so <= nt tiles of runs
+    uint64_t* status = reinterpret_cast<uint64_t*>(p->status);
+    CKS(cudaMemsetAsync(status, 0, sizeof(uint64_t) * nt, st));
+    uint32_t* B = p->vals[0];
+    const int sms = num_sms();
+    k_rle_scan<<<std::max(1, std::min<int>(nt, sms * 8)), RT, 0, st>>>(d_lens, d_run_off, p->nb, N, B, status,
+                                                                     p->ctrl + CTRL_TILE_CTR, p->ctrl);
+    k_rle_check<<<std::max(1u, std::min<uint32_t>((p->nb + 255) / 256, 1024)), 256, 0, st>>>(B, d_run_off, p->blocks,
+                                                                                          p->nb, N, p->ctrl);
+    k_rle_expand<<<std::max(1, std::min<int>(nt, sms * 8)), RT, 0, st>>>(d_chars, B, d_run_off, p->nb, N, d_out);
+    CKS(cudaGetLastError());
+    p->stats.kernel_launches = 4;
+    return p->last = finish_status(p, st);
+}
