@@ -168,6 +168,26 @@ bwt_status bwt_rle_encode(bwt_plan* plan, const uint8_t* d_in, const uint64_t* o
 bwt_status bwt_rle_decode(bwt_plan* plan, const uint8_t* d_chars, const uint32_t* d_lens, const uint64_t* d_run_off,
                           const uint64_t* offsets, uint32_t num_blocks, uint8_t* d_out, void* stream);
 
+/* Variable-length encoding of a batch (Section 3.4, Fig. 3): every byte c is
+ * replaced by its codeword -- the low d_len[c] bits of d_code[c], 1 <= length
+ * <= 32 -- written most significant bit first into a bit stream whose bit p
+ * is bit 7 - (p mod 8) of byte p / 8; each block's stream starts at a byte
+ * boundary and its last byte is padded with zero bits.
+ *   d_code, d_len  device, uint32[256] and uint8[256]: the codeword table (a
+ *                  precomputed table, as the paper proposes; any table works,
+ *                  decodability is the caller's choice).
+ *   d_out          device, 4-byte aligned, out_cap bytes; it must hold the
+ *                  total stream rounded up to a multiple of 4 bytes (at most
+ *                  4 * offsets[num_blocks] + 4).
+ *   d_byte_off     device, uint64[num_blocks + 1]: block b's stream starts at
+ *                  byte d_byte_off[b]; d_byte_off[num_blocks] is the total.
+ *   d_block_bits   device, uint64[num_blocks]: the bits of every stream.
+ * Returns BWT_EINVAL if a byte of the input has a length outside 1..32 (or
+ * d_out is misaligned), BWT_ECAPACITY if out_cap is too small. */
+bwt_status bwt_vle_encode(bwt_plan* plan, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
+                          const uint32_t* d_code, const uint8_t* d_len, uint8_t* d_out, uint64_t out_cap,
+                          uint64_t* d_byte_off, uint64_t* d_block_bits, void* stream);
+
 /* Free the plan and all its device and host memory. NULL is accepted. */
 bwt_status bwt_plan_destroy(bwt_plan* plan);
 

@@ -149,6 +149,31 @@ class Plan:
         self.rle_decode_into(d_chars, d_lens, d_run_off, offsets, out, stream)
         return out
 
+    def vle_encode_into(self, d_in, offsets, d_code, d_len, d_out, d_byte_off, d_block_bits, stream=None,
+                        raise_on_error=True) -> int:
+        keep, off_ptr, nb = self._offsets(offsets)
+        st = self.lib.bwt_vle_encode(self.handle, _ptr(d_in), off_ptr, nb, _ptr(d_code), _ptr(d_len), _ptr(d_out),
+                                     d_out.numel(), _ptr(d_byte_off), _ptr(d_block_bits), _stream_handle(stream))
+        if raise_on_error:
+            check(st, "bwt_vle_encode")
+        return st
+
+    def vle_encode(self, d_in, offsets, code, length, stream=None):
+        """(stream uint8 trimmed to its bytes, byte_off int64[nb + 1], block_bits int64[nb]) CUDA tensors;
+        code / length: uint32[256] / uint8[256] (numpy arrays or CUDA tensors)."""
+        import torch
+        dev = d_in.device
+        d_code = code if isinstance(code, torch.Tensor) else torch.from_numpy(
+            np.ascontiguousarray(code, dtype=np.uint32).view(np.int32)).to(dev)
+        d_len = length if isinstance(length, torch.Tensor) else torch.from_numpy(
+            np.ascontiguousarray(length, dtype=np.uint8)).to(dev)
+        nb = (offsets.size if isinstance(offsets, np.ndarray) else offsets.numel()) - 1
+        out = torch.empty(4 * d_in.numel() + 8, dtype=torch.uint8, device=dev)
+        byte_off = torch.empty(nb + 1, dtype=torch.int64, device=dev)
+        bits = torch.empty(nb, dtype=torch.int64, device=dev)
+        self.vle_encode_into(d_in, offsets, d_code, d_len, out, byte_off, bits, stream)
+        return out[:int(byte_off[nb].item())], byte_off, bits
+
     def stats(self) -> dict:
         s = Stats()
         check(self.lib.bwt_plan_stats(self.handle, ctypes.byref(s)), "bwt_plan_stats")

@@ -9,10 +9,18 @@
 // gives every run's end; flags at the last byte of every run, prefix-summed
 // over the output, give every output byte its run; the byte is copied.
 //
+// Variable-length encoding (Section 3.4, Fig. 3; the substitution method of
+// Balevic it describes): every byte is looked up in a codeword table, the
+// exclusive prefix sum of the codeword lengths gives every codeword's first
+// bit, and the codewords are written there (most significant bit first;
+// each block's stream starts at a byte boundary).
+//
 // GB300 layout: the prefix sums are single passes over 4,096-element tiles
 // (256 threads x 16) with decoupled look-back between tiles, so each of the
-// two steps reads and writes every element once; tiles start in order from
-// a tile counter.
+// steps reads and writes every element once; tiles start in order from a
+// tile counter. A tile's codewords are packed into 32-bit words in shared
+// memory and stored whole; only the two words a tile shares with its
+// neighbours are merged with atomic ORs.
 #include <algorithm>
 #include <cstring>
 
@@ -224,6 +232,180 @@ __global__ void __launch_bounds__(RT) k_rle_expand(const uint8_t* __restrict__ c
     }
 }
 
+// ---- variable-length encoding ------------------------------------------------
+
+// Bits of every block's stream (sum of its bytes' codeword lengths). A byte
+// whose codeword length is outside 1..32 is an input error.
+__global__ void __launch_bounds__(RT) k_vle_bits(const uint8_t* __restrict__ S, const TileDesc* __restrict__ tiles,
+                                                 uint32_t ntiles, const uint8_t* __restrict__ len,
+                                                 unsigned long long* __restrict__ block_bits, uint32_t* ctrl) {
+    __shared__ uint8_t slen[256];
+    __shared__ uint32_t red[RT / 32];
+    slen[threadIdx.x] = len[threadIdx.x];
+    __syncthreads();
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileDesc td = tiles[t];
+        uint32_t sum = 0;
+        for (uint32_t q = threadIdx.x; q < td.len; q += RT) {
+            const uint32_t l = slen[S[td.start + q]];
+            if (l == 0u || l > 32u) atomicOr(&ctrl[CTRL_ERR], ERR_INPUT);
+            sum += l;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int w = 0; w < RT / 32; ++w) tot += red[w];
+            atomicAdd(&block_bits[td.blk], (unsigned long long)tot);
+        }
+        __syncthreads();
+    }
+}
+
+// 64-bit block-wide exclusive scan (1024 threads).
+__device__ __forceinline__ unsigned long long scan64_1024(unsigned long long v, unsigned long long* tmp,
+                                                          unsigned long long* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = tmp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        tmp[lane] = w;
+    }
+    __syncthreads();
+    const unsigned long long r = (warp ? tmp[warp - 1] : 0ull) + x - v;
+    *total = tmp[31];
+    __syncthreads();
+    return r;
+}
+
+// Byte offsets of the block streams (exclusive scan of ceil(bits / 8)); the
+// total goes to byte_off[nb]. The buffer must hold the total rounded up to
+// whole 32-bit words. One CTA.
+__global__ void __launch_bounds__(1024) k_vle_offsets(const unsigned long long* __restrict__ block_bits, uint32_t nb,
+                                                      uint64_t cap, uint64_t* __restrict__ byte_off, uint32_t* ctrl) {
+    __shared__ unsigned long long tmp[32];
+    unsigned long long run = 0;  // the same in every thread
+    for (uint32_t base = 0; base < nb; base += 1024) {
+        const uint32_t b = base + threadIdx.x;
+        const unsigned long long bytes = b < nb ? (block_bits[b] + 7) / 8 : 0ull;
+        unsigned long long tot;
+        const unsigned long long ex = scan64_1024(bytes, tmp, &tot);
+        if (b < nb) byte_off[b] = run + ex;
+        run += tot;
+    }
+    if (threadIdx.x == 0) {
+        byte_off[nb] = run;
+        if ((run + 3) / 4 * 4 > cap) atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
+    }
+}
+
+// Zeroes the output words [0, ceil(byte_off[nb] / 4)) that lie inside the
+// buffer (partial words at the end are merged by atomic OR, so they need it).
+__global__ void k_vle_zero(uint32_t* __restrict__ out32, const uint64_t* __restrict__ byte_off, uint32_t nb,
+                           uint64_t cap_words) {
+    const uint64_t words = min((byte_off[nb] + 3) / 4, cap_words);
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < words; w += (uint64_t)gridDim.x * blockDim.x)
+        out32[w] = 0u;
+}
+
+// Packs every tile's codewords: bit offsets inside the block by a block
+// scan plus look-back over the block's earlier tiles, words assembled in
+// shared memory (stream bit j of a word is bit 31 - j, stored byte-swapped so
+// that memory order is stream order), interior words stored, edge words
+// OR-ed. out32 is the output viewed as 32-bit words (4-byte aligned).
+constexpr uint32_t VLE_WORDS = RTILE + 2;  // a tile spans at most 4096 * 32 bits + alignment
+
+__global__ void __launch_bounds__(RT) k_vle_pack(const uint8_t* __restrict__ S, const TileDesc* __restrict__ tiles,
+                                                 uint32_t ntiles, const uint32_t* __restrict__ code,
+                                                 const uint8_t* __restrict__ len, const uint64_t* __restrict__ byte_off,
+                                                 uint64_t cap_words, uint32_t* __restrict__ out32,
+                                                 uint64_t* __restrict__ status, uint32_t* __restrict__ counter,
+                                                 uint32_t* ctrl) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* words = reinterpret_cast<uint32_t*>(smem);           // [VLE_WORDS]
+    uint32_t* scode = words + VLE_WORDS;                           // [256]
+    uint8_t* slen = reinterpret_cast<uint8_t*>(scode + 256);       // [256]
+    __shared__ uint32_t s_tile, scan_tmp[32];
+    __shared__ uint64_t s_excl;
+    scode[threadIdx.x] = code[threadIdx.x];
+    slen[threadIdx.x] = len[threadIdx.x];
+    const uint32_t spin = ctrl[CTRL_SPIN];
+    if (ld_volatile(&ctrl[CTRL_ERR]) & (ERR_INPUT | ERR_CAPACITY)) return;  // bad table or too small a buffer
+    for (;;) {
+        const uint32_t t = next_tile(&s_tile, counter);
+        if (t >= ntiles) break;
+        const TileDesc td = tiles[t];
+        const uint32_t q0 = threadIdx.x * RI;
+        uint32_t lsum = 0;
+        uint32_t c[RI];
+        uint8_t l[RI];
+#pragma unroll
+        for (int j = 0; j < RI; ++j) {
+            const uint32_t q = q0 + j;
+            l[j] = 0;
+            c[j] = 0;
+            if (q < td.len) {
+                const uint8_t x = S[td.start + q];
+                l[j] = slen[x];
+                c[j] = scode[x];
+                lsum += l[j];
+            }
+        }
+        uint32_t total;
+        const uint32_t pre = block_exclusive_scan<RT>(lsum, scan_tmp, &total);
+        if (threadIdx.x < 32) {
+            const uint64_t e = lookback_u64(status, t, td.firstTile, total, spin, &ctrl[CTRL_ERR]);
+            if (threadIdx.x == 0) s_excl = e;
+        }
+        for (uint32_t w = threadIdx.x; w < VLE_WORDS; w += RT) words[w] = 0u;
+        __syncthreads();
+        const uint64_t g0 = byte_off[td.blk] * 8 + s_excl;  // first bit of the tile
+        const uint64_t w0 = g0 >> 5;
+        uint64_t g = g0 + pre;
+#pragma unroll
+        for (int j = 0; j < RI; ++j) {
+            const uint32_t L = l[j];
+            if (L) {
+                const uint32_t cw = L == 32u ? c[j] : (c[j] & ((1u << L) - 1u));
+                const uint32_t x = (uint32_t)(g - (w0 << 5));  // bit offset inside the tile's words
+                const uint32_t wi = x >> 5, sh = x & 31u;       // codeword bits [sh, sh + L) of word wi
+                if (sh + L <= 32u) {
+                    atomicOr(&words[wi], cw << (32u - sh - L));
+                } else {
+                    const uint32_t rest = sh + L - 32u;          // bits spilling into word wi + 1
+                    atomicOr(&words[wi], cw >> rest);
+                    atomicOr(&words[wi + 1], cw << (32u - rest));
+                }
+                g += L;
+            }
+        }
+        __syncthreads();
+        const uint32_t nwords = (uint32_t)(((g0 + total + 31) >> 5) - w0);
+        for (uint32_t x = threadIdx.x; x < nwords; x += RT) {
+            const uint64_t w = w0 + x;
+            if (w >= cap_words) break;
+            const uint32_t v = __byte_perm(words[x], 0, 0x0123);
+            if (x == 0 || x + 1 == nwords) atomicOr(&out32[w], v);
+            else out32[w] = v;
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 extern "C" bwt_status bwt_rle_encode(bwt_plan* p, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
@@ -270,5 +452,41 @@ extern "C" bwt_status bwt_rle_decode(bwt_plan* p, const uint8_t* d_chars, const 
     k_rle_expand<<<std::max(1, std::min<int>(nt, sms * 8)), RT, 0, st>>>(d_chars, B, d_run_off, p->nb, N, d_out);
     CKS(cudaGetLastError());
     p->stats.kernel_launches = 4;
+    return p->last = finish_status(p, st);
+}
+
+extern "C" bwt_status bwt_vle_encode(bwt_plan* p, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
+                                     const uint32_t* d_code, const uint8_t* d_len, uint8_t* d_out, uint64_t out_cap,
+                                     uint64_t* d_byte_off, uint64_t* d_block_bits, void* stream) {
+    if (!p || !d_in || !offsets || !d_code || !d_len || !d_out || !d_byte_off || !d_block_bits) return BWT_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_out) & 3u) != 0) return BWT_EINVAL;  // written as 32-bit words
+    if (cudaSetDevice(p->device) != cudaSuccess) return BWT_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::memset(&p->stats, 0, sizeof(p->stats));
+    bwt_status s = prepare_batch(p, offsets, num_blocks, st);
+    if (s != BWT_OK) return p->last = s;
+    if ((s = reset_ctrl(p, st)) != BWT_OK) return p->last = s;
+    const uint32_t nb = p->nb, nt = p->ntiles0;
+    if (p->tile > (int)RTILE) return p->last = BWT_EINVAL;
+    static bool attr = [] {
+        cudaFuncSetAttribute((void*)k_vle_pack, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(VLE_WORDS * 4 + 256 * 5));
+        return true;
+    }();
+    (void)attr;
+    const int sms = num_sms();
+    unsigned long long* bits = reinterpret_cast<unsigned long long*>(d_block_bits);
+    CKS(cudaMemsetAsync(bits, 0, sizeof(uint64_t) * nb, st));
+    k_vle_bits<<<std::max(1, std::min<int>(nt, sms * 8)), RT, 0, st>>>(d_in, p->tiles0, nt, d_len, bits, p->ctrl);
+    k_vle_offsets<<<1, 1024, 0, st>>>(bits, nb, out_cap, d_byte_off, p->ctrl);
+    const uint64_t cap_words = out_cap / 4;  // whole words inside the buffer
+    k_vle_zero<<<sms * 8, 256, 0, st>>>(reinterpret_cast<uint32_t*>(d_out), d_byte_off, nb, cap_words);
+    uint64_t* status = reinterpret_cast<uint64_t*>(p->status);
+    CKS(cudaMemsetAsync(status, 0, sizeof(uint64_t) * nt, st));
+    k_vle_pack<<<std::max(1, std::min<int>(nt, sms * 6)), RT, VLE_WORDS * 4 + 256 * 5, st>>>(
+        d_in, p->tiles0, nt, d_code, d_len, d_byte_off, cap_words, reinterpret_cast<uint32_t*>(d_out), status,
+        p->ctrl + CTRL_TILE_CTR, p->ctrl);
+    CKS(cudaGetLastError());
+    p->stats.kernel_launches = 5;
     return p->last = finish_status(p, st);
 }

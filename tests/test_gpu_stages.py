@@ -72,3 +72,105 @@ def test_rle_full_mixed_workload():
     w = datagen.config(2)
     buf, off = w.generate()
     _rle_check([buf[int(off[b]):int(off[b + 1])] for b in range(w.num_blocks)])
+
+
+# ---- variable-length encoding ----------------------------------------------
+
+def huffman_table(counts):
+    """A Huffman code (lengths by the textbook merge of the two rarest
+    weights, canonical code values) for the bytes with counts > 0; absent
+    bytes get the 1-bit code 0 (never used)."""
+    import heapq
+    used = [c for c in range(256) if counts[c] > 0]
+    length = np.ones(256, dtype=np.uint8)
+    if len(used) == 1:
+        length[used[0]] = 1
+    else:
+        heap = [(int(counts[c]), i, [c]) for i, c in enumerate(used)]
+        heapq.heapify(heap)
+        uid = len(heap)
+        depth = {c: 0 for c in used}
+        while len(heap) > 1:
+            w1, _, a = heapq.heappop(heap)
+            w2, _, b = heapq.heappop(heap)
+            for c in a + b:
+                depth[c] += 1
+            heapq.heappush(heap, (w1 + w2, uid, a + b))
+            uid += 1
+        for c in used:
+            length[c] = depth[c]
+    code = np.zeros(256, dtype=np.uint32)
+    nxt, prev = 0, 0
+    for c in sorted(used, key=lambda c: (length[c], c)):
+        nxt <<= int(length[c]) - prev
+        code[c] = nxt
+        nxt += 1
+        prev = int(length[c])
+    return code, length
+
+
+def _vle_check(blocks, code=None, length=None):
+    import torch
+    buf, off = batch_from_blocks(blocks)
+    if code is None:
+        code, length = huffman_table(np.bincount(buf, minlength=256))
+    with _plan(buf, off) as plan:
+        out, byte_off, bits = plan.vle_encode(torch.from_numpy(buf).cuda(), off, code, length)
+        out, byte_off, bits = out.cpu().numpy(), byte_off.cpu().numpy(), bits.cpu().numpy()
+    for b in range(off.size - 1):
+        ref, ref_bits = oracle.vle_encode(buf[int(off[b]):int(off[b + 1])], code, length)
+        assert bits[b] == ref_bits
+        assert byte_off[b + 1] - byte_off[b] == ref.size
+        assert np.array_equal(out[byte_off[b]:byte_off[b + 1]], ref), b
+
+
+def test_vle_fig3_lengths():
+    lens = [1, 8, 16, 7, 14, 9, 4, 4]
+    code = np.zeros(256, dtype=np.uint32)
+    length = np.ones(256, dtype=np.uint8)
+    for i, L in enumerate(lens):
+        code[i] = (1 << L) - 1
+        length[i] = L
+    _vle_check([np.arange(8, dtype=np.uint8)], code, length)
+
+
+@pytest.mark.parametrize("src", [datagen.UNIFORM, datagen.MARKOV3_Z96, datagen.RUNS16, datagen.CONST,
+                                 datagen.FIBONACCI])
+def test_vle_every_source(src):
+    _vle_check([datagen.block(src, 70 + i, n) for i, n in enumerate([1, 3, 4095, 4096, 4097, 70_001])])
+
+
+def test_vle_long_codes_and_many_blocks():
+    rng = np.random.default_rng(8)
+    code = rng.integers(0, 2**32, 256, dtype=np.uint64).astype(np.uint32)
+    length = rng.integers(1, 33, 256).astype(np.uint8)
+    length[:4] = 32
+    blocks = [rng.integers(0, 256, int(n)).astype(np.uint8) for n in rng.integers(1, 9000, 40)]
+    _vle_check(blocks, code, length)
+
+
+def test_vle_rejects_bad_lengths_and_small_buffers():
+    import torch
+    buf = np.arange(10, dtype=np.uint8)
+    off = np.array([0, 10], dtype=np.uint64)
+    code = torch.zeros(256, dtype=torch.int32, device="cuda")
+    with _plan(buf, off) as plan:
+        d_in = torch.from_numpy(buf).cuda()
+        bo = torch.empty(2, dtype=torch.int64, device="cuda")
+        bits = torch.empty(1, dtype=torch.int64, device="cuda")
+        length = torch.full((256,), 8, dtype=torch.uint8, device="cuda")
+        length[3] = 0
+        out = torch.empty(64, dtype=torch.uint8, device="cuda")
+        assert plan.vle_encode_into(d_in, off, code, length, out, bo, bits, raise_on_error=False) == _lib.BWT_EINVAL
+        length[3] = 8
+        small = torch.empty(8, dtype=torch.uint8, device="cuda")  # 10 bytes of stream do not fit
+        assert plan.vle_encode_into(d_in, off, code, length, small, bo, bits,
+                                    raise_on_error=False) == _lib.BWT_ECAPACITY
+        plan.vle_encode_into(d_in, off, code, length, out, bo, bits)
+        assert int(bo[1]) == 10 and int(bits[0]) == 80
+
+
+def test_vle_full_workload_with_its_huffman_table():
+    w = datagen.config(2)
+    buf, off = w.generate()
+    _vle_check([buf[int(off[b]):int(off[b + 1])] for b in range(w.num_blocks)])
