@@ -188,6 +188,15 @@ bwt_status bwt_vle_encode(bwt_plan* plan, const uint8_t* d_in, const uint64_t* o
                           const uint32_t* d_code, const uint8_t* d_len, uint8_t* d_out, uint64_t out_cap,
                           uint64_t* d_byte_off, uint64_t* d_block_bits, void* stream);
 
+/* Move-to-front encoding of a batch (Section 3.3): for every block a list of
+ * the 256 byte values starts in ascending order; every byte is replaced by
+ * its position in the list and then moved to the front.
+ *   d_in   device, uint8[offsets[num_blocks]]; d_out: the same size (the
+ *          positions). Uses the plan's first-sort tiles as chunks, plus about
+ *          0.13 bytes per byte of max_total_bytes allocated on the first call. */
+bwt_status bwt_mtf_encode(bwt_plan* plan, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
+                          uint8_t* d_out, void* stream);
+
 /* Free the plan and all its device and host memory. NULL is accepted. */
 bwt_status bwt_plan_destroy(bwt_plan* plan);
 

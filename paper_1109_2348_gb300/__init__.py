@@ -174,6 +174,19 @@ class Plan:
         self.vle_encode_into(d_in, offsets, d_code, d_len, out, byte_off, bits, stream)
         return out[:int(byte_off[nb].item())], byte_off, bits
 
+    def mtf_encode_into(self, d_in, offsets, d_out, stream=None, raise_on_error=True) -> int:
+        keep, off_ptr, nb = self._offsets(offsets)
+        st = self.lib.bwt_mtf_encode(self.handle, _ptr(d_in), off_ptr, nb, _ptr(d_out), _stream_handle(stream))
+        if raise_on_error:
+            check(st, "bwt_mtf_encode")
+        return st
+
+    def mtf_encode(self, d_in, offsets, stream=None):
+        import torch
+        out = torch.empty_like(d_in)
+        self.mtf_encode_into(d_in, offsets, out, stream)
+        return out
+
     def stats(self) -> dict:
         s = Stats()
         check(self.lib.bwt_plan_stats(self.handle, ctypes.byref(s)), "bwt_plan_stats")

@@ -69,7 +69,7 @@ class Stats(ctypes.Structure):
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = [
     "bwt_plan_create", "bwt_forward_batch", "bwt_inverse_check", "bwt_inverse_batch", "bwt_plan_destroy",
-    "bwt_rle_encode", "bwt_rle_decode", "bwt_vle_encode",
+    "bwt_rle_encode", "bwt_rle_decode", "bwt_vle_encode", "bwt_mtf_encode",
     "bwt_plan_last_status", "bwt_plan_stats", "bwt_plan_set_radix", "bwt_plan_debug_waits",
     "bwt_status_string", "bwt_last_cuda_error",
     "bwt_mlp_forward", "bwt_mlp_loss_grad", "bwt_mlp_adam_step", "bwt_model_train", "bwt_model_samples",
@@ -114,6 +114,8 @@ def load(build_if_missing: bool = True):
     lib.bwt_rle_decode.restype = ctypes.c_int
     lib.bwt_vle_encode.argtypes = [vp, vp, vp, u32, vp, vp, vp, u64, vp, vp, vp]
     lib.bwt_vle_encode.restype = ctypes.c_int
+    lib.bwt_mtf_encode.argtypes = [vp, vp, vp, u32, vp, vp]
+    lib.bwt_mtf_encode.restype = ctypes.c_int
     lib.bwt_plan_destroy.argtypes = [vp]
     lib.bwt_plan_destroy.restype = ctypes.c_int
     lib.bwt_plan_last_status.argtypes = [vp]

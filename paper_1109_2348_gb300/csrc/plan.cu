@@ -115,7 +115,7 @@ void bwt::free_plan_memory(bwt_plan* p) {
     F(p->tiles0); F(p->ltiles); F(p->blocks); F(p->hist); F(p->status); F(p->ctrl);
     for (int s = 0; s < 2; ++s)
         for (int c = 0; c < NCLS; ++c) F(p->bins[s][c]);
-    F(p->splitters); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->route_first); F(p->bstats); F(p->tiles_aux); F(p->inv_slots); F(p->inv_items);
+    F(p->splitters); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->route_first); F(p->bstats); F(p->tiles_aux); F(p->inv_slots); F(p->inv_items); F(p->mtf_lists);
     FH(p->h_ctrl); FH(p->h_tiles); FH(p->h_blocks); FH(p->h_off);
     FH(p->h_route); FH(p->h_bstats); FH(p->h_inv_items);
     for (auto& e : p->events) cudaEventDestroy(e);

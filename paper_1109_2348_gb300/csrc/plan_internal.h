@@ -73,7 +73,8 @@ struct bwt_plan {
     // GPU inverse (allocated on first use)
     uint32_t* inv_slots = nullptr;     // [6][cap_n / 16 + 3 cap_b + 4] sample walks and pointer jumping
     uint32_t* inv_items = nullptr;     // [2][cap_b + 1] prefixes of work items and of samples per block
-    uint32_t* h_inv_items = nullptr;   // pinned staging
+    uint32_t* h_inv_items = nullptr;   // pinned staging (also the move-to-front chunk table)
+    uint8_t* mtf_lists = nullptr;      // move-to-front scratch (allocated on first use)
 
     // pinned host staging
     uint32_t* h_ctrl = nullptr;

@@ -15,6 +15,16 @@
 // bit, and the codewords are written there (most significant bit first;
 // each block's stream starts at a byte boundary).
 //
+// Move-to-front encoding (Section 3.3): the paper's parallelism is over
+// the list -- the 256 list entries are spread over a warp's lanes (8 a
+// lane), found with one compare per lane and a ballot, and moved with lane
+// shifts. A block's bytes form one chain of list states, so blocks are cut
+// into chunks: a chunk's effect on the list is the chunk's distinct bytes
+// in order of last occurrence, followed by the old list without them. Pass
+// 1 finds that list for every chunk, pass 2 chains the chunks of every
+// block to get each chunk's starting list, pass 3 encodes all chunks at
+// once.
+//
 // GB300 layout: the prefix sums are single passes over 4,096-element tiles
 // (256 threads x 16) with decoupled look-back between tiles, so each of the
 // steps reads and writes every element once; tiles start in order from a
@@ -406,6 +416,144 @@ __global__ void __launch_bounds__(RT) k_vle_pack(const uint8_t* __restrict__ S, 
     }
 }
 
+// ---- move-to-front encoding ---------------------------------------------------
+
+// Pass 1: per chunk (a first-sort tile), its distinct bytes ordered by last
+// occurrence, most recent first: mru[chunk][0 .. mcnt[chunk]).
+__global__ void __launch_bounds__(RT) k_mtf_mru(const uint8_t* __restrict__ S, const TileDesc* __restrict__ tiles,
+                                                uint32_t ntiles, uint8_t* __restrict__ mru,
+                                                uint32_t* __restrict__ mcnt) {
+    __shared__ int32_t last[256];
+    __shared__ uint8_t sb[RTILE];
+    __shared__ uint32_t s_cnt;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileDesc td = tiles[t];
+        last[threadIdx.x] = -1;
+        if (threadIdx.x == 0) s_cnt = 0;
+        for (uint32_t q = threadIdx.x; q < td.len; q += RT) sb[q] = S[td.start + q];
+        __syncthreads();
+        const uint32_t q0 = threadIdx.x * RI;
+        for (int j = RI - 1; j >= 0; --j) {  // the last occurrence inside this thread's range only
+            const uint32_t q = q0 + j;
+            if (q >= td.len) continue;
+            const uint8_t x = sb[q];
+            bool later = false;
+            for (int k = j + 1; k < RI && q0 + k < td.len; ++k) later |= sb[q0 + k] == x;
+            if (!later) atomicMax(&last[x], (int32_t)q);
+        }
+        __syncthreads();
+        const int32_t mine = last[threadIdx.x];
+        if (mine >= 0) {
+            uint32_t rank = 0;
+            for (int u = 0; u < 256; ++u) rank += last[u] > mine;
+            mru[(size_t)t * 256 + rank] = (uint8_t)threadIdx.x;
+            atomicAdd(&s_cnt, 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) mcnt[t] = s_cnt;
+        __syncthreads();
+    }
+}
+
+// Pass 2: one warp per block chains its chunks: the list before chunk c
+// goes to tlist[c]; the next list is mru[c] followed by the list without
+// mru[c]'s bytes. A lane holds list entries 8 lane .. 8 lane + 7 (byte k of
+// its 64-bit word is entry 8 lane + k).
+__global__ void __launch_bounds__(256) k_mtf_chain(const uint32_t* __restrict__ tfirst, uint32_t nb,
+                                                   const uint8_t* __restrict__ mru, const uint32_t* __restrict__ mcnt,
+                                                   uint8_t* __restrict__ tlist) {
+    __shared__ uint32_t member[8][8];
+    __shared__ __align__(8) uint8_t nlist[8][256];
+    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    for (uint32_t b = blockIdx.x * 8 + wl; b < nb; b += gridDim.x * 8) {
+        uint64_t L = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) L |= (uint64_t)(lane * 8 + k) << (8 * k);
+        for (uint32_t c = tfirst[b]; c < tfirst[b + 1]; ++c) {
+            reinterpret_cast<uint64_t*>(tlist + (size_t)c * 256)[lane] = L;
+            if (lane < 8) member[wl][lane] = 0u;
+            __syncwarp();
+            const uint32_t cnt = mcnt[c];
+            const uint8_t* m = mru + (size_t)c * 256;
+            for (uint32_t i = lane; i < cnt; i += 32) {
+                const uint32_t v = m[i];
+                atomicOr(&member[wl][v >> 5], 1u << (v & 31));
+                nlist[wl][i] = (uint8_t)v;
+            }
+            __syncwarp();
+            uint32_t keep = 0;  // bit k: entry 8 lane + k stays (not among the chunk's bytes)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t v = (uint32_t)(L >> (8 * k)) & 0xffu;
+                keep |= (uint32_t)(((member[wl][v >> 5] >> (v & 31)) & 1u) == 0u) << k;
+            }
+            uint32_t n = __popc(keep), x = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            uint32_t pos = cnt + x - n;
+            (void)lt;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if ((keep >> k) & 1u) nlist[wl][pos++] = (uint8_t)(L >> (8 * k));
+            __syncwarp();
+            L = reinterpret_cast<const uint64_t*>(nlist[wl])[lane];
+            __syncwarp();
+        }
+    }
+}
+
+// Pass 3: one warp per chunk encodes it from its starting list. The chunk
+// sits in the warp's shared buffer and every byte is replaced there by its
+// list position; a byte already at the front costs one compare.
+constexpr int MTF_WARPS = 8;
+
+__global__ void __launch_bounds__(MTF_WARPS * 32) k_mtf_encode(const uint8_t* __restrict__ S,
+                                                               const TileDesc* __restrict__ tiles, uint32_t ntiles,
+                                                               const uint8_t* __restrict__ tlist,
+                                                               uint8_t* __restrict__ out) {
+    __shared__ __align__(16) uint8_t buf[MTF_WARPS][RTILE];
+    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    uint8_t* bw = buf[wl];
+    for (uint32_t t = blockIdx.x * MTF_WARPS + wl; t < ntiles; t += gridDim.x * MTF_WARPS) {
+        const TileDesc td = tiles[t];
+        for (uint32_t q = lane; q < td.len; q += 32) bw[q] = S[td.start + q];
+        uint64_t L = reinterpret_cast<const uint64_t*>(tlist + (size_t)t * 256)[lane];
+        uint32_t front = __shfl_sync(0xffffffffu, (uint32_t)L & 0xffu, 0);
+        __syncwarp();
+        for (uint32_t i = 0; i < td.len; ++i) {
+            const uint32_t x = bw[i];
+            if (x == front) {  // warp-uniform: x and front are the same in every lane
+                if (lane == 0) bw[i] = 0;
+                continue;
+            }
+            const uint32_t x4 = x * 0x01010101u;
+            const uint32_t m0 = __vcmpeq4((uint32_t)L, x4), m1 = __vcmpeq4((uint32_t)(L >> 32), x4);
+            const uint32_t own = __ballot_sync(0xffffffffu, (m0 | m1) != 0u);
+            const uint32_t o = __ffs(own) - 1;
+            uint32_t k = m0 ? (__ffs(m0) - 1) >> 3 : 4u + ((__ffs(m1) - 1) >> 3);
+            k = __shfl_sync(0xffffffffu, k, o);
+            uint32_t carry = __shfl_up_sync(0xffffffffu, (uint32_t)(L >> 56), 1);
+            if (lane == 0) carry = x;
+            const uint64_t shifted = (L << 8) | carry;
+            if (lane < o) {
+                L = shifted;
+            } else if (lane == o) {
+                const uint64_t mask = k == 7u ? ~0ull : ((1ull << (8 * (k + 1))) - 1ull);
+                L = (shifted & mask) | (L & ~mask);
+            }
+            if (lane == 0) bw[i] = (uint8_t)(o * 8 + k);
+            front = x;
+        }
+        __syncwarp();
+        for (uint32_t q = lane; q < td.len; q += 32) out[td.start + q] = bw[q];
+        __syncwarp();
+    }
+}
+
 }  // namespace
 
 extern "C" bwt_status bwt_rle_encode(bwt_plan* p, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
@@ -489,4 +637,38 @@ extern "C" bwt_status bwt_vle_encode(bwt_plan* p, const uint8_t* d_in, const uin
     CKS(cudaGetLastError());
     p->stats.kernel_launches = 5;
     return p->last = finish_status(p, st);
+}
+
+extern "C" bwt_status bwt_mtf_encode(bwt_plan* p, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
+                                     uint8_t* d_out, void* stream) {
+    if (!p || !d_in || !offsets || !d_out) return BWT_EINVAL;
+    if (cudaSetDevice(p->device) != cudaSuccess) return BWT_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::memset(&p->stats, 0, sizeof(p->stats));
+    bwt_status s = prepare_batch(p, offsets, num_blocks, st);
+    if (s != BWT_OK) return p->last = s;
+    if (p->tile > (int)RTILE) return p->last = BWT_EINVAL;
+    const uint32_t nb = p->nb, nt = p->ntiles0;
+    // scratch (first use): per chunk its list of last occurrences, its count and its starting list;
+    // per block its first chunk
+    if (!p->mtf_lists) CKS(cudaMalloc(&p->mtf_lists, (size_t)p->cap_tiles0 * (512 + 4) + 4 * ((size_t)p->cap_b + 1)));
+    uint8_t* mru = p->mtf_lists;
+    uint8_t* tlist = mru + (size_t)p->cap_tiles0 * 256;
+    uint32_t* mcnt = reinterpret_cast<uint32_t*>(tlist + (size_t)p->cap_tiles0 * 256);
+    uint32_t* tfirst = mcnt + p->cap_tiles0;
+    uint32_t* h_first = p->h_inv_items;  // pinned staging, free outside the inverse
+    for (uint32_t t = 0, b = 0; t < nt; ++t)
+        if (t == 0 || p->h_tiles[t].blk != p->h_tiles[t - 1].blk) h_first[b++] = t;
+    h_first[nb] = nt;
+    CKS(cudaMemcpyAsync(tfirst, h_first, sizeof(uint32_t) * (nb + 1), cudaMemcpyHostToDevice, st));
+    const int sms = num_sms();
+    k_mtf_mru<<<std::max(1, std::min<int>(nt, sms * 8)), RT, 0, st>>>(d_in, p->tiles0, nt, mru, mcnt);
+    k_mtf_chain<<<std::max(1u, std::min<uint32_t>((nb + 7) / 8, (uint32_t)sms * 8)), 256, 0, st>>>(tfirst, nb, mru,
+                                                                                                 mcnt, tlist);
+    k_mtf_encode<<<std::max(1, std::min<int>((nt + MTF_WARPS - 1) / MTF_WARPS, sms * 6)), MTF_WARPS * 32, 0, st>>>(
+        d_in, p->tiles0, nt, tlist, d_out);
+    CKS(cudaGetLastError());
+    p->stats.kernel_launches = 3;
+    CKS(cudaStreamSynchronize(st));
+    return p->last = BWT_OK;
 }

@@ -174,3 +174,45 @@ def test_vle_full_workload_with_its_huffman_table():
     w = datagen.config(2)
     buf, off = w.generate()
     _vle_check([buf[int(off[b]):int(off[b + 1])] for b in range(w.num_blocks)])
+
+
+# ---- move-to-front encoding -------------------------------------------------
+
+def _mtf_check(blocks, tile=0):
+    import torch
+    buf, off = batch_from_blocks(blocks)
+    sizes = np.diff(off.astype(np.int64))
+    with Plan(max_blocks=off.size - 1, max_total_bytes=int(off[-1]), max_block_bytes=int(sizes.max()),
+              tile_keys=tile) as plan:
+        got = plan.mtf_encode(torch.from_numpy(buf).cuda(), off).cpu().numpy()
+    want = np.concatenate([oracle.mtf_encode(buf[int(off[b]):int(off[b + 1])]) for b in range(off.size - 1)])
+    if not np.array_equal(got, want):
+        bad = np.flatnonzero(got != want)
+        raise AssertionError(f"{bad.size} positions differ, first {bad[0]}")
+
+
+def test_mtf_hand_worked_words():
+    _mtf_check([np.frombuffer(w, dtype=np.uint8) for w in (b"banana", b"aaab")])
+
+
+@pytest.mark.parametrize("src", [datagen.UNIFORM, datagen.MARKOV2_Z64, datagen.MARKOV3_Z96, datagen.RUNS16,
+                                 datagen.CONST, datagen.PERIOD7, datagen.PERIOD1000, datagen.FIBONACCI,
+                                 datagen.MUTATED_UNIT])
+def test_mtf_every_source(src):
+    _mtf_check([datagen.block(src, 90 + i, n) for i, n in enumerate([1, 2, 4095, 4096, 4097, 50_001])])
+
+
+@pytest.mark.parametrize("tile", [1024, 4096])
+def test_mtf_chunks_chain_across_tiles(tile):
+    rng = np.random.default_rng(9)
+    blocks = [rng.integers(0, int(a), int(n)).astype(np.uint8)
+              for a, n in zip(rng.choice([2, 5, 40, 256], 30), rng.integers(1, 30_000, 30))]
+    _mtf_check(blocks, tile)
+
+
+def test_mtf_of_the_bwt_output():
+    import torch
+    w = datagen.config(2).subset(range(9))
+    buf, off = w.generate()
+    L, _ = oracle.bwt_batch(buf, off)
+    _mtf_check([L[int(off[b]):int(off[b + 1])] for b in range(w.num_blocks)])
