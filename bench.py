@@ -41,10 +41,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--blocks", type=int, default=0, help="use only the first N blocks of the workload")
-    ap.add_argument("--mode", choices=["host", "graph", "perblock", "learned", "learned-host", "inverse"],
+    ap.add_argument("--mode", choices=["host", "graph", "perblock", "learned", "learned-host", "inverse", "stages"],
                     default="learned",
                     help="learned = learned bucketing + the batched graph launch; learned-host drives its rounds "
-                         "from the host; inverse times the GPU inverse transform of the workload's BWT")
+                         "from the host; inverse times the GPU inverse transform of the workload's BWT; stages "
+                         "times the stages after it (run-length, move-to-front, variable-length encoding)")
     ap.add_argument("--radix-bits", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--model", default=None, help="model file for --mode learned (trained in-process if absent)")
@@ -541,12 +542,155 @@ def inverse_bench(args):
         torch.distributed.destroy_process_group()
 
 
+def huffman_lengths(counts):
+    """Code lengths of a Huffman code for the bytes with counts > 0 (the host
+    builds the table once: a precomputed table, as the paper proposes)."""
+    import heapq
+    used = [c for c in range(256) if counts[c] > 0]
+    length = np.ones(256, dtype=np.uint8)
+    if len(used) > 1:
+        heap = [(int(counts[c]), i, [c]) for i, c in enumerate(used)]
+        heapq.heapify(heap)
+        depth = {c: 0 for c in used}
+        uid = len(heap)
+        while len(heap) > 1:
+            w1, _, a = heapq.heappop(heap)
+            w2, _, b = heapq.heappop(heap)
+            for c in a + b:
+                depth[c] += 1
+            heapq.heappush(heap, (w1 + w2, uid, a + b))
+            uid += 1
+        for c in used:
+            length[c] = depth[c]
+    code = np.zeros(256, dtype=np.uint32)
+    nxt, prev = 0, 0
+    for c in sorted(used, key=lambda c: (length[c], c)):
+        nxt <<= int(length[c]) - prev
+        code[c] = nxt
+        nxt += 1
+        prev = int(length[c])
+    return code, length
+
+
+def stages_bench(args):
+    """The stages of the paper's pipeline on the GPU, each timed with CUDA
+    events (L2 flushed before every step): forward BWT of the workload ->
+    run-length encoding of L -> move-to-front of the runs' bytes ->
+    variable-length encoding of the result with a Huffman table built once
+    from its histogram. Outputs are checked against the oracle once."""
+    import torch
+    import oracle
+    from paper_1109_2348_gb300 import F_GRAPH, Plan
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = rank_workload(args.config, args.blocks, rank, world)
+    buf, off = w.generate()
+    n = buf.size
+    sizes = np.diff(off.astype(np.int64))
+    plan = Plan(max_blocks=w.num_blocks, max_total_bytes=n, max_block_bytes=int(sizes.max()), flags=F_GRAPH,
+                device=local)
+    d_in = torch.from_numpy(buf).to(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    d_L = torch.empty_like(d_in)
+    d_p = torch.empty(w.num_blocks, dtype=torch.int32, device=dev)
+    chars = torch.empty_like(d_in)
+    lens = torch.empty(n, dtype=torch.int32, device=dev)
+    run_off = torch.empty(w.num_blocks + 1, dtype=torch.int64, device=dev)
+    mtf = torch.empty_like(d_in)
+    vle = torch.empty(4 * n + 8, dtype=torch.uint8, device=dev)
+    byte_off = torch.empty(w.num_blocks + 1, dtype=torch.int64, device=dev)
+    bits = torch.empty(w.num_blocks, dtype=torch.int64, device=dev)
+
+    def run_once(table=None):
+        plan.forward_into(d_in, off, d_L, d_p, stream)
+        plan.rle_encode_into(d_L, off, chars, lens, run_off, stream)
+        ro = run_off.cpu().numpy().astype(np.uint64)  # the runs' block layout for the next stages
+        R = int(ro[-1])
+        plan.mtf_encode_into(chars[:R], ro, mtf, stream)
+        if table is not None:
+            plan.vle_encode_into(mtf[:R], ro, table[0], table[1], vle, byte_off, bits, stream)
+        return ro, R
+
+    ro, R = run_once()
+    hist = np.bincount(mtf[:R].cpu().numpy(), minlength=256)
+    code, length = huffman_lengths(hist)
+    table = (torch.from_numpy(code.view(np.int32)).to(dev), torch.from_numpy(length).to(dev))
+    for _ in range(max(3, args.warmup)):
+        ro, R = run_once(table)
+    torch.cuda.synchronize()
+    # check every stage once against the oracle (a sample of blocks for the forward transform)
+    L_h = d_L.cpu().numpy()
+    ref_c, ref_l, ref_ro = oracle.rle_batch(L_h, off)
+    assert np.array_equal(ro, ref_ro) and np.array_equal(chars[:R].cpu().numpy(), ref_c)
+    assert np.array_equal(lens[:R].cpu().numpy().astype(np.uint32), ref_l)
+    m_h = mtf[:R].cpu().numpy()
+    vle_h = vle.cpu().numpy()
+    bo = byte_off.cpu().numpy()
+    for b in range(w.num_blocks):
+        cb = ref_c[int(ro[b]):int(ro[b + 1])]
+        assert np.array_equal(m_h[int(ro[b]):int(ro[b + 1])], oracle.mtf_encode(cb)), b
+        ref_v, _ = oracle.vle_encode(m_h[int(ro[b]):int(ro[b + 1])], code, length)
+        assert np.array_equal(vle_h[bo[b]:bo[b + 1]], ref_v), b
+    sub = list(range(0, w.num_blocks, max(1, w.num_blocks // 4)))[:4]
+    sw = w.subset(sub)
+    sbuf, soff = sw.generate()
+    ref_L, _ = oracle.bwt_batch(sbuf, soff)
+    for j, b in enumerate(sub):
+        assert np.array_equal(L_h[int(off[b]):int(off[b + 1])], ref_L[int(soff[j]):int(soff[j + 1])])
+
+    names = ["bwt", "rle", "mtf", "vle"]
+    ms = {k: 0.0 for k in names}
+    sampler = ClockSampler(local)
+    sampler.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
+        plan.forward_into(d_in, off, d_L, d_p, stream)
+        ev[1].record(stream)
+        plan.rle_encode_into(d_L, off, chars, lens, run_off, stream)
+        ev[2].record(stream)
+        plan.mtf_encode_into(chars[:R], ro, mtf, stream)
+        ev[3].record(stream)
+        plan.vle_encode_into(mtf[:R], ro, table[0], table[1], vle, byte_off, bits, stream)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        for i, k in enumerate(names):
+            ms[k] += ev[i].elapsed_time(ev[i + 1])
+    clocks = sampler.stop()
+    plan.close()
+    vle_bytes = int(byte_off[-1].item())
+    stage = {}
+    for k, inb in (("bwt", n), ("rle", n), ("mtf", R), ("vle", R)):
+        t = ms[k] / args.steps
+        stage[k] = {"ms": round(t, 4), "input_bytes": inb, "input_MB_s": round(inb / (t / 1e3) / 1e6, 1)}
+    total_ms = sum(ms.values()) / args.steps
+    if rank == 0:
+        line = {"metric": "BWT -> RLE -> MTF -> VLE pipeline input MB/s on 1 GB300, bit-exact",
+                "value": round(n / (total_ms / 1e3) / 1e6, 3), "unit": "MB/s", "n_gpus": 1, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": round(total_ms, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+                "data": "synthetic (seeded generators, no dataset)",
+                "config": {"workload": w.name, "blocks": w.num_blocks, "bytes": n, "mode": "stages",
+                           "runs": R, "vle_stream_bytes": vle_bytes,
+                           "note": "run lengths stay uint32 (not entropy-coded); the VLE stream codes the runs' bytes "
+                                   "after move-to-front",
+                           "l2": "256 MB flush before every timed step"},
+                "clocks": clocks, "stages": stage, "e2e": None, "roofline": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
     elif args.mode == "inverse":
         inverse_bench(args)
+    elif args.mode == "stages":
+        stages_bench(args)
     else:
         ours(args)
 
