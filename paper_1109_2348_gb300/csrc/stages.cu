@@ -16,9 +16,9 @@
 // each block's stream starts at a byte boundary).
 //
 // Move-to-front encoding (Section 3.3): the paper's parallelism is over
-// the list -- the 256 list entries are spread over a warp's lanes (8 a
-// lane), found with one compare per lane and a ballot, and moved with lane
-// shifts. A block's bytes form one chain of list states, so blocks are cut
+// the list -- its 256 entries are spread over a warp's lanes, 8 a lane (kept
+// as every value's position, so a byte's position is one shuffle away and
+// the move is one byte-wise compare-and-add per lane). A block's bytes form one chain of list states, so blocks are cut
 // into chunks: a chunk's effect on the list is the chunk's distinct bytes
 // in order of last occurrence, followed by the old list without them. Pass
 // 1 finds that list for every chunk, pass 2 chains the chunks of every
@@ -506,9 +506,13 @@ __global__ void __launch_bounds__(256) k_mtf_chain(const uint32_t* __restrict__ 
     }
 }
 
-// Pass 3: one warp per chunk encodes it from its starting list. The chunk
-// sits in the warp's shared buffer and every byte is replaced there by its
-// list position; a byte already at the front costs one compare.
+// Pass 3: one warp per chunk encodes it from its starting list. The warp
+// keeps every byte value's position in the list instead of the list itself:
+// lane l holds the positions of values 8 l .. 8 l + 7, one byte each. Byte x
+// at position p: output p; every position below p moves up by one (a byte-
+// wise compare and add on the lane's two words) and x's becomes 0. A byte
+// already at the front costs one compare. The chunk sits in the warp's
+// shared buffer and every byte is replaced there by its position.
 constexpr int MTF_WARPS = 8;
 
 __global__ void __launch_bounds__(MTF_WARPS * 32) k_mtf_encode(const uint8_t* __restrict__ S,
@@ -516,13 +520,18 @@ __global__ void __launch_bounds__(MTF_WARPS * 32) k_mtf_encode(const uint8_t* __
                                                                const uint8_t* __restrict__ tlist,
                                                                uint8_t* __restrict__ out) {
     __shared__ __align__(16) uint8_t buf[MTF_WARPS][RTILE];
+    __shared__ __align__(16) uint8_t posb[MTF_WARPS][256];
     const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     uint8_t* bw = buf[wl];
     for (uint32_t t = blockIdx.x * MTF_WARPS + wl; t < ntiles; t += gridDim.x * MTF_WARPS) {
         const TileDesc td = tiles[t];
         for (uint32_t q = lane; q < td.len; q += 32) bw[q] = S[td.start + q];
-        uint64_t L = reinterpret_cast<const uint64_t*>(tlist + (size_t)t * 256)[lane];
-        uint32_t front = __shfl_sync(0xffffffffu, (uint32_t)L & 0xffu, 0);
+        const uint8_t* T = tlist + (size_t)t * 256;  // starting list: T[j] = value at position j
+        for (uint32_t j = lane; j < 256; j += 32) posb[wl][T[j]] = (uint8_t)j;
+        __syncwarp();
+        uint32_t lo = reinterpret_cast<const uint32_t*>(posb[wl])[2 * lane];      // positions of 8 l .. 8 l + 3
+        uint32_t hi = reinterpret_cast<const uint32_t*>(posb[wl])[2 * lane + 1];  // positions of 8 l + 4 .. 8 l + 7
+        uint32_t front = T[0];
         __syncwarp();
         for (uint32_t i = 0; i < td.len; ++i) {
             const uint32_t x = bw[i];
@@ -530,22 +539,17 @@ __global__ void __launch_bounds__(MTF_WARPS * 32) k_mtf_encode(const uint8_t* __
                 if (lane == 0) bw[i] = 0;
                 continue;
             }
-            const uint32_t x4 = x * 0x01010101u;
-            const uint32_t m0 = __vcmpeq4((uint32_t)L, x4), m1 = __vcmpeq4((uint32_t)(L >> 32), x4);
-            const uint32_t own = __ballot_sync(0xffffffffu, (m0 | m1) != 0u);
-            const uint32_t o = __ffs(own) - 1;
-            uint32_t k = m0 ? (__ffs(m0) - 1) >> 3 : 4u + ((__ffs(m1) - 1) >> 3);
-            k = __shfl_sync(0xffffffffu, k, o);
-            uint32_t carry = __shfl_up_sync(0xffffffffu, (uint32_t)(L >> 56), 1);
-            if (lane == 0) carry = x;
-            const uint64_t shifted = (L << 8) | carry;
-            if (lane < o) {
-                L = shifted;
-            } else if (lane == o) {
-                const uint64_t mask = k == 7u ? ~0ull : ((1ull << (8 * (k + 1))) - 1ull);
-                L = (shifted & mask) | (L & ~mask);
+            const uint32_t owner = x >> 3, k = x & 7u;
+            const uint32_t word = __shfl_sync(0xffffffffu, k < 4 ? lo : hi, owner);
+            const uint32_t p = (word >> (8 * (k & 3))) & 0xffu;
+            const uint32_t p4 = p * 0x01010101u;
+            lo += __vcmpltu4(lo, p4) & 0x01010101u;  // positions below p move up (they stay <= 255)
+            hi += __vcmpltu4(hi, p4) & 0x01010101u;
+            if (lane == owner) {
+                const uint32_t clear = ~(0xffu << (8 * (k & 3)));
+                if (k < 4) lo &= clear; else hi &= clear;
             }
-            if (lane == 0) bw[i] = (uint8_t)(o * 8 + k);
+            if (lane == 0) bw[i] = (uint8_t)p;
             front = x;
         }
         __syncwarp();
