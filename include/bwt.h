@@ -212,9 +212,11 @@ bwt_status bwt_plan_stats(const bwt_plan* plan, bwt_stats* out);
  * used by later calls; drops any cached graph. */
 bwt_status bwt_plan_set_radix(bwt_plan* plan, int radix_bits, int tile_keys);
 
-/* Digit width (8 or 11) of the segmented radix that sorts large groups in
- * the prefix-doubling rounds; 0 (the default) means 8. Drops any cached
- * graph. */
+/* Digit width (8, 10 or 11) of the segmented radix that sorts large groups
+ * in the prefix-doubling rounds; 0 (the default) picks by the batch's rank
+ * width: 10 when that takes fewer passes than 8 (ranks of 9-10, 17-20 or
+ * 25-30 bits; blocks of 65,537 to 1,048,576 bytes have 17 to 20), else 8.
+ * Drops any cached graph. Returns BWT_EINVAL for any other width. */
 bwt_status bwt_plan_set_round_radix(bwt_plan* plan, int radix_bits);
 
 /* Autotuner (no paper counterpart): times this batch for radix_bits in

@@ -146,7 +146,7 @@ extern "C" bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, con
     if (status == BWT_OK) {
         bwt_plan_set_radix(plan, best_b, best_t);
         float best_round = 1e30f;
-        for (int rbits : {8, 11}) {
+        for (int rbits : {8, 10, 11}) {
             if ((status = bwt_plan_set_round_radix(plan, rbits)) != BWT_OK) break;
             if ((status = bwt_forward_batch(plan, d_in, offsets, num_blocks, d_L, d_primary, stream)) != BWT_OK) break;
             float total = 0.f;

@@ -619,6 +619,9 @@ cudaError_t launch_large_prologue(const uint32_t* SA, const uint32_t* rank, cons
     if (radix_bits == 8) {
         k_large_prologue<8><<<grid, 256, smem, st>>>(SA, rank, blocks, tiles, num_tiles, depth, kbuf, vbuf, hist,
                                                      passes);
+    } else if (radix_bits == 10) {
+        k_large_prologue<10><<<grid, 256, smem, st>>>(SA, rank, blocks, tiles, num_tiles, depth, kbuf, vbuf, hist,
+                                                      passes);
     } else if (radix_bits == 11) {
         static bool attr = [] {
             cudaFuncSetAttribute((void*)k_large_prologue<11>, cudaFuncAttributeMaxDynamicSharedMemorySize,

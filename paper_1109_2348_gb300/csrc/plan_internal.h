@@ -29,7 +29,7 @@ struct bwt_plan {
     bwt_plan_desc desc{};
     std::string model_path;
     int rbits = 8, tile = 4096;
-    int round_bits = 0;  // digit width of the doubling rounds' radix (0 = by rank width)
+    int round_bits = 0;  // digit width of the doubling rounds' radix (0 = by rank width: 8 or 10)
     uint32_t spin_limit = 0;
     int withhold = 0;
 
@@ -115,6 +115,7 @@ void drop_graph(bwt_plan* p);
 bwt_status prepare_batch(bwt_plan* p, const uint64_t* offsets, uint32_t nb, cudaStream_t st);
 bwt_status upload_tables(bwt_plan* p, const uint64_t* off, uint32_t nb, cudaStream_t st);
 Bins bins_of(bwt_plan* p, int par);
+int round_radix_bits(const bwt_plan* p);
 bwt_status reset_ctrl(bwt_plan* p, cudaStream_t st);
 bwt_status enqueue_initial_sort(bwt_plan* p, const uint8_t* d_in, cudaStream_t st);
 bwt_status enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts, cudaStream_t st);

@@ -176,7 +176,7 @@ def test_autotuner_picks_a_valid_config_and_caches_it(tmp_path):
         assert len(open(cache).readlines()) == 1  # read back, no new sweep
 
 
-@pytest.mark.parametrize("round_bits", [8, 11])
+@pytest.mark.parametrize("round_bits", [8, 10, 11])
 def test_round_radix_widths(round_bits):
     import torch
     w = datagen.Workload("t", [datagen.RUNS16, datagen.PERIOD7, datagen.FIBONACCI, datagen.MUTATED_UNIT],
