@@ -377,9 +377,11 @@ __device__ __forceinline__ uint32_t smem_upper_bound(const T* a, uint32_t n, T x
 // and its last run may continue after it (it ends at carry_end). Writes
 // rank[rotation] = block-local start of the element's group and emits the
 // groups of size > 1 that start inside the tile. SA is the global SA, or with
-// SA_LOCAL the tile's own entries (SA[q] for tile element q). All threads of
-// the CTA call.
-template <typename KeyT, bool SA_LOCAL = false>
+// SA_LOCAL the tile's own entries (SA[q] for tile element q). UNR: unroll
+// factor of the loop over the tile (a full unroll inlines 16 copies of the
+// searches; a shared-memory SA needs no register array, so a partial unroll
+// keeps the code in the instruction cache). All threads of the CTA call.
+template <typename KeyT, bool SA_LOCAL = false, int UNR = 16>
 __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t tstart, uint32_t carry_start,
                                           uint32_t carry_end, const uint32_t* __restrict__ SA, BlockInfo bi,
                                           uint32_t blk, uint32_t* __restrict__ rank, const Bins& bins, bool emit_ok,
@@ -396,7 +398,8 @@ __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t
             sav[it] = q < len ? SA[tstart + q] : 0u;
         }
     }
-#pragma unroll
+    static_assert(SA_LOCAL || UNR == MAXIT, "a global SA is preloaded into a register array");
+#pragma unroll UNR
     for (int it = 0; it < MAXIT; ++it) {
         const uint32_t q = it * 256u + threadIdx.x;
         if (it * 256u >= len) break;  // CTA-uniform

@@ -251,23 +251,39 @@ __global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restri
         __syncthreads();
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
-        for (uint32_t q0 = 0; q0 < td.len; q0 += blockDim.x) {
-            const uint32_t q = q0 + threadIdx.x;
-            const bool valid = q < td.len;
-            uint32_t k2 = 0;
-            if (valid) {
-                const uint32_t k = td.start + q;
-                const uint32_t sa = SA[k];
-                uint32_t r = sa + h;
-                if (r >= bi.n) r -= bi.n;
-                k2 = r < bi.n ? rank[bi.off + r] : 0u;
-                kbuf[k] = k2;
-                vbuf[k] = sa;
+        // PI elements a thread per step: their SA loads, then their rank
+        // gathers, are all in flight at once
+        constexpr int PI = 4;
+        for (uint32_t q0 = 0; q0 < td.len; q0 += 256u * PI) {
+            uint32_t sa[PI], k2[PI];
+#pragma unroll
+            for (int j = 0; j < PI; ++j) {
+                const uint32_t q = q0 + j * 256u + threadIdx.x;
+                sa[j] = q < td.len ? SA[td.start + q] : 0u;
             }
-            for (int ps = 0; ps < passes; ++ps) {
-                const uint32_t d = valid ? ((k2 >> (ps * RBITS)) & (RADIX - 1)) : (uint32_t)RADIX;
-                const uint32_t peers = __match_any_sync(0xffffffffu, d);
-                if (valid && lane == __ffs(peers) - 1) atomicAdd(&sh[ps * RADIX + d], (uint32_t)__popc(peers));
+#pragma unroll
+            for (int j = 0; j < PI; ++j) {
+                const uint32_t q = q0 + j * 256u + threadIdx.x;
+                k2[j] = 0u;
+                if (q < td.len) {
+                    uint32_t r = sa[j] + h;
+                    if (r >= bi.n) r -= bi.n;
+                    k2[j] = r < bi.n ? rank[bi.off + r] : 0u;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < PI; ++j) {
+                const uint32_t q = q0 + j * 256u + threadIdx.x;
+                const bool valid = q < td.len;
+                if (valid) {
+                    kbuf[td.start + q] = k2[j];
+                    vbuf[td.start + q] = sa[j];
+                }
+                for (int ps = 0; ps < passes; ++ps) {
+                    const uint32_t d = valid ? ((k2[j] >> (ps * RBITS)) & (RADIX - 1)) : (uint32_t)RADIX;
+                    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                    if (valid && lane == __ffs(peers) - 1) atomicAdd(&sh[ps * RADIX + d], (uint32_t)__popc(peers));
+                }
             }
         }
         __syncthreads();
@@ -517,6 +533,7 @@ __global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict
                                                       const uint32_t* __restrict__ num_tiles, Bins next,
                                                       const uint32_t* __restrict__ depth, uint32_t* ctrl) {
     __shared__ uint32_t sk[4096];
+    __shared__ uint32_t ssa[4096];
     __shared__ uint32_t s_carry[2];
     __shared__ GroupDesc ebuf[8][NCLS * EMIT_BUF];
     if (ld_volatile(&ctrl[CTRL_ERR])) return;
@@ -531,12 +548,15 @@ __global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict
 #pragma unroll
         for (int it = 0; it < 16; ++it) {  // tiles hold at most 4096 keys
             const uint32_t q = it * 256u + threadIdx.x;
-            if (q < td.len) sk[q] = key2[td.start + q];
+            if (q < td.len) {
+                sk[q] = key2[td.start + q];
+                ssa[q] = SA[td.start + q];
+            }
         }
         if (threadIdx.x < 32) tile_carries<uint32_t>(key2, lo, hi, td.start, td.len, s_carry);
         __syncthreads();
-        name_tile<uint32_t>(sk, td.len, td.start, s_carry[0], s_carry[1], SA, bi, td.blk, rank, next,
-                            new_depth < bi.n, em, &ctrl[CTRL_ERR]);
+        name_tile<uint32_t, true, 2>(sk, td.len, td.start, s_carry[0], s_carry[1], ssa, bi, td.blk, rank, next,
+                                     new_depth < bi.n, em, &ctrl[CTRL_ERR]);
         __syncthreads();
     }
     em.finish(next, &ctrl[CTRL_ERR]);

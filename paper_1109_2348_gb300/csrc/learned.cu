@@ -353,42 +353,71 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
         for (int i = threadIdx.x; i < NBK; i += blockDim.x) st[i] = starts[(size_t)blk * NBK + i];
         if (threadIdx.x == 0) st[NBK] = bi.n;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t nch = 0, nemit = 0, first = 0, len = 0;
-            auto close = [&]() {
-                if (nch < MAXCH) {
-                    cb[nch] = st[first];
-                    chunks[nemit++] = GroupDesc{bi.off + st[first], len, blk, 0u};
-                }
-                ++nch;
-            };
-            for (uint32_t b = 0; b < (uint32_t)NBK; ++b) {
-                const uint32_t sz = st[b + 1] - st[b];
-                if (sz > CHUNK_CAP) {
-                    if (len > 0) close();
-                    cm[b] = (uint16_t)min(nch, MAXCH - 1);
-                    if (nch < MAXCH) cb[nch] = st[b];
+        if (threadIdx.x < 32) {
+            // Greedy packing by one warp, up to 32 buckets a step: the lanes
+            // take the next 32 bucket sizes, an inclusive scan over them
+            // (stopped at the first overflow bucket) shows how many still
+            // fit in the open chunk, and those join it at once.
+            const uint32_t lane = threadIdx.x;
+            uint32_t nch = 0, nemit = 0, len = 0, cstart = 0, b = 0;
+            bool open = false;  // a chunk is open (possibly holding only empty buckets)
+            auto close = [&]() {  // the open chunk, if it holds rotations, becomes chunk nch
+                if (len > 0) {
+                    if (lane == 0 && nch < MAXCH) {
+                        cb[nch] = cstart;
+                        chunks[nemit] = GroupDesc{bi.off + cstart, len, blk, 0u};
+                    }
+                    if (nch < MAXCH) ++nemit;
                     ++nch;
-                    const uint32_t slot = atomicAdd(&out.count[CLS_LARGE], 1u);
-                    if (slot < out.cap[CLS_LARGE]) out.list[CLS_LARGE][slot] = GroupDesc{bi.off + st[b], sz, blk, 0u};
-                    else atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
-                    first = b + 1;
-                    len = 0;
-                } else if (len + sz > CHUNK_CAP) {
-                    close();
-                    first = b;
-                    len = sz;
-                    cm[b] = (uint16_t)min(nch, MAXCH - 1);
-                } else {
-                    if (len == 0) first = b;
-                    len += sz;
-                    cm[b] = (uint16_t)min(nch, MAXCH - 1);
                 }
+                open = false;
+                len = 0;
+            };
+            while (b < (uint32_t)NBK) {
+                const uint32_t bb = b + lane;
+                const uint32_t sz = bb < (uint32_t)NBK ? st[bb + 1] - st[bb] : 0xffffffffu;  // past the end: a stop
+                const uint32_t bigm = __ballot_sync(0xffffffffu, sz > CHUNK_CAP);
+                if (bigm & 1u) {  // bucket b is an overflow bucket: a chunk of its own, sorted by the radix path
+                    close();
+                    if (lane == 0) {
+                        cm[b] = (uint16_t)min(nch, MAXCH - 1);
+                        if (nch < MAXCH) cb[nch] = st[b];
+                        const uint32_t slot = atomicAdd(&out.count[CLS_LARGE], 1u);
+                        if (slot < out.cap[CLS_LARGE]) out.list[CLS_LARGE][slot] = GroupDesc{bi.off + st[b], sz, blk, 0u};
+                        else atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
+                    }
+                    ++nch;
+                    ++b;
+                    continue;
+                }
+                const uint32_t fb = bigm ? (uint32_t)(__ffs(bigm) - 1) : 32u;  // first stop lane (>= 1)
+                uint32_t incl = lane < fb ? sz : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if ((int)lane >= o) incl += y;
+                }
+                const bool fit = lane < fb && len + incl <= CHUNK_CAP;
+                const uint32_t k = __popc(__ballot_sync(0xffffffffu, fit));  // fits are a prefix of the lanes
+                if (k > 0) {
+                    if (!open) {
+                        open = true;
+                        cstart = st[b];
+                    }
+                    if (lane < k) cm[b + lane] = (uint16_t)min(nch, MAXCH - 1);
+                    len += __shfl_sync(0xffffffffu, incl, k - 1);
+                    b += k;
+                }
+                // lane k stopped: an overflow bucket (handled next step) or a
+                // bucket that does not fit (close, it opens the next chunk)
+                if (k < 32 && b < (uint32_t)NBK && !((bigm >> k) & 1u)) close();
             }
-            if (len > 0) close();
-            if (nch > MAXCH) atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
-            s_n[0] = nemit;
-            s_n[1] = atomicAdd(&out.count[0], nemit);
+            close();
+            if (lane == 0) {
+                if (nch > MAXCH) atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
+                s_n[0] = nemit;
+                s_n[1] = atomicAdd(&out.count[0], nemit);
+            }
         }
         __syncthreads();
         for (int i = threadIdx.x; i < NBK; i += blockDim.x) ct.cmap[(size_t)blk * NBK + i] = cm[i];
