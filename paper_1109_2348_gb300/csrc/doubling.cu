@@ -119,7 +119,11 @@ __global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict
                                                       const TileDesc* __restrict__ tiles, uint32_t num_tiles,
                                                       const uint32_t* __restrict__ num_tiles_dev, bool seg_bounds,
                                                       uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl) {
-    __shared__ uint64_t sk[4096];
+    // the tile's keys and SA entries (dynamic: 48 KB; the naming loop reads
+    // SA from shared memory, so it needs no register array and unrolls by 2)
+    extern __shared__ __align__(16) unsigned char name_smem[];
+    uint64_t* sk = reinterpret_cast<uint64_t*>(name_smem);
+    uint32_t* ssa = reinterpret_cast<uint32_t*>(name_smem + 4096 * 8);
     __shared__ uint32_t s_carry[2];
     __shared__ GroupDesc ebuf[8][NCLS * EMIT_BUF];
     if (ld_volatile(&ctrl[CTRL_ERR])) return;  // an earlier stage failed: SA is not a permutation
@@ -134,12 +138,15 @@ __global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict
 #pragma unroll
         for (int it = 0; it < 16; ++it) {  // tiles hold at most 4096 keys
             const uint32_t q = it * 256u + threadIdx.x;
-            if (q < td.len) sk[q] = K[td.start + q];
+            if (q < td.len) {
+                sk[q] = K[td.start + q];
+                ssa[q] = SA[td.start + q];
+            }
         }
         if (threadIdx.x < 32) tile_carries<uint64_t>(K, lo, hi, td.start, td.len, s_carry);
         __syncthreads();
-        name_tile<uint64_t>(sk, td.len, td.start, s_carry[0], s_carry[1], SA, bi, td.blk, rank, bins, bi.n > 8u, em,
-                            &ctrl[CTRL_ERR]);
+        name_tile<uint64_t, true, 2>(sk, td.len, td.start, s_carry[0], s_carry[1], ssa, bi, td.blk, rank, bins,
+                                     bi.n > 8u, em, &ctrl[CTRL_ERR]);
         __syncthreads();
     }
     em.finish(bins, &ctrl[CTRL_ERR]);
@@ -424,20 +431,22 @@ __device__ __forceinline__ void coop_sync() {
 }
 
 // Sorts comp[0..P) (P a power of two) by bitonic merging; NT threads
-// cooperate (a warp or the CTA), t is the thread's index among them.
+// cooperate (a warp or the CTA), t is the thread's index among them. Each
+// step has P/2 compare-exchanges; thread t takes pairs t, t + NT, ..: pair
+// p is (i, i + j) with i = p with a zero bit inserted at j's position.
 template <int NT>
 __device__ __forceinline__ void coop_bitonic(uint64_t* comp, uint32_t P, uint32_t t) {
+    const uint32_t half = P >> 1;
     for (uint32_t kk = 2; kk <= P; kk <<= 1) {
         for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = t; i < P; i += NT) {
-                const uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t a = comp[i], b = comp[ixj];
-                    const bool up = (i & kk) == 0;
-                    if ((a > b) == up) {
-                        comp[i] = b;
-                        comp[ixj] = a;
-                    }
+            for (uint32_t pr = t; pr < half; pr += NT) {
+                const uint32_t i = ((pr & ~(j - 1)) << 1) | (pr & (j - 1));
+                const uint32_t ixj = i | j;
+                const uint64_t a = comp[i], b = comp[ixj];
+                const bool up = (i & kk) == 0;
+                if ((a > b) == up) {
+                    comp[i] = b;
+                    comp[ixj] = a;
                 }
             }
             coop_sync<NT>();
@@ -459,6 +468,43 @@ __device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDes
         comp[i] = i < m ? (((uint64_t)key2[gd.start + i] << 32) | SA[gd.start + i]) : ~0ull;
     coop_sync<NT>();
     coop_bitonic<NT>(comp, P, t);
+    if constexpr (NT == 32) {
+        // One warp: group heads by ballot, 32 elements a step. An element's
+        // group starts at the last head at or before it (carried across
+        // steps); each head closes the group before it, and the last group
+        // is closed after the loop.
+        const bool emit_ok = new_depth < bi.n;
+        uint32_t last_head = 0;
+        for (uint32_t i0 = 0; i0 < m; i0 += 32) {
+            const uint32_t i = i0 + t;
+            const bool valid = i < m;
+            const uint64_t c = valid ? comp[i] : 0ull;
+            const uint32_t key = (uint32_t)(c >> 32), sa = (uint32_t)c;
+            const bool head = valid && (i == 0 || (uint32_t)(comp[i - 1] >> 32) != key);
+            const uint32_t hm = __ballot_sync(0xffffffffu, head);
+            const uint32_t lt = (1u << t) - 1u;  // lanes below t
+            const uint32_t hle = hm & (lt | (1u << t));
+            const uint32_t s = hle ? i0 + 31u - __clz(hle) : last_head;
+            if (valid) {
+                SA[gd.start + i] = sa;
+                if (sa < bi.n) rank[bi.off + sa] = gd.start - bi.off + s;
+            }
+            bool want = false;
+            uint32_t ps = 0, len = 0;
+            if (head && i > 0) {
+                const uint32_t hlt = hm & lt;
+                ps = hlt ? i0 + 31u - __clz(hlt) : last_head;
+                len = i - ps;
+                want = len > 1 && emit_ok;
+            }
+            em.emit(next, want, gd.start + ps, len, gd.blk, err);
+            if (hm) last_head = i0 + 31u - __clz(hm);
+        }
+        const uint32_t len = m - last_head;
+        em.emit(next, t == 0 && len > 1 && emit_ok, gd.start + last_head, len, gd.blk, err);
+        __syncwarp();
+        return;
+    }
     for (uint32_t i0 = 0; i0 < m; i0 += NT) {
         const uint32_t i = i0 + t;
         const bool valid = i < m;
@@ -587,19 +633,30 @@ int grid_for(uint32_t units, uint32_t per_cta, int cap_per_sm) {
 
 }  // namespace
 
+constexpr size_t NAME_SMEM = 4096 * 8 + 4096 * 4;
+constexpr int NAME_CTAS_PER_SM = 3;  // 48 KB dynamic + 10 KB static shared memory each
+
+bool name_attr() {
+    static const bool ok = cudaFuncSetAttribute((void*)k_name_initial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)NAME_SMEM) == cudaSuccess;
+    return ok;
+}
+
 cudaError_t launch_name_initial(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks, const TileDesc* tiles,
                                 uint32_t num_tiles, uint32_t* rank, Bins bins, uint32_t* ctrl, cudaStream_t st) {
     if (!num_tiles) return cudaSuccess;
-    k_name_initial<<<grid_for(num_tiles, 1, 4), 256, 0, st>>>(K, SA, blocks, tiles, num_tiles, nullptr, false, rank,
-                                                              bins, ctrl);
+    if (!name_attr()) return cudaErrorInvalidValue;
+    k_name_initial<<<grid_for(num_tiles, 1, NAME_CTAS_PER_SM), 256, NAME_SMEM, st>>>(
+        K, SA, blocks, tiles, num_tiles, nullptr, false, rank, bins, ctrl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_name_tiles(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks, const TileDesc* tiles,
                               const uint32_t* num_tiles_dev, bool seg_bounds, uint32_t* rank, Bins bins,
                               uint32_t* ctrl, cudaStream_t st) {
-    k_name_initial<<<num_sms() * 4, 256, 0, st>>>(K, SA, blocks, tiles, 0u, num_tiles_dev, seg_bounds, rank, bins,
-                                                  ctrl);
+    if (!name_attr()) return cudaErrorInvalidValue;
+    k_name_initial<<<num_sms() * NAME_CTAS_PER_SM, 256, NAME_SMEM, st>>>(K, SA, blocks, tiles, 0u, num_tiles_dev,
+                                                                          seg_bounds, rank, bins, ctrl);
     return cudaGetLastError();
 }
 
