@@ -372,59 +372,89 @@ __device__ __forceinline__ uint32_t smem_upper_bound(const T* a, uint32_t n, T x
     return lo;
 }
 
-// Names every element of one sorted tile: the tile's keys sit in sk[0..len),
-// its first run may have begun before the tile (it begins at carry_start)
-// and its last run may continue after it (it ends at carry_end). Writes
-// rank[rotation] = block-local start of the element's group and emits the
-// groups of size > 1 that start inside the tile. SA is the global SA, or with
-// SA_LOCAL the tile's own entries (SA[q] for tile element q). UNR: unroll
-// factor of the loop over the tile (a full unroll inlines 16 copies of the
-// searches; a shared-memory SA needs no register array, so a partial unroll
-// keeps the code in the instruction cache). All threads of the CTA call.
-template <typename KeyT, bool SA_LOCAL = false, int UNR = 16>
+// Names every element of one sorted tile: the tile's keys sit in sk[0..len)
+// and its SA entries in sa_tile[0..len) (both in shared memory); its first
+// run may have begun before the tile (it begins at carry_start) and its last
+// run may continue after it (it ends at carry_end). Writes rank[rotation] =
+// block-local start of the element's group and emits the groups of size > 1
+// that start inside the tile.
+//
+// Each warp walks its own range of 512 elements, 32 a step: the heads (an
+// element whose key differs from its predecessor's, and element 0) come
+// from one ballot, an element's group starts at the last head at or before
+// it (carried across steps and, through shared memory, across warps), and
+// the lane at a head emits the group that ends there; the group of the
+// tile's last head is emitted after the walk. All 256 threads of the CTA
+// call (one barrier inside).
+template <typename KeyT>
 __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t tstart, uint32_t carry_start,
-                                          uint32_t carry_end, const uint32_t* __restrict__ SA, BlockInfo bi,
-                                          uint32_t blk, uint32_t* __restrict__ rank, const Bins& bins, bool emit_ok,
+                                          uint32_t carry_end, const uint32_t* sa_tile, BlockInfo bi, uint32_t blk,
+                                          uint32_t* __restrict__ rank, const Bins& bins, bool emit_ok,
                                           WarpEmitter& em, uint32_t* err) {
-    // 256 threads, len <= 4096: at most 16 elements a thread. A global SA's
-    // entries for the tile are read up front (independent loads, all in
-    // flight at once); a shared-memory SA is read in place.
-    constexpr int MAXIT = 16;
-    uint32_t sav[SA_LOCAL ? 1 : MAXIT];
-    if constexpr (!SA_LOCAL) {
-#pragma unroll
-        for (int it = 0; it < MAXIT; ++it) {
-            const uint32_t q = it * 256u + threadIdx.x;
-            sav[it] = q < len ? SA[tstart + q] : 0u;
+    constexpr uint32_t SPAN = 512, NONE = 0xffffffffu, NW = 8;
+    __shared__ uint32_t s_heads[2 * NW];  // per warp: first head, last head of its range (NONE if none)
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    const uint32_t r0 = warp * SPAN, r1 = min(len, r0 + SPAN);
+    auto is_head = [&](uint32_t q) { return q < r1 && (q == 0 || sk[q - 1] != sk[q]); };
+    // 1. first and last head of the warp's range
+    uint32_t fh = NONE, lh = NONE;
+    for (uint32_t b = r0; b < r1; b += 32) {
+        const uint32_t m = __ballot_sync(0xffffffffu, is_head(b + lane));
+        if (m) {
+            fh = b + __ffs(m) - 1;
+            break;
         }
     }
-    static_assert(SA_LOCAL || UNR == MAXIT, "a global SA is preloaded into a register array");
-#pragma unroll UNR
-    for (int it = 0; it < MAXIT; ++it) {
-        const uint32_t q = it * 256u + threadIdx.x;
-        if (it * 256u >= len) break;  // CTA-uniform
-        const bool valid = q < len;
-        bool want = false;
-        uint32_t glen = 0;
-        const uint32_t k = tstart + q;
-        if (valid) {
-            const KeyT key = sk[q];
-            const bool differs_prev = q > 0 && sk[q - 1] != key;
-            const uint32_t lb = differs_prev ? q : (q == 0 ? 0u : smem_lower_bound<KeyT>(sk, q, key));
-            const uint32_t gs = lb == 0 ? carry_start : tstart + lb;
-            uint32_t sa;
-            if constexpr (SA_LOCAL) sa = SA[q];
-            else sa = sav[it];
-            if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
-            if (gs == k && emit_ok) {
-                uint32_t ub;
-                if (q + 1 < len && sk[q + 1] != key) ub = q + 1;
-                else ub = smem_upper_bound<KeyT>(sk, len, key);
-                glen = (ub == len ? carry_end : tstart + ub) - k;
-                want = glen > 1;
+    if (fh != NONE) {
+        for (uint32_t b = r0 + ((r1 - 1 - r0) & ~31u);; b -= 32) {
+            const uint32_t m = __ballot_sync(0xffffffffu, is_head(b + lane));
+            if (m) {
+                lh = b + 31 - __clz(m);
+                break;
             }
+            if (b <= fh) break;  // unreachable: fh itself is a head
         }
-        em.emit(bins, want, k, glen, blk, err);
+    }
+    if (lane == 0) {
+        s_heads[warp] = fh;
+        s_heads[NW + warp] = lh;
+    }
+    __syncthreads();
+    // 2. the last head before the range and the first head after it
+    uint32_t last = NONE, next = NONE;
+    for (uint32_t w = 0; w < warp; ++w)
+        if (s_heads[NW + w] != NONE) last = s_heads[NW + w];
+    for (uint32_t w = NW - 1; w > warp; --w)
+        if (s_heads[w] != NONE) next = s_heads[w];
+    // 3. rank every element; each head closes the group before it
+    for (uint32_t b = r0; b < r1; b += 32) {
+        const uint32_t q = b + lane;
+        const bool valid = q < r1;
+        const bool h = is_head(q);
+        const uint32_t m = __ballot_sync(0xffffffffu, h);
+        const uint32_t hle = m & (lt | (1u << lane));
+        const uint32_t sq = hle ? b + 31 - __clz(hle) : last;  // start of q's group (tile-local)
+        if (valid) {
+            const uint32_t gs = sq == 0 ? carry_start : tstart + sq;
+            const uint32_t sa = sa_tile[q];
+            if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
+        }
+        bool want = false;
+        uint32_t ps = 0;
+        if (h && q > 0) {
+            const uint32_t hlt = m & lt;
+            ps = hlt ? b + 31 - __clz(hlt) : last;  // the closed group is [ps, q)
+            want = emit_ok && q - ps > 1 && (ps > 0 || carry_start == tstart);
+        }
+        em.emit(bins, want, tstart + ps, q - ps, blk, err);
+        if (m) last = b + 31 - __clz(m);
+    }
+    // 4. the tile's last group, if its head is in this range
+    if (r0 < r1 && next == NONE && lh != NONE) {
+        const uint32_t glen = carry_end - (tstart + lh);
+        const bool want = lane == 0 && emit_ok && glen > 1 && (lh > 0 || carry_start == tstart);
+        em.emit(bins, want, tstart + lh, glen, blk, err);
     }
 }
 

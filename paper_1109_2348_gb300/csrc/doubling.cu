@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict
         }
         if (threadIdx.x < 32) tile_carries<uint64_t>(K, lo, hi, td.start, td.len, s_carry);
         __syncthreads();
-        name_tile<uint64_t, true, 2>(sk, td.len, td.start, s_carry[0], s_carry[1], ssa, bi, td.blk, rank, bins,
+        name_tile<uint64_t>(sk, td.len, td.start, s_carry[0], s_carry[1], ssa, bi, td.blk, rank, bins,
                                      bi.n > 8u, em, &ctrl[CTRL_ERR]);
         __syncthreads();
     }
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict
         }
         if (threadIdx.x < 32) tile_carries<uint32_t>(key2, lo, hi, td.start, td.len, s_carry);
         __syncthreads();
-        name_tile<uint32_t, true, 2>(sk, td.len, td.start, s_carry[0], s_carry[1], ssa, bi, td.blk, rank, next,
+        name_tile<uint32_t>(sk, td.len, td.start, s_carry[0], s_carry[1], ssa, bi, td.blk, rank, next,
                                      new_depth < bi.n, em, &ctrl[CTRL_ERR]);
         __syncthreads();
     }

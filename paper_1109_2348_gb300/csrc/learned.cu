@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(MS_NT, 4) k_chunk_sort_name(const uint64_t* __
         __syncthreads();
         cta_merge_sort(sK, sI);
         for (uint32_t i = threadIdx.x; i < len; i += MS_NT) SA[gd.start + i] = sI[i];
-        name_tile<uint64_t, true, 2>(sK, len, gd.start, gd.start, gd.start + len, sI, bi, gd.blk, rank, bins, bi.n > 8u,
+        name_tile<uint64_t>(sK, len, gd.start, gd.start, gd.start + len, sI, bi, gd.blk, rank, bins, bi.n > 8u,
                                      em, &ctrl[CTRL_ERR]);
         __syncthreads();
     }
