@@ -207,11 +207,10 @@ def timed_cpu_baseline(w, cores: int, target_s: float = 12.0):
                       f"{dt * repeats:.1f} s"}
 
 
-# DRAM bytes (read + write) per key of one u64 onesweep pass as ncu counted them
-# for the current kernel on the full mixed3-64x900000 pass
-# (profiles/launches_mixed3-64x900000_graph.md); None
-# when the kernel has changed since.
-ONESWEEP_DRAM_BYTES_PER_KEY = 23.48
+# DRAM bytes (read + write) per key of one u64 onesweep pass as ncu counted
+# them (1-pass metrics) for the current kernel on one full-size pass of the
+# mixed3-64x900000 workload; None when the kernel has changed since.
+ONESWEEP_DRAM_BYTES_PER_KEY = 23.34
 
 
 def add_first_sort(acc, st, n):

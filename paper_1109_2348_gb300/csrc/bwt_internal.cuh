@@ -377,25 +377,31 @@ __device__ __forceinline__ uint32_t smem_upper_bound(const T* a, uint32_t n, T x
 // run may have begun before the tile (it begins at carry_start) and its last
 // run may continue after it (it ends at carry_end). Writes rank[rotation] =
 // block-local start of the element's group and emits the groups of size > 1
-// that start inside the tile.
+// that start inside the tile. old_start: the global start of the group the
+// tile was sorted from, whose members already hold it as their rank (their
+// rank is written only where it changes), or NO_OLD_START for a first naming.
 //
-// Each warp walks its own range of 512 elements, 32 a step: the heads (an
+// Each warp walks its own range (an eighth of the tile, rounded up to whole
+// steps: at most 512 elements), 32 a step: the heads (an
 // element whose key differs from its predecessor's, and element 0) come
 // from one ballot, an element's group starts at the last head at or before
 // it (carried across steps and, through shared memory, across warps), and
 // the lane at a head emits the group that ends there; the group of the
 // tile's last head is emitted after the walk. All 256 threads of the CTA
 // call (one barrier inside).
+constexpr uint32_t NO_OLD_START = 0xffffffffu;
+
 template <typename KeyT>
 __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t tstart, uint32_t carry_start,
                                           uint32_t carry_end, const uint32_t* sa_tile, BlockInfo bi, uint32_t blk,
                                           uint32_t* __restrict__ rank, const Bins& bins, bool emit_ok,
-                                          WarpEmitter& em, uint32_t* err) {
-    constexpr uint32_t SPAN = 512, NONE = 0xffffffffu, NW = 8;
+                                          uint32_t old_start, WarpEmitter& em, uint32_t* err) {
+    constexpr uint32_t NONE = 0xffffffffu, NW = 8;
     __shared__ uint32_t s_heads[2 * NW];  // per warp: first head, last head of its range (NONE if none)
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();
-    const uint32_t r0 = warp * SPAN, r1 = min(len, r0 + SPAN);
+    const uint32_t span = ((len + NW * 32 - 1) / (NW * 32)) * 32;
+    const uint32_t r0 = min(len, warp * span), r1 = min(len, r0 + span);
     auto is_head = [&](uint32_t q) { return q < r1 && (q == 0 || sk[q - 1] != sk[q]); };
     // 1. first and last head of the warp's range
     uint32_t fh = NONE, lh = NONE;
@@ -438,7 +444,7 @@ __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t
         if (valid) {
             const uint32_t gs = sq == 0 ? carry_start : tstart + sq;
             const uint32_t sa = sa_tile[q];
-            if (sa < bi.n) rank[bi.off + sa] = gs - bi.off;
+            if (sa < bi.n && gs != old_start) rank[bi.off + sa] = gs - bi.off;
         }
         bool want = false;
         uint32_t ps = 0;

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict
         if (threadIdx.x < 32) tile_carries<uint64_t>(K, lo, hi, td.start, td.len, s_carry);
         __syncthreads();
         name_tile<uint64_t>(sk, td.len, td.start, s_carry[0], s_carry[1], ssa, bi, td.blk, rank, bins,
-                                     bi.n > 8u, em, &ctrl[CTRL_ERR]);
+                            bi.n > 8u, NO_OLD_START, em, &ctrl[CTRL_ERR]);
         __syncthreads();
     }
     em.finish(bins, &ctrl[CTRL_ERR]);
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(256) k_sort_micro(uint32_t* __restrict__ SA, c
             for (uint32_t e = 0; e < gd.len && e < 4; ++e) {
                 const uint32_t sa = (uint32_t)c[e];
                 SA[gd.start + e] = sa;
-                if (sa < bi.n) rank[bi.off + sa] = gd.start - bi.off + gstart[e];
+                if (sa < bi.n && gstart[e] != 0) rank[bi.off + sa] = gd.start - bi.off + gstart[e];
                 if (gstart[e] == e) {
                     uint32_t f = e + 1;
                     while (f < gd.len && f < 4 && gstart[f] == e) ++f;
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(256) k_sort_tiny(uint32_t* __restrict__ SA, co
         const uint32_t end = above ? (uint32_t)(__ffs(above) - 1) : gd.len;
         if (valid) {
             SA[k] = sa;
-            if (sa < bi.n) rank[bi.off + sa] = gd.start - bi.off + start_lane;
+            if (sa < bi.n && start_lane != 0) rank[bi.off + sa] = gd.start - bi.off + start_lane;
         }
         const uint32_t len = end - lane;
         const bool want = head && len > 1 && new_depth < bi.n;
@@ -487,7 +487,7 @@ __device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDes
             const uint32_t s = hle ? i0 + 31u - __clz(hle) : last_head;
             if (valid) {
                 SA[gd.start + i] = sa;
-                if (sa < bi.n) rank[bi.off + sa] = gd.start - bi.off + s;
+                if (sa < bi.n && s != 0) rank[bi.off + sa] = gd.start - bi.off + s;
             }
             bool want = false;
             uint32_t ps = 0, len = 0;
@@ -516,7 +516,7 @@ __device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDes
             const bool head = (i == 0) || (uint32_t)(comp[i - 1] >> 32) != key;
             const uint32_t s = head ? i : smem_lower_bound<uint64_t>(comp, m, (uint64_t)key << 32);
             SA[gd.start + i] = sa;
-            if (sa < bi.n) rank[bi.off + sa] = gd.start - bi.off + s;
+            if (sa < bi.n && s != 0) rank[bi.off + sa] = gd.start - bi.off + s;
             if (head) {
                 len = smem_lower_bound<uint64_t>(comp, m, (uint64_t)(key + 1) << 32) - i;
                 want = len > 1 && new_depth < bi.n;
@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict
         if (threadIdx.x < 32) tile_carries<uint32_t>(key2, lo, hi, td.start, td.len, s_carry);
         __syncthreads();
         name_tile<uint32_t>(sk, td.len, td.start, s_carry[0], s_carry[1], ssa, bi, td.blk, rank, next,
-                                     new_depth < bi.n, em, &ctrl[CTRL_ERR]);
+                            new_depth < bi.n, td.segStart, em, &ctrl[CTRL_ERR]);
         __syncthreads();
     }
     em.finish(next, &ctrl[CTRL_ERR]);
@@ -615,12 +615,30 @@ __global__ void __launch_bounds__(256) k_gather_L(const uint8_t* __restrict__ S,
     for (uint32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
-        for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) {
-            const uint32_t k = td.start + q;
-            const uint32_t sa = SA[k];
-            const uint32_t src = sa == 0 || sa > bi.n ? bi.n - 1 : sa - 1;
-            L[k] = S[bi.off + src];
-            if (sa == 0) primary[td.blk] = (int32_t)(k - bi.off);
+        // four elements a thread per step: their SA loads, then their byte
+        // gathers, are all in flight at once
+        constexpr int PI = 4;
+        for (uint32_t q0 = 0; q0 < td.len; q0 += 256u * PI) {
+            uint32_t sa[PI];
+            uint8_t c[PI];
+#pragma unroll
+            for (int j = 0; j < PI; ++j) {
+                const uint32_t q = q0 + j * 256u + threadIdx.x;
+                sa[j] = q < td.len ? SA[td.start + q] : 1u;
+            }
+#pragma unroll
+            for (int j = 0; j < PI; ++j) {
+                const uint32_t src = sa[j] == 0 || sa[j] > bi.n ? bi.n - 1 : sa[j] - 1;
+                c[j] = S[bi.off + src];
+            }
+#pragma unroll
+            for (int j = 0; j < PI; ++j) {
+                const uint32_t q = q0 + j * 256u + threadIdx.x;
+                if (q < td.len) {
+                    L[td.start + q] = c[j];
+                    if (sa[j] == 0) primary[td.blk] = (int32_t)q + (int32_t)(td.start - bi.off);
+                }
+            }
         }
     }
 }

@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(MS_NT, 4) k_chunk_sort_name(const uint64_t* __
         cta_merge_sort(sK, sI);
         for (uint32_t i = threadIdx.x; i < len; i += MS_NT) SA[gd.start + i] = sI[i];
         name_tile<uint64_t>(sK, len, gd.start, gd.start, gd.start + len, sI, bi, gd.blk, rank, bins, bi.n > 8u,
-                                     em, &ctrl[CTRL_ERR]);
+                            NO_OLD_START, em, &ctrl[CTRL_ERR]);
         __syncthreads();
     }
     em.finish(bins, &ctrl[CTRL_ERR]);
