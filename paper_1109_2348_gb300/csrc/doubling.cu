@@ -113,24 +113,35 @@ __device__ __forceinline__ void tile_carries(const KeyT* __restrict__ K, uint32_
 // seg_bounds: every tile's segment [segStart, segStart + pad0) is a whole
 // range of groups (its first element starts a group, its last ends one), so
 // the carries never look past it; else the carries search the whole block.
-// num_tiles_dev, when non-null, holds the tile count on the device.
+// num_tiles_dev, when non-null, holds the tile count on the device. Tiles
+// are taken in order from an atomic counter (zeroed before the launch), so
+// the tiles in flight stay within a few blocks: the rank writes of a block
+// land while its rank range is still in L2 (a fixed grid stride lets the
+// CTAs drift apart over many tiles; at 1,200 blocks that doubled the DRAM
+// traffic).
 __global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict__ K, const uint32_t* __restrict__ SA,
                                                       const BlockInfo* __restrict__ blocks,
                                                       const TileDesc* __restrict__ tiles, uint32_t num_tiles,
                                                       const uint32_t* __restrict__ num_tiles_dev, bool seg_bounds,
-                                                      uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl) {
+                                                      uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl,
+                                                      uint32_t* __restrict__ tile_counter) {
     // the tile's keys and SA entries (dynamic: 48 KB; the naming loop reads
     // SA from shared memory, so it needs no register array and unrolls by 2)
     extern __shared__ __align__(16) unsigned char name_smem[];
     uint64_t* sk = reinterpret_cast<uint64_t*>(name_smem);
     uint32_t* ssa = reinterpret_cast<uint32_t*>(name_smem + 4096 * 8);
     __shared__ uint32_t s_carry[2];
+    __shared__ uint32_t s_t;
     __shared__ GroupDesc ebuf[8][NCLS * EMIT_BUF];
     if (ld_volatile(&ctrl[CTRL_ERR])) return;  // an earlier stage failed: SA is not a permutation
     WarpEmitter em;
     em.init(ebuf[threadIdx.x >> 5]);
     if (num_tiles_dev) num_tiles = *num_tiles_dev;
-    for (uint32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_t = atomicAdd(tile_counter, 1u);
+        __syncthreads();
+        const uint32_t t = s_t;
+        if (t >= num_tiles) break;
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
         const uint32_t lo = seg_bounds ? td.segStart : bi.off;
@@ -608,11 +619,19 @@ __global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict
     em.finish(next, &ctrl[CTRL_ERR]);
 }
 
+// Tiles in order from an atomic counter (zeroed before the launch): the
+// blocks whose bytes are gathered stay few, so their S stays in L2.
 __global__ void __launch_bounds__(256) k_gather_L(const uint8_t* __restrict__ S, const uint32_t* __restrict__ SA,
                                                   const BlockInfo* __restrict__ blocks,
                                                   const TileDesc* __restrict__ tiles, uint32_t num_tiles,
-                                                  uint8_t* __restrict__ L, int32_t* __restrict__ primary) {
-    for (uint32_t t = blockIdx.x; t < num_tiles; t += gridDim.x) {
+                                                  uint8_t* __restrict__ L, int32_t* __restrict__ primary,
+                                                  uint32_t* __restrict__ tile_counter) {
+    __shared__ uint32_t s_t;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = atomicAdd(tile_counter, 1u);
+        __syncthreads();
+        const uint32_t t = s_t;
+        if (t >= num_tiles) break;
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
         // four elements a thread per step: their SA loads, then their byte
@@ -640,6 +659,7 @@ __global__ void __launch_bounds__(256) k_gather_L(const uint8_t* __restrict__ S,
                 }
             }
         }
+        __syncthreads();  // every thread has read s_t before it is replaced
     }
 }
 
@@ -660,12 +680,18 @@ bool name_attr() {
     return ok;
 }
 
+// Tile counters of the naming and the L gather (control words no radix pass
+// uses); each launch zeroes its counter first.
+constexpr int NAME_CTR = CTRL_TILE_CTR + 56, GATHER_L_CTR = CTRL_TILE_CTR + 57;
+
 cudaError_t launch_name_initial(const uint64_t* K, const uint32_t* SA, const BlockInfo* blocks, const TileDesc* tiles,
                                 uint32_t num_tiles, uint32_t* rank, Bins bins, uint32_t* ctrl, cudaStream_t st) {
     if (!num_tiles) return cudaSuccess;
     if (!name_attr()) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(ctrl + NAME_CTR, 0, 4, st);
+    if (e != cudaSuccess) return e;
     k_name_initial<<<grid_for(num_tiles, 1, NAME_CTAS_PER_SM), 256, NAME_SMEM, st>>>(
-        K, SA, blocks, tiles, num_tiles, nullptr, false, rank, bins, ctrl);
+        K, SA, blocks, tiles, num_tiles, nullptr, false, rank, bins, ctrl, ctrl + NAME_CTR);
     return cudaGetLastError();
 }
 
@@ -673,8 +699,11 @@ cudaError_t launch_name_tiles(const uint64_t* K, const uint32_t* SA, const Block
                               const uint32_t* num_tiles_dev, bool seg_bounds, uint32_t* rank, Bins bins,
                               uint32_t* ctrl, cudaStream_t st) {
     if (!name_attr()) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(ctrl + NAME_CTR, 0, 4, st);
+    if (e != cudaSuccess) return e;
     k_name_initial<<<num_sms() * NAME_CTAS_PER_SM, 256, NAME_SMEM, st>>>(K, SA, blocks, tiles, 0u, num_tiles_dev,
-                                                                          seg_bounds, rank, bins, ctrl);
+                                                                          seg_bounds, rank, bins, ctrl,
+                                                                          ctrl + NAME_CTR);
     return cudaGetLastError();
 }
 
@@ -770,9 +799,12 @@ cudaError_t launch_rename_large(const uint32_t* SA, const uint32_t* key2, uint32
 }
 
 cudaError_t launch_gather_L(const uint8_t* S, const uint32_t* SA, const BlockInfo* blocks, const TileDesc* tiles,
-                            uint32_t num_tiles, uint8_t* L, int32_t* primary, cudaStream_t st) {
+                            uint32_t num_tiles, uint8_t* L, int32_t* primary, uint32_t* ctrl, cudaStream_t st) {
     if (!num_tiles) return cudaSuccess;
-    k_gather_L<<<grid_for(num_tiles, 1, 16), 256, 0, st>>>(S, SA, blocks, tiles, num_tiles, L, primary);
+    cudaError_t e = cudaMemsetAsync(ctrl + GATHER_L_CTR, 0, 4, st);
+    if (e != cudaSuccess) return e;
+    k_gather_L<<<grid_for(num_tiles, 1, 16), 256, 0, st>>>(S, SA, blocks, tiles, num_tiles, L, primary,
+                                                           ctrl + GATHER_L_CTR);
     return cudaGetLastError();
 }
 

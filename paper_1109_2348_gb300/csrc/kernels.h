@@ -117,8 +117,9 @@ cudaError_t launch_set_cond_initial(const uint32_t* ctrl, uint32_t max_n, cudaGr
                                     cudaStream_t st);
 
 // L[k] = S[(SA[k] + n - 1) mod n]; primary[b] = the k with SA[k] = 0.
+// ctrl: its tile-counter word for the gather is zeroed and used.
 cudaError_t launch_gather_L(const uint8_t* S, const uint32_t* SA, const BlockInfo* blocks, const TileDesc* tiles,
-                            uint32_t num_tiles, uint8_t* L, int32_t* primary, cudaStream_t st);
+                            uint32_t num_tiles, uint8_t* L, int32_t* primary, uint32_t* ctrl, cudaStream_t st);
 
 int num_sms();
 

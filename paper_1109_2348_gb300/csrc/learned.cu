@@ -635,16 +635,25 @@ constexpr size_t CHUNK_SORT_SMEM = (size_t)CHUNK_CAP * 12;
 __global__ void __launch_bounds__(MS_NT, 4) k_chunk_sort_name(const uint64_t* __restrict__ K,
                                                           uint32_t* __restrict__ SA,
                                                           const BlockInfo* __restrict__ blocks, Bins chunks,
-                                                          uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl) {
+                                                          uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl,
+                                                          uint32_t* __restrict__ chunk_counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* sK = reinterpret_cast<uint64_t*>(smem);
     uint32_t* sI = reinterpret_cast<uint32_t*>(smem + (size_t)CHUNK_CAP * 8);
     __shared__ GroupDesc ebuf[MS_NT / 32][NCLS * EMIT_BUF];
+    __shared__ uint32_t s_c;
     if (ld_volatile(&ctrl[CTRL_ERR])) return;  // an earlier stage failed: the chunks are not permutations
     WarpEmitter em;
     em.init(ebuf[threadIdx.x >> 5]);
     const uint32_t count = bin_count(chunks, 0);
-    for (uint32_t c = blockIdx.x; c < count; c += gridDim.x) {
+    // chunks in list order from an atomic counter (zeroed before the launch):
+    // the chunks in flight stay within a few blocks, whose rank ranges stay
+    // in L2 while their scattered rank writes land
+    for (;;) {
+        if (threadIdx.x == 0) s_c = atomicAdd(chunk_counter, 1u);
+        __syncthreads();
+        const uint32_t c = s_c;
+        if (c >= count) break;
         const GroupDesc gd = chunks.list[0][c];
         const BlockInfo bi = blocks[gd.blk];
         const uint32_t len = min(gd.len, CHUNK_CAP);
@@ -928,8 +937,11 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     }
 
     // 4c. bucketed blocks: chunk sorts with naming, then the overflow buckets
+    uint32_t* chunk_counter = ctrl + CTRL_TILE_CTR + 58;  // a control word no radix pass uses
+    CKL(cudaMemsetAsync(chunk_counter, 0, 4, st));
     k_chunk_sort_name<<<sms * p->chunk_sort_ctas, MS_NT, CHUNK_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks,
-                                                                                  aux, p->rank, bins_of(p, 0), ctrl);
+                                                                                  aux, p->rank, bins_of(p, 0), ctrl,
+                                                                                  chunk_counter);
     CKL(cudaGetLastError());
     p->stats.kernel_launches++;
 
@@ -1010,7 +1022,7 @@ bwt_status bwt::run_learned(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int3
     if ((s = reset_ctrl(p, st)) != BWT_OK) return s;
     if ((s = enqueue_learned(p, d_in, st)) != BWT_OK) return s;
     if ((s = run_doubling_host_loop(p, st)) != BWT_OK) return s;
-    CKL(launch_gather_L(d_in, p->sa, p->blocks, p->tiles0, p->ntiles0, d_L, d_primary, st));
+    CKL(launch_gather_L(d_in, p->sa, p->blocks, p->tiles0, p->ntiles0, d_L, d_primary, p->ctrl, st));
     p->stats.kernel_launches++;
     return BWT_OK;
 }

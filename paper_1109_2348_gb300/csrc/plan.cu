@@ -564,7 +564,7 @@ bwt_status bwt::run_plain_host_loop(bwt_plan* p, const uint8_t* d_in, uint8_t* d
     if ((s = reset_ctrl(p, st)) != BWT_OK) return s;
     if ((s = enqueue_initial_sort(p, d_in, st)) != BWT_OK) return s;
     if ((s = run_doubling_host_loop(p, st)) != BWT_OK) return s;
-    CK(launch_gather_L(d_in, p->sa, p->blocks, p->tiles0, p->ntiles0, d_L, d_primary, st));
+    CK(launch_gather_L(d_in, p->sa, p->blocks, p->tiles0, p->ntiles0, d_L, d_primary, p->ctrl, st));
     p->stats.kernel_launches++;
     return BWT_OK;
 }
