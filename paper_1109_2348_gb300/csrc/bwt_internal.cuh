@@ -286,6 +286,7 @@ struct WarpEmitter {
 
     __device__ __forceinline__ void emit(const Bins& bins, bool want, uint32_t start, uint32_t len, uint32_t blk,
                                          uint32_t* err) {
+        if (__ballot_sync(0xffffffffu, want) == 0u) return;  // the common case: nothing to emit
         const int cls = want ? size_class(len) : -1;
         if (want) active += len;
         const uint32_t lt = lanemask_lt();

@@ -475,8 +475,22 @@ __device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDes
     const uint32_t m = gd.len;
     uint32_t P = 32;
     while (P < m) P <<= 1;
-    for (uint32_t i = t; i < P; i += NT)
-        comp[i] = i < m ? (((uint64_t)key2[gd.start + i] << 32) | SA[gd.start + i]) : ~0ull;
+    static_assert((NT == 32 ? SMALL_MAX : MED_MAX) <= 8 * NT, "a group fits 8 elements a thread");
+    {
+        // up to 8 elements a thread (P <= 8 NT): all loads in flight before any store
+        uint32_t lk[8], ls[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t i = t + j * NT;
+            lk[j] = i < m ? key2[gd.start + i] : 0u;
+            ls[j] = i < m ? SA[gd.start + i] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t i = t + j * NT;
+            if (i < P) comp[i] = i < m ? (((uint64_t)lk[j] << 32) | ls[j]) : ~0ull;
+        }
+    }
     coop_sync<NT>();
     coop_bitonic<NT>(comp, P, t);
     if constexpr (NT == 32) {

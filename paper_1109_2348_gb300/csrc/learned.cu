@@ -551,7 +551,9 @@ __device__ __forceinline__ bool ki_less(uint64_t ak, uint32_t ai, uint64_t bk, u
 // transposition), then log2(MS_NT) rounds merge pairs of sorted runs, each
 // thread producing MS_IT outputs from its merge-path split (binary search
 // on its output diagonal, then a sequential merge). All threads call; the
-// arrays hold CHUNK_CAP entries (pad with (~0, ~0), above every real pair).
+// arrays hold CHUNK_CAP distinct entries (pad with (~0, 0xffff0000 + slot),
+// above every real pair, whose indices are below 2^30; (~0, ~0) stays free
+// as the merge's end-of-run sentinel).
 __device__ __forceinline__ void cta_merge_sort(uint64_t* sK, uint32_t* sI) {
     const uint32_t t = threadIdx.x;
     uint64_t k[MS_IT];
@@ -595,26 +597,24 @@ __device__ __forceinline__ void cta_merge_sort(uint64_t* sK, uint32_t* sI) {
             const bool a_first = a != b ? a < b : AI[mid] <= BI[diag - 1 - mid];
             if (a_first) lo = mid + 1; else hi = mid;
         }
+        // an exhausted run reads as (~0, ~0), above every element (padding
+        // carries indices below ~0), so the choice needs no bounds test
         uint32_t ia = lo, ib = diag - lo;
-        uint64_t ka = ia < w ? AK[ia] : 0ull, kb = ib < w ? BK[ib] : 0ull;
-        uint32_t va = ia < w ? AI[ia] : 0u, vb = ib < w ? BI[ib] : 0u;
+        uint64_t ka = ia < w ? AK[ia] : ~0ull, kb = ib < w ? BK[ib] : ~0ull;
+        uint32_t va = ia < w ? AI[ia] : ~0u, vb = ib < w ? BI[ib] : ~0u;
 #pragma unroll
         for (int j = 0; j < MS_IT; ++j) {
-            const bool take_a = ib >= w || (ia < w && !ki_less(kb, vb, ka, va));
-            k[j] = take_a ? ka : kb;
-            v[j] = take_a ? va : vb;
-            if (take_a) {
-                ++ia;
-                if (ia < w) {
-                    ka = AK[ia];
-                    va = AI[ia];
-                }
-            } else {
+            const bool take_b = ki_less(kb, vb, ka, va);  // elements are distinct; a tie cannot occur
+            k[j] = take_b ? kb : ka;
+            v[j] = take_b ? vb : va;
+            if (take_b) {
                 ++ib;
-                if (ib < w) {
-                    kb = BK[ib];
-                    vb = BI[ib];
-                }
+                kb = ib < w ? BK[ib] : ~0ull;
+                vb = ib < w ? BI[ib] : ~0u;
+            } else {
+                ++ia;
+                ka = ia < w ? AK[ia] : ~0ull;
+                va = ia < w ? AI[ia] : ~0u;
             }
         }
         __syncthreads();
@@ -657,10 +657,13 @@ __global__ void __launch_bounds__(MS_NT, 4) k_chunk_sort_name(const uint64_t* __
         const GroupDesc gd = chunks.list[0][c];
         const BlockInfo bi = blocks[gd.blk];
         const uint32_t len = min(gd.len, CHUNK_CAP);
-        for (uint32_t i = threadIdx.x; i < CHUNK_CAP; i += MS_NT) {
-            const bool in = i < len;
-            sK[i] = in ? K[gd.start + i] : ~0ull;
-            sI[i] = in ? SA[gd.start + i] : ~0u;
+        // unrolled, so a thread's loads are in flight together (the loop
+        // bound is a constant: every thread stores MS_IT entries)
+#pragma unroll
+        for (int j = 0; j < MS_IT; ++j) {
+            const uint32_t i = j * MS_NT + threadIdx.x;
+            sK[i] = i < len ? K[gd.start + i] : ~0ull;
+            sI[i] = i < len ? SA[gd.start + i] : 0xffff0000u + i;  // padding: last, distinct
         }
         __syncthreads();
         cta_merge_sort(sK, sI);
