@@ -172,11 +172,18 @@ __global__ void __launch_bounds__(256) k_gather_micro(const uint32_t* __restrict
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < count; g += gridDim.x * blockDim.x) {
         const GroupDesc gd = cur.list[0][g];
         const BlockInfo bi = blocks[gd.blk];
-        for (uint32_t e = 0; e < gd.len; ++e) {
-            const uint32_t k = gd.start + e;
-            uint32_t r = SA[k] + h;
-            if (r >= bi.n) r -= bi.n;
-            key2[k] = r < bi.n ? rank[bi.off + r] : 0u;
+        // a micro group has at most MICRO_MAX members: their SA loads, then
+        // their rank gathers, in flight together
+        uint32_t sa[MICRO_MAX];
+#pragma unroll
+        for (uint32_t e = 0; e < MICRO_MAX; ++e) sa[e] = e < gd.len ? SA[gd.start + e] : 0u;
+#pragma unroll
+        for (uint32_t e = 0; e < MICRO_MAX; ++e) {
+            if (e < gd.len) {
+                uint32_t r = sa[e] + h;
+                if (r >= bi.n) r -= bi.n;
+                key2[gd.start + e] = r < bi.n ? rank[bi.off + r] : 0u;
+            }
         }
     }
 }
@@ -190,14 +197,29 @@ __global__ void __launch_bounds__(256) k_gather_small(const uint32_t* __restrict
     const uint32_t total = c1 + c2 + c3;
     const int lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
-    for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += nwarps) {
-        const GroupDesc gd = g < c1 ? cur.list[1][g] : (g < c1 + c2 ? cur.list[2][g - c1] : cur.list[3][g - c1 - c2]);
-        const BlockInfo bi = blocks[gd.blk];
-        for (uint32_t e = lane; e < gd.len; e += 32) {
-            const uint32_t k = gd.start + e;
-            uint32_t r = SA[k] + h;
-            if (r >= bi.n) r -= bi.n;
-            key2[k] = r < bi.n ? rank[bi.off + r] : 0u;
+    auto desc = [&](uint32_t g) {
+        return g < c1 ? cur.list[1][g] : (g < c1 + c2 ? cur.list[2][g - c1] : cur.list[3][g - c1 - c2]);
+    };
+    // two groups a warp (g and g + nwarps), their chains of loads interleaved:
+    // the gather is bound by the latency of descriptor -> SA -> rank
+    for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < total; g += 2 * nwarps) {
+        const uint32_t g1 = g + nwarps;
+        const GroupDesc gd0 = desc(g);
+        const GroupDesc gd1 = g1 < total ? desc(g1) : GroupDesc{0u, 0u, 0u, 0u};
+        const BlockInfo b0 = blocks[gd0.blk];
+        const BlockInfo b1 = blocks[gd1.blk];
+        const uint32_t len = max(gd0.len, gd1.len);
+        for (uint32_t e = lane; e < len; e += 32) {
+            const bool v0 = e < gd0.len, v1 = e < gd1.len;
+            const uint32_t s0 = v0 ? SA[gd0.start + e] : 0u;
+            const uint32_t s1 = v1 ? SA[gd1.start + e] : 0u;
+            uint32_t r0 = s0 + h, r1 = s1 + h;
+            if (r0 >= b0.n) r0 -= b0.n;
+            if (r1 >= b1.n) r1 -= b1.n;
+            const uint32_t k0 = v0 && r0 < b0.n ? rank[b0.off + r0] : 0u;
+            const uint32_t k1 = v1 && r1 < b1.n ? rank[b1.off + r1] : 0u;
+            if (v0) key2[gd0.start + e] = k0;
+            if (v1) key2[gd1.start + e] = k1;
         }
     }
 }
