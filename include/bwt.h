@@ -77,7 +77,9 @@ typedef struct {
     double radix_bytes;         /* their algorithmic HBM bytes: 24 per u64 key (8 + 4 read, 8 + 4
                                    written), 13 for the first pass (1 byte read), 16 per u32 key */
     uint64_t active_elements;   /* rotations re-sorted by doubling rounds, summed over rounds */
-    uint64_t buckets_overflowed;/* learned bucketing: buckets sent to the radix path */
+    uint64_t buckets_overflowed;/* learned bucketing: buckets above the 3,328-rotation chunk (each
+                                   sorted whole by one CTA up to 13,312 rotations, by the radix
+                                   path beyond) */
     uint64_t keys_overflowed;   /* learned bucketing: keys in those buckets */
     uint32_t max_bucket;        /* learned bucketing: largest bucket */
     uint32_t graph_replayed;    /* 1 if the last call replayed a cached CUDA graph */

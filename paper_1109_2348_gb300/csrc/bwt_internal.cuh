@@ -382,22 +382,22 @@ __device__ __forceinline__ uint32_t smem_upper_bound(const T* a, uint32_t n, T x
 // tile was sorted from, whose members already hold it as their rank (their
 // rank is written only where it changes), or NO_OLD_START for a first naming.
 //
-// Each warp walks its own range (an eighth of the tile, rounded up to whole
-// steps: at most 512 elements), 32 a step: the heads (an
+// Each of the NW warps walks its own range (an NW-th of the tile, rounded up
+// to whole steps), 32 elements a step: the heads (an
 // element whose key differs from its predecessor's, and element 0) come
 // from one ballot, an element's group starts at the last head at or before
 // it (carried across steps and, through shared memory, across warps), and
 // the lane at a head emits the group that ends there; the group of the
-// tile's last head is emitted after the walk. All 256 threads of the CTA
-// call (one barrier inside).
+// tile's last head is emitted after the walk. All NW warps of the CTA call
+// (one barrier inside).
 constexpr uint32_t NO_OLD_START = 0xffffffffu;
 
-template <typename KeyT>
+template <typename KeyT, int NW = 8>
 __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t tstart, uint32_t carry_start,
                                           uint32_t carry_end, const uint32_t* sa_tile, BlockInfo bi, uint32_t blk,
                                           uint32_t* __restrict__ rank, const Bins& bins, bool emit_ok,
                                           uint32_t old_start, WarpEmitter& em, uint32_t* err) {
-    constexpr uint32_t NONE = 0xffffffffu, NW = 8;
+    constexpr uint32_t NONE = 0xffffffffu;
     __shared__ uint32_t s_heads[2 * NW];  // per warp: first head, last head of its range (NONE if none)
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = lanemask_lt();

@@ -326,10 +326,14 @@ __global__ void __launch_bounds__(256) k_bucket_stats(const uint32_t* __restrict
 // key interval, so a chunk holds every rotation of its key range: its first
 // rotation starts a group and its last ends one, and naming needs nothing
 // outside the chunk. A fine bucket larger than CHUNK_CAP is a chunk of its
-// own and goes to the overflow radix.
+// own: up to BIG_CAP rotations one 1,024-thread CTA sorts it the same way (a
+// model's over-full buckets are mostly a few thousand distinct keys), beyond
+// that it goes to the overflow radix.
 constexpr int MS_NT = 256;                           // threads of the chunk sort
 constexpr int MS_IT = 13;                            // rotations per thread (odd: conflict-free strides)
 constexpr uint32_t CHUNK_CAP = MS_NT * MS_IT;        // 3328
+constexpr int BIG_NT = 1024;                         // threads of the big-chunk sort
+constexpr uint32_t BIG_CAP = BIG_NT * MS_IT;         // 13312
 constexpr uint32_t MAXCH = 1024;  // chunks per block (blocks above (MAXCH - 2) * CHUNK_CAP / 2 go plain)
 
 struct ChunkTables {
@@ -382,8 +386,9 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
                     if (lane == 0) {
                         cm[b] = (uint16_t)min(nch, MAXCH - 1);
                         if (nch < MAXCH) cb[nch] = st[b];
-                        const uint32_t slot = atomicAdd(&out.count[CLS_LARGE], 1u);
-                        if (slot < out.cap[CLS_LARGE]) out.list[CLS_LARGE][slot] = GroupDesc{bi.off + st[b], sz, blk, 0u};
+                        const int li = sz <= BIG_CAP ? 1 : CLS_LARGE;  // big-chunk sort, else the overflow radix
+                        const uint32_t slot = atomicAdd(&out.count[li], 1u);
+                        if (slot < out.cap[li]) out.list[li][slot] = GroupDesc{bi.off + st[b], sz, blk, 0u};
                         else atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
                     }
                     ++nch;
@@ -546,14 +551,15 @@ __device__ __forceinline__ bool ki_less(uint64_t ak, uint32_t ai, uint64_t bk, u
     return ak < bk || (ak == bk && ai < bi);
 }
 
-// Sorts sK/sI[0 .. CHUNK_CAP) by (K, i), ascending, with MS_NT threads: each
+// Sorts sK/sI[0 .. NT * MS_IT) by (K, i), ascending, with NT threads: each
 // thread sorts its MS_IT consecutive entries in registers (odd-even
-// transposition), then log2(MS_NT) rounds merge pairs of sorted runs, each
+// transposition), then log2(NT) rounds merge pairs of sorted runs, each
 // thread producing MS_IT outputs from its merge-path split (binary search
 // on its output diagonal, then a sequential merge). All threads call; the
-// arrays hold CHUNK_CAP distinct entries (pad with (~0, 0xffff0000 + slot),
+// arrays hold NT * MS_IT distinct entries (pad with (~0, 0xffff0000 + slot),
 // above every real pair, whose indices are below 2^30; (~0, ~0) stays free
 // as the merge's end-of-run sentinel).
+template <int NT>
 __device__ __forceinline__ void cta_merge_sort(uint64_t* sK, uint32_t* sI) {
     const uint32_t t = threadIdx.x;
     uint64_t k[MS_IT];
@@ -582,7 +588,7 @@ __device__ __forceinline__ void cta_merge_sort(uint64_t* sK, uint32_t* sI) {
         sI[t * MS_IT + j] = v[j];
     }
     __syncthreads();
-    for (uint32_t m = 2; m <= (uint32_t)MS_NT; m <<= 1) {  // m threads per merged run of m * MS_IT
+    for (uint32_t m = 2; m <= (uint32_t)NT; m <<= 1) {  // m threads per merged run of m * MS_IT
         const uint32_t w = (m >> 1) * MS_IT;                // length of each input run
         const uint32_t base = (t & ~(m - 1)) * MS_IT;
         const uint32_t diag = (t & (m - 1)) * MS_IT;
@@ -629,23 +635,28 @@ __device__ __forceinline__ void cta_merge_sort(uint64_t* sK, uint32_t* sI) {
 
 // One CTA per chunk: sort it by (K, i), write its SA, and name it (rank of
 // every rotation = block-local start of its group; groups of size > 1 go to
-// `bins` for the doubling rounds).
+// `bins` for the doubling rounds). NT threads sort chunks of up to NT * MS_IT
+// rotations taken from chunks.list[LIST] (256 threads: the packed chunks;
+// 1,024 threads: the single over-full buckets up to BIG_CAP).
 constexpr size_t CHUNK_SORT_SMEM = (size_t)CHUNK_CAP * 12;
+constexpr size_t BIG_SORT_SMEM = (size_t)BIG_CAP * 12;
 
-__global__ void __launch_bounds__(MS_NT, 4) k_chunk_sort_name(const uint64_t* __restrict__ K,
-                                                          uint32_t* __restrict__ SA,
-                                                          const BlockInfo* __restrict__ blocks, Bins chunks,
-                                                          uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl,
-                                                          uint32_t* __restrict__ chunk_counter) {
+template <int NT, int MINB, int LIST>
+__global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __restrict__ K,
+                                                              uint32_t* __restrict__ SA,
+                                                              const BlockInfo* __restrict__ blocks, Bins chunks,
+                                                              uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl,
+                                                              uint32_t* __restrict__ chunk_counter) {
+    constexpr uint32_t CAP = NT * MS_IT;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* sK = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* sI = reinterpret_cast<uint32_t*>(smem + (size_t)CHUNK_CAP * 8);
-    __shared__ GroupDesc ebuf[MS_NT / 32][NCLS * EMIT_BUF];
+    uint32_t* sI = reinterpret_cast<uint32_t*>(smem + (size_t)CAP * 8);
+    __shared__ GroupDesc ebuf[NT / 32][NCLS * EMIT_BUF];
     __shared__ uint32_t s_c;
     if (ld_volatile(&ctrl[CTRL_ERR])) return;  // an earlier stage failed: the chunks are not permutations
     WarpEmitter em;
     em.init(ebuf[threadIdx.x >> 5]);
-    const uint32_t count = bin_count(chunks, 0);
+    const uint32_t count = bin_count(chunks, LIST);
     // chunks in list order from an atomic counter (zeroed before the launch):
     // the chunks in flight stay within a few blocks, whose rank ranges stay
     // in L2 while their scattered rank writes land
@@ -654,22 +665,22 @@ __global__ void __launch_bounds__(MS_NT, 4) k_chunk_sort_name(const uint64_t* __
         __syncthreads();
         const uint32_t c = s_c;
         if (c >= count) break;
-        const GroupDesc gd = chunks.list[0][c];
+        const GroupDesc gd = chunks.list[LIST][c];
         const BlockInfo bi = blocks[gd.blk];
-        const uint32_t len = min(gd.len, CHUNK_CAP);
+        const uint32_t len = min(gd.len, CAP);
         // unrolled, so a thread's loads are in flight together (the loop
         // bound is a constant: every thread stores MS_IT entries)
 #pragma unroll
         for (int j = 0; j < MS_IT; ++j) {
-            const uint32_t i = j * MS_NT + threadIdx.x;
+            const uint32_t i = j * NT + threadIdx.x;
             sK[i] = i < len ? K[gd.start + i] : ~0ull;
             sI[i] = i < len ? SA[gd.start + i] : 0xffff0000u + i;  // padding: last, distinct
         }
         __syncthreads();
-        cta_merge_sort(sK, sI);
-        for (uint32_t i = threadIdx.x; i < len; i += MS_NT) SA[gd.start + i] = sI[i];
-        name_tile<uint64_t>(sK, len, gd.start, gd.start, gd.start + len, sI, bi, gd.blk, rank, bins, bi.n > 8u,
-                            NO_OLD_START, em, &ctrl[CTRL_ERR]);
+        cta_merge_sort<NT>(sK, sI);
+        for (uint32_t i = threadIdx.x; i < len; i += NT) SA[gd.start + i] = sI[i];
+        name_tile<uint64_t, NT / 32>(sK, len, gd.start, gd.start, gd.start + len, sI, bi, gd.blk, rank, bins,
+                                     bi.n > 8u, NO_OLD_START, em, &ctrl[CTRL_ERR]);
         __syncthreads();
     }
     em.finish(bins, &ctrl[CTRL_ERR]);
@@ -819,10 +830,13 @@ bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
     // kernel attributes and occupancy: set up here, outside any stream capture
     static const int sort_ctas = [] {
         cudaFuncSetAttribute((void*)k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COUNT_SMEM);
-        cudaFuncSetAttribute((void*)k_chunk_sort_name, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute((void*)k_chunk_sort_name<MS_NT, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)CHUNK_SORT_SMEM);
+        cudaFuncSetAttribute((void*)k_chunk_sort_name<BIG_NT, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BIG_SORT_SMEM);
         int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_sort_name, MS_NT, CHUNK_SORT_SMEM);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_sort_name<MS_NT, 4, 0>, MS_NT,
+                                                      CHUNK_SORT_SMEM);
         return std::max(1, per_sm);
     }();
     p->chunk_sort_ctas = sort_ctas;
@@ -940,13 +954,17 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     }
 
     // 4c. bucketed blocks: chunk sorts with naming, then the overflow buckets
-    uint32_t* chunk_counter = ctrl + CTRL_TILE_CTR + 58;  // a control word no radix pass uses
-    CKL(cudaMemsetAsync(chunk_counter, 0, 4, st));
-    k_chunk_sort_name<<<sms * p->chunk_sort_ctas, MS_NT, CHUNK_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks,
-                                                                                  aux, p->rank, bins_of(p, 0), ctrl,
-                                                                                  chunk_counter);
+    uint32_t* chunk_counter = ctrl + CTRL_TILE_CTR + 58;  // control words no radix pass uses
+    uint32_t* big_counter = ctrl + CTRL_TILE_CTR + 59;
+    CKL(cudaMemsetAsync(chunk_counter, 0, 8, st));
+    k_chunk_sort_name<MS_NT, 4, 0><<<sms * p->chunk_sort_ctas, MS_NT, CHUNK_SORT_SMEM, st>>>(
+        p->keys[0], p->vals[0], p->blocks, aux, p->rank, bins_of(p, 0), ctrl, chunk_counter);
     CKL(cudaGetLastError());
-    p->stats.kernel_launches++;
+    // over-full buckets up to BIG_CAP: one 1,024-thread CTA each
+    k_chunk_sort_name<BIG_NT, 1, 1><<<sms, BIG_NT, BIG_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks, aux,
+                                                                        p->rank, bins_of(p, 0), ctrl, big_counter);
+    CKL(cudaGetLastError());
+    p->stats.kernel_launches += 2;
 
     // overflow buckets: radix on the index, then on the key
     const int PI = std::max(1, (bits_needed(p->max_n - 1) + 7) / 8), PK = 8, PT = PI + PK;

@@ -160,6 +160,57 @@ def test_learned_path_exact_for_any_splitters(small_model, which, graph):
     assert st["blocks_routed_plain"] >= 1, st  # the constant block overflows every bucketing
 
 
+def _prefix_keys(block):
+    """Every rotation's 8-byte big-endian prefix (cyclic), as the bucketing sees it."""
+    n = block.size
+    idx = (np.arange(n)[:, None] + np.arange(8)[None, :]) % n
+    k = np.zeros(n, dtype=np.uint64)
+    for j in range(8):
+        k = (k << np.uint64(8)) | block[idx[:, j]].astype(np.uint64)
+    return k
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_overfull_buckets_big_chunk_sort_and_radix(small_model, graph):
+    """A bucket above the 3,328-rotation chunk capacity is sorted whole by one
+    1,024-thread CTA up to 13,312 rotations and by the overflow radix beyond.
+    Splitters merged on purpose give a learned-routed Markov block one bucket of
+    each kind (sizes checked on the host first)."""
+    w = datagen.Workload("t", [datagen.MARKOV3_Z96, datagen.MARKOV3_Z96], [11, 12], [300_000, 250_000])
+    buf, off = w.generate()
+    keys = _prefix_keys(buf[:300_000])
+    spl = np.array(small_model.splitters, dtype=np.uint64).copy()
+
+    def sizes(sp):
+        return np.bincount(np.searchsorted(sp, keys, side="right"), minlength=sp.size + 1)
+
+    base = sizes(spl)
+
+    def merge_to(sp, j, lo, hi):
+        """Splitters j+1 .. j+m set to splitter j: buckets j+1 .. j+m+1 become one,
+        with m the first count that puts it in (lo, hi]."""
+        for m in range(1, sp.size - j - 1):
+            tot = int(base[j + 1:j + m + 2].sum())
+            if lo < tot <= hi:
+                t = sp.copy()
+                t[j + 1:j + 1 + m] = t[j]
+                return t, j + m + 1
+            if tot > hi:
+                break
+        raise AssertionError("could not build the bucket")
+
+    spl, end1 = merge_to(spl, 1000, 6_000, 13_312)
+    assert end1 < 2600
+    spl, _ = merge_to(spl, 2600, 20_000, 1 << 30)
+    sz = sizes(spl)
+    assert ((sz > 3_328) & (sz <= 13_312)).any() and (sz > 13_312).any(), sz.max()
+    assert sz[sz > 3_328].sum() * 4 <= keys.size  # still routed to the learned buckets
+    L, prim, st = _learned_run(buf, off, spl, graph=graph)
+    assert_matches_oracle(buf, off, L, prim, f"over-full buckets graph={graph}")
+    assert st["blocks_routed_plain"] == 0 and st["blocks_routed_flat"] == 0, st
+    assert st["buckets_overflowed"] >= 2, st
+
+
 def test_learned_graph_equals_oracle_and_replays(small_model):
     """Learned + batched: the learned stage (device-side routing included) and
     the doubling loop captured as one CUDA graph. The first call captures, the
