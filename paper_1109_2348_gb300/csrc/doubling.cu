@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restri
                 const bool valid = q < td.len;
                 if (valid) {
                     kbuf[td.start + q] = k2[j];
-                    vbuf[td.start + q] = sa[j];
+                    if (vbuf) vbuf[td.start + q] = sa[j];
                 }
                 for (int ps = 0; ps < passes; ++ps) {
                     const uint32_t d = valid ? ((k2[j] >> (ps * RBITS)) & (RADIX - 1)) : (uint32_t)RADIX;

@@ -90,8 +90,10 @@ cudaError_t launch_gather_small(const uint32_t* SA, const uint32_t* rank, const 
 cudaError_t launch_build_large_tiles(Bins cur, int tile, TileDesc* tiles, uint32_t max_tiles, uint32_t* ctrl,
                                      cudaStream_t st);
 
-// Large groups: gathers key2 and copies SA into (kbuf, vbuf) at the same
-// positions and builds per-group digit histograms hist[group][passes][radix].
+// Large groups: gathers key2 into kbuf at the positions of SA and builds
+// per-group digit histograms hist[group][passes][radix]. With vbuf it also
+// copies SA there (needed only when one pass both reads and writes the
+// values; with several passes the first reads SA itself).
 cudaError_t launch_large_prologue(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks,
                                   const TileDesc* tiles, const uint32_t* num_tiles, const uint32_t* depth,
                                   uint32_t* kbuf, uint32_t* vbuf, uint32_t* hist, int radix_bits, int passes,

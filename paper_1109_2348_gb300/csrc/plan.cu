@@ -445,8 +445,10 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
     if (large) {
         CK(launch_build_large_tiles(cur, p->tile, p->ltiles, p->cap_ltiles, ctrl, st));
         CK(launch_zero_by_count(p->hist, cur.count + CLS_LARGE, (uint32_t)(P2 * RADIX), hist_cap, st));
-        CK(launch_large_prologue(p->sa, p->rank, p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, depth, p->kA, p->vA,
-                                 p->hist, rb, P2, st));
+        // with one pass only, that pass would read and write SA in place: it
+        // reads a copy instead
+        CK(launch_large_prologue(p->sa, p->rank, p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, depth, p->kA,
+                                 P2 == 1 ? p->vA : nullptr, p->hist, rb, P2, st));
         CK(launch_scan_rows(p->hist, RADIX, cur.count + CLS_LARGE, (uint32_t)P2, 0, (uint32_t)(p->cap_hist / RADIX),
                             st));
         p->stats.kernel_launches += 4;
@@ -457,7 +459,7 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
             OneSweepParams a{};
             const bool last = ps == P2 - 1;
             a.kin = ps == 0 ? p->kA : ((ps - 1) & 1 ? p->kA : p->kB);
-            a.vin = ps == 0 ? p->vA : ((ps - 1) & 1 ? p->vA : p->vB);
+            a.vin = ps == 0 ? (P2 == 1 ? p->vA : p->sa) : ((ps - 1) & 1 ? p->vA : p->vB);
             a.kout = last ? p->key2 : (ps & 1 ? p->kA : p->kB);
             a.vout = last ? p->sa : (ps & 1 ? p->vA : p->vB);
             a.blocks = p->blocks;
