@@ -498,7 +498,39 @@ __device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDes
     uint32_t P = 32;
     while (P < m) P <<= 1;
     static_assert((NT == 32 ? SMALL_MAX : MED_MAX) <= 8 * NT, "a group fits 8 elements a thread");
-    {
+    bool sorted = false;
+    if constexpr (NT == 32) {
+        if (P == 64) {
+            // 33..64 elements: element e = r * 32 + t in register c[r]; the
+            // bitonic network by shuffles (its one distance-32 step pairs a
+            // lane's own two elements), then the result to shared memory
+            uint64_t c0 = t < m ? (((uint64_t)key2[gd.start + t] << 32) | SA[gd.start + t]) : ~0ull;
+            uint64_t c1 = t + 32 < m ? (((uint64_t)key2[gd.start + t + 32] << 32) | SA[gd.start + t + 32]) : ~0ull;
+#pragma unroll
+            for (uint32_t kk = 2; kk <= 64; kk <<= 1) {
+#pragma unroll
+                for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+                    if (j == 32) {  // kk == 64: both elements in the ascending half
+                        const uint64_t lo = c0 < c1 ? c0 : c1, hi = c0 < c1 ? c1 : c0;
+                        c0 = lo;
+                        c1 = hi;
+                    } else {
+                        const uint64_t o0 = __shfl_xor_sync(0xffffffffu, c0, j);
+                        const uint64_t o1 = __shfl_xor_sync(0xffffffffu, c1, j);
+                        const bool lower = (t & j) == 0;
+                        const bool up0 = (t & kk) == 0, up1 = ((t + 32) & kk) == 0;
+                        c0 = (lower == up0) ? (c0 < o0 ? c0 : o0) : (c0 > o0 ? c0 : o0);
+                        c1 = (lower == up1) ? (c1 < o1 ? c1 : o1) : (c1 > o1 ? c1 : o1);
+                    }
+                }
+            }
+            comp[t] = c0;
+            comp[t + 32] = c1;
+            __syncwarp();
+            sorted = true;
+        }
+    }
+    if (!sorted) {
         // up to 8 elements a thread (P <= 8 NT): all loads in flight before any store
         uint32_t lk[8], ls[8];
 #pragma unroll
@@ -512,9 +544,9 @@ __device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDes
             const uint32_t i = t + j * NT;
             if (i < P) comp[i] = i < m ? (((uint64_t)lk[j] << 32) | ls[j]) : ~0ull;
         }
+        coop_sync<NT>();
+        coop_bitonic<NT>(comp, P, t);
     }
-    coop_sync<NT>();
-    coop_bitonic<NT>(comp, P, t);
     if constexpr (NT == 32) {
         // One warp: group heads by ballot, 32 elements a step. An element's
         // group starts at the last head at or before it (carried across
