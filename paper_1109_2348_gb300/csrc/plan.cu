@@ -534,7 +534,9 @@ static void resolve_large_keys(bwt_plan* p, uint32_t large_keys) {
 bwt_status bwt::run_doubling_host_loop(bwt_plan* p, cudaStream_t st) {
     int par = 0;
     uint32_t depth = 8;
-    while (depth < p->max_n && p->stats.rounds < 40) {
+    // rounds of this batch (the statistic sums over the blocks of a
+    // per-block call); doubling from 8 passes 2^32 after 29 rounds
+    for (int round = 0; depth < p->max_n && round < 40; ++round) {
         CK(cudaMemcpyAsync(p->h_ctrl, p->ctrl, sizeof(uint32_t) * 24, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         resolve_large_keys(p, p->h_ctrl[CTRL_LARGE_KEYS]);
@@ -551,6 +553,7 @@ bwt_status bwt::run_doubling_host_loop(bwt_plan* p, cudaStream_t st) {
         CK(launch_round_end(p->ctrl, par, p->max_n, 0, 0, 0, st));
         p->stats.kernel_launches++;
         p->stats.rounds++;
+        if (depth > 0x7fffffffu) break;
         depth *= 2;
         par ^= 1;
     }

@@ -4,12 +4,15 @@ byte for byte in full (the oracle runs on all host cores). Workload 5 (1.08
 GB) is checked block by block with the host inverse transform and the
 permutation invariant, and byte for byte against the oracle on a sample of 32
 blocks (the oracle would need over a minute for all 1,200), and the GPU
-inverse of the whole output must give the input back."""
+inverse of the whole output must give the input back. Workload 2 also runs
+in the configuration bench.py times by default (learned bucketing inside the
+batched graph: capture, then replay), workload 4 also with one launch chain
+per block."""
 import numpy as np
 import pytest
 
 import oracle
-from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, Plan, bwt_inverse_check, datagen, model
+from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, F_PER_BLOCK_LAUNCH, Plan, bwt_inverse_check, datagen, model
 
 from gpu_util import assert_matches_oracle
 
@@ -51,6 +54,11 @@ def test_workload4_uneven_256_graph():
     assert_matches_oracle(buf, off, L, prim, "workload 4")
 
 
+def test_workload4_uneven_256_one_launch_chain_per_block():
+    buf, off, L, prim, _ = _run(datagen.config(4), flags=F_PER_BLOCK_LAUNCH)
+    assert_matches_oracle(buf, off, L, prim, "workload 4, one launch chain per block")
+
+
 @pytest.fixture(scope="module")
 def trained_model_path(tmp_path_factory):
     m = model.train(num_samples=1_000_000, epochs=8)
@@ -81,3 +89,32 @@ def test_workload5_learned_1200x900k(trained_model_path):
         s, e = int(off[b]), int(off[b + 1])
         assert np.array_equal(L[s:e], ref_L[int(soff[j]):int(soff[j + 1])]), b
         assert prim[b] == ref_p[j], b
+
+
+def test_workload2_learned_graph_as_benched(trained_model_path):
+    """The configuration bench.py times by default: learned bucketing inside the
+    batched CUDA graph on the mixed workload, with a model trained as the bench
+    trains it. The first call captures the graph, the second replays it; both
+    outputs must equal the oracle's."""
+    import torch
+    w = datagen.config(2)
+    buf, off = w.generate()
+    with Plan(max_blocks=w.num_blocks, max_total_bytes=buf.size, max_block_bytes=900_000,
+              flags=F_LEARNED | F_GRAPH, model_path=trained_model_path) as plan:
+        d_in = torch.from_numpy(buf).cuda()
+        d_L = torch.empty_like(d_in)
+        d_p = torch.empty(w.num_blocks, dtype=torch.int32, device="cuda")
+        outs = []
+        for _ in range(2):
+            d_L.fill_(0)
+            plan.forward_into(d_in, off, d_L, d_p)
+            torch.cuda.synchronize()
+            outs.append((d_L.cpu().numpy(), d_p.cpu().numpy(), plan.stats()))
+    for i, (L, prim, st) in enumerate(outs):
+        assert_matches_oracle(buf, off, L, prim, f"workload 2 learned+graph call {i}")
+    st0, st1 = outs[0][2], outs[1][2]
+    assert st1["graph_replayed"] == 1
+    # the three sources take the three routes: Markov -> learned, uniform ->
+    # equal-width, geometric runs -> plain radix
+    assert st0["blocks_routed_flat"] >= 1 and st0["blocks_routed_plain"] >= 1
+    assert st0["blocks_routed_flat"] + st0["blocks_routed_plain"] < w.num_blocks
