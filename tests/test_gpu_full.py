@@ -12,7 +12,8 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, F_PER_BLOCK_LAUNCH, Plan, bwt_inverse_check, datagen, model
+from paper_1109_2348_gb300 import (F_GRAPH, F_LEARNED, F_PER_BLOCK_LAUNCH, F_TIMING, Plan, bwt_inverse_check, datagen,
+                                   model)
 
 from gpu_util import assert_matches_oracle
 
@@ -118,3 +119,14 @@ def test_workload2_learned_graph_as_benched(trained_model_path):
     # equal-width, geometric runs -> plain radix
     assert st0["blocks_routed_flat"] >= 1 and st0["blocks_routed_plain"] >= 1
     assert st0["blocks_routed_flat"] + st0["blocks_routed_plain"] < w.num_blocks
+
+
+def test_workload2_host_driven_modes(trained_model_path):
+    """The mixed workload in the two host-driven launch modes: plain with
+    events around every radix launch (the mode bench.py times its roofline
+    in) and learned with host-driven rounds."""
+    buf, off, L, prim, st = _run(datagen.config(2), flags=F_TIMING)
+    assert_matches_oracle(buf, off, L, prim, "workload 2, host-driven with timing")
+    assert st["first_launches"] == 8 and st["first_ms"] > 0
+    buf, off, L, prim, st = _run(datagen.config(2), flags=F_LEARNED, model_path=trained_model_path)
+    assert_matches_oracle(buf, off, L, prim, "workload 2, learned with host-driven rounds")
