@@ -130,3 +130,38 @@ def test_workload2_host_driven_modes(trained_model_path):
     assert st["first_launches"] == 8 and st["first_ms"] > 0
     buf, off, L, prim, st = _run(datagen.config(2), flags=F_LEARNED, model_path=trained_model_path)
     assert_matches_oracle(buf, off, L, prim, "workload 2, learned with host-driven rounds")
+
+
+MAX_BLOCK = (1 << 30) - 1  # the largest block the interface takes
+
+
+def test_max_block_constant_closed_form():
+    """One block of the largest size, all bytes equal: every rotation is the
+    same, so the order is by index, L = S and the primary index is 0."""
+    import torch
+    S = torch.full((MAX_BLOCK,), 0x61, dtype=torch.uint8, device="cuda")
+    off = np.array([0, MAX_BLOCK], dtype=np.uint64)
+    with Plan(max_blocks=1, max_total_bytes=MAX_BLOCK, max_block_bytes=MAX_BLOCK, flags=F_GRAPH) as plan:
+        L, prim = plan.forward(S, off)
+        torch.cuda.synchronize()
+        st = plan.stats()
+        assert bool(torch.equal(L, S)) and int(prim[0]) == 0
+        assert st["rounds"] >= 26  # the doubling runs until the prefix length passes n
+    del S, L
+
+
+def test_max_block_uniform_round_trip():
+    """One block of the largest size, uniform bytes: L is a permutation of S
+    and the GPU inverse of (L, primary) gives S back."""
+    import torch
+    S = datagen.block(datagen.UNIFORM, 77, MAX_BLOCK)
+    off = np.array([0, MAX_BLOCK], dtype=np.uint64)
+    d_S = torch.from_numpy(S).cuda()
+    with Plan(max_blocks=1, max_total_bytes=MAX_BLOCK, max_block_bytes=MAX_BLOCK, flags=F_GRAPH) as plan:
+        L, prim = plan.forward(d_S, off)
+        torch.cuda.synchronize()
+        assert torch.equal(torch.bincount(L.to(torch.int64), minlength=256),
+                           torch.bincount(d_S.to(torch.int64), minlength=256))
+        back = plan.inverse(L, off, prim)
+        torch.cuda.synchronize()
+        assert bool(torch.equal(back, d_S))
