@@ -68,29 +68,48 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks / throttle reasons sampled every 20 ms from before the
+    warm-up; only the samples taken inside the timed window (begin() .. end(),
+    host clock at each line's arrival) are reported."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines: list[str] = []
+        self.lines: list[tuple[float, str]] = []
+        self.t0 = self.t1 = None
+        self.interval_ms = self.INTERVAL_MS
 
-    def start(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    def start(self, wait_s: float = 3.0):
+        for interval in (self.INTERVAL_MS, 200):  # 200 ms if this nvidia-smi refuses the short interval
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                              "--format=csv,noheader,nounits", "-lms", str(interval)],
+                                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except (OSError, FileNotFoundError):
+                self.proc = None
+                return
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
-        except (OSError, FileNotFoundError):
-            self.proc = None
+            t = time.perf_counter()
+            while not self.lines and time.perf_counter() - t < wait_s and self.proc.poll() is None:
+                time.sleep(0.01)  # sampling has started before the timed window opens
+            if self.lines or self.proc.poll() is None:
+                self.interval_ms = interval
+                return
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def begin(self):
+        self.t0 = time.perf_counter()
+
+    def end(self):
+        self.t1 = time.perf_counter()
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -100,9 +119,17 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        lines = self.lines
+        if self.t0 is not None and self.t1 is not None:
+            inside = [ln for t, ln in lines if self.t0 <= t <= self.t1 + self.interval_ms / 1000]
+            if not inside:  # a window shorter than one interval: the first sample after it opened
+                inside = [ln for t, ln in lines if t >= self.t0][:1]
+            lines = inside
+        else:
+            lines = [ln for _, ln in lines]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -117,7 +144,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "interval_ms": self.interval_ms}
 
 
 def workload(cfg: int, blocks: int = 0):
@@ -319,14 +346,16 @@ def ours(args):
         torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in ev], st, launches
 
+    sampler = ClockSampler(local)
+    sampler.start()
     warm(plan, (d_L, d_p))
     radix = {"ms": 0.0, "bytes": 0.0, "launches": 0, "keys": 0.0}
-    sampler = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    sampler.start()
+    sampler.begin()
     step_ms, stats, launches = timed_steps(plan, radix if args.mode == "host" else None)
+    sampler.end()
     clocks = sampler.stop()
     learned_stats = {k: stats[k] for k in ("blocks_routed_plain", "blocks_routed_flat", "buckets_overflowed",
                                            "keys_overflowed", "max_bucket", "bucket_sq_sum", "buckets_nonempty")} \
@@ -471,15 +500,16 @@ def inverse_bench(args):
     d_out = torch.empty_like(d_in)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
     for _ in range(max(3, args.warmup)):
         plan.inverse_into(d_L, off, d_p, d_out, stream)
     torch.cuda.synchronize()
     assert torch.equal(d_out, d_in), "the GPU inverse does not give the input back"
-    sampler = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    sampler.start()
+    sampler.begin()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches = 0
     for i in range(args.steps):
@@ -489,6 +519,7 @@ def inverse_bench(args):
         ev[i][1].record(stream)
         launches += plan.stats()["kernel_launches"]
     torch.cuda.synchronize()
+    sampler.end()
     clocks = sampler.stop()
     assert torch.equal(d_out, d_in)
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -644,6 +675,8 @@ def stages_bench(args):
     ms = {k: 0.0 for k in names}
     sampler = ClockSampler(local)
     sampler.start()
+    torch.cuda.synchronize()
+    sampler.begin()
     for _ in range(args.steps):
         flush.zero_()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -659,6 +692,7 @@ def stages_bench(args):
         torch.cuda.synchronize()
         for i, k in enumerate(names):
             ms[k] += ev[i].elapsed_time(ev[i + 1])
+    sampler.end()
     clocks = sampler.stop()
     plan.close()
     vle_bytes = int(byte_off[-1].item())
