@@ -552,8 +552,8 @@ __device__ __forceinline__ bool ki_less(uint64_t ak, uint32_t ai, uint64_t bk, u
 }
 
 // Sorts sK/sI[0 .. NT * MS_IT) by (K, i), ascending, with NT threads: each
-// thread sorts its MS_IT consecutive entries in registers (odd-even
-// transposition), then log2(NT) rounds merge pairs of sorted runs, each
+// thread sorts its MS_IT consecutive entries in registers (a sorting
+// network), then log2(NT) rounds merge pairs of sorted runs, each
 // thread producing MS_IT outputs from its merge-path split (binary search
 // on its output diagonal, then a sequential merge). All threads call; the
 // arrays hold NT * MS_IT distinct entries (pad with (~0, 0xffff0000 + slot),
@@ -569,18 +569,27 @@ __device__ __forceinline__ void cta_merge_sort(uint64_t* sK, uint32_t* sI) {
         k[j] = sK[t * MS_IT + j];
         v[j] = sI[t * MS_IT + j];
     }
+    // Batcher's odd-even merge sorting network for 16 inputs with every
+    // comparator that touches slots 13..15 dropped: those slots would hold
+    // +infinity, which a comparator never moves to a lower slot, so the rest
+    // sorts 13 entries (48 compare-exchanges instead of the 78 of odd-even
+    // transposition; checked on every 0/1 input, which suffices for a network)
+    static_assert(MS_IT == 13, "the network below sorts 13 entries");
+    constexpr int NET[48][2] = {
+        {0, 1}, {2, 3}, {0, 2}, {1, 3}, {1, 2}, {4, 5}, {6, 7}, {4, 6}, {5, 7}, {5, 6}, {0, 4}, {2, 6}, {2, 4},
+        {1, 5}, {3, 7}, {3, 5}, {1, 2}, {3, 4}, {5, 6}, {8, 9}, {10, 11}, {8, 10}, {9, 11}, {9, 10}, {8, 12},
+        {10, 12}, {9, 10}, {11, 12}, {0, 8}, {4, 12}, {4, 8}, {2, 10}, {6, 10}, {2, 4}, {6, 8}, {10, 12}, {1, 9},
+        {5, 9}, {3, 11}, {7, 11}, {3, 5}, {7, 9}, {1, 2}, {3, 4}, {5, 6}, {7, 8}, {9, 10}, {11, 12}};
 #pragma unroll
-    for (int r = 0; r < MS_IT; ++r) {
-#pragma unroll
-        for (int j = r & 1; j + 1 < MS_IT; j += 2) {
-            const bool sw = ki_less(k[j + 1], v[j + 1], k[j], v[j]);
-            const uint64_t a = sw ? k[j + 1] : k[j], b = sw ? k[j] : k[j + 1];
-            const uint32_t x = sw ? v[j + 1] : v[j], y = sw ? v[j] : v[j + 1];
-            k[j] = a;
-            k[j + 1] = b;
-            v[j] = x;
-            v[j + 1] = y;
-        }
+    for (int c = 0; c < 48; ++c) {
+        const int i = NET[c][0], j = NET[c][1];
+        const bool sw = ki_less(k[j], v[j], k[i], v[i]);
+        const uint64_t a = sw ? k[j] : k[i], b = sw ? k[i] : k[j];
+        const uint32_t x = sw ? v[j] : v[i], y = sw ? v[i] : v[j];
+        k[i] = a;
+        k[j] = b;
+        v[i] = x;
+        v[j] = y;
     }
 #pragma unroll
     for (int j = 0; j < MS_IT; ++j) {
