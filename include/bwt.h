@@ -68,7 +68,8 @@ typedef struct {
 
 /* Plan statistics of the last bwt_forward_batch call. */
 typedef struct {
-    uint32_t rounds;            /* prefix-doubling rounds executed (over all blocks) */
+    uint32_t rounds;            /* prefix-doubling rounds executed (a batch shares its rounds; with
+                                   BWT_F_PER_BLOCK_LAUNCH, summed over the blocks) */
     uint32_t radix_bits, tile_keys;
     uint64_t kernel_launches;   /* kernels launched (graph replays count the kernels they run) */
     uint64_t radix_launches;    /* onesweep radix-pass launches */
