@@ -187,3 +187,18 @@ def test_round_radix_widths(round_bits):
         L, prim = plan.forward(torch.from_numpy(buf).cuda(), off)
         assert plan.stats()["round_radix_bits"] == round_bits
         assert_matches_oracle(buf, off, L.cpu().numpy(), prim.cpu().numpy(), f"round bits {round_bits}")
+
+
+@pytest.mark.parametrize("n, want", [(60_000, 8), (65_536, 8), (65_537, 10), (300_000, 10)])
+def test_default_round_radix_follows_the_rank_width(n, want):
+    """By default the rounds' digit width is 10 when that takes fewer passes
+    than 8 over the batch's ranks (17 to 20 bits: two passes instead of
+    three), else 8; the result is exact either way."""
+    import torch
+    w = datagen.Workload("t", [datagen.RUNS16], [31], [n])
+    buf, off = w.generate()
+    with Plan(max_blocks=1, max_total_bytes=n, max_block_bytes=n) as plan:
+        L, prim = plan.forward(torch.from_numpy(buf).cuda(), off)
+        st = plan.stats()
+        assert st["round_radix_bits"] == want and st["rounds"] >= 1
+        assert_matches_oracle(buf, off, L.cpu().numpy(), prim.cpu().numpy(), f"n={n}")
