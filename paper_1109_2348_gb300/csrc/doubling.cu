@@ -498,6 +498,26 @@ __device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDes
     uint32_t P = 32;
     while (P < m) P <<= 1;
     static_assert((NT == 32 ? SMALL_MAX : MED_MAX) <= 8 * NT, "a group fits 8 elements a thread");
+    // A group whose members all have the same key2 cannot split: it stays in
+    // index order with its ranks (every member already holds the group's
+    // start) and only moves on to the next round. Periodic blocks keep such
+    // groups of identical rotations for every round until 2h >= n.
+    {
+        const uint32_t k0 = key2[gd.start];
+        bool mine = true;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t i = t + j * NT;
+            if (i < m) mine &= key2[gd.start + i] == k0;
+        }
+        bool same;
+        if constexpr (NT == 32) same = __all_sync(0xffffffffu, mine);
+        else same = __syncthreads_and(mine);
+        if (same) {
+            em.emit(next, t == 0 && new_depth < bi.n, gd.start, m, gd.blk, err);
+            return;
+        }
+    }
     bool sorted = false;
     if constexpr (NT == 32) {
         if (P == 64) {
