@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(256) k_gather_small(const uint32_t* __restrict
 }
 
 __global__ void __launch_bounds__(1024) k_build_large_tiles(Bins cur, int tile, TileDesc* __restrict__ tiles,
-                                                            uint32_t max_tiles, uint32_t* ctrl) {
+                                                            uint32_t max_tiles, uint32_t* ctrl,
+                                                            uint32_t* __restrict__ seg_varied) {
     __shared__ uint32_t tmp[32];
     __shared__ uint32_t s_keys;
     if (threadIdx.x == 0) s_keys = 0;
@@ -240,6 +241,7 @@ __global__ void __launch_bounds__(1024) k_build_large_tiles(Bins cur, int tile, 
             gd = cur.list[CLS_LARGE][i];
             nt = (gd.len + tile - 1) / tile;
             atomicAdd(&s_keys, gd.len);
+            if (seg_varied) seg_varied[i] = 0u;  // set by the prologue if the group's key2 differ
         }
         uint32_t tot;
         const uint32_t first = running + block_exclusive_scan<1024>(nt, tmp, &tot);
@@ -279,7 +281,8 @@ __global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restri
                                                         const uint32_t* __restrict__ num_tiles,
                                                         const uint32_t* __restrict__ depth,
                                                         uint32_t* __restrict__ kbuf, uint32_t* __restrict__ vbuf,
-                                                        uint32_t* __restrict__ hist, int passes) {
+                                                        uint32_t* __restrict__ hist, int passes,
+                                                        uint32_t* __restrict__ seg_varied) {
     constexpr int RADIX = 1 << RBITS;
     const uint32_t h = *depth;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -291,6 +294,15 @@ __global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restri
         __syncthreads();
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
+        // key2 of the group's first member: the group does not move this
+        // round if every member has it
+        uint32_t k0;
+        {
+            uint32_t r = SA[td.segStart] + h;
+            if (r >= bi.n) r -= bi.n;
+            k0 = r < bi.n ? rank[bi.off + r] : 0u;
+        }
+        bool same = true;
         // PI elements a thread per step: their SA loads, then their rank
         // gathers, are all in flight at once
         constexpr int PI = 4;
@@ -318,6 +330,7 @@ __global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restri
                 if (valid) {
                     kbuf[td.start + q] = k2[j];
                     if (vbuf) vbuf[td.start + q] = sa[j];
+                    same &= k2[j] == k0;
                 }
                 for (int ps = 0; ps < passes; ++ps) {
                     const uint32_t d = valid ? ((k2[j] >> (ps * RBITS)) & (RADIX - 1)) : (uint32_t)RADIX;
@@ -326,7 +339,7 @@ __global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restri
                 }
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(!same) && threadIdx.x == 0) seg_varied[td.seg] = 1u;
         for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) {
             const uint32_t c = sh[i];
             if (c) atomicAdd(&hist[(size_t)td.seg * passes * RADIX + i], c);
@@ -676,7 +689,8 @@ __global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict
                                                       const BlockInfo* __restrict__ blocks,
                                                       const TileDesc* __restrict__ tiles,
                                                       const uint32_t* __restrict__ num_tiles, Bins next,
-                                                      const uint32_t* __restrict__ depth, uint32_t* ctrl) {
+                                                      const uint32_t* __restrict__ depth,
+                                                      const uint32_t* __restrict__ seg_varied, uint32_t* ctrl) {
     __shared__ uint32_t sk[4096];
     __shared__ uint32_t ssa[4096];
     __shared__ uint32_t s_carry[2];
@@ -689,6 +703,14 @@ __global__ void __launch_bounds__(256) k_rename_large(const uint32_t* __restrict
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const TileDesc td = tiles[t];
         const BlockInfo bi = blocks[td.blk];
+        if (seg_varied[td.seg] == 0u) {
+            // every key2 of the group is the same: the radix left it alone, it
+            // does not split and its ranks stand; it moves on whole (once, from
+            // its first tile); no shared memory is touched on this path
+            em.emit(next, threadIdx.x == 0 && td.start == td.segStart && new_depth < bi.n, td.segStart, td.pad0,
+                    td.blk, &ctrl[CTRL_ERR]);
+            continue;
+        }
         const uint32_t lo = td.segStart, hi = td.segStart + td.pad0;
 #pragma unroll
         for (int it = 0; it < 16; ++it) {  // tiles hold at most 4096 keys
@@ -817,23 +839,23 @@ cudaError_t launch_gather_small(const uint32_t* SA, const uint32_t* rank, const 
 }
 
 cudaError_t launch_build_large_tiles(Bins cur, int tile, TileDesc* tiles, uint32_t max_tiles, uint32_t* ctrl,
-                                     cudaStream_t st) {
-    k_build_large_tiles<<<1, 1024, 0, st>>>(cur, tile, tiles, max_tiles, ctrl);
+                                     cudaStream_t st, uint32_t* seg_varied) {
+    k_build_large_tiles<<<1, 1024, 0, st>>>(cur, tile, tiles, max_tiles, ctrl, seg_varied);
     return cudaGetLastError();
 }
 
 cudaError_t launch_large_prologue(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks,
                                   const TileDesc* tiles, const uint32_t* num_tiles, const uint32_t* depth,
                                   uint32_t* kbuf, uint32_t* vbuf, uint32_t* hist, int radix_bits, int passes,
-                                  cudaStream_t st) {
+                                  uint32_t* seg_varied, cudaStream_t st) {
     const size_t smem = (size_t)passes * (1u << radix_bits) * 4;
     const int grid = num_sms() * 8;
     if (radix_bits == 8) {
         k_large_prologue<8><<<grid, 256, smem, st>>>(SA, rank, blocks, tiles, num_tiles, depth, kbuf, vbuf, hist,
-                                                     passes);
+                                                     passes, seg_varied);
     } else if (radix_bits == 10) {
         k_large_prologue<10><<<grid, 256, smem, st>>>(SA, rank, blocks, tiles, num_tiles, depth, kbuf, vbuf, hist,
-                                                      passes);
+                                                      passes, seg_varied);
     } else if (radix_bits == 11) {
         static bool attr = [] {
             cudaFuncSetAttribute((void*)k_large_prologue<11>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -842,7 +864,7 @@ cudaError_t launch_large_prologue(const uint32_t* SA, const uint32_t* rank, cons
         }();
         (void)attr;
         k_large_prologue<11><<<grid, 256, smem, st>>>(SA, rank, blocks, tiles, num_tiles, depth, kbuf, vbuf, hist,
-                                                      passes);
+                                                      passes, seg_varied);
     } else {
         return cudaErrorInvalidValue;
     }
@@ -881,8 +903,9 @@ cudaError_t launch_sort_small(uint32_t* SA, uint32_t* key2, uint32_t* rank, cons
 
 cudaError_t launch_rename_large(const uint32_t* SA, const uint32_t* key2, uint32_t* rank, const BlockInfo* blocks,
                                 const TileDesc* tiles, const uint32_t* num_tiles, Bins next, const uint32_t* depth,
-                                uint32_t* ctrl, cudaStream_t st) {
-    k_rename_large<<<num_sms() * 4, 256, 0, st>>>(SA, key2, rank, blocks, tiles, num_tiles, next, depth, ctrl);
+                                const uint32_t* seg_varied, uint32_t* ctrl, cudaStream_t st) {
+    k_rename_large<<<num_sms() * 4, 256, 0, st>>>(SA, key2, rank, blocks, tiles, num_tiles, next, depth, seg_varied,
+                                                  ctrl);
     return cudaGetLastError();
 }
 

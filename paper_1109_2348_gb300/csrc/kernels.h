@@ -27,6 +27,9 @@ struct OneSweepParams {
     uint32_t* tile_counter;       // zeroed before the pass
     uint32_t* ctrl;               // device control words (spin limit, error)
     int shift;                    // digit = (key >> shift) & (radix - 1)
+    // u32 passes of the doubling rounds: per segment, nonzero if its keys are
+    // not all equal; the tiles of the other segments are skipped (null: none)
+    const uint32_t* seg_varied = nullptr;
 };
 
 // key_bytes: 8 (u64 rotation prefixes), 4 (u32 doubling ranks) or -8 (u64
@@ -86,18 +89,19 @@ cudaError_t launch_gather_small(const uint32_t* SA, const uint32_t* rank, const 
                                 int* launched);
 
 // Builds the radix tile table of the large groups of `cur`, its count and
-// the number of keys in large groups.
+// the number of keys in large groups; zeroes seg_varied[group] when given.
 cudaError_t launch_build_large_tiles(Bins cur, int tile, TileDesc* tiles, uint32_t max_tiles, uint32_t* ctrl,
-                                     cudaStream_t st);
+                                     cudaStream_t st, uint32_t* seg_varied = nullptr);
 
 // Large groups: gathers key2 into kbuf at the positions of SA and builds
 // per-group digit histograms hist[group][passes][radix]. With vbuf it also
 // copies SA there (needed only when one pass both reads and writes the
-// values; with several passes the first reads SA itself).
+// values; with several passes the first reads SA itself). seg_varied[group]
+// becomes nonzero if the group's key2 are not all equal.
 cudaError_t launch_large_prologue(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks,
                                   const TileDesc* tiles, const uint32_t* num_tiles, const uint32_t* depth,
                                   uint32_t* kbuf, uint32_t* vbuf, uint32_t* hist, int radix_bits, int passes,
-                                  cudaStream_t st);
+                                  uint32_t* seg_varied, cudaStream_t st);
 
 // Micro, tiny, small and medium groups: sort by (key2, SA), rename, emit
 // refined groups.
@@ -105,10 +109,12 @@ cudaError_t launch_sort_small(uint32_t* SA, uint32_t* key2, uint32_t* rank, cons
                               Bins next, const uint32_t* depth, const uint32_t* host_counts, uint32_t* ctrl,
                               cudaStream_t st, int* launched);
 
-// Large groups after their radix sort: rename and emit refined groups.
+// Large groups after their radix sort: rename and emit refined groups; a
+// group with seg_varied[group] == 0 (all key2 equal, skipped by the radix)
+// is passed on unchanged.
 cudaError_t launch_rename_large(const uint32_t* SA, const uint32_t* key2, uint32_t* rank, const BlockInfo* blocks,
                                 const TileDesc* tiles, const uint32_t* num_tiles, Bins next, const uint32_t* depth,
-                                uint32_t* ctrl, cudaStream_t st);
+                                const uint32_t* seg_varied, uint32_t* ctrl, cudaStream_t st);
 
 // Control words: reset before a batch; advance after a round (and set the
 // graph loop condition); set the condition before the loop.

@@ -124,7 +124,7 @@ void bwt::free_plan_memory(bwt_plan* p) {
         if (q) cudaFreeHost(q);
     };
     F(p->keys[0]); F(p->keys[1]); F(p->vals[0]); F(p->vals[1]); F(p->rank);
-    F(p->tiles0); F(p->ltiles); F(p->blocks); F(p->hist); F(p->status); F(p->ctrl);
+    F(p->tiles0); F(p->ltiles); F(p->blocks); F(p->hist); F(p->status); F(p->ctrl); F(p->seg_varied);
     for (int s = 0; s < 2; ++s)
         for (int c = 0; c < NCLS; ++c) F(p->bins[s][c]);
     F(p->splitters); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->route_first); F(p->bstats); F(p->tiles_aux); F(p->inv_slots); F(p->inv_items); F(p->mtf_lists);
@@ -191,6 +191,7 @@ extern "C" bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt
     A(dev_alloc(&p->hist, p->cap_hist, &total));
     A(dev_alloc(&p->status, p->cap_status, &total));
     A(dev_alloc(&p->ctrl, CTRL_WORDS, &total));
+    A(dev_alloc(&p->seg_varied, (size_t)p->bincap[CLS_LARGE] + 1, &total));
     for (int par = 0; par < 2; ++par)
         for (int c = 0; c < NCLS; ++c) A(dev_alloc(&p->bins[par][c], p->bincap[c], &total));
     A(host_alloc(&p->h_ctrl, CTRL_WORDS));
@@ -443,12 +444,12 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
     const uint32_t hist_cap = (uint32_t)std::min<uint64_t>(p->cap_hist, 0xffffffffu);
     const uint32_t status_cap = (uint32_t)std::min<uint64_t>(p->cap_status, 0xffffffffu);
     if (large) {
-        CK(launch_build_large_tiles(cur, p->tile, p->ltiles, p->cap_ltiles, ctrl, st));
+        CK(launch_build_large_tiles(cur, p->tile, p->ltiles, p->cap_ltiles, ctrl, st, p->seg_varied));
         CK(launch_zero_by_count(p->hist, cur.count + CLS_LARGE, (uint32_t)(P2 * RADIX), hist_cap, st));
         // with one pass only, that pass would read and write SA in place: it
         // reads a copy instead
         CK(launch_large_prologue(p->sa, p->rank, p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, depth, p->kA,
-                                 P2 == 1 ? p->vA : nullptr, p->hist, rb, P2, st));
+                                 P2 == 1 ? p->vA : nullptr, p->hist, rb, P2, p->seg_varied, st));
         CK(launch_scan_rows(p->hist, RADIX, cur.count + CLS_LARGE, (uint32_t)P2, 0, (uint32_t)(p->cap_hist / RADIX),
                             st));
         p->stats.kernel_launches += 4;
@@ -471,6 +472,7 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
             a.tile_counter = ctrl + CTRL_TILE_CTR + 16 + ps;
             a.ctrl = ctrl;
             a.shift = ps * rb;
+            a.seg_varied = p->seg_varied;  // groups whose key2 are all equal do not move
             CK(timed_onesweep(p, 4, false, a, 16.0, 0, CTRL_LARGE_KEYS, st, rb));
         }
         p->pending_large_passes = (uint32_t)P2;
@@ -480,7 +482,7 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
     p->stats.kernel_launches += launched;
     if (large) {
         CK(launch_rename_large(p->sa, p->key2, p->rank, p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, nxt, depth,
-                               ctrl, st));
+                               p->seg_varied, ctrl, st));
         p->stats.kernel_launches++;
     }
     return BWT_OK;

@@ -50,6 +50,7 @@ struct bwt_plan {
     uint32_t* hist = nullptr;
     uint32_t* status = nullptr;
     uint32_t* ctrl = nullptr;
+    uint32_t* seg_varied = nullptr;  // [large groups] nonzero if a large group's key2 are not all equal
     bwt::GroupDesc* bins[2][bwt::NCLS] = {};
 
     // learned bucketing (allocated when a model is installed)

@@ -93,6 +93,15 @@ __global__ void __launch_bounds__(OsThreads<TILE>::value, OsMinBlocks<TILE>::val
         const uint32_t t = *s_tile;
         if (t >= num_tiles) break;
         const TileDesc td = p.tiles[t];
+        if constexpr (sizeof(KeyT) == 4) {
+            // a doubling round's group whose keys are all equal does not move:
+            // its tiles are skipped whole (no tile of another group looks
+            // back at them)
+            if (p.seg_varied && p.seg_varied[td.seg] == 0u) {
+                __syncthreads();  // every thread has read s_tile
+                continue;
+            }
+        }
 
         // ---- load the tile (warp-striped: item j of lane l of warp w is
         //      tile index w*WKEYS + j*32 + l)
