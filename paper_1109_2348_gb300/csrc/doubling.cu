@@ -209,17 +209,33 @@ __global__ void __launch_bounds__(256) k_gather_small(const uint32_t* __restrict
         const BlockInfo b0 = blocks[gd0.blk];
         const BlockInfo b1 = blocks[gd1.blk];
         const uint32_t len = max(gd0.len, gd1.len);
-        for (uint32_t e = lane; e < len; e += 32) {
-            const bool v0 = e < gd0.len, v1 = e < gd1.len;
-            const uint32_t s0 = v0 ? SA[gd0.start + e] : 0u;
-            const uint32_t s1 = v1 ? SA[gd1.start + e] : 0u;
-            uint32_t r0 = s0 + h, r1 = s1 + h;
-            if (r0 >= b0.n) r0 -= b0.n;
-            if (r1 >= b1.n) r1 -= b1.n;
-            const uint32_t k0 = v0 && r0 < b0.n ? rank[b0.off + r0] : 0u;
-            const uint32_t k1 = v1 && r1 < b1.n ? rank[b1.off + r1] : 0u;
-            if (v0) key2[gd0.start + e] = k0;
-            if (v1) key2[gd1.start + e] = k1;
+        // U elements of each group a lane per step (medium groups run to
+        // 2,048): all their SA loads, then all their rank gathers, in flight
+        constexpr int U = 4;
+        for (uint32_t e0 = lane; e0 < len; e0 += 32 * U) {
+            uint32_t s0[U], s1[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t e = e0 + 32 * u;
+                s0[u] = e < gd0.len ? SA[gd0.start + e] : 0u;
+                s1[u] = e < gd1.len ? SA[gd1.start + e] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t e = e0 + 32 * u;
+                const bool v0 = e < gd0.len, v1 = e < gd1.len;
+                uint32_t r0 = s0[u] + h, r1 = s1[u] + h;
+                if (r0 >= b0.n) r0 -= b0.n;
+                if (r1 >= b1.n) r1 -= b1.n;
+                s0[u] = v0 && r0 < b0.n ? rank[b0.off + r0] : 0u;
+                s1[u] = v1 && r1 < b1.n ? rank[b1.off + r1] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t e = e0 + 32 * u;
+                if (e < gd0.len) key2[gd0.start + e] = s0[u];
+                if (e < gd1.len) key2[gd1.start + e] = s1[u];
+            }
         }
     }
 }
