@@ -240,15 +240,22 @@ __global__ void __launch_bounds__(256) k_gather_small(const uint32_t* __restrict
     }
 }
 
+// One CTA: numbers the tiles of every large group (a block scan over 1,024
+// groups at a time), then all threads write the tiles, each finding its
+// tile's group by binary search over the scanned first tiles (a group of
+// 900,000 rotations has 220 tiles: written by one thread they took most of
+// the kernel's time).
 __global__ void __launch_bounds__(1024) k_build_large_tiles(Bins cur, int tile, TileDesc* __restrict__ tiles,
                                                             uint32_t max_tiles, uint32_t* ctrl,
                                                             uint32_t* __restrict__ seg_varied) {
     __shared__ uint32_t tmp[32];
     __shared__ uint32_t s_keys;
+    __shared__ uint32_t s_first[1024];  // first tile of each group of the chunk, relative to the chunk
+    __shared__ GroupDesc s_gd[1024];
     if (threadIdx.x == 0) s_keys = 0;
     __syncthreads();
     const uint32_t n = bin_count(cur, CLS_LARGE);
-    uint32_t running = 0;
+    uint32_t running = 0, keys = 0;
     for (uint32_t base = 0; base < n; base += 1024) {
         const uint32_t i = base + threadIdx.x;
         GroupDesc gd{0, 0, 0, 0};
@@ -256,28 +263,39 @@ __global__ void __launch_bounds__(1024) k_build_large_tiles(Bins cur, int tile, 
         if (i < n) {
             gd = cur.list[CLS_LARGE][i];
             nt = (gd.len + tile - 1) / tile;
-            atomicAdd(&s_keys, gd.len);
+            keys += gd.len;
             if (seg_varied) seg_varied[i] = 0u;  // set by the prologue if the group's key2 differ
         }
         uint32_t tot;
-        const uint32_t first = running + block_exclusive_scan<1024>(nt, tmp, &tot);
-        for (uint32_t j = 0; j < nt; ++j) {
-            const uint32_t ti = first + j;
+        s_first[threadIdx.x] = block_exclusive_scan<1024>(nt, tmp, &tot);  // non-decreasing
+        s_gd[threadIdx.x] = gd;
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < tot; k += 1024) {
+            uint32_t lo = 0, hi = 1024;  // the last group whose first tile is <= k (it has tiles)
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_first[mid] <= k) lo = mid; else hi = mid;
+            }
+            const GroupDesc g = s_gd[lo];
+            const uint32_t j = k - s_first[lo], ti = running + k;
             if (ti < max_tiles) {
                 TileDesc td;
-                td.start = gd.start + j * tile;
-                td.len = min((uint32_t)tile, gd.len - j * tile);
-                td.seg = i;
-                td.firstTile = first;
-                td.segStart = gd.start;
-                td.blk = gd.blk;
-                td.pad0 = gd.len;
+                td.start = g.start + j * tile;
+                td.len = min((uint32_t)tile, g.len - j * tile);
+                td.seg = base + lo;
+                td.firstTile = running + s_first[lo];
+                td.segStart = g.start;
+                td.blk = g.blk;
+                td.pad0 = g.len;
                 td.pad1 = 0;
                 tiles[ti] = td;
             }
         }
         running += tot;
+        __syncthreads();  // the chunk's tables are read before the next chunk rewrites them
     }
+    keys = __reduce_add_sync(0xffffffffu, keys);
+    if ((threadIdx.x & 31) == 0 && keys) atomicAdd(&s_keys, keys);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (running > max_tiles) {
