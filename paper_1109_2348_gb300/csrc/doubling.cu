@@ -17,10 +17,15 @@
 //   gather (micro: thread per group; tiny/small/medium: warp per group) and
 //   large_prologue (large groups, by tile)
 //   -> sorts: micro (sorting network in registers), tiny (bitonic across a
-//      warp's lanes), small (warp bitonic in shared memory), medium (CTA
-//      bitonic in shared memory), large (segmented onesweep radix)
+//      warp's lanes), small (warp: 33..64 bitonic in registers by shuffles,
+//      larger in shared memory), medium (CTA bitonic in shared memory),
+//      large (segmented onesweep radix)
 //   -> renames (fused into the small sorts; rename_large for large groups).
-// Refined groups are appended to the next round's size-class bins.
+// Refined groups are appended to the next round's size-class bins. A group
+// whose key2 are all equal cannot split: it keeps its order and ranks and is
+// passed on whole (small and medium groups check first; large groups are
+// flagged by the prologue and skipped by the radix and the rename). A rank
+// is written only where it changes.
 #include <algorithm>
 
 #include "kernels.h"
