@@ -169,8 +169,10 @@ extern "C" bwt_status bwt_model_samples(bwt_plan* p, const uint8_t* d_in, const 
 //            slot reservation per tile and chunk);
 //   sort:    one CTA per chunk merge-sorts it by (K, i) in shared memory,
 //            writes its SA and names it (a chunk is a whole key range, so
-//            its groups begin and end inside it);
-//   overflow buckets are sorted by the segmented radix: first by the
+//            its groups begin and end inside it); an overflow bucket of up
+//            to 13,312 rotations is sorted the same way by one 1,024-thread
+//            CTA;
+//   larger overflow buckets are sorted by the segmented radix: first by the
 //            rotation index (digits taken from the value), then by K, which
 //            leaves equal prefixes in index order as the doubling rounds
 //            require, and named inside their own bounds.
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(256) k_bucket_stats(const uint32_t* __restrict
 // Writing every rotation straight to its fine bucket scatters a tile over up
 // to 4096 places (about one key each), so nearly every 12-byte write is a
 // separate memory sector. Instead each block's consecutive fine buckets are
-// grouped into chunks of at most CHUNK_CAP rotations (greedy, one thread per
+// grouped into chunks of at most CHUNK_CAP rotations (greedy, one warp per
 // block); the scatter writes each tile's keys chunk by chunk in runs, and one
 // CTA per chunk then sorts the whole chunk by (K, i) in shared memory and
 // names it. A chunk is a union of whole fine buckets, and a fine bucket is a
