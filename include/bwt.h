@@ -223,8 +223,9 @@ bwt_status bwt_plan_set_radix(bwt_plan* plan, int radix_bits, int tile_keys);
 bwt_status bwt_plan_set_round_radix(bwt_plan* plan, int radix_bits);
 
 /* Autotuner (no paper counterpart): times this batch for radix_bits in
- * {8, 11} x tile_keys in {1024, 2048, 4096} (one untimed run, then `repeats`
- * runs between CUDA events on `stream`), keeps the fastest in the plan and
+ * {8, 11} x tile_keys in {1024, 2048, 4096}, then for the rounds' digit width
+ * in {8, 10, 11} (one untimed run, then `repeats` runs between CUDA events
+ * on `stream`, for each candidate), keeps the fastest in the plan and
  * reports it through the out-pointers (any may be NULL). With cache_path,
  * the result is appended to that JSON-lines file under (GPU name, workload
  * signature = block count, total bytes, largest block, plan flags) and a

@@ -1,12 +1,13 @@
 // bwt_plan_autotune: picks the radix digit width and tile size for a plan by
 // timing the real batch, and remembers the choice in a small JSON-lines file.
 //
-// Sweep: radix_bits in {8, 11} x tile_keys in {1024, 2048, 4096}; each
+// Sweep: radix_bits in {8, 11} x tile_keys in {1024, 2048, 4096}, then the
+// doubling rounds' digit width in {8, 10, 11} with the best of those; each
 // candidate runs once untimed and then `repeats` times between CUDA events on
 // the caller's stream; the fastest mean wins. The cache file holds one JSON
 // object per line:
 //   {"gpu": "<device name>", "key": "<workload signature>", "radix_bits": 8,
-//    "tile_keys": 4096, "ms": 1.234}
+//    "tile_keys": 4096, "round_radix_bits": 10, "ms": 1.234}
 // The workload signature is the block count, total bytes, largest block and
 // plan flags, so uneven batches of the same shape reuse one entry. A later
 // entry for the same (gpu, key) overrides an earlier one.
