@@ -112,6 +112,26 @@ def test_round_trip_through_gpu_forward_mixed_workload():
         assert torch.equal(back, d_in)
 
 
+@pytest.mark.parametrize("cfg", [1, 3, 4])
+def test_round_trip_full_workload(cfg):
+    """GPU forward, then GPU inverse, of a whole benchmark workload: the one
+    100,000-byte block, the degenerate blocks (constant and periodic: the
+    primary's cycle covers one period and is repeated) and the 256 uneven
+    blocks."""
+    import torch
+    from paper_1109_2348_gb300 import F_GRAPH
+    w = datagen.config(cfg)
+    buf, off = w.generate()
+    sizes = np.diff(off.astype(np.int64))
+    with Plan(max_blocks=w.num_blocks, max_total_bytes=buf.size, max_block_bytes=int(sizes.max()),
+              flags=F_GRAPH) as plan:
+        d_in = torch.from_numpy(buf).cuda()
+        L, prim = plan.forward(d_in, off)
+        back = plan.inverse(L, off, prim)
+        torch.cuda.synchronize()
+        assert torch.equal(back, d_in)
+
+
 def test_bad_primary_is_einval():
     import torch
     buf = np.frombuffer(b"banana", dtype=np.uint8).copy()

@@ -216,3 +216,12 @@ def test_mtf_of_the_bwt_output():
     buf, off = w.generate()
     L, _ = oracle.bwt_batch(buf, off)
     _mtf_check([L[int(off[b]):int(off[b + 1])] for b in range(w.num_blocks)])
+
+
+def test_mtf_of_the_bwt_output_full_mixed_workload():
+    """Move-to-front of the whole mixed workload's L column (57.6 MB, 64
+    blocks of the three sources) against the oracle."""
+    w = datagen.config(2)
+    buf, off = w.generate()
+    L, _ = oracle.bwt_batch(buf, off)
+    _mtf_check([L[int(off[b]):int(off[b + 1])] for b in range(w.num_blocks)])
