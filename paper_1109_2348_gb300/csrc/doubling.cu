@@ -554,8 +554,8 @@ __device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDes
     // index order with its ranks (every member already holds the group's
     // start) and only moves on to the next round. Periodic blocks keep such
     // groups of identical rotations for every round until 2h >= n.
-    {
-        const uint32_t k0 = key2[gd.start];
+    const uint32_t k0 = key2[gd.start];
+    if (key2[gd.start + m - 1] == k0) {  // else the group splits for sure: no full check
         bool mine = true;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
