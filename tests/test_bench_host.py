@@ -1,0 +1,58 @@
+"""Host logic of bench.py that needs no GPU: the clock record keeps only the
+nvidia-smi samples taken inside the timed window, and reports throttle
+reasons seen there."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def _line(sm, smax=2070, reasons=("Not Active",) * 4):
+    return ", ".join(["0", str(sm), str(smax), "600.0", "0x0", *reasons])
+
+
+class _Done:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+    def kill(self):
+        pass
+
+
+def _sampler(lines, t0, t1):
+    import bench
+    s = bench.ClockSampler(0)
+    s.proc = _Done()
+    s.lines = list(lines)
+    s.t0, s.t1 = t0, t1
+    return s
+
+
+def test_only_samples_inside_the_window_count():
+    lines = [(0.00, _line(1000)), (0.10, _line(2070)), (0.12, _line(2050)), (0.50, _line(900))]
+    rec = _sampler(lines, 0.09, 0.13).stop()
+    assert rec["samples"] == 2 and rec["sm_mhz"] == 2060.0 and rec["sm_max_mhz"] == 2070.0
+    assert rec["reasons"] == []
+
+
+def test_short_window_takes_the_first_sample_after_it_opened():
+    lines = [(0.00, _line(1000)), (0.30, _line(2070)), (0.60, _line(900))]
+    rec = _sampler(lines, 0.10, 0.11).stop()
+    assert rec["samples"] == 1 and rec["sm_mhz"] == 2070.0
+
+
+def test_throttle_reasons_inside_the_window_are_reported():
+    hot = ("Not Active", "Active", "Not Active", "Active")  # hw_slowdown .. sw_power_cap
+    lines = [(0.00, _line(2070, reasons=("Active",) * 4)), (0.10, _line(1900, reasons=hot))]
+    rec = _sampler(lines, 0.05, 0.15).stop()
+    assert rec["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_no_samples_is_reported_as_such():
+    rec = _sampler([], 0.0, 1.0).stop()
+    assert rec["samples"] == 0 and rec["reasons"] == ["no samples"]
