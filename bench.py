@@ -279,10 +279,10 @@ def ours(args):
     from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, F_PER_BLOCK_LAUNCH, F_TIMING, Plan
 
     rank, world, local = dist_env()
+    torch.cuda.set_device(local)  # before the process group, so its communicator is on this rank's GPU
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = rank_workload(args.config, args.blocks, rank, world)
     buf, off = w.generate()
@@ -485,10 +485,10 @@ def inverse_bench(args):
     from paper_1109_2348_gb300 import Plan
 
     rank, world, local = dist_env()
+    torch.cuda.set_device(local)  # before the process group, so its communicator is on this rank's GPU
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = rank_workload(args.config, args.blocks, rank, world)
     buf, off = w.generate()
