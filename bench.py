@@ -607,9 +607,10 @@ def stages_bench(args):
     events (L2 flushed before every step): forward BWT of the workload ->
     run-length encoding of L -> move-to-front of the runs' bytes ->
     variable-length encoding of the result with a Huffman table built once
-    from its histogram. Outputs are checked against the oracle once."""
+    from its histogram. Checked once on the GPU: run-length decoding gives L
+    back and the inverse of (L, primary) gives the input back (parity of every
+    stage with the oracle is the tests' job)."""
     import torch
-    import oracle
     from paper_1109_2348_gb300 import F_GRAPH, Plan
 
     rank, world, local = dist_env()
@@ -651,25 +652,10 @@ def stages_bench(args):
     for _ in range(max(3, args.warmup)):
         ro, R = run_once(table)
     torch.cuda.synchronize()
-    # check every stage once against the oracle (a sample of blocks for the forward transform)
-    L_h = d_L.cpu().numpy()
-    ref_c, ref_l, ref_ro = oracle.rle_batch(L_h, off)
-    assert np.array_equal(ro, ref_ro) and np.array_equal(chars[:R].cpu().numpy(), ref_c)
-    assert np.array_equal(lens[:R].cpu().numpy().astype(np.uint32), ref_l)
-    m_h = mtf[:R].cpu().numpy()
-    vle_h = vle.cpu().numpy()
-    bo = byte_off.cpu().numpy()
-    for b in range(w.num_blocks):
-        cb = ref_c[int(ro[b]):int(ro[b + 1])]
-        assert np.array_equal(m_h[int(ro[b]):int(ro[b + 1])], oracle.mtf_encode(cb)), b
-        ref_v, _ = oracle.vle_encode(m_h[int(ro[b]):int(ro[b + 1])], code, length)
-        assert np.array_equal(vle_h[bo[b]:bo[b + 1]], ref_v), b
-    sub = list(range(0, w.num_blocks, max(1, w.num_blocks // 4)))[:4]
-    sw = w.subset(sub)
-    sbuf, soff = sw.generate()
-    ref_L, _ = oracle.bwt_batch(sbuf, soff)
-    for j, b in enumerate(sub):
-        assert np.array_equal(L_h[int(off[b]):int(off[b + 1])], ref_L[int(soff[j]):int(soff[j + 1])])
+    # self-checks of the pipeline's output, on the GPU
+    assert torch.equal(plan.rle_decode(chars[:R], lens[:R], run_off, off), d_L), "run-length round trip"
+    assert torch.equal(plan.inverse(d_L, off, d_p), d_in), "inverse round trip"
+    torch.cuda.synchronize()
 
     names = ["bwt", "rle", "mtf", "vle"]
     ms = {k: 0.0 for k in names}
