@@ -70,6 +70,18 @@ def test_doubling_equals_bruteforce_all_ab_strings_up_to_12():
             assert p1 == p2 and np.array_equal(SA1, SA2), bytes(bits)
 
 
+def test_every_abc_string_up_to_7_against_python_sort():
+    """The definition in plain Python, independent of the oracle's C code: SA
+    sorts the rotations as byte strings, ties by lower index."""
+    for n in range(1, 8):
+        for chars in itertools.product(b"abc", repeat=n):
+            s = bytes(chars)
+            sa = sorted(range(n), key=lambda i: (s[i:] + s[:i], i))
+            want_L = bytes(s[(i - 1) % n] for i in sa)
+            L, p = oracle.bwt_block(np.frombuffer(s, dtype=np.uint8))
+            assert bytes(L) == want_L and p == sa.index(0), s
+
+
 def test_doubling_equals_bruteforce_random():
     rng = np.random.default_rng(11)
     for trial in range(120):
