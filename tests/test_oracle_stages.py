@@ -149,3 +149,32 @@ def test_mtf_closed_forms_and_round_trip():
             if c not in seen:
                 assert out[i] == len(seen) + sum(1 for v in range(c) if v not in seen)
                 seen.append(c)
+
+
+def test_stage_oracles_against_plain_python():
+    """The three definitions written out in plain Python, independent of the
+    oracle's C code, on random short inputs over small and full alphabets:
+    maximal runs in order; the position of each byte in a list that starts
+    0..255 and moves every byte to the front; codewords concatenated most
+    significant bit first, the last byte padded with zeros."""
+    import itertools
+    rng = np.random.default_rng(23)
+    code = rng.integers(0, 1 << 12, 256).astype(np.uint32)
+    length = rng.integers(1, 13, 256).astype(np.uint8)
+    code &= (np.uint32(1) << length.astype(np.uint32)) - np.uint32(1)
+    for trial in range(200):
+        alpha = int(rng.choice([1, 2, 3, 256]))
+        s = rng.integers(0, alpha, int(rng.integers(1, 400))).astype(np.uint8)
+        runs = [(k, len(list(g))) for k, g in itertools.groupby(s.tolist())]
+        chars, lens = oracle.rle_encode(s)
+        assert chars.tolist() == [k for k, _ in runs] and lens.tolist() == [n for _, n in runs]
+        lst, mtf = list(range(256)), []
+        for c in s.tolist():
+            i = lst.index(c)
+            mtf.append(i)
+            lst.insert(0, lst.pop(i))
+        assert oracle.mtf_encode(s).tolist() == mtf
+        bits = "".join(format(int(code[c]), "0%db" % int(length[c])) for c in s.tolist())
+        want = bytes(int((bits + "0" * 7)[i:i + 8], 2) for i in range(0, len(bits), 8))
+        out, nbits = oracle.vle_encode(s, code, length)
+        assert nbits == len(bits) and bytes(out) == want
