@@ -211,3 +211,105 @@ def test_adam_first_step_closed_form():
     oracle.adam_step(p, g, m, v, 1, lr=1e-3)
     assert np.allclose(p, -1e-3 * g / (np.abs(g) + 1e-8))
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+# A hand-built network for the closed forms below (every number worked out on
+# paper from the definitions: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2),
+# y = W3 h2 + b3, loss = mean (y - t)^2, W row-major [out][in]):
+#   h1[1] = relu(2 x[2] - 1)        clamps for x[2] = 0.25 (pre-activation -0.5)
+#   h1[4] = relu(0.3 - x[5])        clamps for x[5] = 0.6  (pre-activation -0.3)
+#   h2[3] = relu(h1[1] + 2 h1[4])   W2[3][1] and W2[3][4]: off-diagonal entries
+#   h2[6] = relu(0.2 - h1[1])       clamps when h1[1] = 0.5 (pre-activation -0.3)
+#   y     = 0.1 + h2[3] + 3 h2[6]
+# x[0] = 0.4 in every sample (it feeds no unit, but its gradient pins W1's
+# orientation: W1[1][0] sees d1[1] * x[0]).
+_W1, _B1, _W2, _B2, _W3, _B3 = 0, 256, 288, 1312, 1344, 1376
+
+
+def _relu_net():
+    p = np.zeros(oracle.MLP_NPARAMS)
+    p[_W1 + 1 * 8 + 2] = 2.0
+    p[_B1 + 1] = -1.0
+    p[_W1 + 4 * 8 + 5] = -1.0
+    p[_B1 + 4] = 0.3
+    p[_W2 + 3 * 32 + 1] = 1.0
+    p[_W2 + 3 * 32 + 4] = 2.0
+    p[_W2 + 6 * 32 + 1] = -1.0
+    p[_B2 + 6] = 0.2
+    p[_W3 + 3] = 1.0
+    p[_W3 + 6] = 3.0
+    p[_B3] = 0.1
+    x = np.zeros((4, 8))
+    x[:, 0] = 0.4
+    x[:, 2] = [0.25, 0.75, 0.75, 0.25]
+    x[:, 5] = [0.1, 0.6, 0.1, 0.6]
+    return p, x
+
+
+def test_mlp_forward_relu_clamps_and_w2_orientation():
+    """Per sample (h1[1], h1[4]) = (0, .2), (.5, 0), (.5, .2), (0, 0) and
+    (h2[3], h2[6]) = (.4, .2), (.5, 0), (.9, 0), (0, .2), so y = 1.1, 0.6,
+    1.0, 0.7. A dropped first-layer ReLU gives 2.2 for sample 0, a dropped
+    second-layer ReLU -0.3 for sample 1, and W2 read transposed loses h2[3]."""
+    p, x = _relu_net()
+    assert np.allclose(oracle.mlp_forward(p, x), [1.1, 0.6, 1.0, 0.7], rtol=0, atol=1e-12)
+
+
+def test_mlp_gradient_closed_form_through_clamped_units():
+    """t = (1.0, 0.6, 0.5, 0.9): errors e = (0.1, 0, 0.5, -0.2), loss = 0.075,
+    dL/dy = 2e/4 = (.05, 0, .25, -.1). Back through the layers:
+      d2[3] = dy * W3[3] where h2[3] > 0 = (.05, 0, .25, 0)   (sample 3 clamped)
+      d2[6] = dy * W3[6] where h2[6] > 0 = (.15, 0, 0, -.3)   (samples 1, 2 clamped)
+      d1[1] = (W2[3][1] d2[3] + W2[6][1] d2[6]) where h1[1] > 0 = (0, 0, .25, 0)
+      d1[4] = W2[3][4] d2[3] where h1[4] > 0 = (.1, 0, .5, 0)
+    so gb3 = .2, gW3[3] = .05*.4 + .25*.9 = .245, gW3[6] = .05*.2 - .1*.2 = -.01,
+    gb2[3] = .3, gb2[6] = -.15, gW2[3][1] = .25*.5 = .125,
+    gW2[3][4] = .05*.2 + .25*.2 = .06, gW2[6][4] = .15*.2 = .03 (a weight that
+    is zero still gets a gradient), gb1[1] = .25, gb1[4] = .6,
+    gW1[1][2] = .25*.75 = .1875, gW1[1][0] = .25*.4 = .1,
+    gW1[4][5] = .1*.1 + .5*.1 = .06, gW1[4][0] = .6*.4 = .24, and the
+    transposed slots W2[1][3], W2[4][3], W2[1][6] get 0."""
+    p, x = _relu_net()
+    t = np.array([1.0, 0.6, 0.5, 0.9])
+    loss, g = oracle.mlp_loss_grad(p, x, t)
+    assert abs(loss - 0.075) < 1e-12
+    want = {
+        _B3: 0.2, _W3 + 3: 0.245, _W3 + 6: -0.01,
+        _B2 + 3: 0.3, _B2 + 6: -0.15,
+        _W2 + 3 * 32 + 1: 0.125, _W2 + 3 * 32 + 4: 0.06, _W2 + 6 * 32 + 1: 0.0, _W2 + 6 * 32 + 4: 0.03,
+        _W2 + 1 * 32 + 3: 0.0, _W2 + 4 * 32 + 3: 0.0, _W2 + 1 * 32 + 6: 0.0,
+        _B1 + 1: 0.25, _B1 + 4: 0.6,
+        _W1 + 1 * 8 + 2: 0.1875, _W1 + 1 * 8 + 0: 0.1, _W1 + 4 * 8 + 5: 0.06, _W1 + 4 * 8 + 0: 0.24,
+        _W1 + 2 * 8 + 1: 0.0,
+    }
+    for i, v in want.items():
+        assert abs(g[i] - v) < 1e-12, (i, g[i], v)
+    # every parameter not listed has zero gradient here except the first-layer
+    # weights of units 1 and 4 on the inputs that are not zero (x[0], x[2], x[5])
+    nonzero = set(np.flatnonzero(np.abs(g) > 1e-15))
+    allowed = {i for i, v in want.items() if v != 0.0} | {_W1 + 1 * 8 + 5, _W1 + 4 * 8 + 2}
+    assert nonzero <= allowed, sorted(nonzero - allowed)
+    assert abs(g[_W1 + 1 * 8 + 5] - 0.25 * 0.1) < 1e-12   # d1[1] x[5] in sample 2
+    assert abs(g[_W1 + 4 * 8 + 2] - (0.1 * 0.25 + 0.5 * 0.75)) < 1e-12   # d1[4] x[2]
+
+
+def test_adam_second_step_bias_correction():
+    """Two steps at lr = 0.01 (beta1 0.9, beta2 0.999, eps 1e-8), worked out
+    by hand. Element 0, g = 1 then -1: m2 = .9 * .1 - .1 = -.01, v2 = .999 *
+    .001 + .001 = .001999; the corrections at t = 2 are 1 - .81 = .19 and
+    1 - .998001 = .001999, so m^ = -.01 / .19 and v^ = 1 and the second step
+    is +.01 * (.01 / .19) / (1 + eps). Element 1, g = 2 then 2: m2 = .38,
+    v2 = .007996, m^ = 2, v^ = 4, both steps are -.01 * 2 / (2 + eps). A
+    correction that ignored t (1 - beta instead of 1 - beta^t) would give m^ =
+    -.1, v^ = 1.999 for element 0."""
+    p = np.array([0.5, -0.25])
+    m = np.zeros(2)
+    v = np.zeros(2)
+    oracle.adam_step(p, np.array([1.0, 2.0]), m, v, 1, lr=0.01)
+    oracle.adam_step(p, np.array([-1.0, 2.0]), m, v, 2, lr=0.01)
+    eps = 1e-8
+    p0 = 0.5 - 0.01 * 1.0 / (1.0 + eps) + 0.01 * (0.01 / 0.19) / (1.0 + eps)
+    p1 = -0.25 - 2 * 0.01 * 2.0 / (2.0 + eps)
+    assert abs(p[0] - p0) < 1e-13 and abs(p[1] - p1) < 1e-13, (p, p0, p1)
+    assert np.allclose(m, [-0.01, 0.38], rtol=0, atol=1e-15)
+    assert np.allclose(v, [0.001999, 0.007996], rtol=0, atol=1e-15)
