@@ -1,15 +1,17 @@
 """Benchmark of the GB300 forward BWT block sort.
 
-Default workload: 64 blocks x 900,000 bytes (the bzip2 -9 block size) from
-three seeded sources (uniform bytes, order-3 Markov text-like, geometric
-runs), sorted by the learned bucketing in one batched, graph-captured call
-with inputs resident in HBM; the plain batched path on the same batch is
-timed beside it ("plain"). Prints one JSON line (rank 0). Metric: input MB/s
-(10^6 bytes of blocks per second).
+Default workload (learned-eval-1200x900000): 1,200 blocks of 900,000 bytes
+(the bzip2 -9 block size), 1.08 GB -- 1,080 held-out order-3 Markov blocks and
+120 uniform-random ones -- sorted by the learned-CDF bucketing in one batched,
+graph-captured call with inputs resident in HBM (the model is trained on the
+GPU first, outside the timed region); the plain batched path on the same batch
+is timed beside it ("plain"). The other four workloads are timed after it in
+their own launch modes ("workloads"). Prints one JSON line (rank 0). Metric:
+input MB/s (10^6 bytes of blocks per second).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1..5]
                   [--mode learned|graph|host|perblock|learned-host]
-                  [--impl ours|reference]
+                  [--impl ours|reference] [--no-workloads]
 
 --impl reference times the CPU oracle (the only other place this script runs
 it) on a bounded sample of the same workload.
@@ -39,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=5)
     ap.add_argument("--blocks", type=int, default=0, help="use only the first N blocks of the workload")
     ap.add_argument("--mode", choices=["host", "graph", "perblock", "learned", "learned-host", "inverse", "stages"],
                     default="learned",
@@ -57,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--verify", action="store_true", help="check every block with the host inverse")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the timing of the other workloads after the main one")
     return ap.parse_args()
 
 
@@ -190,18 +194,21 @@ def measured_peaks():
 
 
 def cpu_sample(w, max_blocks: int):
-    """A bounded sample of the workload for the oracle: the first blocks,
-    taking each source of the workload in turn."""
+    """A bounded sample of the workload for the oracle that keeps its mix of
+    sources: each source contributes blocks in proportion to its share of the
+    workload (at least one), spread evenly over that source's blocks."""
+    k = min(max_blocks, w.num_blocks)
     by_src: dict[int, list[int]] = {}
     for i, s in enumerate(w.sources):
         by_src.setdefault(s, []).append(i)
+    want = {s: max(1, int(round(k * len(ix) / w.num_blocks))) for s, ix in by_src.items()}
+    while sum(want.values()) > k and any(v > 1 for v in want.values()):
+        s = max(want, key=lambda q: want[q])
+        want[s] -= 1
     order = []
-    while len(order) < min(max_blocks, w.num_blocks):
-        for s in sorted(by_src):
-            if by_src[s]:
-                order.append(by_src[s].pop(0))
-            if len(order) >= max_blocks:
-                break
+    for s, ix in by_src.items():
+        m = min(want[s], len(ix))
+        order += [ix[int(j * len(ix) / m)] for j in range(m)]
     return w.subset(sorted(order))
 
 
@@ -238,14 +245,10 @@ def timed_cpu_baseline(w, cores: int, target_s: float = 12.0):
 # them (1-pass metrics) for the current kernel on one full-size pass of the
 # mixed3-64x900000 workload; None when the kernel has changed since.
 ONESWEEP_DRAM_BYTES_PER_KEY = 23.34
-
-
-def add_first_sort(acc, st, n):
-    """Accumulates the first sort's passes of one call (BWT_F_TIMING stats)."""
-    acc["ms"] += st["first_ms"]
-    acc["bytes"] += st["first_bytes"]
-    acc["launches"] += st["first_launches"]
-    acc["keys"] += n * st["first_launches"]
+# DRAM bytes (read + write) per rotation of the learned chunk sort
+# (k_chunk_sort_name<256, 4, 0>) as ncu counted them for the current kernel on
+# 24 blocks of the learned-eval workload; None when the kernel has changed since.
+CHUNK_SORT_DRAM_BYTES_PER_KEY = 18.0
 
 
 def reference_arm(args):
@@ -274,9 +277,70 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def make_model(args, local):
+    """Trains the learned-CDF model on the GPU (outside every timed region)
+    unless --model names a file; returns (path, description)."""
+    if args.model:
+        return args.model, None
+    import tempfile
+    from paper_1109_2348_gb300 import model as mdl
+    t0 = time.perf_counter()
+    trained = mdl.train(num_samples=args.train_samples, epochs=args.train_epochs, device=local)
+    path = os.path.join(tempfile.mkdtemp(), "bwt.model")
+    trained.save(path)
+    return path, {"trained_s": round(time.perf_counter() - t0, 2), "samples": args.train_samples,
+                  "epochs": args.train_epochs, "final_loss": float(trained.epoch_loss[-1]),
+                  "train_blocks": "100 x 900000 order-3 Markov, seeds 5000..5099"}
+
+
+class Runner:
+    """One workload resident in HBM and the plans that time it."""
+
+    def __init__(self, w, dev, local, flush):
+        import torch
+        self.w, self.dev, self.local, self.flush = w, dev, local, flush
+        self.buf, self.off = w.generate()
+        self.n = self.buf.size
+        self.sizes = np.diff(self.off.astype(np.int64))
+        self.pinned = torch.from_numpy(self.buf).pin_memory()
+        self.d_in = self.pinned.to(dev)
+        self.d_L = torch.empty_like(self.d_in)
+        self.d_p = torch.empty(w.num_blocks, dtype=torch.int32, device=dev)
+        self.stream = torch.cuda.current_stream()
+
+    def plan(self, flags, rb=0, tk=0, model_path=None):
+        from paper_1109_2348_gb300 import F_LEARNED, Plan
+        return Plan(max_blocks=self.w.num_blocks, max_total_bytes=self.n, max_block_bytes=int(self.sizes.max()),
+                    radix_bits=rb, tile_keys=tk, flags=flags, model_path=model_path if flags & F_LEARNED else None,
+                    device=self.local)
+
+    def warm(self, pl, count):
+        import torch
+        for _ in range(max(3, count)):
+            pl.forward_into(self.d_in, self.off, self.d_L, self.d_p, self.stream)
+        torch.cuda.synchronize()
+        assert pl.last_status() == 0
+
+    def timed(self, pl, steps):
+        """`steps` calls, L2 flushed before each, CUDA events on the launch
+        stream; no host synchronisation between the calls. Returns the step
+        times and the statistics of the last call (every step is the same call
+        on the same batch)."""
+        import torch
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            self.flush.zero_()
+            ev[i][0].record(self.stream)
+            pl.forward_into(self.d_in, self.off, self.d_L, self.d_p, self.stream)
+            ev[i][1].record(self.stream)
+        torch.cuda.synchronize()
+        assert pl.last_status() == 0
+        return [a.elapsed_time(b) for a, b in ev], pl.stats()
+
+
 def ours(args):
     import torch
-    from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, F_PER_BLOCK_LAUNCH, F_TIMING, Plan
+    from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, F_PER_BLOCK_LAUNCH, F_TIMING
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)  # before the process group, so its communicator is on this rank's GPU
@@ -284,134 +348,92 @@ def ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", local)
-    w = rank_workload(args.config, args.blocks, rank, world)
-    buf, off = w.generate()
-    n = buf.size
     learned = args.mode.startswith("learned")
     flags = {"host": F_TIMING, "graph": F_GRAPH, "perblock": F_PER_BLOCK_LAUNCH, "learned": F_LEARNED | F_GRAPH,
              "learned-host": F_LEARNED}[args.mode]
-    sizes = np.diff(off.astype(np.int64))
-    model_info = None
-    if learned and not args.model:
-        import tempfile
-        from paper_1109_2348_gb300 import model as mdl
-        t0 = time.perf_counter()
-        trained = mdl.train(num_samples=args.train_samples, epochs=args.train_epochs, device=local)
-        args.model = os.path.join(tempfile.mkdtemp(), "bwt.model")
-        trained.save(args.model)
-        model_info = {"trained_s": round(time.perf_counter() - t0, 2), "samples": args.train_samples,
-                      "epochs": args.train_epochs, "final_loss": float(trained.epoch_loss[-1]),
-                      "train_blocks": "100 x 900000 order-3 Markov, seeds 5000..5099"}
-
-    def make_plan(fl, rb=None, tk=None):
-        return Plan(max_blocks=w.num_blocks, max_total_bytes=n, max_block_bytes=int(sizes.max()),
-                    radix_bits=args.radix_bits if rb is None else rb, tile_keys=args.tile if tk is None else tk,
-                    flags=fl, model_path=args.model if fl & F_LEARNED else None, device=local)
-
-    plan = make_plan(flags)
-    pinned = torch.from_numpy(buf).pin_memory()
-    d_in = pinned.to(dev)
-    d_L = torch.empty_like(d_in)
-    d_p = torch.empty(w.num_blocks, dtype=torch.int32, device=dev)
+    model_path, model_info = make_model(args, local) if learned or (rank == 0 and not args.no_workloads) \
+        else (None, None)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
-    stream = torch.cuda.current_stream()
+    R = Runner(rank_workload(args.config, args.blocks, rank, world), dev, local, flush)
+    w, n = R.w, R.n
 
+    plan = R.plan(flags, args.radix_bits, args.tile, model_path)
     tuned = None
     if args.autotune:
         import tempfile
         cache = args.autotune_cache or os.path.join(tempfile.mkdtemp(), "autotune.jsonl")
-        rb, tk, ms = plan.autotune(d_in, off, d_L, d_p, cache_path=cache, repeats=3, stream=stream)
+        rb, tk, ms = plan.autotune(R.d_in, R.off, R.d_L, R.d_p, cache_path=cache, repeats=3, stream=R.stream)
         tuned = {"radix_bits": rb, "tile_keys": tk, "ms": round(ms, 4)}
     rb_used = tuned["radix_bits"] if tuned else args.radix_bits
     tk_used = tuned["tile_keys"] if tuned else args.tile
 
-    def warm(pl, outs):
-        for _ in range(max(3, args.warmup)):
-            pl.forward_into(d_in, off, outs[0], outs[1], stream)
-        torch.cuda.synchronize()
-
-    def timed_steps(pl, radix=None):
-        """K steps, L2 flushed before each, CUDA events on the launch stream."""
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        launches, st = 0, None
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(stream)
-            pl.forward_into(d_in, off, d_L, d_p, stream)
-            ev[i][1].record(stream)
-            st = pl.stats()
-            launches += st["kernel_launches"]
-            if radix is not None:
-                add_first_sort(radix, st, n)
-        torch.cuda.synchronize()
-        return [a.elapsed_time(b) for a, b in ev], st, launches
-
     sampler = ClockSampler(local)
     sampler.start()
-    warm(plan, (d_L, d_p))
-    radix = {"ms": 0.0, "bytes": 0.0, "launches": 0, "keys": 0.0}
+    R.warm(plan, args.warmup)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.begin()
-    step_ms, stats, launches = timed_steps(plan, radix if args.mode == "host" else None)
+    step_ms, stats = R.timed(plan, args.steps)
     sampler.end()
     clocks = sampler.stop()
+    launches = stats["kernel_launches"] * args.steps
     learned_stats = {k: stats[k] for k in ("blocks_routed_plain", "blocks_routed_flat", "buckets_overflowed",
-                                           "keys_overflowed", "max_bucket", "bucket_sq_sum", "buckets_nonempty")} \
-        if learned else None
+                                           "keys_overflowed", "max_bucket", "bucket_sq_sum", "buckets_nonempty",
+                                           "chunk_keys")} if learned else None
     t_ms = reduce_max(float(np.sum(step_ms)), world, dev)
     value = job_value(n, world, args.steps, t_ms)
 
     if args.verify and rank == 0:
         from paper_1109_2348_gb300 import bwt_inverse_check
-        Lh = d_L.cpu().numpy()
-        ph = d_p.cpu().numpy()
+        Lh = R.d_L.cpu().numpy()
+        ph = R.d_p.cpu().numpy()
         for b in range(w.num_blocks):
-            s, e = int(off[b]), int(off[b + 1])
-            assert bwt_inverse_check(Lh[s:e], int(ph[b]), buf[s:e]) == 0, f"block {b} fails the inverse check"
+            s, e = int(R.off[b]), int(R.off[b + 1])
+            assert bwt_inverse_check(Lh[s:e], int(ph[b]), R.buf[s:e]) == 0, f"block {b} fails the inverse check"
 
     e2e = None
     if not args.no_e2e:
         # End to end through the public call, two buffer sets in flight: step
         # k+1's host->device copy and step k-1's device->host copy run on the
         # copy engines while step k sorts; every step's copies are inside the
-        # timed region.
-        plan2 = make_plan(flags, rb_used, tk_used)
+        # timed region, and no call waits on the host.
+        plan2 = R.plan(flags, rb_used, tk_used, model_path)
         sets = []
         for pl in (plan, plan2):
-            sets.append({"plan": pl, "in": torch.empty_like(d_in), "L": torch.empty_like(d_in),
-                         "p": torch.empty_like(d_p), "hL": torch.empty(n, dtype=torch.uint8).pin_memory(),
+            sets.append({"plan": pl, "in": torch.empty_like(R.d_in), "L": torch.empty_like(R.d_in),
+                         "p": torch.empty_like(R.d_p), "hL": torch.empty(n, dtype=torch.uint8).pin_memory(),
                          "hp": torch.empty(w.num_blocks, dtype=torch.int32).pin_memory(),
                          "st": torch.cuda.Stream(device=dev)})
         for st_ in sets:  # capture / warm each set's own buffers
-            st_["in"].copy_(d_in)
+            st_["in"].copy_(R.d_in)
             for _ in range(2):
-                st_["plan"].forward_into(st_["in"], off, st_["L"], st_["p"], st_["st"])
+                st_["plan"].forward_into(st_["in"], R.off, st_["L"], st_["p"], st_["st"])
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        e0.record(R.stream)
         for st_ in sets:
             st_["st"].wait_event(e0)
         with torch.cuda.stream(sets[0]["st"]):
-            sets[0]["in"].copy_(pinned, non_blocking=True)
+            sets[0]["in"].copy_(R.pinned, non_blocking=True)
         for i in range(args.steps):
             cur, nxt = sets[i % 2], sets[(i + 1) % 2]
             if i + 1 < args.steps:
                 with torch.cuda.stream(nxt["st"]):
-                    nxt["in"].copy_(pinned, non_blocking=True)
-            cur["plan"].forward_into(cur["in"], off, cur["L"], cur["p"], cur["st"])
+                    nxt["in"].copy_(R.pinned, non_blocking=True)
+            cur["plan"].forward_into(cur["in"], R.off, cur["L"], cur["p"], cur["st"])
             with torch.cuda.stream(cur["st"]):
                 cur["hL"].copy_(cur["L"], non_blocking=True)
                 cur["hp"].copy_(cur["p"], non_blocking=True)
         for st_ in sets:
-            stream.wait_stream(st_["st"])
-        e1.record(stream)
+            R.stream.wait_stream(st_["st"])
+        e1.record(R.stream)
         torch.cuda.synchronize()
+        assert all(st_["plan"].last_status() == 0 for st_ in sets)
         e_ms = reduce_max(e0.elapsed_time(e1), world, dev)
-        assert np.array_equal(sets[(args.steps - 1) % 2]["hL"].numpy(), d_L.cpu().numpy())
+        assert np.array_equal(sets[(args.steps - 1) % 2]["hL"].numpy(), R.d_L.cpu().numpy())
         e2e = {"value": round(n * world * args.steps / (e_ms / 1e3) / 1e6, 3), "unit": "MB/s",
-               "h2d_bytes_per_step": int(n + off.nbytes), "d2h_bytes_per_step": int(n + 4 * w.num_blocks),
+               "h2d_bytes_per_step": int(n + R.off.nbytes), "d2h_bytes_per_step": int(n + 4 * w.num_blocks),
                "pipelined": "2 buffer sets: copies of steps k-1 and k+1 overlap step k"}
         plan2.close()
         del sets
@@ -420,40 +442,90 @@ def ours(args):
     plain_cmp = None
     if learned or args.compare_plain:
         # the plain path on the same batch, batched the same way (graph)
-        pg = make_plan(F_GRAPH, rb_used, tk_used)
-        warm(pg, (d_L, d_p))
-        pms, _, _ = timed_steps(pg)
+        pg = R.plan(F_GRAPH, rb_used, tk_used)
+        R.warm(pg, args.warmup)
+        pms, pst = R.timed(pg, args.steps)
         pg.close()
         p_ms = reduce_max(float(np.sum(pms)), world, dev)
         plain_cmp = {"value": round(job_value(n, world, args.steps, p_ms), 3), "unit": "MB/s",
-                     "mode": "plain radix, batched (graph)", "ms_per_step": round(p_ms / args.steps, 4)}
-    if args.mode != "host":
-        # the roofline's timing: the same batch in host-driven mode with CUDA
-        # events around every radix launch of the first sort
-        th = make_plan(F_TIMING, rb_used, tk_used)
-        warm(th, (d_L, d_p))
-        timed_steps(th, radix)
-        th.close()
+                     "mode": "plain radix, batched (graph)", "ms_per_step": round(p_ms / args.steps, 4),
+                     "rounds": pst["rounds"]}
     peak, peak_kind = measured_peaks()
-    roof = None
-    if radix["ms"] > 0:
-        # the first sort's u64 onesweep passes: algorithmic bytes (13 per key for
-        # the pass that packs the keys from the bytes, 24 for the others) over
-        # their CUDA-event time; traffic = the DRAM bytes per key ncu measured for
-        # the current kernel, times the keys of one launch
-        achieved = radix["bytes"] / (radix["ms"] / 1e3) / 1e9
-        per_launch_keys = radix["keys"] / max(1, radix["launches"])
-        traffic = None if ONESWEEP_DRAM_BYTES_PER_KEY is None else \
-            round(ONESWEEP_DRAM_BYTES_PER_KEY * per_launch_keys)
-        roof = {"bound": "hbm", "kernel": "k_onesweep<u64, 8, 4096> (first-sort radix pass)",
-                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_kind + " hbm_gbs",
-                "traffic": traffic, "algorithmic_bytes_per_launch": round(radix["bytes"] / max(1, radix["launches"])),
-                "launches_timed": radix["launches"],
-                "avg_launch_ms": round(radix["ms"] / max(1, radix["launches"]), 4)}
+
+    def first_sort_roofline():
+        # the plain first sort's u64 onesweep passes in host-driven mode with
+        # CUDA events around every radix launch on the launch stream (events
+        # cannot sit between the kernels of a graph replay): algorithmic bytes
+        # (13 per key for the pass that packs the keys from the bytes, 24 for
+        # the others) over their event time; traffic = the DRAM bytes per key
+        # ncu measured for the current kernel, times the keys of one launch
+        th = R.plan(F_TIMING, rb_used, tk_used)
+        R.warm(th, 3)
+        acc = {"ms": 0.0, "bytes": 0.0, "launches": 0, "keys": 0.0}
+        for _ in range(max(1, args.steps // 2)):
+            R.flush.zero_()
+            th.forward_into(R.d_in, R.off, R.d_L, R.d_p, R.stream)
+            st = th.stats()
+            acc["ms"] += st["first_ms"]
+            acc["bytes"] += st["first_bytes"]
+            acc["launches"] += st["first_launches"]
+            acc["keys"] += n * st["first_launches"]
+        th.close()
+        achieved = acc["bytes"] / (acc["ms"] / 1e3) / 1e9
+        per_launch_keys = acc["keys"] / max(1, acc["launches"])
+        return {"bound": "hbm", "kernel": f"k_onesweep<u64, {stats['radix_bits']}, {stats['tile_keys']}> "
+                                          "(plain first-sort radix pass)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "peak_source": peak_kind + " hbm_gbs",
+                "traffic": None if ONESWEEP_DRAM_BYTES_PER_KEY is None else
+                round(ONESWEEP_DRAM_BYTES_PER_KEY * per_launch_keys),
+                "algorithmic_bytes_per_launch": round(acc["bytes"] / max(1, acc["launches"])),
+                "launches_timed": acc["launches"], "avg_launch_ms": round(acc["ms"] / max(1, acc["launches"]), 4)}
+
+    def chunk_sort_roofline():
+        # the learned step's dominant kernel, the 256-thread chunk sort, timed
+        # in host-driven learned mode with CUDA events around its launch:
+        # 20 algorithmic bytes per rotation it sorts (8-byte key and 4-byte
+        # index read, SA entry and rank written) over its event time
+        th = R.plan(F_TIMING | F_LEARNED, rb_used, tk_used, model_path)
+        R.warm(th, 3)
+        ms = by = 0.0
+        la = keys = 0
+        for _ in range(max(1, args.steps // 2)):
+            R.flush.zero_()
+            th.forward_into(R.d_in, R.off, R.d_L, R.d_p, R.stream)
+            st = th.stats()
+            ms += st["chunk_ms"]
+            by += st["chunk_bytes"]
+            la += st["chunk_launches"]
+            keys += st["chunk_keys"]
+        th.close()
+        if ms <= 0 or la == 0:
+            return None
+        achieved = by / (ms / 1e3) / 1e9
+        per_launch_keys = keys / la
+        return {"bound": "hbm", "kernel": "k_chunk_sort_name<256, 4, 0> (learned chunk sort: sort, SA, naming)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "peak_source": peak_kind + " hbm_gbs",
+                "traffic": None if CHUNK_SORT_DRAM_BYTES_PER_KEY is None else
+                round(CHUNK_SORT_DRAM_BYTES_PER_KEY * per_launch_keys),
+                "algorithmic_bytes_per_launch": round(by / la), "bytes_per_rotation": 20,
+                "rotations_per_launch": round(per_launch_keys), "launches_timed": la,
+                "avg_launch_ms": round(ms / la, 4)}
+
+    roof, roof_plain = None, None
+    if args.mode not in ("perblock",):
+        roof_plain = first_sort_roofline()
+        roof = chunk_sort_roofline() if learned else roof_plain
+    if roof is None:
+        roof = roof_plain
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = timed_cpu_baseline(w, os.cpu_count() or 1)
+    del R
+    others = None
+    if rank == 0 and world == 1 and not args.no_workloads:
+        others = other_workloads(args, dev, local, flush, model_path)
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "MB/s", "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": round(t_ms / args.steps, 4),
@@ -467,15 +539,48 @@ def ours(args):
                 "cpu_baseline": cpu, "step_ms": [round(x, 3) for x in step_ms]}
         if plain_cmp:
             line["plain"] = plain_cmp
+        if learned and roof_plain is not None:
+            line["roofline_plain_first_sort"] = roof_plain
         if tuned:
             line["config"]["autotuned"] = tuned
         if learned_stats:
             line["config"]["learned"] = learned_stats
         if model_info:
             line["config"]["model"] = model_info
+        if others:
+            line["workloads"] = others
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def other_workloads(args, dev, local, flush, model_path):
+    """The other workloads, each timed in its own launch modes on the same
+    GPU (inputs resident in HBM, L2 flushed before every step, CUDA events on
+    the launch stream): input MB/s and ms per step."""
+    from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, F_PER_BLOCK_LAUNCH
+    runs = {1: [("graph", F_GRAPH)], 2: [("learned", F_LEARNED | F_GRAPH), ("graph", F_GRAPH)],
+            3: [("graph", F_GRAPH)], 4: [("graph", F_GRAPH), ("perblock", F_PER_BLOCK_LAUNCH)],
+            5: [("learned", F_LEARNED | F_GRAPH), ("graph", F_GRAPH)]}
+    out = {}
+    steps = max(3, min(args.steps, 10))
+    for cfg in (1, 2, 3, 4, 5):
+        if cfg == args.config:
+            continue
+        R = Runner(workload(cfg), dev, local, flush)
+        res = {"workload": R.w.name, "blocks": R.w.num_blocks, "bytes": R.n}
+        for label, fl in runs[cfg]:
+            pl = R.plan(fl, model_path=model_path)
+            R.warm(pl, 3)
+            k = 2 if label == "perblock" else steps
+            ms, st = R.timed(pl, k)
+            pl.close()
+            t = float(np.sum(ms))
+            res[label] = {"value": round(R.n * k / (t / 1e3) / 1e6, 3), "unit": "MB/s",
+                          "ms_per_step": round(t / k, 4), "rounds": st["rounds"], "steps": k}
+        out[f"config{cfg}"] = res
+        del R
+    return out
 
 
 def inverse_bench(args):

@@ -16,13 +16,19 @@
  *
  * Memory: every pointer named d_* is device memory owned by the caller. The
  * plan owns all scratch; it is sized at plan creation from the descriptor
- * and nothing is allocated per call. All entry points return a bwt_status and
- * never abort the process; kernels never trap. Device-side failures (a
- * bounded wait that ran out, a capacity overflow) are recorded in a device
- * status word and returned by the call, which synchronises its stream before
- * returning.
+ * (including the learned bucketing's tables when BWT_F_LEARNED is set), so
+ * bwt_forward_batch allocates nothing. bwt_inverse_batch and bwt_mtf_encode
+ * allocate their extra scratch once, on their first call on the plan; the
+ * MLP training calls allocate temporaries (each says so). All entry points
+ * return a bwt_status and never abort the process; kernels never trap.
+ * Device-side failures (a bounded wait that ran out, a capacity overflow) are
+ * recorded in a device status word: the synchronous calls return it, and an
+ * asynchronous bwt_forward_batch (BWT_F_GRAPH) leaves it for
+ * bwt_plan_last_status.
  *
- * Thread safety: a plan may be used by one host thread at a time.
+ * Thread safety and ordering: a plan may be used by one host thread at a
+ * time, and its calls must run in order on the GPU (one stream, or streams
+ * the caller orders with events): consecutive calls share the plan's scratch.
  */
 #ifndef BWT_GB300_H
 #define BWT_GB300_H
@@ -96,6 +102,13 @@ typedef struct {
     uint64_t first_launches;    /* the first sort's u64 passes alone (a subset of radix_launches) */
     double first_ms;            /* their summed device time (only with BWT_F_TIMING) */
     double first_bytes;         /* their algorithmic HBM bytes (13 per key for the first pass, 24 after) */
+    uint64_t chunk_launches;    /* learned bucketing: timed launches of the 256-thread chunk sort (only
+                                   with BWT_F_TIMING and without BWT_F_GRAPH) */
+    double chunk_ms;            /* their summed device time */
+    uint64_t chunk_keys;        /* learned bucketing: rotations in packed chunks (the ones that chunk
+                                   sort sorts: the bucketed blocks' rotations outside over-full buckets) */
+    double chunk_bytes;         /* their algorithmic HBM bytes: 20 per rotation (8-byte key and 4-byte
+                                   index read, 4-byte SA entry and 4-byte rank written) */
 } bwt_stats;
 
 /* Create a plan on CUDA device `device` (made current for the call). The plan
@@ -110,14 +123,24 @@ bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt_plan** out
  *   d_in        device, uint8[offsets[num_blocks]]: the blocks, concatenated.
  *   offsets     uint64[num_blocks + 1], offsets[0] = 0, strictly increasing
  *               (empty blocks are BWT_EINVAL). Host or device memory; device
- *               offsets are copied to the host once per call.
+ *               offsets are copied to the host in stream order, which waits
+ *               for `stream` (pass host offsets to avoid that).
  *   num_blocks  1 .. max_blocks.
  *   d_L         device, uint8[offsets[num_blocks]]: the L column, same layout.
  *   d_primary   device, int32[num_blocks].
  *   stream      cudaStream_t to run on (NULL = the legacy default stream).
- * The work is stream-ordered; the call synchronises `stream` before it
- * returns so it can report device-side status. Outputs are undefined unless
- * BWT_OK is returned. d_in must not alias d_L. */
+ * Argument errors are returned at once. The work is stream-ordered:
+ *   - with BWT_F_GRAPH (and not BWT_F_PER_BLOCK_LAUNCH) the call only
+ *     enqueues it -- the block and tile tables when the layout differs from
+ *     the plan's last one, then the batch's CUDA graph -- and returns BWT_OK
+ *     without waiting for the GPU (with host offsets). The device-side status
+ *     and the statistics of the call are read by bwt_plan_last_status and
+ *     bwt_plan_stats, which wait for the call's work to finish; they describe
+ *     the most recent call only. Outputs are valid once the stream has
+ *     reached the end of the call and bwt_plan_last_status is BWT_OK;
+ *   - the other modes decide the doubling rounds on the host, synchronise
+ *     `stream` and return the device-side status themselves.
+ * d_in must not alias d_L. */
 bwt_status bwt_forward_batch(bwt_plan* plan, const uint8_t* d_in, const uint64_t* offsets,
                              uint32_t num_blocks, uint8_t* d_L, int32_t* d_primary, void* stream);
 
@@ -205,10 +228,14 @@ bwt_status bwt_plan_destroy(bwt_plan* plan);
 
 /* ---- plan control and introspection (no paper counterpart) ----------- */
 
-/* Status recorded by the last bwt_forward_batch call on this plan. */
+/* Status of the last call on this plan. For an asynchronous
+ * bwt_forward_batch this waits until the call's work has finished on the GPU
+ * (immediately, if the caller has synchronised) and returns its device-side
+ * status: BWT_OK, BWT_ETIMEOUT, BWT_ECAPACITY or BWT_EINVAL. */
 bwt_status bwt_plan_last_status(const bwt_plan* plan);
 
-/* Copies the statistics of the last call into *out. */
+/* Copies the statistics of the last call into *out (waiting for an
+ * asynchronous bwt_forward_batch to finish, as bwt_plan_last_status does). */
 bwt_status bwt_plan_stats(const bwt_plan* plan, bwt_stats* out);
 
 /* Changes the radix digit width (8 or 11) and tile size (1024, 2048, 4096)

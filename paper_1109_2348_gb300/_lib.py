@@ -60,6 +60,10 @@ class Stats(ctypes.Structure):
         ("first_launches", ctypes.c_uint64),
         ("first_ms", ctypes.c_double),
         ("first_bytes", ctypes.c_double),
+        ("chunk_launches", ctypes.c_uint64),
+        ("chunk_ms", ctypes.c_double),
+        ("chunk_keys", ctypes.c_uint64),
+        ("chunk_bytes", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:

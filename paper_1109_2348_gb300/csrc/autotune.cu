@@ -128,6 +128,7 @@ extern "C" bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, con
                 status = bwt_forward_batch(plan, d_in, offsets, num_blocks, d_L, d_primary, stream);
                 cudaEventRecord(e1, st);
                 cudaEventSynchronize(e1);
+                if (status == BWT_OK) status = bwt_plan_last_status(plan);  // device-side status of the run
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
                 total += ms;
@@ -156,6 +157,7 @@ extern "C" bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, con
                 status = bwt_forward_batch(plan, d_in, offsets, num_blocks, d_L, d_primary, stream);
                 cudaEventRecord(e1, st);
                 cudaEventSynchronize(e1);
+                if (status == BWT_OK) status = bwt_plan_last_status(plan);  // device-side status of the run
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
                 total += ms;
@@ -174,6 +176,7 @@ extern "C" bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, con
     bwt_plan_set_round_radix(plan, best_r);
     // one run with the chosen configuration: outputs and statistics are its
     if ((status = bwt_forward_batch(plan, d_in, offsets, num_blocks, d_L, d_primary, stream)) != BWT_OK) return status;
+    if ((status = bwt_plan_last_status(plan)) != BWT_OK) return status;
     if (out_radix_bits) *out_radix_bits = best_b;
     if (out_tile_keys) *out_tile_keys = best_t;
     if (out_ms) *out_ms = best;

@@ -1,5 +1,6 @@
 // BWT_F_GRAPH: the whole batch as one CUDA graph, replayed when the block
-// layout and buffers repeat.
+// layout and buffers repeat (the plan keeps the last few graphs, so callers
+// that alternate between buffer sets replay too).
 //
 // Graph = reset -> first stage (plain: first sort + naming; with
 //         BWT_F_LEARNED: the learned first stage) -> set loop condition ->
@@ -41,6 +42,25 @@ static std::vector<uint64_t> graph_key_of(bwt_plan* p, const uint8_t* d_in, uint
     return k;
 }
 
+// Launches a cached graph on the caller's stream and records its event; the
+// kernel counts of the call come from the graph's own (filled in by
+// graph_stats once the call has finished).
+static bwt_status launch_entry(bwt_plan* p, GraphEntry& ge, cudaStream_t st, bool replay) {
+    cudaError_t e = cudaGraphLaunch(ge.exec, st);
+    if (e != cudaSuccess) return record_cuda(e, "cudaGraphLaunch");
+    e = cudaEventRecord(ge.launched, st);
+    if (e != cudaSuccess) return record_cuda(e, "cudaEventRecord");
+    ge.last_use = ++p->graph_use;
+    p->graph_main_kernels = ge.main_kernels;
+    p->graph_body_kernels = ge.body_kernels;
+    p->graph_main_radix = ge.main_radix;
+    p->graph_body_radix = ge.body_radix;
+    p->stats.graph_replayed = replay ? 1u : 0u;
+    p->stats.kernel_launches = 0;
+    p->stats.radix_launches = 0;
+    return BWT_OK;
+}
+
 bwt_status bwt::run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st) {
     const bool learned = (p->desc.flags & BWT_F_LEARNED) != 0;
     if (learned) {
@@ -49,20 +69,16 @@ bwt_status bwt::run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_
         if (s != BWT_OK) return s;
     }
     std::vector<uint64_t> key = graph_key_of(p, d_in, d_L, d_primary);
-    if (p->graph_exec && key == p->graph_key) {
-        cudaError_t e = cudaGraphLaunch(p->graph_exec, st);
-        if (e != cudaSuccess) return record_cuda(e, "cudaGraphLaunch");
-        p->stats.graph_replayed = 1;
-        p->stats.kernel_launches = 0;
-        p->stats.radix_launches = 0;
-        return BWT_OK;
+    for (auto& ge : p->graphs) {
+        if (ge.key != key) continue;
+        return launch_entry(p, ge, st, true);
     }
-    drop_graph(p);
 
     bwt_status status = BWT_OK;
     cudaStream_t cs = nullptr, bs = nullptr;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaEvent_t launched = nullptr;
     cudaGraphConditionalHandle cond;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -110,22 +126,39 @@ bwt_status bwt::run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_
     CKG(cudaStreamEndCapture(cs, &g));
     p->capturing = false;
     CKG(cudaGraphInstantiate(&exec, g, 0));
-    p->graph = g;
-    p->graph_exec = exec;
-    p->graph_key = key;
-    p->graph_main_kernels = (k1 - k0) + (k3 - k2);
-    p->graph_body_kernels = k2 - k1;
-    p->graph_main_radix = (r1 - r0) + (r3 - r2);
-    p->graph_body_radix = r2 - r1;
+    CKG(cudaEventCreateWithFlags(&launched, cudaEventDisableTiming));
     cudaStreamDestroy(cs);
     cudaStreamDestroy(bs);
-    p->stats.kernel_launches = 0;
-    p->stats.radix_launches = 0;
+    cs = bs = nullptr;
     {
-        cudaError_t e = cudaGraphLaunch(exec, st);
-        if (e != cudaSuccess) return record_cuda(e, "cudaGraphLaunch");
+        // the least recently used graph makes room (its last launch may still run)
+        if (p->graphs.size() >= kGraphCache) {
+            size_t lru = 0;
+            for (size_t i = 1; i < p->graphs.size(); ++i)
+                if (p->graphs[i].last_use < p->graphs[lru].last_use) lru = i;
+            GraphEntry& old = p->graphs[lru];
+            if (old.launched) {
+                cudaEventSynchronize(old.launched);
+                cudaEventDestroy(old.launched);
+            }
+            if (old.exec) cudaGraphExecDestroy(old.exec);
+            if (old.graph) cudaGraphDestroy(old.graph);
+            p->graphs.erase(p->graphs.begin() + (long)lru);
+        }
+        GraphEntry ge;
+        ge.key = std::move(key);
+        ge.graph = g;
+        ge.exec = exec;
+        g = nullptr;
+        exec = nullptr;
+        ge.main_kernels = (k1 - k0) + (k3 - k2);
+        ge.body_kernels = k2 - k1;
+        ge.main_radix = (r1 - r0) + (r3 - r2);
+        ge.body_radix = r2 - r1;
+        ge.launched = launched;
+        p->graphs.push_back(std::move(ge));
     }
-    return BWT_OK;
+    return launch_entry(p, p->graphs.back(), st, false);
 
 fail:
     p->capturing = false;
@@ -139,6 +172,7 @@ fail:
         cudaStreamEndCapture(bs, &tmp);
         cudaStreamDestroy(bs);
     }
+    if (launched) cudaEventDestroy(launched);
     if (exec) cudaGraphExecDestroy(exec);
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();

@@ -968,9 +968,19 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     uint32_t* chunk_counter = ctrl + CTRL_TILE_CTR + 58;  // control words no radix pass uses
     uint32_t* big_counter = ctrl + CTRL_TILE_CTR + 59;
     CKL(cudaMemsetAsync(chunk_counter, 0, 8, st));
+    const bool timing = !p->events.empty() && !p->capturing && p->ev_used + 2 <= p->events.size();
+    if (timing) CKL(cudaEventRecord(p->events[p->ev_used], st));
     k_chunk_sort_name<MS_NT, 4, 0><<<sms * p->chunk_sort_ctas, MS_NT, CHUNK_SORT_SMEM, st>>>(
         p->keys[0], p->vals[0], p->blocks, aux, p->rank, bins_of(p, 0), ctrl, chunk_counter);
     CKL(cudaGetLastError());
+    if (timing) {
+        CKL(cudaEventRecord(p->events[p->ev_used + 1], st));
+        EvMeta m{};
+        m.ctrl_word = -1;
+        m.chunk_sort = true;
+        p->ev_meta.push_back(m);
+        p->ev_used += 2;
+    }
     // over-full buckets up to BIG_CAP: one 1,024-thread CTA each
     k_chunk_sort_name<BIG_NT, 1, 1><<<sms, BIG_NT, BIG_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks, aux,
                                                                         p->rank, bins_of(p, 0), ctrl, big_counter);
@@ -1040,8 +1050,10 @@ void bwt::learned_stats(bwt_plan* p) {
             if (r == 2u) p->stats.blocks_routed_flat++;
             p->stats.buckets_overflowed += bs[1];
             p->stats.keys_overflowed += bs[0];
+            p->stats.chunk_keys += p->h_blocks[b].n - bs[0];
         }
     }
+    p->stats.chunk_bytes = 20.0 * (double)p->stats.chunk_keys;
     p->stats.radix_keys += (uint64_t)p->learned_overflow_passes * p->stats.keys_overflowed;
 }
 

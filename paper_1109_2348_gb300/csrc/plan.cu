@@ -128,14 +128,17 @@ void bwt::free_plan_memory(bwt_plan* p) {
     for (int s = 0; s < 2; ++s)
         for (int c = 0; c < NCLS; ++c) F(p->bins[s][c]);
     F(p->splitters); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->route_first); F(p->bstats); F(p->tiles_aux); F(p->inv_slots); F(p->inv_items); F(p->mtf_lists);
-    FH(p->h_ctrl); FH(p->h_tiles); FH(p->h_blocks); FH(p->h_off);
+    drop_graph(p);
+    FH(p->h_ctrl); FH(p->h_off);
+    for (int s = 0; s < 2; ++s) {
+        FH(p->stage_tiles[s]);
+        FH(p->stage_blocks[s]);
+        if (p->stage_ev[s]) cudaEventDestroy(p->stage_ev[s]);
+    }
+    if (p->done_ev) cudaEventDestroy(p->done_ev);
     FH(p->h_route); FH(p->h_bstats); FH(p->h_inv_items);
     for (auto& e : p->events) cudaEventDestroy(e);
     p->events.clear();
-    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
-    if (p->graph) cudaGraphDestroy(p->graph);
-    p->graph_exec = nullptr;
-    p->graph = nullptr;
 }
 
 extern "C" bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt_plan** out) {
@@ -195,10 +198,19 @@ extern "C" bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt
     for (int par = 0; par < 2; ++par)
         for (int c = 0; c < NCLS; ++c) A(dev_alloc(&p->bins[par][c], p->bincap[c], &total));
     A(host_alloc(&p->h_ctrl, CTRL_WORDS));
-    A(host_alloc(&p->h_tiles, p->cap_tiles0));
-    A(host_alloc(&p->h_blocks, B));
+    for (int sl = 0; sl < 2; ++sl) {
+        A(host_alloc(&p->stage_tiles[sl], p->cap_tiles0));
+        A(host_alloc(&p->stage_blocks[sl], B));
+        if (s == BWT_OK && cudaEventCreateWithFlags(&p->stage_ev[sl], cudaEventDisableTiming) != cudaSuccess)
+            s = BWT_ECUDA;
+    }
+    p->h_tiles = p->stage_tiles[0];
+    p->h_blocks = p->stage_blocks[0];
+    if (s == BWT_OK && cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming) != cudaSuccess) s = BWT_ECUDA;
     A(host_alloc(&p->h_off, (size_t)B + 1));
     A(host_alloc(&p->h_inv_items, 2 * ((size_t)B + 1)));
+    // the learned bucketing's tables, so that no forward call allocates
+    if (s == BWT_OK && (desc->flags & BWT_F_LEARNED)) s = ensure_learned_buffers(p);
     p->device_bytes = total;
     if (s == BWT_OK && (desc->flags & BWT_F_TIMING)) {
         p->events.resize(512);
@@ -228,11 +240,14 @@ extern "C" bwt_status bwt_plan_destroy(bwt_plan* plan) {
 }
 
 extern "C" bwt_status bwt_plan_last_status(const bwt_plan* plan) {
-    return plan ? plan->last : BWT_EINVAL;
+    if (!plan) return BWT_EINVAL;
+    resolve_pending(const_cast<bwt_plan*>(plan));
+    return plan->last;
 }
 
 extern "C" bwt_status bwt_plan_stats(const bwt_plan* plan, bwt_stats* out) {
     if (!plan || !out) return BWT_EINVAL;
+    resolve_pending(const_cast<bwt_plan*>(plan));
     *out = plan->stats;
     return BWT_OK;
 }
@@ -261,11 +276,15 @@ extern "C" bwt_status bwt_plan_debug_waits(bwt_plan* plan, uint32_t spin_limit, 
 }
 
 void bwt::drop_graph(bwt_plan* p) {
-    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
-    if (p->graph) cudaGraphDestroy(p->graph);
-    p->graph_exec = nullptr;
-    p->graph = nullptr;
-    p->graph_key.clear();
+    for (auto& g : p->graphs) {
+        if (g.launched) {
+            cudaEventSynchronize(g.launched);  // its last launch may still run
+            cudaEventDestroy(g.launched);
+        }
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    p->graphs.clear();
 }
 
 // ---------------------------------------------------------------------------
@@ -279,8 +298,8 @@ bwt_status bwt::prepare_batch(bwt_plan* p, const uint64_t* offsets, uint32_t nb,
         cudaGetLastError();
         attr.type = cudaMemoryTypeUnregistered;
     }
-    CK(cudaStreamSynchronize(st));  // the pinned staging tables of the last call are free again
     if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) {
+        // device offsets: read in stream order, which waits for the stream
         CK(cudaMemcpyAsync(p->h_off, offsets, sizeof(uint64_t) * (nb + 1), cudaMemcpyDefault, st));
         CK(cudaStreamSynchronize(st));
     } else {
@@ -299,8 +318,20 @@ bwt_status bwt::prepare_batch(bwt_plan* p, const uint64_t* offsets, uint32_t nb,
 // Block and first-sort tile tables for blocks off[b] .. off[b+1] (global
 // positions as given), uploaded from pinned staging memory.
 bwt_status bwt::upload_tables(bwt_plan* p, const uint64_t* off, uint32_t nb, cudaStream_t st) {
-    uint32_t max_n = 0;
     const uint32_t T = (uint32_t)p->tile;
+    std::vector<uint64_t> key;
+    key.reserve((size_t)nb + 3);
+    key.push_back(T);
+    key.push_back(nb);
+    key.insert(key.end(), off, off + nb + 1);
+    if (key == p->tables_key) return BWT_OK;  // the device tables already hold this layout
+    p->tables_key.clear();
+    // a staging slot is refilled only after the copy from it has run
+    const int sl = p->stage_next;
+    if (p->stage_used[sl]) CK(cudaEventSynchronize(p->stage_ev[sl]));
+    p->h_tiles = p->stage_tiles[sl];
+    p->h_blocks = p->stage_blocks[sl];
+    uint32_t max_n = 0;
     uint32_t nt = 0;
     for (uint32_t b = 0; b < nb; ++b) {
         const uint32_t o = (uint32_t)off[b], n = (uint32_t)(off[b + 1] - off[b]);
@@ -326,6 +357,10 @@ bwt_status bwt::upload_tables(bwt_plan* p, const uint64_t* off, uint32_t nb, cud
     p->ntiles0 = nt;
     CK(cudaMemcpyAsync(p->blocks, p->h_blocks, sizeof(BlockInfo) * nb, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(p->tiles0, p->h_tiles, sizeof(TileDesc) * nt, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(p->stage_ev[sl], st));
+    p->stage_used[sl] = true;
+    p->stage_next = sl ^ 1;
+    p->tables_key = std::move(key);
     return BWT_OK;
 }
 
@@ -488,14 +523,35 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
     return BWT_OK;
 }
 
-bwt_status bwt::finish_status(bwt_plan* p, cudaStream_t st) {
-    CK(cudaMemcpyAsync(p->h_ctrl, p->ctrl, sizeof(uint32_t) * CTRL_WORDS, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+bwt_status bwt::status_of_ctrl(const bwt_plan* p) {
     const uint32_t err = p->h_ctrl[CTRL_ERR];
     if (err & ERR_TIMEOUT) return BWT_ETIMEOUT;
     if (err & ERR_CAPACITY) return BWT_ECAPACITY;
     if (err & ERR_INPUT) return BWT_EINVAL;
     return BWT_OK;
+}
+
+bwt_status bwt::finish_status(bwt_plan* p, cudaStream_t st) {
+    resolve_pending(p);  // the staging of h_ctrl below replaces an unread asynchronous result
+    CK(cudaMemcpyAsync(p->h_ctrl, p->ctrl, sizeof(uint32_t) * CTRL_WORDS, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return status_of_ctrl(p);
+}
+
+void bwt::resolve_pending(bwt_plan* p) {
+    if (!p->pending) return;
+    p->pending = false;
+    const cudaError_t e = cudaEventSynchronize(p->done_ev);
+    if (e != cudaSuccess) {
+        p->last = record_cuda(e, "cudaEventSynchronize");
+        return;
+    }
+    p->last = status_of_ctrl(p);
+    graph_stats(p);
+    if (p->pending_learned) learned_stats(p);
+    p->pending_learned = false;
+    const uint64_t act = (uint64_t)p->h_ctrl[CTRL_ACTIVE] | ((uint64_t)p->h_ctrl[CTRL_ACTIVE + 1] << 32);
+    p->stats.active_elements = act;
 }
 
 void bwt::collect_timing(bwt_plan* p) {
@@ -506,6 +562,11 @@ void bwt::collect_timing(bwt_plan* p) {
             continue;
         }
         const EvMeta& m = p->ev_meta[i];
+        if (m.chunk_sort) {
+            p->stats.chunk_launches++;
+            p->stats.chunk_ms += ms;
+            continue;
+        }
         const uint64_t keys = m.keys_host ? m.keys_host : m.keys_dev;
         p->stats.radix_ms += ms;
         p->radix_bytes += m.bytes_per_key * (double)keys;
@@ -602,6 +663,8 @@ extern "C" bwt_status bwt_forward_batch(bwt_plan* p, const uint8_t* d_in, const 
     if (!p || !d_in || !offsets || !d_L || !d_primary) return BWT_EINVAL;
     if (cudaSetDevice(p->device) != cudaSuccess) return BWT_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    p->pending = false;  // an unread result of an earlier call is superseded by this one
+    p->pending_learned = false;
     std::memset(&p->stats, 0, sizeof(p->stats));
     p->radix_bytes = 0;
     p->pending_large_passes = 0;
@@ -619,10 +682,28 @@ extern "C" bwt_status bwt_forward_batch(bwt_plan* p, const uint8_t* d_in, const 
     const bool per_block = (p->desc.flags & BWT_F_PER_BLOCK_LAUNCH) != 0;
     const bool graph = !per_block && (p->desc.flags & BWT_F_GRAPH);
     const bool learned = !per_block && (p->desc.flags & BWT_F_LEARNED);
+    if (graph) {
+        // stream-ordered: enqueue the graph, then a copy of the control words
+        // and an event; status and statistics are read when asked for
+        s = run_graph(p, d_in, d_L, d_primary, st);  // plain or learned first stage
+        if (s == BWT_OK) {
+            cudaError_t e = cudaMemcpyAsync(p->h_ctrl, p->ctrl, sizeof(uint32_t) * CTRL_WORDS,
+                                            cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaEventRecord(p->done_ev, st);
+            if (e == cudaSuccess) {
+                p->pending = true;
+                p->pending_learned = learned && p->h_bstats != nullptr;
+                p->stats.radix_bytes = p->radix_bytes;
+                p->last = BWT_OK;
+                return BWT_OK;
+            }
+            s = record_cuda(e, "cudaMemcpyAsync / cudaEventRecord");
+        }
+        p->last = s;
+        return s;
+    }
     if (per_block) {
         s = run_per_block(p, d_in, d_L, d_primary, st);
-    } else if (graph) {
-        s = run_graph(p, d_in, d_L, d_primary, st);  // plain or learned first stage
     } else if (learned) {
         s = run_learned(p, d_in, d_L, d_primary, st);
     } else {
@@ -630,7 +711,6 @@ extern "C" bwt_status bwt_forward_batch(bwt_plan* p, const uint8_t* d_in, const 
     }
     if (s == BWT_OK) s = finish_status(p, st);
     else cudaStreamSynchronize(st);
-    if (graph) graph_stats(p);
     if (learned && s != BWT_ENOMODEL && p->h_bstats) learned_stats(p);
     if (!p->events.empty()) collect_timing(p);
     const uint64_t act = (uint64_t)p->h_ctrl[CTRL_ACTIVE] | ((uint64_t)p->h_ctrl[CTRL_ACTIVE + 1] << 32);

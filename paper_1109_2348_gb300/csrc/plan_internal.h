@@ -20,7 +20,20 @@ struct EvMeta {
     int ctrl_word;       // else: the ctrl word holding it (read after the round), -1 if none
     uint64_t keys_dev = 0;
     bool resolved = false;
+    bool chunk_sort = false;  // the learned bucketing's 256-thread chunk sort, not a radix pass
 };
+
+// One instantiated CUDA graph of a batch (BWT_F_GRAPH).
+struct GraphEntry {
+    std::vector<uint64_t> key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t launched = nullptr;  // recorded after its last launch
+    uint64_t last_use = 0;
+    uint64_t main_kernels = 0, body_kernels = 0, main_radix = 0, body_radix = 0;
+};
+
+constexpr size_t kGraphCache = 4;
 
 }  // namespace bwt
 
@@ -79,9 +92,25 @@ struct bwt_plan {
 
     // pinned host staging
     uint32_t* h_ctrl = nullptr;
-    bwt::TileDesc* h_tiles = nullptr;
+    bwt::TileDesc* h_tiles = nullptr;    // the staging slot of the last upload (block and tile tables)
     bwt::BlockInfo* h_blocks = nullptr;
     uint64_t* h_off = nullptr;
+    // Two staging slots for the block and tile tables, each with an event
+    // recorded after its upload, so a call overwrites a slot only once the
+    // copy from it two uploads ago has run (no stream synchronisation).
+    bwt::TileDesc* stage_tiles[2] = {nullptr, nullptr};
+    bwt::BlockInfo* stage_blocks[2] = {nullptr, nullptr};
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+    bool stage_used[2] = {false, false};
+    int stage_next = 0;
+    std::vector<uint64_t> tables_key;  // layout (tile size, offsets) now in the device tables; empty = unknown
+
+    // end of the last asynchronous forward call: its status and statistics
+    // are read from h_ctrl (and the learned counters) once this event has
+    // completed
+    cudaEvent_t done_ev = nullptr;
+    bool pending = false;       // a call's status and statistics are still to be read
+    bool pending_learned = false;
 
     // current batch
     uint32_t nb = 0, total = 0, max_n = 0, ntiles0 = 0;
@@ -96,10 +125,11 @@ struct bwt_plan {
     double radix_bytes = 0;
     uint32_t pending_large_passes = 0;  // u32 passes enqueued whose key count is still on the device
 
-    // CUDA graph cache
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
-    std::vector<uint64_t> graph_key;
+    // CUDA graph cache: the most recently used graphs, one per (buffers,
+    // block layout, radix settings); the counts describe the graph the last
+    // call launched
+    std::vector<bwt::GraphEntry> graphs;
+    uint64_t graph_use = 0;
     uint64_t graph_main_kernels = 0, graph_body_kernels = 0;
     uint64_t graph_main_radix = 0, graph_body_radix = 0;
     bool capturing = false;
@@ -122,6 +152,11 @@ bwt_status enqueue_initial_sort(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
 bwt_status enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts, cudaStream_t st);
 bwt_status enqueue_naming(bwt_plan* p, const uint64_t* K, cudaStream_t st);
 bwt_status finish_status(bwt_plan* p, cudaStream_t st);
+// Status of the control words' error field as read into h_ctrl.
+bwt_status status_of_ctrl(const bwt_plan* p);
+// Waits for the last asynchronous forward call and fills in its status and
+// statistics (a no-op when nothing is pending).
+void resolve_pending(bwt_plan* p);
 void collect_timing(bwt_plan* p);
 bwt_status run_plain_host_loop(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st);
 bwt_status run_doubling_host_loop(bwt_plan* p, cudaStream_t st);

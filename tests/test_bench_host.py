@@ -56,3 +56,19 @@ def test_throttle_reasons_inside_the_window_are_reported():
 def test_no_samples_is_reported_as_such():
     rec = _sampler([], 0.0, 1.0).stop()
     assert rec["samples"] == 0 and rec["reasons"] == ["no samples"]
+
+
+def test_cpu_sample_keeps_the_mix_of_sources():
+    """The oracle's bounded sample takes each source in proportion to its
+    share of the workload: 1,080 Markov and 120 uniform blocks give 14 and 2
+    of 16; the mixed workload's three sources give 6, 5 and 5."""
+    import bench
+    from paper_1109_2348_gb300 import datagen
+    s = bench.cpu_sample(datagen.config(5), 16)
+    srcs = list(s.sources)
+    assert len(srcs) == 16 and srcs.count(datagen.UNIFORM) == 2 and srcs.count(datagen.MARKOV3_Z96) == 14
+    s = bench.cpu_sample(datagen.config(2), 16)
+    counts = sorted(list(s.sources).count(x) for x in set(s.sources))
+    assert counts == [5, 5, 6]
+    s = bench.cpu_sample(datagen.config(1), 16)
+    assert s.num_blocks == 1
