@@ -66,7 +66,9 @@ typedef struct {
     uint32_t max_blocks;       /* most blocks per call (>= 1) */
     uint64_t max_total_bytes;  /* most bytes per call, summed over blocks (< 2^32) */
     uint32_t max_block_bytes;  /* largest block (1 .. 2^30 - 1) */
-    int radix_bits;            /* LSD digit width: 8 or 11; 0 = the default (8) or the autotuned value */
+    int radix_bits;            /* first sort's LSD digit width: 8, 11 or 16; 0 = the default (8) or the
+                                  autotuned value. 16 adds about 4.3 bytes per byte of max_total_bytes
+                                  plus 256 KB per block of scratch */
     int tile_keys;             /* keys per radix tile: 1024, 2048 or 4096; 0 = default (4096) */
     uint32_t flags;            /* BWT_F_* */
     const char* model_path;    /* splitter table for BWT_F_LEARNED (bwt_model_compile output); may be NULL */
@@ -82,7 +84,8 @@ typedef struct {
     uint64_t radix_keys;        /* keys moved by those launches, summed */
     double radix_ms;            /* their summed device time (only with BWT_F_TIMING) */
     double radix_bytes;         /* their algorithmic HBM bytes: 24 per u64 key (8 + 4 read, 8 + 4
-                                   written), 13 for the first pass (1 byte read), 16 per u32 key */
+                                   written), 13 for the first pass (1 byte read), 16 per u32 key;
+                                   a 16-bit pass counts 32 (8 histogram read + 24), its first 14 */
     uint64_t active_elements;   /* rotations re-sorted by doubling rounds, summed over rounds */
     uint64_t buckets_overflowed;/* learned bucketing: buckets above the 3,328-rotation chunk (each
                                    sorted whole by one CTA up to 13,312 rotations, by the radix
@@ -238,8 +241,11 @@ bwt_status bwt_plan_last_status(const bwt_plan* plan);
  * asynchronous bwt_forward_batch to finish, as bwt_plan_last_status does). */
 bwt_status bwt_plan_stats(const bwt_plan* plan, bwt_stats* out);
 
-/* Changes the radix digit width (8 or 11) and tile size (1024, 2048, 4096)
- * used by later calls; drops any cached graph. */
+/* Changes the first sort's digit width (8, 11 or 16) and tile size (1024,
+ * 2048, 4096) used by later calls; drops any cached graph. Choosing 16 the
+ * first time allocates its scratch (BWT_ENOMEM if that fails; the plan keeps
+ * its old width). With BWT_F_LEARNED, blocks routed to the plain sort take
+ * 8-bit passes when the width is 16. */
 bwt_status bwt_plan_set_radix(bwt_plan* plan, int radix_bits, int tile_keys);
 
 /* Digit width (8, 10 or 11) of the segmented radix that sorts large groups
@@ -250,7 +256,8 @@ bwt_status bwt_plan_set_radix(bwt_plan* plan, int radix_bits, int tile_keys);
 bwt_status bwt_plan_set_round_radix(bwt_plan* plan, int radix_bits);
 
 /* Autotuner (no paper counterpart): times this batch for radix_bits in
- * {8, 11} x tile_keys in {1024, 2048, 4096}, then for the rounds' digit width
+ * {8, 11, 16} x tile_keys in {1024, 2048, 4096} (16 is skipped when its
+ * scratch cannot be allocated), then for the rounds' digit width
  * in {8, 10, 11} (one untimed run, then `repeats` runs between CUDA events
  * on `stream`, for each candidate), keeps the fastest in the plan and
  * reports it through the out-pointers (any may be NULL). With cache_path,
@@ -265,10 +272,12 @@ bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, const uint64_t
 
 /* Test knob for the bounded device waits: `spin_limit` caps every wait loop
  * (0 = the built-in default of about one second); `withhold_publish` = 1 makes
- * the first tile of every radix pass skip publishing its counts, so every
- * later tile's look-back wait runs out and the call returns BWT_ETIMEOUT.
- * The GPU is never left waiting: each wait gives up after `spin_limit`
- * polls. */
+ * the first tile of every radix pass, and of every single-pass scan of the
+ * later stages (run-length encoding and decoding, variable-length encoding),
+ * skip publishing its counts, so the look-back waits behind it run out and
+ * the call reports BWT_ETIMEOUT. The GPU is never left waiting: each wait
+ * gives up after `spin_limit` polls, and every index derived from a prefix
+ * that gave up stays inside its buffer. */
 bwt_status bwt_plan_debug_waits(bwt_plan* plan, uint32_t spin_limit, int withhold_publish);
 
 /* ---- learned CDF model (the learned bucketing of BWT_F_LEARNED) -------
@@ -359,14 +368,16 @@ bwt_status bwt_model_load(const char* path, float* params, float* norm, uint64_t
  * current device and the caller's `stream`; it allocates nothing and does
  * not synchronise. Its scratch is a fixed array of 5 * BWT_NOALLOC_MAX_BYTES
  * u32 words (1.25 MiB) that lives in the library's device image: every GPU
- * that loads the library holds it until the process exits. The first call on
- * a device looks up that array's device address (once per device, with the
- * device current); make that first call before any stream capture.
+ * that loads the library holds it until the process exits. Every call looks
+ * up that array's device address on the current device (cudaGetSymbolAddress,
+ * a host-side query); the first call on a device also loads the library's
+ * device code there, so make that first call before any stream capture.
  *   d_in       device, uint8[n]: the block.
- *   d_L        device, uint8[n]: its L column (must not alias d_in).
+ *   d_L        device, uint8[n]: its L column.
  *   d_primary  device, int32[1]: its primary index.
- * Returns BWT_ETOOBIG if n > BWT_NOALLOC_MAX_BYTES, BWT_EINVAL for n = 0 or
- * bad pointers, BWT_ECUDA if the launch fails. All calls share the one
+ * No two of the three buffers may share a byte. Returns BWT_ETOOBIG if
+ * n > BWT_NOALLOC_MAX_BYTES, BWT_EINVAL for n = 0, NULL or overlapping
+ * buffers, BWT_ECUDA if the lookup or the launch fails. All calls share the one
  * scratch array, so calls whose kernels overlap on the GPU (other streams,
  * other host threads on the same device) race and give wrong results;
  * serialise them, e.g. on one stream. Each call writes every scratch word it

@@ -1,13 +1,16 @@
 // bwt_plan_autotune: picks the radix digit width and tile size for a plan by
 // timing the real batch, and remembers the choice in a small JSON-lines file.
 //
-// Sweep: radix_bits in {8, 11} x tile_keys in {1024, 2048, 4096}, then the
+// Sweep: radix_bits in {8, 11, 16} x tile_keys in {1024, 2048, 4096} (16-bit
+// digits are skipped if their scratch cannot be allocated), then the
 // doubling rounds' digit width in {8, 10, 11} with the best of those; each
 // candidate runs once untimed and then `repeats` times between CUDA events on
 // the caller's stream; the fastest mean wins. The cache file holds one JSON
-// object per line:
+// object per line, with every candidate's mean time as
+// [radix_bits, tile_keys, round_radix_bits (0 = by rank width), ms]:
 //   {"gpu": "<device name>", "key": "<workload signature>", "radix_bits": 8,
-//    "tile_keys": 4096, "round_radix_bits": 10, "ms": 1.234}
+//    "tile_keys": 4096, "round_radix_bits": 10, "ms": 1.234,
+//    "candidates": [[8, 1024, 0, 1.5], ...]}
 // The workload signature is the block count, total bytes, largest block and
 // plan flags, so uneven batches of the same shape reuse one entry. A later
 // entry for the same (gpu, key) overrides an earlier one.
@@ -113,14 +116,27 @@ extern "C" bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, con
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bwt::record_cuda(cudaGetLastError(), "cudaEventCreate");
-    const int bits[] = {8, 11};
+    const int bits[] = {8, 11, 16};
     const int tiles[] = {1024, 2048, 4096};
     float best = 1e30f;
     int best_b = plan->rbits, best_t = plan->tile;
     bwt_status status = BWT_OK;
+    std::ostringstream cand;  // every timed candidate, for the cache line
+    auto add_cand = [&](int b, int t, int r, float ms) {
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "%s[%d, %d, %d, %.4f]", cand.tellp() > 0 ? ", " : "", b, t, r, ms);
+        cand << buf;
+    };
     for (int b : bits) {
         for (int t : tiles) {
-            if ((status = bwt_plan_set_radix(plan, b, t)) != BWT_OK) break;
+            if ((status = bwt_plan_set_radix(plan, b, t)) != BWT_OK) {
+                if (b == 16 && (status == BWT_ENOMEM || status == BWT_EINVAL)) {  // no room for its scratch
+                    cudaGetLastError();
+                    status = BWT_OK;
+                    continue;
+                }
+                break;
+            }
             if ((status = bwt_forward_batch(plan, d_in, offsets, num_blocks, d_L, d_primary, stream)) != BWT_OK) break;
             float total = 0.f;
             for (int r = 0; r < repeats && status == BWT_OK; ++r) {
@@ -135,6 +151,7 @@ extern "C" bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, con
             }
             if (status != BWT_OK) break;
             const float mean = total / repeats;
+            add_cand(b, t, plan->round_bits, mean);
             if (mean < best) {
                 best = mean;
                 best_b = b;
@@ -162,6 +179,7 @@ extern "C" bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, con
                 cudaEventElapsedTime(&ms, e0, e1);
                 total += ms;
             }
+            if (status == BWT_OK) add_cand(best_b, best_t, rbits, total / repeats);
             if (status == BWT_OK && total / repeats < best_round) {
                 best_round = total / repeats;
                 best_r = rbits;
@@ -185,8 +203,9 @@ extern "C" bwt_status bwt_plan_autotune(bwt_plan* plan, const uint8_t* d_in, con
         if (f) {
             std::fprintf(f,
                          "{\"gpu\": \"%s\", \"key\": \"%s\", \"radix_bits\": %d, \"tile_keys\": %d, "
-                         "\"round_radix_bits\": %d, \"ms\": %.4f}\n",
-                         json_escape(gpu).c_str(), json_escape(key).c_str(), best_b, best_t, best_r, best);
+                         "\"round_radix_bits\": %d, \"ms\": %.4f, \"candidates\": [%s]}\n",
+                         json_escape(gpu).c_str(), json_escape(key).c_str(), best_b, best_t, best_r, best,
+                         cand.str().c_str());
             std::fclose(f);
         }
     }

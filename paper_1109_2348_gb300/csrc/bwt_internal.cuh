@@ -168,12 +168,14 @@ __device__ __forceinline__ void st_volatile64(uint64_t* p, uint64_t v) {
 // All 32 lanes of one warp call; returns the exclusive prefix of tile t in
 // every lane. A wait that runs past spin_limit polls sets ERR_TIMEOUT in *err
 // and counts the word as an inclusive zero (the result is then wrong but in
-// range: callers bound every index they derive from it).
+// range: callers bound every index they derive from it). withhold (a test
+// knob): the first tile of the segment does not publish, so the next tile's
+// wait runs out.
 __device__ __forceinline__ uint64_t lookback_u64(uint64_t* status, uint32_t t, uint32_t first, uint64_t agg,
-                                                 uint32_t spin_limit, uint32_t* err) {
+                                                 uint32_t spin_limit, uint32_t* err, uint32_t withhold = 0) {
     const uint32_t lane = threadIdx.x & 31;
     if (t == first) {
-        if (lane == 0) st_volatile64(status + t, LB_INC | agg);
+        if (lane == 0 && !withhold) st_volatile64(status + t, LB_INC | agg);
         return 0;
     }
     if (lane == 0) st_volatile64(status + t, LB_AGG | agg);

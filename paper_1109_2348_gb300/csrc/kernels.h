@@ -40,6 +40,26 @@ cudaError_t launch_onesweep(int key_bytes, bool from_s, int radix_bits, int tile
 int onesweep_grid(int key_bytes, bool from_s, int radix_bits, int tile);
 size_t onesweep_smem(int key_bytes, bool from_s, int radix_bits, int tile);
 
+// ---- 16-bit digits of the first sort (radix16.cu) ------------------------
+
+// Keys per part of a 16-bit pass: parts never straddle blocks, and a part's
+// per-digit counts fit 16 bits.
+constexpr uint32_t PART16_KEYS = 61440;
+
+// One stable 16-bit LSD pass (digit = (key >> shift) & 0xffff) over every
+// block, as four launches: part histograms, prefix over each block's parts,
+// prefix over the digits, scatter. kin == nullptr: the first pass, keys packed
+// from S (values = rotation indices). parts: the part table (TileDesc with
+// seg = blk); part_first[b] .. part_first[b + 1]: block b's parts. partcnt:
+// [nparts][65536] u32, segtot: [nseg][65536] u32 (scratch). A destination
+// outside its block (counts that disagree with the keys) is not written and
+// sets ERR_CAPACITY in ctrl.
+cudaError_t launch_first16_pass(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
+                                const uint8_t* S, const BlockInfo* blocks, const TileDesc* parts, uint32_t nparts,
+                                const uint32_t* part_first, uint32_t nseg, int shift, uint32_t* partcnt,
+                                uint32_t* segtot, uint32_t* ctrl, cudaStream_t st);
+size_t scatter16_smem();
+
 // ---- histograms of the first sort ---------------------------------------
 
 // Byte histogram of every block (d = 8: every pass of the first sort has the

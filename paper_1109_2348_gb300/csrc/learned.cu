@@ -919,8 +919,10 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
 
     // 4b. plain-routed blocks: the first sort of the plain path, ending in
     //     buffer 0, and its naming (with no plain-routed block every kernel
-    //     here finds zero tiles and returns)
-    const int rb = p->rbits, RADIX = 1 << rb;
+    //     here finds zero tiles and returns). Their tile table is only known
+    //     on the device, so with 16-bit digits (whose part table is built on
+    //     the host) they take 8-bit onesweep passes.
+    const int rb = p->rbits == 16 ? 8 : p->rbits, RADIX = 1 << rb;
     const uint32_t status_cap = (uint32_t)std::min<uint64_t>(p->cap_status, 0xffffffffu);
     {
         const int P = (64 + rb - 1) / rb;
@@ -1034,7 +1036,8 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
 
 void bwt::learned_stats(bwt_plan* p) {
     const uint32_t nb = p->nb;
-    const int P = (64 + p->rbits - 1) / p->rbits;
+    const int rb = p->rbits == 16 ? 8 : p->rbits;  // the plain-routed blocks' digit width
+    const int P = (64 + rb - 1) / rb;
     for (uint32_t b = 0; b < nb; ++b) {
         const unsigned long long* bl = p->h_bstats + 5 * (size_t)b;
         const unsigned long long* bf = p->h_bstats + 5 * ((size_t)nb + b);

@@ -23,7 +23,6 @@
 // calls whose kernels overlap on the GPU (different streams, or different
 // host threads on one device) race and corrupt each other's results.
 #include <cstdint>
-#include <mutex>
 
 #include "bwt.h"
 #include "plan_internal.h"
@@ -191,27 +190,23 @@ __global__ void __launch_bounds__(NA_THREADS, 1) k_bwt_block_noalloc(const uint8
     }
 }
 
-std::mutex g_na_mu;
-void* g_na_ptr[64];
-bool g_na_ready[64];
-
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side symbol is only a stand-in for it).
+// Device address of the scratch array on the current device. The host-side
+// symbol is only a stand-in for it, and the address belongs to the module
+// loaded in the current context, so it is looked up on every call (a host-side
+// query once the module is loaded): a cached address would go stale after
+// cudaDeviceReset or in a new primary context.
 bwt_status noalloc_scratch(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return bwt::record_cuda(e, "cudaGetDevice");
-    if (dev < 0 || dev >= 64) return BWT_EINVAL;
-    std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ready[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return bwt::record_cuda(e, "cudaGetSymbolAddress");
-        g_na_ptr[dev] = p;
-        g_na_ready[dev] = true;
-    }
-    *out = g_na_ptr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return bwt::record_cuda(e, "cudaGetSymbolAddress");
+    *out = p;
     return BWT_OK;
+}
+
+// [a, a + na) and [b, b + nb) share a byte.
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
 }
 
 }  // namespace
@@ -220,7 +215,9 @@ extern "C" bwt_status bwt_forward_block_noalloc(const uint8_t* d_in, uint32_t n,
                                                 void* stream) {
     if (!d_in || !d_L || !d_primary || n == 0) return BWT_EINVAL;
     if (n > NA_MAX) return BWT_ETOOBIG;
-    if ((const void*)d_in == (const void*)d_L) return BWT_EINVAL;
+    if (overlaps(d_in, n, d_L, n) || overlaps(d_primary, sizeof(int32_t), d_L, n) ||
+        overlaps(d_primary, sizeof(int32_t), d_in, n))
+        return BWT_EINVAL;
     void* scratch = nullptr;
     bwt_status s = noalloc_scratch(&scratch);
     if (s != BWT_OK) return s;

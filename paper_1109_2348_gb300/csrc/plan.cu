@@ -99,7 +99,7 @@ int bits_for(uint32_t max_value) {  // bits to hold 0..max_value
     return b;
 }
 
-bool valid_radix(int rb) { return rb == 8 || rb == 11; }
+bool valid_radix(int rb) { return rb == 8 || rb == 11 || rb == 16; }
 bool valid_round_radix(int rb) { return rb == 8 || rb == 10 || rb == 11; }
 bool valid_tile(int t) { return t == 1024 || t == 2048 || t == 4096; }
 
@@ -127,6 +127,11 @@ void bwt::free_plan_memory(bwt_plan* p) {
     F(p->tiles0); F(p->ltiles); F(p->blocks); F(p->hist); F(p->status); F(p->ctrl); F(p->seg_varied);
     for (int s = 0; s < 2; ++s)
         for (int c = 0; c < NCLS; ++c) F(p->bins[s][c]);
+    F(p->parts16); F(p->part_first16); F(p->partcnt16); F(p->segtot16);
+    for (int sl = 0; sl < 2; ++sl) {
+        FH(p->stage_parts[sl]);
+        FH(p->stage_pfirst[sl]);
+    }
     F(p->splitters); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->route_first); F(p->bstats); F(p->tiles_aux); F(p->inv_slots); F(p->inv_items); F(p->mtf_lists);
     drop_graph(p);
     FH(p->h_ctrl); FH(p->h_off);
@@ -209,8 +214,10 @@ extern "C" bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt
     if (s == BWT_OK && cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming) != cudaSuccess) s = BWT_ECUDA;
     A(host_alloc(&p->h_off, (size_t)B + 1));
     A(host_alloc(&p->h_inv_items, 2 * ((size_t)B + 1)));
-    // the learned bucketing's tables, so that no forward call allocates
+    // the learned bucketing's tables and the 16-bit passes' scratch, so that
+    // no forward call allocates
     if (s == BWT_OK && (desc->flags & BWT_F_LEARNED)) s = ensure_learned_buffers(p);
+    if (s == BWT_OK && p->rbits == 16) s = ensure_radix16(p);
     p->device_bytes = total;
     if (s == BWT_OK && (desc->flags & BWT_F_TIMING)) {
         p->events.resize(512);
@@ -252,8 +259,50 @@ extern "C" bwt_status bwt_plan_stats(const bwt_plan* plan, bwt_stats* out) {
     return BWT_OK;
 }
 
+bwt_status bwt::ensure_radix16(bwt_plan* p) {
+    if (p->partcnt16) return BWT_OK;
+    const uint64_t cap_parts = p->cap_n / PART16_KEYS + p->cap_b;
+    if (cap_parts >= (1ull << 32)) return BWT_EINVAL;
+    size_t total = 0;
+    bwt_status s = BWT_OK;
+    auto A = [&](bwt_status r) {
+        if (s == BWT_OK && r != BWT_OK) s = r;
+    };
+    A(dev_alloc(&p->parts16, cap_parts, &total));
+    A(dev_alloc(&p->part_first16, (size_t)p->cap_b + 1, &total));
+    A(dev_alloc(&p->partcnt16, cap_parts * 65536, &total));
+    A(dev_alloc(&p->segtot16, (size_t)p->cap_b * 65536, &total));
+    for (int sl = 0; sl < 2; ++sl) {
+        A(host_alloc(&p->stage_parts[sl], cap_parts));
+        A(host_alloc(&p->stage_pfirst[sl], (size_t)p->cap_b + 1));
+    }
+    if (s != BWT_OK) {
+        auto F = [](void* q) {
+            if (q) cudaFree(q);
+        };
+        F(p->parts16); F(p->part_first16); F(p->partcnt16); F(p->segtot16);
+        p->parts16 = nullptr;
+        p->part_first16 = p->partcnt16 = p->segtot16 = nullptr;
+        for (int sl = 0; sl < 2; ++sl) {
+            if (p->stage_parts[sl]) cudaFreeHost(p->stage_parts[sl]);
+            if (p->stage_pfirst[sl]) cudaFreeHost(p->stage_pfirst[sl]);
+            p->stage_parts[sl] = nullptr;
+            p->stage_pfirst[sl] = nullptr;
+        }
+        return s;
+    }
+    p->cap_parts = (uint32_t)cap_parts;
+    p->device_bytes += total;
+    return BWT_OK;
+}
+
 extern "C" bwt_status bwt_plan_set_radix(bwt_plan* plan, int radix_bits, int tile_keys) {
     if (!plan || !valid_radix(radix_bits) || !valid_tile(tile_keys)) return BWT_EINVAL;
+    if (radix_bits == 16) {
+        if (cudaSetDevice(plan->device) != cudaSuccess) return BWT_ECUDA;
+        const bwt_status s = ensure_radix16(plan);
+        if (s != BWT_OK) return s;
+    }
     plan->rbits = radix_bits;
     plan->tile = tile_keys;
     drop_graph(plan);
@@ -322,6 +371,7 @@ bwt_status bwt::upload_tables(bwt_plan* p, const uint64_t* off, uint32_t nb, cud
     std::vector<uint64_t> key;
     key.reserve((size_t)nb + 3);
     key.push_back(T);
+    key.push_back((uint64_t)p->rbits);  // 16-bit digits add the part table
     key.push_back(nb);
     key.insert(key.end(), off, off + nb + 1);
     if (key == p->tables_key) return BWT_OK;  // the device tables already hold this layout
@@ -357,6 +407,25 @@ bwt_status bwt::upload_tables(bwt_plan* p, const uint64_t* off, uint32_t nb, cud
     p->ntiles0 = nt;
     CK(cudaMemcpyAsync(p->blocks, p->h_blocks, sizeof(BlockInfo) * nb, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(p->tiles0, p->h_tiles, sizeof(TileDesc) * nt, cudaMemcpyHostToDevice, st));
+    p->nparts = 0;
+    if (p->rbits == 16) {
+        // parts of the 16-bit passes: up to PART16_KEYS consecutive rotations of one block
+        TileDesc* hp = p->stage_parts[sl];
+        uint32_t* hf = p->stage_pfirst[sl];
+        uint32_t np = 0;
+        for (uint32_t b = 0; b < nb; ++b) {
+            const uint32_t o = (uint32_t)off[b], n = (uint32_t)(off[b + 1] - off[b]);
+            hf[b] = np;
+            for (uint32_t s0 = 0; s0 < n; s0 += PART16_KEYS) {
+                if (np >= p->cap_parts) return BWT_EINVAL;
+                hp[np++] = TileDesc{o + s0, std::min(PART16_KEYS, n - s0), b, hf[b], o, b, n, 0u};
+            }
+        }
+        hf[nb] = np;
+        p->nparts = np;
+        CK(cudaMemcpyAsync(p->parts16, hp, sizeof(TileDesc) * np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(p->part_first16, hf, sizeof(uint32_t) * (nb + 1), cudaMemcpyHostToDevice, st));
+    }
     CK(cudaEventRecord(p->stage_ev[sl], st));
     p->stage_used[sl] = true;
     p->stage_next = sl ^ 1;
@@ -406,7 +475,41 @@ bwt_status bwt::reset_ctrl(bwt_plan* p, cudaStream_t st) {
 
 // First sort: P passes over the u64 prefixes (the first pass builds the keys
 // from the bytes), then naming into bins[0].
+// The first sort with 16-bit digits: four reduce-then-scan passes (each four
+// launches) over the part table, ending in buffer 1, then naming.
+static bwt_status enqueue_initial_sort16(bwt_plan* p, const uint8_t* d_in, cudaStream_t st) {
+    constexpr int P = 4;
+    for (int ps = 0; ps < P; ++ps) {
+        const bool timing = !p->events.empty() && !p->capturing && p->ev_used + 2 <= p->events.size();
+        if (timing) cudaEventRecord(p->events[p->ev_used], st);
+        CK(launch_first16_pass(ps == 0 ? nullptr : p->keys[(ps - 1) & 1], ps == 0 ? nullptr : p->vals[(ps - 1) & 1],
+                               p->keys[ps & 1], p->vals[ps & 1], d_in, p->blocks, p->parts16, p->nparts,
+                               p->part_first16, p->nb, 16 * ps, p->partcnt16, p->segtot16, p->ctrl, st));
+        if (timing) {
+            cudaEventRecord(p->events[p->ev_used + 1], st);
+            EvMeta m{};
+            m.bytes_per_key = ps == 0 ? 14.0 : 32.0;  // histogram key read (8) + scatter (12 + 12); S bytes first
+            m.first_sort = true;
+            m.keys_host = p->total;
+            m.ctrl_word = -1;
+            p->ev_meta.push_back(m);
+            p->ev_used += 2;
+        }
+        p->stats.kernel_launches += 4;
+        p->stats.radix_launches++;
+        p->stats.radix_keys += p->total;
+    }
+    p->sa = p->vals[(P - 1) & 1];
+    p->key2 = p->vals[P & 1];
+    p->kA = reinterpret_cast<uint32_t*>(p->keys[P & 1]);
+    p->vA = p->kA + p->cap_n;
+    p->kB = reinterpret_cast<uint32_t*>(p->keys[(P - 1) & 1]);
+    p->vB = p->kB + p->cap_n;
+    return enqueue_naming(p, p->keys[(P - 1) & 1], st);
+}
+
 bwt_status bwt::enqueue_initial_sort(bwt_plan* p, const uint8_t* d_in, cudaStream_t st) {
+    if (p->rbits == 16) return enqueue_initial_sort16(p, d_in, st);
     const int rb = p->rbits, RADIX = 1 << rb;
     const int P = (64 + rb - 1) / rb;
     const uint32_t nb = p->nb, nt = p->ntiles0;

@@ -84,6 +84,15 @@ struct bwt_plan {
     int chunk_sort_ctas = 1;            // resident chunk-sort CTAs per SM
     uint32_t learned_overflow_passes = 0;  // radix passes over the overflow buckets (index + key)
 
+    // 16-bit digits of the first sort (allocated when radix_bits 16 is first chosen)
+    bwt::TileDesc* parts16 = nullptr;    // [cap_parts] parts of up to PART16_KEYS keys, block by block
+    uint32_t* part_first16 = nullptr;    // [cap_b + 1] first part of every block
+    uint32_t* partcnt16 = nullptr;       // [cap_parts][65536] per-part digit counts, then prefixes
+    uint32_t* segtot16 = nullptr;        // [cap_b][65536] per-block digit totals, then starts
+    bwt::TileDesc* stage_parts[2] = {nullptr, nullptr};  // pinned staging of the part table
+    uint32_t* stage_pfirst[2] = {nullptr, nullptr};
+    uint32_t cap_parts = 0, nparts = 0;
+
     // GPU inverse (allocated on first use)
     uint32_t* inv_slots = nullptr;     // [6][cap_n / 16 + 3 cap_b + 4] sample walks and pointer jumping
     uint32_t* inv_items = nullptr;     // [2][cap_b + 1] prefixes of work items and of samples per block
@@ -173,5 +182,7 @@ void learned_stats(bwt_plan* p);
 bwt_status load_model(bwt_plan* p, const char* path);
 void graph_stats(bwt_plan* p);
 bwt_status ensure_learned_buffers(bwt_plan* p);
+// Scratch of the 16-bit digit passes (a no-op once allocated).
+bwt_status ensure_radix16(bwt_plan* p);
 
 }  // namespace bwt

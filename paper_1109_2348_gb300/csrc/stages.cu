@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(RT) k_rle_encode(const uint8_t* __restrict__ S
     __shared__ uint32_t s_tile, scan_tmp[32];
     __shared__ uint64_t s_excl;
     const uint32_t ntiles = (N + RTILE - 1) / RTILE;
-    const uint32_t spin = ctrl[CTRL_SPIN];
+    const uint32_t spin = ctrl[CTRL_SPIN], withhold = ctrl[CTRL_WITHHOLD];
     for (;;) {
         const uint32_t t = next_tile(&s_tile, counter);
         if (t >= ntiles) break;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(RT) k_rle_encode(const uint8_t* __restrict__ S
         uint32_t total;
         const uint32_t pre = block_exclusive_scan<RT>(__popc(flags), scan_tmp, &total);
         if (threadIdx.x < 32) {
-            const uint64_t e = lookback_u64(status, t, 0, total, spin, &ctrl[CTRL_ERR]);
+            const uint64_t e = lookback_u64(status, t, 0, total, spin, &ctrl[CTRL_ERR], withhold);
             if (threadIdx.x == 0) s_excl = e;
         }
         __syncthreads();
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(RT) k_rle_scan(const uint32_t* __restrict__ le
     __shared__ uint64_t s_excl;
     const uint64_t R = min(run_off[nb], (uint64_t)N);  // a run holds at least one byte
     const uint32_t ntiles = (uint32_t)((R + RTILE - 1) / RTILE);
-    const uint32_t spin = ctrl[CTRL_SPIN];
+    const uint32_t spin = ctrl[CTRL_SPIN], withhold = ctrl[CTRL_WITHHOLD];
     for (;;) {
         const uint32_t t = next_tile(&s_tile, counter);
         if (t >= ntiles) break;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(RT) k_rle_scan(const uint32_t* __restrict__ le
         uint32_t total;
         const uint32_t pre = block_exclusive_scan<RT>(sum, scan_tmp, &total);
         if (threadIdx.x < 32) {
-            const uint64_t e = lookback_u64(status, t, 0, total, spin, &ctrl[CTRL_ERR]);
+            const uint64_t e = lookback_u64(status, t, 0, total, spin, &ctrl[CTRL_ERR], withhold);
             if (threadIdx.x == 0) s_excl = e;
         }
         __syncthreads();
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(RT) k_vle_pack(const uint8_t* __restrict__ S, 
     __shared__ uint64_t s_excl;
     scode[threadIdx.x] = code[threadIdx.x];
     slen[threadIdx.x] = len[threadIdx.x];
-    const uint32_t spin = ctrl[CTRL_SPIN];
+    const uint32_t spin = ctrl[CTRL_SPIN], withhold = ctrl[CTRL_WITHHOLD];
     if (ld_volatile(&ctrl[CTRL_ERR]) & (ERR_INPUT | ERR_CAPACITY)) return;  // bad table or too small a buffer
     for (;;) {
         const uint32_t t = next_tile(&s_tile, counter);
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(RT) k_vle_pack(const uint8_t* __restrict__ S, 
         uint32_t total;
         const uint32_t pre = block_exclusive_scan<RT>(lsum, scan_tmp, &total);
         if (threadIdx.x < 32) {
-            const uint64_t e = lookback_u64(status, t, td.firstTile, total, spin, &ctrl[CTRL_ERR]);
+            const uint64_t e = lookback_u64(status, t, td.firstTile, total, spin, &ctrl[CTRL_ERR], withhold);
             if (threadIdx.x == 0) s_excl = e;
         }
         for (uint32_t w = threadIdx.x; w < VLE_WORDS; w += RT) words[w] = 0u;

@@ -19,6 +19,7 @@ def gpu_bwt(buf: np.ndarray, off: np.ndarray, plan: Plan | None = None, **plan_k
     try:
         L, prim = plan.forward(d_in, off)
         torch.cuda.synchronize()
+        assert plan.last_status() == 0, f"device-side status {plan.last_status()}"
         stats = plan.stats()
         return L.cpu().numpy(), prim.cpu().numpy(), stats
     finally:

@@ -25,6 +25,7 @@ def _run(w, flags=0, model_path=None, **kw):
         d_in = torch.from_numpy(buf).cuda()
         L, prim = plan.forward(d_in, off)
         torch.cuda.synchronize()
+        assert plan.last_status() == 0
         st = plan.stats()
         return buf, off, L.cpu().numpy(), prim.cpu().numpy(), st
 
@@ -38,6 +39,13 @@ def test_workload2_mixed_64x900k_graph():
     buf, off, L, prim, st = _run(datagen.config(2), flags=F_GRAPH)
     assert_matches_oracle(buf, off, L, prim, "workload 2")
     assert st["rounds"] >= 5
+
+
+@pytest.mark.parametrize("cfg", [2, 4])
+def test_workloads_2_and_4_with_16_bit_digits(cfg):
+    buf, off, L, prim, st = _run(datagen.config(cfg), flags=F_GRAPH, radix_bits=16)
+    assert st["radix_bits"] == 16
+    assert_matches_oracle(buf, off, L, prim, f"workload {cfg}, 16-bit digits")
 
 
 def test_workload3_degenerate_5x900k():

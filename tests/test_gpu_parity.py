@@ -40,7 +40,7 @@ def test_every_source_small(src):
     assert_matches_oracle(buf, off, L, prim, datagen.SOURCE_NAMES[src])
 
 
-@pytest.mark.parametrize("rb", [8, 11])
+@pytest.mark.parametrize("rb", [8, 11, 16])
 @pytest.mark.parametrize("tile", [1024, 2048, 4096])
 def test_radix_and_tile_variants(rb, tile):
     w = datagen.Workload("t", [datagen.MARKOV3_Z96, datagen.RUNS16, datagen.UNIFORM, datagen.PERIOD1000,
@@ -162,12 +162,16 @@ def test_autotuner_picks_a_valid_config_and_caches_it(tmp_path):
         L = torch.empty_like(d_in)
         p = torch.empty(16, dtype=torch.int32, device="cuda")
         rb, tile, ms = plan.autotune(d_in, off, L, p, cache_path=cache, repeats=2)
-        assert rb in (8, 11) and tile in (1024, 2048, 4096) and ms > 0
+        assert rb in (8, 11, 16) and tile in (1024, 2048, 4096) and ms > 0
         st = plan.stats()
         assert st["radix_bits"] == rb and st["tile_keys"] == tile
         assert_matches_oracle(buf, off, L.cpu().numpy(), p.cpu().numpy(), "autotuned")
         lines = [json.loads(x) for x in open(cache)]
         assert lines[-1]["radix_bits"] == rb and lines[-1]["tile_keys"] == tile
+        cands = lines[-1]["candidates"]  # [radix_bits, tile_keys, round_radix_bits, ms], all timed
+        assert len(cands) == 3 * 3 + 3 and all(c[3] > 0 for c in cands)
+        assert {c[0] for c in cands} == {8, 11, 16}
+        assert min(c[3] for c in cands) == pytest.approx(ms, rel=1e-3)
     with Plan(max_blocks=16, max_total_bytes=buf.size, max_block_bytes=60_000, flags=F_GRAPH) as plan2:
         L = torch.empty_like(d_in)
         p = torch.empty(16, dtype=torch.int32, device="cuda")
@@ -202,3 +206,53 @@ def test_default_round_radix_follows_the_rank_width(n, want):
         st = plan.stats()
         assert st["round_radix_bits"] == want and st["rounds"] >= 1
         assert_matches_oracle(buf, off, L.cpu().numpy(), prim.cpu().numpy(), f"n={n}")
+
+
+PART16 = 61440  # keys per part of a 16-bit pass
+
+
+@pytest.mark.parametrize("flags", [0, F_GRAPH])
+def test_radix16_parts_and_sub_tiles(flags):
+    """16-bit digits: blocks that end just before, at and after a part and a
+    4,096-key sub-tile, several parts a block, and tiny blocks whose 8-byte
+    key wraps more than once."""
+    rng = np.random.default_rng(16)
+    sizes = [PART16 - 1, PART16, PART16 + 1, 2 * PART16 + 4097, 4095, 4096, 4097, 1, 2, 3, 7, 8, 9]
+    srcs = [datagen.UNIFORM, datagen.MARKOV3_Z96, datagen.RUNS16, datagen.PERIOD7, datagen.FIBONACCI,
+            datagen.MUTATED_UNIT, datagen.UNIFORM, datagen.UNIFORM, datagen.UNIFORM, datagen.CONST,
+            datagen.UNIFORM, datagen.UNIFORM, datagen.UNIFORM]
+    blocks = [datagen.block(src, 500 + i, n) for i, (src, n) in enumerate(zip(srcs, sizes))]
+    blocks.append(rng.integers(0, 2, 70_000, dtype=np.uint8) + 97)  # few digits: long runs inside sub-tiles
+    buf, off = batch_from_blocks(blocks)
+    L, prim, st = gpu_bwt(buf, off, radix_bits=16, flags=flags)
+    assert st["radix_bits"] == 16
+    assert_matches_oracle(buf, off, L, prim, f"16-bit digits, flags={flags}")
+
+
+def test_radix16_constant_block_is_one_run():
+    """Every key of a constant block has the same digit in every pass: one run
+    of 900,000 keys spans every part and sub-tile; the order stays the index
+    order (L = S, primary 0)."""
+    w = datagen.Workload("t", [datagen.CONST, datagen.MARKOV3_Z96], [1, 2], [900_000, 50_000])
+    buf, off = w.generate()
+    L, prim, _ = gpu_bwt(buf, off, radix_bits=16, flags=F_GRAPH)
+    assert_matches_oracle(buf, off, L, prim, "16-bit, constant block")
+    assert prim[0] == 0
+
+
+def test_radix16_with_learned_bucketing():
+    """With BWT_F_LEARNED and 16-bit digits, blocks the routing sends to the
+    plain sort take 8-bit passes; the result is exact either way."""
+    from paper_1109_2348_gb300 import F_LEARNED, model
+    tiny = model.train(datagen.learned_train(num_blocks=2, n=50_000), num_samples=20_000, epochs=2)
+    w = datagen.mixed_64x900k(num_blocks=6, n=70_000)
+    buf, off = w.generate()
+    import torch
+    with Plan(max_blocks=6, max_total_bytes=buf.size, max_block_bytes=70_000, radix_bits=16,
+              flags=F_LEARNED | F_GRAPH) as plan:
+        model.install(plan, tiny.splitters)
+        L, prim = plan.forward(torch.from_numpy(buf).cuda(), off)
+        assert plan.last_status() == 0
+        st = plan.stats()
+        assert st["blocks_routed_plain"] >= 1
+        assert_matches_oracle(buf, off, L.cpu().numpy(), prim.cpu().numpy(), "learned + 16-bit")

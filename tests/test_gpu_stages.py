@@ -225,3 +225,57 @@ def test_mtf_of_the_bwt_output_full_mixed_workload():
     buf, off = w.generate()
     L, _ = oracle.bwt_batch(buf, off)
     _mtf_check([L[int(off[b]):int(off[b + 1])] for b in range(w.num_blocks)])
+
+
+# ---- bounded waits of the single-pass scans -----------------------------------
+
+@pytest.mark.parametrize("stage", ["rle_encode", "rle_decode", "vle_encode"])
+def test_stage_scan_wait_times_out_and_the_plan_recovers(stage):
+    """The first tile of each scan withholds its publish (the test knob), so
+    the look-back wait behind it runs out after 2,000 polls: the call returns
+    BWT_ETIMEOUT, and the next call on the same plan, with the knob off, is
+    exact against the oracle. Uniform bytes give about one run a byte, so the
+    decoding scan over the runs also spans several tiles."""
+    import torch
+    blocks = [datagen.block(datagen.UNIFORM, 90 + i, n) for i, n in enumerate([20_000, 13_001])]
+    buf, off = batch_from_blocks(blocks)
+    ref_c, ref_l, ref_ro = oracle.rle_batch(buf, off)
+    code = np.arange(256, dtype=np.uint32)
+    length = np.full(256, 8, dtype=np.uint8)  # every byte codes as itself
+    with _plan(buf, off) as plan:
+        d_in = torch.from_numpy(buf).cuda()
+        n = buf.size
+        chars = torch.empty_like(d_in)
+        lens = torch.empty(n, dtype=torch.int32, device="cuda")
+        ro = torch.empty(off.size, dtype=torch.int64, device="cuda")
+        out = torch.empty(n, dtype=torch.uint8, device="cuda")
+        vout = torch.empty(4 * n + 8, dtype=torch.uint8, device="cuda")
+        bo = torch.empty(off.size, dtype=torch.int64, device="cuda")
+        bits = torch.empty(off.size - 1, dtype=torch.int64, device="cuda")
+        d_code = torch.from_numpy(code.view(np.int32)).cuda()
+        d_len = torch.from_numpy(length).cuda()
+        R = int(ref_ro[-1])
+        if stage == "rle_decode":
+            chars[:R].copy_(torch.from_numpy(ref_c))
+            lens[:R].copy_(torch.from_numpy(ref_l.view(np.int32)))
+            ro.copy_(torch.from_numpy(ref_ro.view(np.int64)))
+
+        def call():
+            if stage == "rle_encode":
+                return plan.rle_encode_into(d_in, off, chars, lens, ro, raise_on_error=False)
+            if stage == "rle_decode":
+                return plan.rle_decode_into(chars, lens, ro, off, out, raise_on_error=False)
+            return plan.vle_encode_into(d_in, off, d_code, d_len, vout, bo, bits, raise_on_error=False)
+
+        plan.debug_waits(2000, True)
+        assert call() == _lib.BWT_ETIMEOUT
+        plan.debug_waits(0, False)
+        assert call() == _lib.BWT_OK
+        if stage == "rle_encode":
+            assert np.array_equal(ro.cpu().numpy().view(np.uint64), ref_ro)
+            assert np.array_equal(chars[:R].cpu().numpy(), ref_c)
+            assert np.array_equal(lens[:R].cpu().numpy().view(np.uint32), ref_l)
+        elif stage == "rle_decode":
+            assert np.array_equal(out.cpu().numpy(), buf)
+        else:
+            assert int(bo[-1]) == n and np.array_equal(vout[:n].cpu().numpy(), buf)
