@@ -338,6 +338,65 @@ class Runner:
         return [a.elapsed_time(b) for a, b in ev], pl.stats()
 
 
+def e2e_pipeline(R, plan, steps, world, dev, nsets: int = 3):
+    """End to end through the public call: every step copies its input from
+    pinned host memory to the device, sorts it with bwt_forward_batch and
+    copies L and the primary indices back to pinned host memory, all inside
+    the timed region. The copies run on their own streams (one per
+    direction) and the sorts on one compute stream, ordered by events, with
+    `nsets` buffer sets in flight, so step k+1's upload and step k-1's
+    download overlap step k's sort; no call waits on the host. Returns the
+    e2e record (input MB/s)."""
+    import torch
+    n = R.n
+    st_h2d, st_cmp, st_d2h = (torch.cuda.Stream(device=dev) for _ in range(3))
+    sets = [{"in": torch.empty_like(R.d_in), "L": torch.empty_like(R.d_in), "p": torch.empty_like(R.d_p),
+             "hL": torch.empty(n, dtype=torch.uint8).pin_memory(),
+             "hp": torch.empty(R.w.num_blocks, dtype=torch.int32).pin_memory()} for _ in range(nsets)]
+    for s_ in sets:  # capture each set's graph before timing
+        s_["in"].copy_(R.d_in)
+        plan.forward_into(s_["in"], R.off, s_["L"], s_["p"], st_cmp)
+    torch.cuda.synchronize()
+    assert plan.last_status() == 0
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    up, done, down = [None] * steps, [None] * steps, [None] * steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(R.stream)
+    for s_ in (st_h2d, st_cmp, st_d2h):
+        s_.wait_event(e0)
+    for i in range(steps):
+        cur = sets[i % nsets]
+        with torch.cuda.stream(st_h2d):
+            if i >= nsets:
+                st_h2d.wait_event(done[i - nsets])  # the sort that read this input buffer has finished
+            cur["in"].copy_(R.pinned, non_blocking=True)
+            up[i] = ev()
+            up[i].record(st_h2d)
+        st_cmp.wait_event(up[i])
+        if i >= nsets:
+            st_cmp.wait_event(down[i - nsets])  # this L buffer has been copied out
+        plan.forward_into(cur["in"], R.off, cur["L"], cur["p"], st_cmp)
+        done[i] = ev()
+        done[i].record(st_cmp)
+        with torch.cuda.stream(st_d2h):
+            st_d2h.wait_event(done[i])
+            cur["hL"].copy_(cur["L"], non_blocking=True)
+            cur["hp"].copy_(cur["p"], non_blocking=True)
+            down[i] = ev()
+            down[i].record(st_d2h)
+    for s_ in (st_h2d, st_cmp, st_d2h):
+        R.stream.wait_stream(s_)
+    e1.record(R.stream)
+    torch.cuda.synchronize()
+    assert plan.last_status() == 0
+    e_ms = reduce_max(e0.elapsed_time(e1), world, dev)
+    assert np.array_equal(sets[(steps - 1) % nsets]["hL"].numpy(), R.d_L.cpu().numpy())
+    return {"value": round(n * world * steps / (e_ms / 1e3) / 1e6, 3), "unit": "MB/s",
+            "h2d_bytes_per_step": int(n + R.off.nbytes), "d2h_bytes_per_step": int(n + 4 * R.w.num_blocks),
+            "ms_per_step": round(e_ms / steps, 4),
+            "pipelined": f"{nsets} buffer sets; uploads, sorts and downloads on three streams ordered by events"}
+
+
 def ours(args):
     import torch
     from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, F_PER_BLOCK_LAUNCH, F_TIMING
@@ -394,49 +453,7 @@ def ours(args):
 
     e2e = None
     if not args.no_e2e:
-        # End to end through the public call, two buffer sets in flight: step
-        # k+1's host->device copy and step k-1's device->host copy run on the
-        # copy engines while step k sorts; every step's copies are inside the
-        # timed region, and no call waits on the host.
-        plan2 = R.plan(flags, rb_used, tk_used, model_path)
-        sets = []
-        for pl in (plan, plan2):
-            sets.append({"plan": pl, "in": torch.empty_like(R.d_in), "L": torch.empty_like(R.d_in),
-                         "p": torch.empty_like(R.d_p), "hL": torch.empty(n, dtype=torch.uint8).pin_memory(),
-                         "hp": torch.empty(w.num_blocks, dtype=torch.int32).pin_memory(),
-                         "st": torch.cuda.Stream(device=dev)})
-        for st_ in sets:  # capture / warm each set's own buffers
-            st_["in"].copy_(R.d_in)
-            for _ in range(2):
-                st_["plan"].forward_into(st_["in"], R.off, st_["L"], st_["p"], st_["st"])
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(R.stream)
-        for st_ in sets:
-            st_["st"].wait_event(e0)
-        with torch.cuda.stream(sets[0]["st"]):
-            sets[0]["in"].copy_(R.pinned, non_blocking=True)
-        for i in range(args.steps):
-            cur, nxt = sets[i % 2], sets[(i + 1) % 2]
-            if i + 1 < args.steps:
-                with torch.cuda.stream(nxt["st"]):
-                    nxt["in"].copy_(R.pinned, non_blocking=True)
-            cur["plan"].forward_into(cur["in"], R.off, cur["L"], cur["p"], cur["st"])
-            with torch.cuda.stream(cur["st"]):
-                cur["hL"].copy_(cur["L"], non_blocking=True)
-                cur["hp"].copy_(cur["p"], non_blocking=True)
-        for st_ in sets:
-            R.stream.wait_stream(st_["st"])
-        e1.record(R.stream)
-        torch.cuda.synchronize()
-        assert all(st_["plan"].last_status() == 0 for st_ in sets)
-        e_ms = reduce_max(e0.elapsed_time(e1), world, dev)
-        assert np.array_equal(sets[(args.steps - 1) % 2]["hL"].numpy(), R.d_L.cpu().numpy())
-        e2e = {"value": round(n * world * args.steps / (e_ms / 1e3) / 1e6, 3), "unit": "MB/s",
-               "h2d_bytes_per_step": int(n + R.off.nbytes), "d2h_bytes_per_step": int(n + 4 * w.num_blocks),
-               "pipelined": "2 buffer sets: copies of steps k-1 and k+1 overlap step k"}
-        plan2.close()
-        del sets
+        e2e = e2e_pipeline(R, plan, args.steps, world, dev)
 
     plan.close()
     plain_cmp = None

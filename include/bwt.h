@@ -51,7 +51,9 @@ typedef enum {
     BWT_ETIMEOUT = 5,   /* a bounded device-side wait ran out; outputs are undefined */
     BWT_EMISMATCH = 6,  /* bwt_inverse_check: the inverse of L does not reproduce the block */
     BWT_ENOMODEL = 7,   /* BWT_F_LEARNED without a loaded splitter table */
-    BWT_ETOOBIG = 8     /* bwt_forward_block_noalloc: block larger than BWT_NOALLOC_MAX_BYTES */
+    BWT_ETOOBIG = 8,    /* bwt_forward_block_noalloc: block larger than BWT_NOALLOC_MAX_BYTES */
+    BWT_EINTERNAL = 9   /* a bounds check of the debug build (-DBWT_DEBUG) failed: an internal error; the
+                           release build clamps the same indices and never reports it */
 } bwt_status;
 
 /* plan flags */

@@ -25,6 +25,10 @@ INCLUDE = ROOT / "include"
 
 GEN_SO = DATAGEN / "libbwtgen.so"
 BWT_SO = CSRC / "libbwt_gb300.so"
+# The same library built with -DBWT_DEBUG: bounds checks in the kernels record
+# an internal error (BWT_EINTERNAL) instead of clamping silently. Loaded in
+# place of the release library when the environment sets BWT_DEBUG=1.
+BWT_DEBUG_SO = CSRC / "libbwt_gb300_debug.so"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -67,15 +71,18 @@ def _cuda_headers() -> list[Path]:
     return sorted(CSRC.glob("*.cuh")) + sorted(CSRC.glob("*.h")) + sorted(INCLUDE.glob("*.h"))
 
 
-def build_bwt(force: bool = False, jobs: int | None = None) -> Path:
+def build_bwt(force: bool = False, jobs: int | None = None, debug: bool = False) -> Path:
     srcs = _cuda_sources()
     hdrs = _cuda_headers()
-    if not (force or _stale(BWT_SO, srcs + hdrs)):
-        return BWT_SO
+    target = BWT_DEBUG_SO if debug else BWT_SO
+    if not (force or _stale(target, srcs + hdrs)):
+        return target
     nvcc = _nvcc()
-    objdir = ROOT / "_build" / "bwt"
+    objdir = ROOT / "_build" / ("bwt_debug" if debug else "bwt")
     objdir.mkdir(parents=True, exist_ok=True)
     common = ["-std=c++17", "-O3", "-Xcompiler", "-fPIC", "-I", str(INCLUDE), "-I", str(CSRC)]
+    if debug:
+        common.append("-DBWT_DEBUG")
 
     def compile_one(src: Path) -> Path:
         obj = objdir / (src.name + ".o")
@@ -89,10 +96,10 @@ def build_bwt(force: bool = False, jobs: int | None = None) -> Path:
     workers = jobs or min(len(srcs), max(1, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = BWT_SO.with_suffix(f".so.tmp{os.getpid()}")
+    tmp = target.with_suffix(f".so.tmp{os.getpid()}")
     _run([nvcc, "-shared", *ARCH, "-o", str(tmp), *map(str, objs), "-lcudart", "-lpthread"])
-    os.replace(tmp, BWT_SO)
-    return BWT_SO
+    os.replace(tmp, target)
+    return target
 
 
 def build_all(force: bool = False) -> None:

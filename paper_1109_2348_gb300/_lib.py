@@ -8,14 +8,15 @@ or no CUDA device is present, calls raise.
 from __future__ import annotations
 
 import ctypes
+import os
 from pathlib import Path
 
 from . import _build
 
 (BWT_OK, BWT_EINVAL, BWT_ENOMEM, BWT_ECAPACITY, BWT_ECUDA, BWT_ETIMEOUT, BWT_EMISMATCH, BWT_ENOMODEL,
- BWT_ETOOBIG) = range(9)
+ BWT_ETOOBIG, BWT_EINTERNAL) = range(10)
 STATUS_NAMES = ["BWT_OK", "BWT_EINVAL", "BWT_ENOMEM", "BWT_ECAPACITY", "BWT_ECUDA", "BWT_ETIMEOUT",
-                "BWT_EMISMATCH", "BWT_ENOMODEL", "BWT_ETOOBIG"]
+                "BWT_EMISMATCH", "BWT_ENOMODEL", "BWT_ETOOBIG", "BWT_EINTERNAL"]
 NOALLOC_MAX_BYTES = 65536
 
 F_GRAPH = 0x1
@@ -88,20 +89,27 @@ BUCKETS = 4096
 _lib = None
 
 
+def debug_build() -> bool:
+    """True when the environment asks for the bounds-checked library (BWT_DEBUG=1)."""
+    return os.environ.get("BWT_DEBUG", "") == "1"
+
+
 def library_path() -> Path:
-    return _build.BWT_SO
+    return _build.BWT_DEBUG_SO if debug_build() else _build.BWT_SO
 
 
 def load(build_if_missing: bool = True):
-    """Load libbwt_gb300.so (building it in-tree with nvcc if it is missing)."""
+    """Load libbwt_gb300.so, or libbwt_gb300_debug.so with BWT_DEBUG=1
+    (building it in-tree with nvcc if it is missing)."""
     global _lib
     if _lib is not None:
         return _lib
-    so = _build.BWT_SO
+    debug = debug_build()
+    so = library_path()
     if not so.exists():
-        if not build_if_missing:
+        if not build_if_missing and not debug:
             raise RuntimeError(f"{so} is missing: run __graft_entry__.build() first")
-        _build.build_bwt()
+        _build.build_bwt(debug=debug)
     lib = ctypes.CDLL(str(so))
     vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
     lib.bwt_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.c_int, ctypes.POINTER(vp)]

@@ -39,6 +39,23 @@ constexpr uint32_t ST_VALUE = (1u << 30) - 1;
 constexpr uint32_t ERR_TIMEOUT = 1u;
 constexpr uint32_t ERR_CAPACITY = 2u;
 constexpr uint32_t ERR_INPUT = 4u;  // device-checked input out of range (the inverse's primary index)
+constexpr uint32_t ERR_BOUNDS = 8u; // a bounds check of the debug build failed (an internal error)
+
+// Bounds checks of the debug build (-DBWT_DEBUG): index < n for every
+// SA-derived index, destinations inside their segment. A failed check sets
+// ERR_BOUNDS in the error word *err (the call then returns BWT_EINTERNAL) and
+// the kernel goes on with the clamped index the release build uses; no
+// kernel traps. In the release build the checks compile to nothing.
+#ifdef BWT_DEBUG
+#define BWT_DCHECK(cond, err)                                  \
+    do {                                                       \
+        if (!(cond)) atomicOr((err), ::bwt::ERR_BOUNDS);       \
+    } while (0)
+#else
+#define BWT_DCHECK(cond, err) \
+    do {                      \
+    } while (0)
+#endif
 
 // Group size classes of a doubling round.
 constexpr int NCLS = 5;
@@ -447,6 +464,7 @@ __device__ __forceinline__ void name_tile(const KeyT* sk, uint32_t len, uint32_t
         if (valid) {
             const uint32_t gs = sq == 0 ? carry_start : tstart + sq;
             const uint32_t sa = sa_tile[q];
+            BWT_DCHECK(sa < bi.n && gs - bi.off < bi.n, err);
             if (sa < bi.n && gs != old_start) rank[bi.off + sa] = gs - bi.off;
         }
         bool want = false;

@@ -437,6 +437,7 @@ __global__ void __launch_bounds__(256) k_sort_micro(uint32_t* __restrict__ SA, c
             for (uint32_t e = 0; e < gd.len && e < 4; ++e) {
                 const uint32_t sa = (uint32_t)c[e];
                 SA[gd.start + e] = sa;
+                BWT_DCHECK(sa < bi.n, &ctrl[CTRL_ERR]);
                 if (sa < bi.n && gstart[e] != 0) rank[bi.off + sa] = gd.start - bi.off + gstart[e];
                 if (gstart[e] == e) {
                     uint32_t f = e + 1;
@@ -501,6 +502,7 @@ __global__ void __launch_bounds__(256) k_sort_tiny(uint32_t* __restrict__ SA, co
         const uint32_t end = above ? (uint32_t)(__ffs(above) - 1) : gd.len;
         if (valid) {
             SA[k] = sa;
+            BWT_DCHECK(!valid || sa < bi.n, &ctrl[CTRL_ERR]);
             if (sa < bi.n && start_lane != 0) rank[bi.off + sa] = gd.start - bi.off + start_lane;
         }
         const uint32_t len = end - lane;
@@ -638,6 +640,7 @@ __device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDes
             const uint32_t s = hle ? i0 + 31u - __clz(hle) : last_head;
             if (valid) {
                 SA[gd.start + i] = sa;
+                BWT_DCHECK(sa < bi.n, err);
                 if (sa < bi.n && s != 0) rank[bi.off + sa] = gd.start - bi.off + s;
             }
             bool want = false;
@@ -667,7 +670,8 @@ __device__ __forceinline__ void sort_rename_group(uint64_t* comp, const GroupDes
             const bool head = (i == 0) || (uint32_t)(comp[i - 1] >> 32) != key;
             const uint32_t s = head ? i : smem_lower_bound<uint64_t>(comp, m, (uint64_t)key << 32);
             SA[gd.start + i] = sa;
-            if (sa < bi.n && s != 0) rank[bi.off + sa] = gd.start - bi.off + s;
+            BWT_DCHECK(sa < bi.n, err);
+                if (sa < bi.n && s != 0) rank[bi.off + sa] = gd.start - bi.off + s;
             if (head) {
                 len = smem_lower_bound<uint64_t>(comp, m, (uint64_t)(key + 1) << 32) - i;
                 want = len > 1 && new_depth < bi.n;
@@ -774,7 +778,7 @@ __global__ void __launch_bounds__(256) k_gather_L(const uint8_t* __restrict__ S,
                                                   const BlockInfo* __restrict__ blocks,
                                                   const TileDesc* __restrict__ tiles, uint32_t num_tiles,
                                                   uint8_t* __restrict__ L, int32_t* __restrict__ primary,
-                                                  uint32_t* __restrict__ tile_counter) {
+                                                  uint32_t* __restrict__ tile_counter, uint32_t* err) {
     __shared__ uint32_t s_t;
     for (;;) {
         if (threadIdx.x == 0) s_t = atomicAdd(tile_counter, 1u);
@@ -796,6 +800,7 @@ __global__ void __launch_bounds__(256) k_gather_L(const uint8_t* __restrict__ S,
             }
 #pragma unroll
             for (int j = 0; j < PI; ++j) {
+                BWT_DCHECK(q0 + j * 256u + threadIdx.x >= td.len || sa[j] < bi.n, err);
                 const uint32_t src = sa[j] == 0 || sa[j] > bi.n ? bi.n - 1 : sa[j] - 1;
                 c[j] = S[bi.off + src];
             }
@@ -954,7 +959,7 @@ cudaError_t launch_gather_L(const uint8_t* S, const uint32_t* SA, const BlockInf
     cudaError_t e = cudaMemsetAsync(ctrl + GATHER_L_CTR, 0, 4, st);
     if (e != cudaSuccess) return e;
     k_gather_L<<<grid_for(num_tiles, 1, 16), 256, 0, st>>>(S, SA, blocks, tiles, num_tiles, L, primary,
-                                                           ctrl + GATHER_L_CTR);
+                                                           ctrl + GATHER_L_CTR, ctrl + CTRL_ERR);
     return cudaGetLastError();
 }
 

@@ -119,7 +119,10 @@ bwt_status bwt::run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_
     CKG(cudaStreamEndCapture(bs, &body));
     k2 = p->stats.kernel_launches;
     r2 = p->stats.radix_launches;
-    CKG(launch_gather_L(d_in, p->sa, p->blocks, p->tiles0, p->ntiles0, d_L, d_primary, p->ctrl, cs));
+    {
+        NvtxRange nv("gather");
+        CKG(launch_gather_L(d_in, p->sa, p->blocks, p->tiles0, p->ntiles0, d_L, d_primary, p->ctrl, cs));
+    }
     p->stats.kernel_launches++;
     k3 = p->stats.kernel_launches;
     r3 = p->stats.radix_launches;

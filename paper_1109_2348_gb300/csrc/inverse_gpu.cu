@@ -271,6 +271,7 @@ extern "C" bwt_status bwt_inverse_batch(bwt_plan* p, const uint8_t* d_L, const u
                                         uint32_t num_blocks, const int32_t* d_primary, uint8_t* d_out,
                                         void* stream) {
     if (!p || !d_L || !offsets || !d_primary || !d_out || (const void*)d_L == (const void*)d_out) return BWT_EINVAL;
+    bwt::NvtxRange nvtx_range("inverse");
     if (cudaSetDevice(p->device) != cudaSuccess) return BWT_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::memset(&p->stats, 0, sizeof(p->stats));

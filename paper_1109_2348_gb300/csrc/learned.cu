@@ -119,6 +119,7 @@ __global__ void k_byte_norm(const uint32_t* __restrict__ hist, uint64_t n, float
 
 extern "C" bwt_status bwt_model_byte_norm(const uint8_t* d_in, uint64_t n, float* d_norm, void* stream) {
     if (!d_in || !d_norm || n == 0 || n >= (1ull << 32)) return BWT_EINVAL;
+    bwt::NvtxRange nvtx_range("mlp_byte_norm");
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t* hist = nullptr;
     CKL(cudaMalloc(&hist, 256 * sizeof(uint32_t)));
@@ -138,6 +139,7 @@ extern "C" bwt_status bwt_model_samples(bwt_plan* p, const uint8_t* d_in, const 
                                         uint32_t num_blocks, const uint64_t* d_pos, uint32_t count,
                                         const float* d_norm, float* d_x, float* d_t, void* stream) {
     if (!p || !d_in || !offsets || !d_pos || !d_norm || !d_x || !d_t) return BWT_EINVAL;
+    bwt::NvtxRange nvtx_range("mlp_samples");
     CKL(cudaSetDevice(p->device));
     cudaStream_t st = (cudaStream_t)stream;
     std::memset(&p->stats, 0, sizeof(p->stats));
@@ -458,7 +460,8 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
                                                        const uint32_t* __restrict__ ntiles_dev,
                                                        const uint16_t* __restrict__ fb,
                                                        const uint32_t* __restrict__ route, ChunkTables ct,
-                                                       uint64_t* __restrict__ K, uint32_t* __restrict__ I) {
+                                                       uint64_t* __restrict__ K, uint32_t* __restrict__ I,
+                                                       uint32_t* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint8_t* sb = smem;                                                  // [TILE_BYTES], 16-aligned
     uint16_t* cm = reinterpret_cast<uint16_t*>(smem + TILE_BYTES);       // [NBK] chunk of each bucket
@@ -541,6 +544,7 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
             for (uint32_t r = threadIdx.x; r < td.len; r += blockDim.x) {
                 const uint32_t q = stQ[r], c = stC[r];
                 const uint32_t dst = dbase[c] + (r - pre[c]);
+                BWT_DCHECK(dst - bi.off < bi.n, err);  // inside the tile's block
                 K[dst] = pack8_smem(sb, shift + q);
                 I[dst] = i0 + q;
             }
@@ -679,6 +683,7 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
         const GroupDesc gd = chunks.list[LIST][c];
         const BlockInfo bi = blocks[gd.blk];
         const uint32_t len = min(gd.len, CAP);
+        BWT_DCHECK(gd.len <= CAP && gd.start - bi.off < bi.n && gd.start - bi.off + gd.len <= bi.n, &ctrl[CTRL_ERR]);
         // unrolled, so a thread's loads are in flight together (the loop
         // bound is a constant: every thread stores MS_IT entries)
 #pragma unroll
@@ -870,6 +875,8 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     //    bucket (in the u16 view of keys[1], free until the scatter has run),
     // 2. per-block statistics of both, 3. route every block and split the
     //    tile table by route -- all on the device
+    NvtxStages nv;
+    nv.next("bucket_count");
     uint16_t* fb = reinterpret_cast<uint16_t*>(p->keys[1]);
     CKL(cudaMemsetAsync(p->bucket_count, 0, sizeof(uint32_t) * 2 * NBK * nb, st));
     {
@@ -879,6 +886,7 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
         k_bucket_count<<<grid, 256, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles0, nt, span, p->splitters, nb,
                                                       p->bucket_count, fb);
     }
+    nv.next("bucket_route");
     k_bucket_stats<<<std::min<uint32_t>(2 * nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, 2 * nb, p->bstats);
     k_route_scan<<<1, 1024, 0, st>>>(p->bstats, p->blocks, nb, T, p->route, p->route_first, ctrl);
     TileDesc* tilesP = p->tiles_aux;
@@ -895,6 +903,7 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
 
     // 4a. bucketed blocks: bucket starts, chunk plan and scatter (the scatter
     //     consumes fb, so it runs before the plain passes reuse keys[1])
+    nv.next("bucket_scatter");
     Bins aux = bins_of(p, 1);
     CKL(cudaMemsetAsync(aux.count, 0, sizeof(uint32_t) * NCLS, st));
     k_select_rows<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, p->route, nb);
@@ -906,13 +915,13 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
         const int g = sms * 4;
         if (T <= 1024)
             k_chunk_scatter<4><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, fb, p->route, ct,
-                                                                   p->keys[0], p->vals[0]);
+                                                                   p->keys[0], p->vals[0], ctrl + CTRL_ERR);
         else if (T <= 2048)
             k_chunk_scatter<8><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, fb, p->route, ct,
-                                                                   p->keys[0], p->vals[0]);
+                                                                   p->keys[0], p->vals[0], ctrl + CTRL_ERR);
         else
             k_chunk_scatter<16><<<g, 256, CHUNK_SCATTER_SMEM, st>>>(d_in, p->blocks, tilesB, ntb, fb, p->route, ct,
-                                                                    p->keys[0], p->vals[0]);
+                                                                    p->keys[0], p->vals[0], ctrl + CTRL_ERR);
     }
     CKL(cudaGetLastError());
     p->stats.kernel_launches += 4;
@@ -922,6 +931,7 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     //     here finds zero tiles and returns). Their tile table is only known
     //     on the device, so with 16-bit digits (whose part table is built on
     //     the host) they take 8-bit onesweep passes.
+    nv.next("bucket_plain");
     const int rb = p->rbits == 16 ? 8 : p->rbits, RADIX = 1 << rb;
     const uint32_t status_cap = (uint32_t)std::min<uint64_t>(p->cap_status, 0xffffffffu);
     {
@@ -967,6 +977,7 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     }
 
     // 4c. bucketed blocks: chunk sorts with naming, then the overflow buckets
+    nv.next("bucket_sort");
     uint32_t* chunk_counter = ctrl + CTRL_TILE_CTR + 58;  // control words no radix pass uses
     uint32_t* big_counter = ctrl + CTRL_TILE_CTR + 59;
     CKL(cudaMemsetAsync(chunk_counter, 0, 8, st));
@@ -990,6 +1001,7 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     p->stats.kernel_launches += 2;
 
     // overflow buckets: radix on the index, then on the key
+    nv.next("bucket_overflow");
     const int PI = std::max(1, (bits_needed(p->max_n - 1) + 7) / 8), PK = 8, PT = PI + PK;
     CKL(launch_build_large_tiles(aux, p->tile, p->ltiles, p->cap_ltiles, ctrl, st));
     CKL(launch_zero_by_count(p->hist, aux.count + CLS_LARGE, (uint32_t)(PT * 256),

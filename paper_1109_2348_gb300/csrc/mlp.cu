@@ -296,6 +296,7 @@ using namespace bwt;
 extern "C" bwt_status bwt_mlp_forward(const float* d_params, const float* d_x, uint32_t count, float* d_y,
                                       void* stream) {
     if (!d_params || (!d_x && count) || (!d_y && count)) return BWT_EINVAL;
+    bwt::NvtxRange nvtx_range("mlp_forward");
     if (!count) return BWT_OK;
     k_mlp_forward<<<(count + 127) / 128, 128, 0, (cudaStream_t)stream>>>(d_params, d_x, count, d_y);
     CKM(cudaGetLastError());
@@ -305,6 +306,7 @@ extern "C" bwt_status bwt_mlp_forward(const float* d_params, const float* d_x, u
 extern "C" bwt_status bwt_mlp_loss_grad(const float* d_params, const float* d_x, const float* d_t, uint32_t count,
                                         float* d_grad, float* d_loss, void* stream) {
     if (!d_params || !d_x || !d_t || !d_grad || count == 0) return BWT_EINVAL;
+    bwt::NvtxRange nvtx_range("mlp_loss_grad");
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t nblk = (count + GS - 1) / GS;
     MlpScratch s;
@@ -323,6 +325,7 @@ extern "C" bwt_status bwt_mlp_loss_grad(const float* d_params, const float* d_x,
 extern "C" bwt_status bwt_mlp_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v, uint32_t step,
                                         float lr, void* stream) {
     if (!d_params || !d_grad || !d_m || !d_v || step == 0) return BWT_EINVAL;
+    bwt::NvtxRange nvtx_range("mlp_adam");
     k_adam<<<(NP + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_params, d_grad, d_m, d_v, (int)step, lr, 0.9f,
                                                                0.999f, 1e-8f);
     CKM(cudaGetLastError());
@@ -333,6 +336,7 @@ extern "C" bwt_status bwt_model_train(float* d_params, const float* d_x, const f
                                       const uint32_t* d_order, uint32_t epochs, uint32_t batch, float lr,
                                       float* d_epoch_loss, void* stream) {
     if (!d_params || !d_x || !d_t || !d_order || count == 0 || batch == 0 || epochs == 0) return BWT_EINVAL;
+    bwt::NvtxRange nvtx_range("mlp_train");
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t nblk = (batch + GS - 1) / GS;
     MlpScratch s;
@@ -386,6 +390,7 @@ extern "C" bwt_status bwt_model_train(float* d_params, const float* d_x, const f
 extern "C" bwt_status bwt_model_compile(const float* d_params, const float* d_norm, uint64_t* d_splitters,
                                         void* stream) {
     if (!d_params || !d_norm || !d_splitters) return BWT_EINVAL;
+    bwt::NvtxRange nvtx_range("mlp_compile");
     cudaStream_t st = (cudaStream_t)stream;
     k_compile_splitters<<<(BWT_SPLITTERS + 127) / 128, 128, 0, st>>>(d_params, d_norm, d_splitters, BWT_SPLITTERS);
     k_sort_splitters<<<1, 1024, 0, st>>>(d_splitters, BWT_SPLITTERS);

@@ -58,6 +58,7 @@ extern "C" const char* bwt_status_string(bwt_status s) {
     case BWT_EMISMATCH: return "BWT_EMISMATCH";
     case BWT_ENOMODEL: return "BWT_ENOMODEL";
     case BWT_ETOOBIG: return "BWT_ETOOBIG";
+    case BWT_EINTERNAL: return "BWT_EINTERNAL";
     }
     return "BWT_UNKNOWN";
 }
@@ -482,6 +483,7 @@ static bwt_status enqueue_initial_sort16(bwt_plan* p, const uint8_t* d_in, cudaS
     for (int ps = 0; ps < P; ++ps) {
         const bool timing = !p->events.empty() && !p->capturing && p->ev_used + 2 <= p->events.size();
         if (timing) cudaEventRecord(p->events[p->ev_used], st);
+        NvtxRange nv(ps == 0 ? "pack+radix16" : "radix16", ps);
         CK(launch_first16_pass(ps == 0 ? nullptr : p->keys[(ps - 1) & 1], ps == 0 ? nullptr : p->vals[(ps - 1) & 1],
                                p->keys[ps & 1], p->vals[ps & 1], d_in, p->blocks, p->parts16, p->nparts,
                                p->part_first16, p->nb, 16 * ps, p->partcnt16, p->segtot16, p->ctrl, st));
@@ -528,6 +530,7 @@ bwt_status bwt::enqueue_initial_sort(bwt_plan* p, const uint8_t* d_in, cudaStrea
     }
     p->stats.kernel_launches += 2;
     for (int ps = 0; ps < P; ++ps) {
+        NvtxRange nv(ps == 0 ? "pack+radix" : "radix", ps);
         CK(cudaMemsetAsync(p->status, 0, sizeof(uint32_t) * (size_t)nt * RADIX, st));
         OneSweepParams a{};
         a.kin = ps == 0 ? nullptr : p->keys[(ps - 1) & 1];
@@ -556,6 +559,7 @@ bwt_status bwt::enqueue_initial_sort(bwt_plan* p, const uint8_t* d_in, cudaStrea
 }
 
 bwt_status bwt::enqueue_naming(bwt_plan* p, const uint64_t* K, cudaStream_t st) {
+    NvtxRange nv("name");
     CK(cudaMemsetAsync(p->ctrl + CTRL_BINS, 0, sizeof(uint32_t) * 2 * NCLS, st));
     CK(launch_name_initial(K, p->sa, p->blocks, p->tiles0, p->ntiles0, p->rank, bins_of(p, 0), p->ctrl, st));
     p->stats.kernel_launches++;
@@ -566,6 +570,7 @@ bwt_status bwt::enqueue_naming(bwt_plan* p, const uint64_t* K, cudaStream_t st) 
 // length h sits in ctrl[CTRL_DEPTH]. host_counts: the three group counts when
 // the host knows them (else null: persistent grids read them on the device).
 bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts, cudaStream_t st) {
+    NvtxRange nv("double", (int)p->stats.rounds);  // the round's index (0 while a graph is captured)
     const int kbits = bits_for(p->max_n - 1);
     const int rb = round_radix_bits(p), RADIX = 1 << rb;
     const int P2 = std::max(1, (kbits + rb - 1) / rb);
@@ -628,6 +633,7 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
 
 bwt_status bwt::status_of_ctrl(const bwt_plan* p) {
     const uint32_t err = p->h_ctrl[CTRL_ERR];
+    if (err & ERR_BOUNDS) return BWT_EINTERNAL;
     if (err & ERR_TIMEOUT) return BWT_ETIMEOUT;
     if (err & ERR_CAPACITY) return BWT_ECAPACITY;
     if (err & ERR_INPUT) return BWT_EINVAL;
@@ -735,6 +741,7 @@ bwt_status bwt::run_plain_host_loop(bwt_plan* p, const uint8_t* d_in, uint8_t* d
     if ((s = reset_ctrl(p, st)) != BWT_OK) return s;
     if ((s = enqueue_initial_sort(p, d_in, st)) != BWT_OK) return s;
     if ((s = run_doubling_host_loop(p, st)) != BWT_OK) return s;
+    NvtxRange nv("gather");
     CK(launch_gather_L(d_in, p->sa, p->blocks, p->tiles0, p->ntiles0, d_L, d_primary, p->ctrl, st));
     p->stats.kernel_launches++;
     return BWT_OK;
@@ -756,7 +763,7 @@ bwt_status bwt::run_per_block(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, in
         if ((s = run_plain_host_loop(p, d_in + off[b], d_L + off[b], d_primary + b, st)) != BWT_OK) return s;
         CK(cudaMemcpyAsync(p->h_ctrl, p->ctrl, sizeof(uint32_t) * CTRL_WORDS, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (p->h_ctrl[CTRL_ERR]) return p->h_ctrl[CTRL_ERR] & ERR_TIMEOUT ? BWT_ETIMEOUT : BWT_ECAPACITY;
+        if (p->h_ctrl[CTRL_ERR]) return status_of_ctrl(p);
     }
     return BWT_OK;
 }
@@ -765,6 +772,7 @@ extern "C" bwt_status bwt_forward_batch(bwt_plan* p, const uint8_t* d_in, const 
                                         uint32_t num_blocks, uint8_t* d_L, int32_t* d_primary, void* stream) {
     if (!p || !d_in || !offsets || !d_L || !d_primary) return BWT_EINVAL;
     if (cudaSetDevice(p->device) != cudaSuccess) return BWT_ECUDA;
+    NvtxRange nv("bwt_forward_batch");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     p->pending = false;  // an unread result of an earlier call is superseded by this one
     p->pending_learned = false;

@@ -3,15 +3,47 @@
 #pragma once
 
 #include <cstdint>
+#include <cstdio>
 #include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "bwt.h"
 #include "bwt_internal.cuh"
 
 namespace bwt {
+
+// Host-side NVTX range around the launches of one stage ("pack+radix[0]",
+// "radix[p]", "name", "double[r]", "gather", "bucket_*", "mlp_*", ...); a
+// profiler shows them on the host timeline (in graph mode they mark the
+// capture). Without a profiler attached the calls do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    NvtxRange(const char* name, int index) {
+        char b[64];
+        std::snprintf(b, sizeof b, "%s[%d]", name, index);
+        nvtxRangePushA(b);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Consecutive NVTX ranges through one function: next() closes the open
+// range and opens another; the last one closes with the object.
+struct NvtxStages {
+    bool open = false;
+    void next(const char* name) {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+    }
+    ~NvtxStages() {
+        if (open) nvtxRangePop();
+    }
+};
 
 struct EvMeta {
     double bytes_per_key;

@@ -317,6 +317,7 @@ __global__ void __launch_bounds__(OsThreads<TILE>::value, OsMinBlocks<TILE>::val
             if constexpr (VDIG) d = (v >> p.shift) & (uint32_t)(RADIX - 1);
             else d = (uint32_t)((k >> p.shift) & (KeyT)(RADIX - 1));
             const uint32_t dst = gbase[d] + q;
+            BWT_DCHECK(dst - td.segStart < td.pad0, &p.ctrl[CTRL_ERR]);  // inside the tile's segment
             kout[dst] = k;
             p.vout[dst] = v;
         }

@@ -563,6 +563,7 @@ __global__ void __launch_bounds__(MTF_WARPS * 32) k_mtf_encode(const uint8_t* __
 extern "C" bwt_status bwt_rle_encode(bwt_plan* p, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
                                      uint8_t* d_chars, uint32_t* d_lens, uint64_t* d_run_off, void* stream) {
     if (!p || !d_in || !offsets || !d_chars || !d_lens || !d_run_off) return BWT_EINVAL;
+    bwt::NvtxRange nvtx_range("rle_encode");
     if (cudaSetDevice(p->device) != cudaSuccess) return BWT_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::memset(&p->stats, 0, sizeof(p->stats));
@@ -586,6 +587,7 @@ extern "C" bwt_status bwt_rle_decode(bwt_plan* p, const uint8_t* d_chars, const 
                                      const uint64_t* d_run_off, const uint64_t* offsets, uint32_t num_blocks,
                                      uint8_t* d_out, void* stream) {
     if (!p || !d_chars || !d_lens || !d_run_off || !offsets || !d_out) return BWT_EINVAL;
+    bwt::NvtxRange nvtx_range("rle_decode");
     if (cudaSetDevice(p->device) != cudaSuccess) return BWT_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::memset(&p->stats, 0, sizeof(p->stats));
@@ -611,6 +613,7 @@ extern "C" bwt_status bwt_vle_encode(bwt_plan* p, const uint8_t* d_in, const uin
                                      const uint32_t* d_code, const uint8_t* d_len, uint8_t* d_out, uint64_t out_cap,
                                      uint64_t* d_byte_off, uint64_t* d_block_bits, void* stream) {
     if (!p || !d_in || !offsets || !d_code || !d_len || !d_out || !d_byte_off || !d_block_bits) return BWT_EINVAL;
+    bwt::NvtxRange nvtx_range("vle_encode");
     if ((reinterpret_cast<uintptr_t>(d_out) & 3u) != 0) return BWT_EINVAL;  // written as 32-bit words
     if (cudaSetDevice(p->device) != cudaSuccess) return BWT_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -646,6 +649,7 @@ extern "C" bwt_status bwt_vle_encode(bwt_plan* p, const uint8_t* d_in, const uin
 extern "C" bwt_status bwt_mtf_encode(bwt_plan* p, const uint8_t* d_in, const uint64_t* offsets, uint32_t num_blocks,
                                      uint8_t* d_out, void* stream) {
     if (!p || !d_in || !offsets || !d_out) return BWT_EINVAL;
+    bwt::NvtxRange nvtx_range("mtf_encode");
     if (cudaSetDevice(p->device) != cudaSuccess) return BWT_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::memset(&p->stats, 0, sizeof(p->stats));

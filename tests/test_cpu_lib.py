@@ -85,3 +85,15 @@ def test_plan_create_without_gpu_reports_cuda_error():
     st = lib.bwt_plan_create(ctypes.byref(desc), 0, ctypes.byref(h))
     assert st in (_lib.BWT_ECUDA, _lib.BWT_EINVAL)
     assert not h.value
+
+
+def test_debug_library_builds_and_exports_every_declared_symbol():
+    """The -DBWT_DEBUG build (bounds checks that record BWT_EINTERNAL) compiles
+    for sm_103a here and exports the same C ABI."""
+    from paper_1109_2348_gb300 import _build
+    so = _build.build_bwt(debug=True)
+    lib = ctypes.CDLL(str(so))
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    lib.bwt_status_string.restype = ctypes.c_char_p
+    assert lib.bwt_status_string(_lib.BWT_EINTERNAL).decode() == "BWT_EINTERNAL"
