@@ -78,7 +78,7 @@ enum : int {
     CTRL_WITHHOLD = 17,     // debug: first tile withholds its look-back publish
     CTRL_DEPTH = 18,        // prefix length h the current round doubles
     CTRL_NTILES0 = 19,      // tiles of the first sort
-    CTRL_BODY_ITERS = 20,   // graph mode: iterations of the doubling loop body
+    CTRL_BODY_ITERS = 20,   // graph mode: doubling rounds whose launches ran (a round skipped by its condition is not counted)
     CTRL_AUX0 = 21,         // learned: tiles of plain-routed blocks
     CTRL_AUX1 = 22,         // learned: tiles of bucketed blocks
     CTRL_TILE_CTR = 32,     // [64] atomic tile counters, one per radix pass

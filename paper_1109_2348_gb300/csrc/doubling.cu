@@ -984,20 +984,25 @@ __device__ __forceinline__ bool any_groups(const uint32_t* c) {
 }
 
 // After a round that read bins[par]: advance the depth if the round had
-// work, and (graph mode) set the loop condition from bins[par ^ 1].
-__global__ void k_round_end(uint32_t* ctrl, int par, uint32_t max_n, cudaGraphConditionalHandle cond, int use_cond,
-                            int count_body) {
+// work; in graph mode also count the round and set conditions from whether
+// another round is due (bins[par ^ 1] holds groups, the prefix is below the
+// largest block, no device error, fewer than 40 rounds): flags bit 0 sets
+// the doubling loop's condition, bit 1 the next round's own condition (the
+// loop body's second round), bit 2 counts the round.
+__global__ void k_round_end(uint32_t* ctrl, int par, uint32_t max_n, cudaGraphConditionalHandle loop,
+                            cudaGraphConditionalHandle next_round, int flags) {
     const uint32_t* cur = ctrl + CTRL_BINS + NCLS * par;
     const uint32_t* nxt = ctrl + CTRL_BINS + NCLS * (par ^ 1);
     if (any_groups(cur)) {
         ctrl[CTRL_DEPTH] *= 2u;
         ctrl[CTRL_ROUNDS] += 1u;
     }
-    if (count_body) ctrl[CTRL_BODY_ITERS] += 1u;
-    if (use_cond) {
+    if (flags & 4) ctrl[CTRL_BODY_ITERS] += 1u;
+    if (flags & 3) {
         const bool more = any_groups(nxt) && ctrl[CTRL_DEPTH] < max_n && ctrl[CTRL_ROUNDS] < 40u &&
                           ctrl[CTRL_ERR] == 0u;
-        cudaGraphSetConditional(cond, more ? 1u : 0u);
+        if (flags & 1) cudaGraphSetConditional(loop, more ? 1u : 0u);
+        if (flags & 2) cudaGraphSetConditional(next_round, more ? 1u : 0u);
     }
 }
 
@@ -1011,9 +1016,9 @@ cudaError_t launch_reset_ctrl(uint32_t* ctrl, uint32_t spin, uint32_t withhold, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_round_end(uint32_t* ctrl, int par, uint32_t max_n, cudaGraphConditionalHandle cond, int use_cond,
-                             int count_body, cudaStream_t st) {
-    k_round_end<<<1, 1, 0, st>>>(ctrl, par, max_n, cond, use_cond, count_body);
+cudaError_t launch_round_end(uint32_t* ctrl, int par, uint32_t max_n, cudaGraphConditionalHandle loop,
+                             cudaGraphConditionalHandle next_round, int flags, cudaStream_t st) {
+    k_round_end<<<1, 1, 0, st>>>(ctrl, par, max_n, loop, next_round, flags);
     return cudaGetLastError();
 }
 

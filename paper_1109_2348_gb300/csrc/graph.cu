@@ -4,13 +4,16 @@
 //
 // Graph = reset -> first stage (plain: first sort + naming; with
 //         BWT_F_LEARNED: the learned first stage) -> set loop condition ->
-//         WHILE(cond) { round on bins[0]; round on bins[1]; set cond } ->
-//         L gather.
+//         WHILE(cond) { round on bins[0]; IF(another round due) { round on
+//         bins[1] } } -> L gather.
 // The body holds two rounds so the double-buffered group bins alternate
-// inside one fixed graph; a round whose input bins are empty is a chain of
-// early-exiting persistent kernels. The loop condition (groups left, depth
-// below the largest block, no device error, at most 40 rounds) is computed
-// on the device, so a replay never returns to the host between rounds.
+// inside one fixed graph; the second is skipped when the first finished the
+// batch (about twenty launches that would find no work). The conditions
+// (groups left, depth below the largest block, no device error, at most 40
+// rounds) are computed on the device, so a replay never returns to the host
+// between rounds. (Conditional nodes around each round's large-group section
+// were measured too: evaluating them cost about what the skipped launches
+// did, and more on workloads whose rounds mostly have large groups.)
 #include <cstring>
 #include <vector>
 
@@ -52,13 +55,35 @@ static bwt_status launch_entry(bwt_plan* p, GraphEntry& ge, cudaStream_t st, boo
     if (e != cudaSuccess) return record_cuda(e, "cudaEventRecord");
     ge.last_use = ++p->graph_use;
     p->graph_main_kernels = ge.main_kernels;
-    p->graph_body_kernels = ge.body_kernels;
+    p->graph_round_kernels = ge.round_kernels;
+    p->graph_large_kernels = ge.large_kernels;
     p->graph_main_radix = ge.main_radix;
-    p->graph_body_radix = ge.body_radix;
+    p->graph_large_radix = ge.large_radix;
     p->stats.graph_replayed = replay ? 1u : 0u;
     p->stats.kernel_launches = 0;
     p->stats.radix_launches = 0;
     return BWT_OK;
+}
+
+bwt_status bwt::begin_if_capture(cudaStream_t st, cudaStream_t inner, cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cst, nullptr, &g, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return record_cuda(e, "cudaStreamGetCaptureInfo");
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp)) != cudaSuccess) return record_cuda(e, "IF node");
+    if ((e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+        return record_cuda(e, "cudaStreamUpdateCaptureDependencies");
+    e = cudaStreamBeginCaptureToGraph(inner, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    return e == cudaSuccess ? BWT_OK : record_cuda(e, "cudaStreamBeginCaptureToGraph");
 }
 
 bwt_status bwt::run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_t* d_primary, cudaStream_t st) {
@@ -75,21 +100,23 @@ bwt_status bwt::run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_
     }
 
     bwt_status status = BWT_OK;
-    cudaStream_t cs = nullptr, bs = nullptr;
+    // capture streams: the main graph, the loop body, the body's second round
+    cudaStream_t cs = nullptr, bs = nullptr, rs = nullptr;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t launched = nullptr;
-    cudaGraphConditionalHandle cond;
+    cudaGraphConditionalHandle cond, cond_r1;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
     cudaStreamCaptureStatus cst;
     cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
     cudaGraphNode_t cnode;
-    cudaGraph_t body;
-    uint64_t k0, k1, k2, k3, r0, r1, r2, r3;
+    cudaGraph_t body, tmp;
+    uint64_t k0, k1, k2, k3, k4, r0, r1, r3, r4;
 
     CKG(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     CKG(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+    CKG(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
     CKG(cudaGraphCreate(&g, 0));
     CKG(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
     p->capturing = true;
@@ -110,29 +137,37 @@ bwt_status bwt::run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_
     CKG(cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp));
     body = cp.conditional.phGraph_out[0];
     CKG(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    // loop body: a round on bins[0]; then, if another round is due, a round
+    // on bins[1] (an IF node, so a finished batch skips it)
     CKG(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     CKS(enqueue_round(p, 0, nullptr, bs));
-    CKG(launch_round_end(p->ctrl, 0, p->max_n, cond, 0, 0, bs));
-    CKS(enqueue_round(p, 1, nullptr, bs));
-    CKG(launch_round_end(p->ctrl, 1, p->max_n, cond, 1, 1, bs));
-    p->stats.kernel_launches += 2;
-    CKG(cudaStreamEndCapture(bs, &body));
+    CKG(cudaGraphConditionalHandleCreate(&cond_r1, body, 0, 0));
+    CKG(launch_round_end(p->ctrl, 0, p->max_n, cond, cond_r1, 1 | 2 | 4, bs));
+    p->stats.kernel_launches++;
     k2 = p->stats.kernel_launches;
-    r2 = p->stats.radix_launches;
+    CKS(begin_if_capture(bs, rs, cond_r1));
+    CKS(enqueue_round(p, 1, nullptr, rs));
+    CKG(launch_round_end(p->ctrl, 1, p->max_n, cond, 0, 1 | 4, rs));
+    p->stats.kernel_launches++;
+    CKG(cudaStreamEndCapture(rs, &tmp));
+    CKG(cudaStreamEndCapture(bs, &body));
+    k3 = p->stats.kernel_launches;
+    r3 = p->stats.radix_launches;
     {
         NvtxRange nv("gather");
         CKG(launch_gather_L(d_in, p->sa, p->blocks, p->tiles0, p->ntiles0, d_L, d_primary, p->ctrl, cs));
     }
     p->stats.kernel_launches++;
-    k3 = p->stats.kernel_launches;
-    r3 = p->stats.radix_launches;
+    k4 = p->stats.kernel_launches;
+    r4 = p->stats.radix_launches;
     CKG(cudaStreamEndCapture(cs, &g));
     p->capturing = false;
     CKG(cudaGraphInstantiate(&exec, g, 0));
     CKG(cudaEventCreateWithFlags(&launched, cudaEventDisableTiming));
     cudaStreamDestroy(cs);
     cudaStreamDestroy(bs);
-    cs = bs = nullptr;
+    cudaStreamDestroy(rs);
+    cs = bs = rs = nullptr;
     {
         // the least recently used graph makes room (its last launch may still run)
         if (p->graphs.size() >= kGraphCache) {
@@ -154,10 +189,11 @@ bwt_status bwt::run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_
         ge.exec = exec;
         g = nullptr;
         exec = nullptr;
-        ge.main_kernels = (k1 - k0) + (k3 - k2);
-        ge.body_kernels = k2 - k1;
-        ge.main_radix = (r1 - r0) + (r3 - r2);
-        ge.body_radix = r2 - r1;
+        ge.main_kernels = (k1 - k0) + (k4 - k3);
+        ge.large_kernels = p->cap_large_kernels;
+        ge.round_kernels = (k2 - k1) - ge.large_kernels;  // one round and its end kernel, the section aside
+        ge.main_radix = (r1 - r0) + (r4 - r3);
+        ge.large_radix = p->cap_large_radix;
         ge.launched = launched;
         p->graphs.push_back(std::move(ge));
     }
@@ -165,15 +201,11 @@ bwt_status bwt::run_graph(bwt_plan* p, const uint8_t* d_in, uint8_t* d_L, int32_
 
 fail:
     p->capturing = false;
-    if (cs) {
-        cudaGraph_t tmp = nullptr;
-        cudaStreamEndCapture(cs, &tmp);
-        cudaStreamDestroy(cs);
-    }
-    if (bs) {
-        cudaGraph_t tmp = nullptr;
-        cudaStreamEndCapture(bs, &tmp);
-        cudaStreamDestroy(bs);
+    for (cudaStream_t s : {rs, bs, cs}) {  // innermost captures first
+        if (!s) continue;
+        cudaGraph_t t = nullptr;
+        cudaStreamEndCapture(s, &t);
+        cudaStreamDestroy(s);
     }
     if (launched) cudaEventDestroy(launched);
     if (exec) cudaGraphExecDestroy(exec);
@@ -182,10 +214,12 @@ fail:
     return status;
 }
 
-// After a graph run: kernel and round counts from the device control words.
+// After a graph run: kernel and round counts from the device control words
+// (the rounds whose launches ran).
 void bwt::graph_stats(bwt_plan* p) {
-    const uint64_t iters = p->h_ctrl[CTRL_BODY_ITERS];
+    const uint64_t rounds_run = p->h_ctrl[CTRL_BODY_ITERS];
     p->stats.rounds = p->h_ctrl[CTRL_ROUNDS];
-    p->stats.kernel_launches = p->graph_main_kernels + iters * p->graph_body_kernels;
-    p->stats.radix_launches = p->graph_main_radix + iters * p->graph_body_radix;
+    p->stats.kernel_launches =
+        p->graph_main_kernels + rounds_run * (p->graph_round_kernels + p->graph_large_kernels);
+    p->stats.radix_launches = p->graph_main_radix + rounds_run * p->graph_large_radix;
 }

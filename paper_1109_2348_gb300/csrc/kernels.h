@@ -139,8 +139,11 @@ cudaError_t launch_rename_large(const uint32_t* SA, const uint32_t* key2, uint32
 // Control words: reset before a batch; advance after a round (and set the
 // graph loop condition); set the condition before the loop.
 cudaError_t launch_reset_ctrl(uint32_t* ctrl, uint32_t spin, uint32_t withhold, uint32_t ntiles0, cudaStream_t st);
-cudaError_t launch_round_end(uint32_t* ctrl, int par, uint32_t max_n, cudaGraphConditionalHandle cond, int use_cond,
-                             int count_body, cudaStream_t st);
+// flags: 1 = set the loop condition `loop`, 2 = set `next_round`, 4 = count
+// the round (graph mode); both conditions get "another round is due".
+cudaError_t launch_round_end(uint32_t* ctrl, int par, uint32_t max_n, cudaGraphConditionalHandle loop,
+                             cudaGraphConditionalHandle next_round, int flags, cudaStream_t st);
+
 cudaError_t launch_set_cond_initial(const uint32_t* ctrl, uint32_t max_n, cudaGraphConditionalHandle cond,
                                     cudaStream_t st);
 

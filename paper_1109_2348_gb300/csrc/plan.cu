@@ -529,9 +529,15 @@ bwt_status bwt::enqueue_initial_sort(bwt_plan* p, const uint8_t* d_in, cudaStrea
         seg_stride = 6 * 2048;
     }
     p->stats.kernel_launches += 2;
+    // 8-bit digits: every pass gets its own look-back region (8 x 256 words a
+    // tile fit the status array), all zeroed by one memset; 11-bit passes
+    // reuse one region, zeroed before each
+    const size_t region = (size_t)nt * RADIX;
+    const bool one_memset = region * P <= p->cap_status;
+    if (one_memset) CK(cudaMemsetAsync(p->status, 0, sizeof(uint32_t) * region * P, st));
     for (int ps = 0; ps < P; ++ps) {
         NvtxRange nv(ps == 0 ? "pack+radix" : "radix", ps);
-        CK(cudaMemsetAsync(p->status, 0, sizeof(uint32_t) * (size_t)nt * RADIX, st));
+        if (!one_memset) CK(cudaMemsetAsync(p->status, 0, sizeof(uint32_t) * region, st));
         OneSweepParams a{};
         a.kin = ps == 0 ? nullptr : p->keys[(ps - 1) & 1];
         a.vin = ps == 0 ? nullptr : p->vals[(ps - 1) & 1];
@@ -543,7 +549,7 @@ bwt_status bwt::enqueue_initial_sort(bwt_plan* p, const uint8_t* d_in, cudaStrea
         a.num_tiles = ctrl + CTRL_NTILES0;
         a.seg_base = p->hist + (rb == 8 ? 0 : ps * 2048);
         a.seg_base_stride = seg_stride;
-        a.status = p->status;
+        a.status = p->status + (one_memset ? region * ps : 0);
         a.tile_counter = ctrl + CTRL_TILE_CTR + ps;
         a.ctrl = ctrl;
         a.shift = ps * rb;
@@ -584,21 +590,23 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
         p->stats.kernel_launches += launched;
     }
     const bool large = !host_counts || host_counts[CLS_LARGE] > 0;
+    const uint64_t k0 = p->stats.kernel_launches, r0 = p->stats.radix_launches;
     const uint32_t hist_cap = (uint32_t)std::min<uint64_t>(p->cap_hist, 0xffffffffu);
     const uint32_t status_cap = (uint32_t)std::min<uint64_t>(p->cap_status, 0xffffffffu);
     if (large) {
-        CK(launch_build_large_tiles(cur, p->tile, p->ltiles, p->cap_ltiles, ctrl, st, p->seg_varied));
-        CK(launch_zero_by_count(p->hist, cur.count + CLS_LARGE, (uint32_t)(P2 * RADIX), hist_cap, st));
+        const cudaStream_t ls = st;
+        CK(launch_build_large_tiles(cur, p->tile, p->ltiles, p->cap_ltiles, ctrl, ls, p->seg_varied));
+        CK(launch_zero_by_count(p->hist, cur.count + CLS_LARGE, (uint32_t)(P2 * RADIX), hist_cap, ls));
         // with one pass only, that pass would read and write SA in place: it
         // reads a copy instead
         CK(launch_large_prologue(p->sa, p->rank, p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, depth, p->kA,
-                                 P2 == 1 ? p->vA : nullptr, p->hist, rb, P2, p->seg_varied, st));
+                                 P2 == 1 ? p->vA : nullptr, p->hist, rb, P2, p->seg_varied, ls));
         CK(launch_scan_rows(p->hist, RADIX, cur.count + CLS_LARGE, (uint32_t)P2, 0, (uint32_t)(p->cap_hist / RADIX),
-                            st));
+                            ls));
         p->stats.kernel_launches += 4;
         for (int ps = 0; ps < P2; ++ps) {
-            CK(launch_zero_by_count(p->status, ctrl + CTRL_NUM_LTILES, (uint32_t)RADIX, status_cap, st));
-            CK(cudaMemsetAsync(ctrl + CTRL_TILE_CTR + 16 + ps, 0, 4, st));
+            CK(launch_zero_by_count(p->status, ctrl + CTRL_NUM_LTILES, (uint32_t)RADIX, status_cap, ls));
+            CK(cudaMemsetAsync(ctrl + CTRL_TILE_CTR + 16 + ps, 0, 4, ls));
             p->stats.kernel_launches++;
             OneSweepParams a{};
             const bool last = ps == P2 - 1;
@@ -616,18 +624,22 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
             a.ctrl = ctrl;
             a.shift = ps * rb;
             a.seg_varied = p->seg_varied;  // groups whose key2 are all equal do not move
-            CK(timed_onesweep(p, 4, false, a, 16.0, 0, CTRL_LARGE_KEYS, st, rb));
+            CK(timed_onesweep(p, 4, false, a, 16.0, 0, CTRL_LARGE_KEYS, ls, rb));
         }
         p->pending_large_passes = (uint32_t)P2;
     }
+    const uint64_t k1 = p->stats.kernel_launches, r1 = p->stats.radix_launches;
     int launched = 0;
     CK(launch_sort_small(p->sa, p->key2, p->rank, p->blocks, cur, nxt, depth, host_counts, ctrl, st, &launched));
     p->stats.kernel_launches += launched;
+    const uint64_t k2 = p->stats.kernel_launches;
     if (large) {
         CK(launch_rename_large(p->sa, p->key2, p->rank, p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, nxt, depth,
                                p->seg_varied, ctrl, st));
         p->stats.kernel_launches++;
     }
+    p->cap_large_kernels = (k1 - k0) + (p->stats.kernel_launches - k2);  // one round's large-group section
+    p->cap_large_radix = r1 - r0;
     return BWT_OK;
 }
 
@@ -722,7 +734,7 @@ bwt_status bwt::run_doubling_host_loop(bwt_plan* p, cudaStream_t st) {
         if (any == 0) break;
         bwt_status s = enqueue_round(p, par, counts, st);
         if (s != BWT_OK) return s;
-        CK(launch_round_end(p->ctrl, par, p->max_n, 0, 0, 0, st));
+        CK(launch_round_end(p->ctrl, par, p->max_n, 0, 0, 0, st));  // advance the depth only
         p->stats.kernel_launches++;
         p->stats.rounds++;
         if (depth > 0x7fffffffu) break;

@@ -62,7 +62,9 @@ struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t launched = nullptr;  // recorded after its last launch
     uint64_t last_use = 0;
-    uint64_t main_kernels = 0, body_kernels = 0, main_radix = 0, body_radix = 0;
+    // kernels of the graph outside the doubling loop, of one round without its
+    // large-group section, and of that section; radix passes likewise
+    uint64_t main_kernels = 0, round_kernels = 0, large_kernels = 0, main_radix = 0, large_radix = 0;
 };
 
 constexpr size_t kGraphCache = 4;
@@ -171,8 +173,9 @@ struct bwt_plan {
     // call launched
     std::vector<bwt::GraphEntry> graphs;
     uint64_t graph_use = 0;
-    uint64_t graph_main_kernels = 0, graph_body_kernels = 0;
-    uint64_t graph_main_radix = 0, graph_body_radix = 0;
+    uint64_t graph_main_kernels = 0, graph_round_kernels = 0, graph_large_kernels = 0;
+    uint64_t graph_main_radix = 0, graph_large_radix = 0;
+    uint64_t cap_large_kernels = 0, cap_large_radix = 0;  // one round's large-group section, as enqueued
     bool capturing = false;
 
     bwt_stats stats{};
@@ -190,7 +193,13 @@ Bins bins_of(bwt_plan* p, int par);
 int round_radix_bits(const bwt_plan* p);
 bwt_status reset_ctrl(bwt_plan* p, cudaStream_t st);
 bwt_status enqueue_initial_sort(bwt_plan* p, const uint8_t* d_in, cudaStream_t st);
+// One doubling round on bins[par]; records the kernels and radix passes of
+// its large-group section (cap_large_kernels, cap_large_radix).
 bwt_status enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts, cudaStream_t st);
+// Graph capture helper: an IF node on handle h appended to the graph `st`
+// is capturing (after st's work so far), whose body `inner` then captures
+// until cudaStreamEndCapture(inner).
+bwt_status begin_if_capture(cudaStream_t st, cudaStream_t inner, cudaGraphConditionalHandle h);
 bwt_status enqueue_naming(bwt_plan* p, const uint64_t* K, cudaStream_t st);
 bwt_status finish_status(bwt_plan* p, cudaStream_t st);
 // Status of the control words' error field as read into h_ctrl.

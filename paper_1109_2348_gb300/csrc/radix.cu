@@ -239,24 +239,39 @@ __global__ void __launch_bounds__(OsThreads<TILE>::value, OsMinBlocks<TILE>::val
                 const int d = tid;
                 uint32_t excl = 0;
                 if (!first) {
-                    uint32_t q = t - 1;
+                    // Walk back LB predecessors a step: their words are loaded
+                    // together, then added in order until an inclusive one. When
+                    // the tiles of a segment run at once (a small batch), their
+                    // words are mostly aggregates, and the walk is a chain of
+                    // L2 round trips that this shortens LB-fold.
+                    constexpr uint32_t LB = 4;
+                    uint32_t q = t - 1;  // the next predecessor to add (>= firstTile)
                     for (;;) {
-                        const uint32_t* w = p.status + (size_t)q * RADIX + d;
-                        uint32_t v = ld_volatile(w);
-                        uint32_t it = 0;
-                        while ((v & (ST_AGG | ST_INC)) == 0u) {
-                            if (++it > spin_limit) {
-                                atomicOr(&p.ctrl[CTRL_ERR], ERR_TIMEOUT);
-                                v = ST_INC;  // give up: proceed with a short prefix (stays in bounds)
-                                break;
+                        const uint32_t m = min(LB, q - td.firstTile + 1);
+                        uint32_t v[LB];
+#pragma unroll
+                        for (uint32_t k = 0; k < LB; ++k)
+                            v[k] = k < m ? ld_volatile(p.status + (size_t)(q - k) * RADIX + d) : 0u;
+                        bool done = false;
+#pragma unroll
+                        for (uint32_t k = 0; k < LB; ++k) {
+                            if (k >= m || done) break;
+                            uint32_t it = 0;
+                            while ((v[k] & (ST_AGG | ST_INC)) == 0u) {
+                                if (++it > spin_limit) {
+                                    atomicOr(&p.ctrl[CTRL_ERR], ERR_TIMEOUT);
+                                    v[k] = ST_INC;  // give up: proceed with a short prefix (stays in bounds)
+                                    break;
+                                }
+                                if (it > 32) __nanosleep(64);
+                                v[k] = ld_volatile(p.status + (size_t)(q - k) * RADIX + d);
                             }
-                            if (it > 32) __nanosleep(64);
-                            v = ld_volatile(w);
+                            excl += v[k] & ST_VALUE;
+                            if (v[k] & ST_INC) done = true;
                         }
-                        excl += v & ST_VALUE;
-                        if (v & ST_INC) break;
-                        if (q == td.firstTile) break;  // defensive: the first tile is always inclusive
-                        --q;
+                        // the segment's first tile is always inclusive: reaching it ends the walk
+                        if (done || q + 1 - m == td.firstTile) break;
+                        q -= m;
                     }
                     st_volatile(p.status + (size_t)t * RADIX + d, ST_INC | ((excl + cnt[0]) & ST_VALUE));
                 }

@@ -256,3 +256,31 @@ def test_radix16_with_learned_bucketing():
         st = plan.stats()
         assert st["blocks_routed_plain"] >= 1
         assert_matches_oracle(buf, off, L.cpu().numpy(), prim.cpu().numpy(), "learned + 16-bit")
+
+
+@pytest.mark.parametrize("src, n", [(datagen.MARKOV2_Z64, 100_000), (datagen.CONST, 50_000),
+                                     (datagen.PERIOD7, 30_001), (datagen.RUNS16, 80_000),
+                                     (datagen.UNIFORM, 20_000), (datagen.FIBONACCI, 40_000)])
+def test_graph_skips_empty_rounds_and_sections_like_the_host_loop(src, n):
+    """In graph mode the body's second round and each round's large-group
+    sections are conditional nodes. On inputs from one round without large
+    groups (uniform) to many rounds with them (constant, periodic,
+    Fibonacci), the graph must run exactly the rounds the host-driven loop
+    runs and give the oracle's output, on capture and on replay."""
+    import torch
+    w = datagen.Workload("t", [src], [77], [n])
+    buf, off = w.generate()
+    _, _, st_host = gpu_bwt(buf, off)
+    d_in = torch.from_numpy(buf).cuda()
+    L = torch.empty_like(d_in)
+    prim = torch.empty(1, dtype=torch.int32, device="cuda")
+    with Plan(max_blocks=1, max_total_bytes=n, max_block_bytes=n, flags=F_GRAPH) as plan:
+        for call in range(2):
+            L.zero_()
+            plan.forward_into(d_in, off, L, prim)
+            torch.cuda.synchronize()
+            assert plan.last_status() == 0
+            st = plan.stats()
+            assert st["rounds"] == st_host["rounds"], (st["rounds"], st_host["rounds"])
+            assert st["graph_replayed"] == call
+            assert_matches_oracle(buf, off, L.cpu().numpy(), prim.cpu().numpy(), f"graph call {call}")
