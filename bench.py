@@ -244,7 +244,7 @@ def timed_cpu_baseline(w, cores: int, target_s: float = 12.0):
 # DRAM bytes (read + write) per key of one u64 onesweep pass as ncu counted
 # them (1-pass metrics) for the current kernel on one full-size pass of the
 # mixed3-64x900000 workload; None when the kernel has changed since.
-ONESWEEP_DRAM_BYTES_PER_KEY = 23.34
+ONESWEEP_DRAM_BYTES_PER_KEY = 23.37
 # DRAM bytes (read + write) per rotation of the learned chunk sort
 # (k_chunk_sort_name<256, 4, 0>) as ncu counted them for the current kernel on
 # 24 blocks of the learned-eval workload; None when the kernel has changed since.
@@ -495,11 +495,13 @@ def ours(args):
         th.close()
         achieved = acc["bytes"] / (acc["ms"] / 1e3) / 1e9
         per_launch_keys = acc["keys"] / max(1, acc["launches"])
-        return {"bound": "hbm", "kernel": f"k_onesweep<u64, {stats['radix_bits']}, {stats['tile_keys']}> "
-                                          "(plain first-sort radix pass)",
+        kname = ("k_hist16 + k_scan16_cols + k_scan16_digits + k_scatter16 (plain first-sort 16-bit pass)"
+                 if stats["radix_bits"] == 16 else
+                 f"k_onesweep<u64, {stats['radix_bits']}, {stats['tile_keys']}> (plain first-sort radix pass)")
+        return {"bound": "hbm", "kernel": kname,
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "peak_source": peak_kind + " hbm_gbs",
-                "traffic": None if ONESWEEP_DRAM_BYTES_PER_KEY is None else
+                "traffic": None if ONESWEEP_DRAM_BYTES_PER_KEY is None or stats["radix_bits"] != 8 else
                 round(ONESWEEP_DRAM_BYTES_PER_KEY * per_launch_keys),
                 "algorithmic_bytes_per_launch": round(acc["bytes"] / max(1, acc["launches"])),
                 "launches_timed": acc["launches"], "avg_launch_ms": round(acc["ms"] / max(1, acc["launches"]), 4)}
@@ -581,7 +583,8 @@ def other_workloads(args, dev, local, flush, model_path):
     GPU (inputs resident in HBM, L2 flushed before every step, CUDA events on
     the launch stream): input MB/s and ms per step."""
     from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, F_PER_BLOCK_LAUNCH
-    runs = {1: [("graph", F_GRAPH)], 2: [("learned", F_LEARNED | F_GRAPH), ("graph", F_GRAPH)],
+    runs = {1: [("graph", F_GRAPH), ("graph_autotuned", F_GRAPH)],
+            2: [("learned", F_LEARNED | F_GRAPH), ("graph", F_GRAPH)],
             3: [("graph", F_GRAPH)], 4: [("graph", F_GRAPH), ("perblock", F_PER_BLOCK_LAUNCH)],
             5: [("learned", F_LEARNED | F_GRAPH), ("graph", F_GRAPH)]}
     out = {}
@@ -593,6 +596,10 @@ def other_workloads(args, dev, local, flush, model_path):
         res = {"workload": R.w.name, "blocks": R.w.num_blocks, "bytes": R.n}
         for label, fl in runs[cfg]:
             pl = R.plan(fl, model_path=model_path)
+            tuned = None
+            if label.endswith("autotuned"):  # the plan's autotuner picks digit width and tile size first
+                rb, tk, _ = pl.autotune(R.d_in, R.off, R.d_L, R.d_p, repeats=3, stream=R.stream)
+                tuned = {"radix_bits": rb, "tile_keys": tk}
             R.warm(pl, 3)
             k = 2 if label == "perblock" else steps
             ms, st = R.timed(pl, k)
@@ -600,6 +607,8 @@ def other_workloads(args, dev, local, flush, model_path):
             t = float(np.sum(ms))
             res[label] = {"value": round(R.n * k / (t / 1e3) / 1e6, 3), "unit": "MB/s",
                           "ms_per_step": round(t / k, 4), "rounds": st["rounds"], "steps": k}
+            if tuned:
+                res[label]["autotuned"] = tuned
         out[f"config{cfg}"] = res
         del R
     return out
