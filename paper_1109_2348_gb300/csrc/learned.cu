@@ -59,6 +59,7 @@ extern "C" bwt_status bwt_plan_set_splitters(bwt_plan* p, const uint64_t* splitt
     bwt_status s = ensure_learned_buffers(p);
     if (s != BWT_OK) return s;
     CKL(cudaMemcpy(p->splitters, h.data(), sizeof(uint64_t) * BWT_SPLITTERS, cudaMemcpyHostToDevice));
+    if ((s = build_splitter_index(p)) != BWT_OK) return s;
     p->have_model = true;
     return BWT_OK;
 }
@@ -185,11 +186,15 @@ namespace {
 constexpr int NBK = BWT_BUCKETS;
 constexpr int NSP = BWT_SPLITTERS;
 
-// Bucket of a key: #{j : spl[j] <= key}. first[c] = #{j : spl[j] < c << 52}
-// narrows the search to the splitters that share the key's top 12 bits (the
-// ones below all count, the ones above none).
-constexpr int IDX_BITS = 12;
+// Bucket of a key: #{j : spl[j] <= key}. first[c] = #{j : spl[j] < c << 48}
+// narrows the search to the splitters that share the key's first two bytes
+// (the ones below all count, the ones above none). Text keys use a few
+// thousand of the 65,536 two-byte prefixes and the splitters spread over
+// them, so a search takes one or two steps (five or six with an index on the
+// top 12 bits, whose bank conflicts bound the counting kernel).
+constexpr int IDX_BITS = 16;
 constexpr int IDX_CELLS = 1 << IDX_BITS;
+constexpr int IDX_WORDS = IDX_CELLS + 8;  // u16 entries (first[IDX_CELLS] = NSP), padded for 16-byte copies
 
 __device__ __forceinline__ uint32_t bucket_of(const uint64_t* spl, const uint16_t* first, uint64_t key) {
     const uint32_t c = (uint32_t)(key >> (64 - IDX_BITS));
@@ -201,27 +206,38 @@ __device__ __forceinline__ uint32_t bucket_of(const uint64_t* spl, const uint16_
     return lo;
 }
 
-// Loads the splitters into shared memory and builds the top-12-bit index.
-__device__ __forceinline__ void load_splitters(const uint64_t* __restrict__ splitters, uint64_t* spl, uint16_t* first) {
-    for (int i = threadIdx.x; i < NSP; i += blockDim.x) spl[i] = splitters[i];
-    __syncthreads();
-    for (int c = threadIdx.x; c < IDX_CELLS; c += blockDim.x) {
-        const uint64_t x = (uint64_t)c << (64 - IDX_BITS);
-        uint32_t lo = 0, hi = NSP;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (spl[mid] < x) lo = mid + 1; else hi = mid;
+// The index of a splitter table (built once when the table is installed).
+__global__ void k_build_index(const uint64_t* __restrict__ spl, uint16_t* __restrict__ first) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < IDX_WORDS; c += gridDim.x * blockDim.x) {
+        uint32_t lo = NSP;
+        if (c < IDX_CELLS) {
+            const uint64_t x = (uint64_t)c << (64 - IDX_BITS);
+            uint32_t hi = NSP;
+            lo = 0;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (spl[mid] < x) lo = mid + 1; else hi = mid;
+            }
         }
         first[c] = (uint16_t)lo;
     }
-    if (threadIdx.x == 0) first[IDX_CELLS] = (uint16_t)NSP;
+}
+
+// Loads the splitters and their index into shared memory.
+__device__ __forceinline__ void load_splitters(const uint64_t* __restrict__ splitters,
+                                               const uint16_t* __restrict__ index, uint64_t* spl, uint16_t* first) {
+    for (int i = threadIdx.x; i < NSP; i += blockDim.x) spl[i] = splitters[i];
+    const uint4* src = reinterpret_cast<const uint4*>(index);
+    uint4* dst = reinterpret_cast<uint4*>(first);
+    for (int i = threadIdx.x; i < IDX_WORDS / 8; i += blockDim.x) dst[i] = src[i];
     __syncthreads();
 }
 
-constexpr size_t SPL_BYTES = 4096 * 8 + (IDX_CELLS + 8) * 2;  // splitters + top-12-bit index (padded)
+constexpr size_t SPL_BYTES = 4096 * 8 + IDX_WORDS * 2;  // splitters + two-byte-prefix index
 constexpr size_t CNT_BYTES = 4096 * 4;
 constexpr size_t TILE_BYTES = 4096 + 48;
 constexpr size_t COUNT_SMEM = SPL_BYTES + CNT_BYTES + TILE_BYTES;
+constexpr int COUNT_THREADS = 1024;  // one CTA an SM: its shared memory holds the splitters and the index
 
 // Counts every rotation in two bucketings at once -- the learned splitters
 // and equal-width buckets (the top 12 key bits) -- and stores its learned
@@ -241,17 +257,20 @@ __device__ __forceinline__ void flush_counts(uint32_t* h, uint32_t* __restrict__
     }
 }
 
-__global__ void __launch_bounds__(256) k_bucket_count(const uint8_t* __restrict__ S, const BlockInfo* __restrict__ blocks,
-                                                      const TileDesc* __restrict__ tiles, uint32_t ntiles,
-                                                      uint32_t span, const uint64_t* __restrict__ splitters,
-                                                      uint32_t nb, uint32_t* __restrict__ counts,
-                                                      uint16_t* __restrict__ fb) {
+__global__ void __launch_bounds__(COUNT_THREADS, 1) k_bucket_count(const uint8_t* __restrict__ S,
+                                                                    const BlockInfo* __restrict__ blocks,
+                                                                    const TileDesc* __restrict__ tiles,
+                                                                    uint32_t ntiles, uint32_t span,
+                                                                    const uint64_t* __restrict__ splitters,
+                                                                    const uint16_t* __restrict__ index,
+                                                                    uint32_t nb, uint32_t* __restrict__ counts,
+                                                                    uint16_t* __restrict__ fb) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* spl = reinterpret_cast<uint64_t*>(smem);
     uint16_t* first = reinterpret_cast<uint16_t*>(smem + 4096 * 8);
     uint32_t* h = reinterpret_cast<uint32_t*>(smem + SPL_BYTES);
     uint8_t* sb = smem + SPL_BYTES + CNT_BYTES;
-    load_splitters(splitters, spl, first);
+    load_splitters(splitters, index, spl, first);
     for (int i = threadIdx.x; i < NBK; i += blockDim.x) h[i] = 0;
     const uint32_t nspan = (ntiles + span - 1) / span;
     for (uint32_t s = blockIdx.x; s < nspan; s += gridDim.x) {
@@ -827,6 +846,7 @@ int bits_needed(uint32_t max_value) {
 bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
     const size_t nbk = (size_t)p->cap_b * NBK;
     if (!p->splitters) CKL(cudaMalloc(&p->splitters, sizeof(uint64_t) * NSP));
+    if (!p->splitter_index) CKL(cudaMalloc(&p->splitter_index, sizeof(uint16_t) * IDX_WORDS));
     if (!p->bucket_count) CKL(cudaMalloc(&p->bucket_count, sizeof(uint32_t) * 2 * nbk));
     if (!p->bucket_cursor) CKL(cudaMalloc(&p->bucket_cursor, sizeof(uint32_t) * nbk));
     if (!p->chunk_map) CKL(cudaMalloc(&p->chunk_map, sizeof(uint16_t) * nbk));
@@ -859,6 +879,13 @@ bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
     return BWT_OK;
 }
 
+bwt_status bwt::build_splitter_index(bwt_plan* p) {
+    k_build_index<<<(IDX_WORDS + 255) / 256, 256>>>(p->splitters, p->splitter_index);
+    CKL(cudaGetLastError());
+    CKL(cudaStreamSynchronize(0));
+    return BWT_OK;
+}
+
 bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t st) {
     const uint32_t nb = p->nb, nt = p->ntiles0;
     const int sms = num_sms();
@@ -881,10 +908,10 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     CKL(cudaMemsetAsync(p->bucket_count, 0, sizeof(uint32_t) * 2 * NBK * nb, st));
     {
         const uint32_t span_max = 65535u / T;  // packed 16-bit counts per span
-        const uint32_t span = std::max(1u, std::min(span_max, nt / (uint32_t)(sms * 8)));
-        const int grid = std::max(1, std::min<int>((nt + span - 1) / span, sms * 3));
-        k_bucket_count<<<grid, 256, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles0, nt, span, p->splitters, nb,
-                                                      p->bucket_count, fb);
+        const uint32_t span = std::max(1u, std::min(span_max, nt / (uint32_t)(sms * 4)));
+        const int grid = std::max(1, std::min<int>((nt + span - 1) / span, sms));
+        k_bucket_count<<<grid, COUNT_THREADS, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles0, nt, span, p->splitters,
+                                                                p->splitter_index, nb, p->bucket_count, fb);
     }
     nv.next("bucket_route");
     k_bucket_stats<<<std::min<uint32_t>(2 * nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, 2 * nb, p->bstats);

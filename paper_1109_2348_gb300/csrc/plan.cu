@@ -133,7 +133,7 @@ void bwt::free_plan_memory(bwt_plan* p) {
         FH(p->stage_parts[sl]);
         FH(p->stage_pfirst[sl]);
     }
-    F(p->splitters); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->route_first); F(p->bstats); F(p->tiles_aux); F(p->inv_slots); F(p->inv_items); F(p->mtf_lists);
+    F(p->splitters); F(p->splitter_index); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->route_first); F(p->bstats); F(p->tiles_aux); F(p->inv_slots); F(p->inv_items); F(p->mtf_lists);
     drop_graph(p);
     FH(p->h_ctrl); FH(p->h_off);
     for (int s = 0; s < 2; ++s) {

@@ -102,6 +102,7 @@ struct bwt_plan {
 
     // learned bucketing (allocated when a model is installed)
     uint64_t* splitters = nullptr;      // [BWT_SPLITTERS] sorted
+    uint16_t* splitter_index = nullptr; // [65,544] first splitter of every two-byte key prefix
     uint64_t* splitters_flat = nullptr; // [BWT_SPLITTERS] equal-width fallback (top 12 key bits)
     uint32_t* bucket_count = nullptr;   // [2][block][BWT_BUCKETS] counts (learned, equal-width), then starts
     uint32_t* bucket_cursor = nullptr;  // [block][BWT_BUCKETS] slots taken so far (per chunk)
@@ -223,6 +224,8 @@ void learned_stats(bwt_plan* p);
 bwt_status load_model(bwt_plan* p, const char* path);
 void graph_stats(bwt_plan* p);
 bwt_status ensure_learned_buffers(bwt_plan* p);
+// The two-byte-prefix index of the installed splitter table (synchronous).
+bwt_status build_splitter_index(bwt_plan* p);
 // Scratch of the 16-bit digit passes (a no-op once allocated).
 bwt_status ensure_radix16(bwt_plan* p);
 
