@@ -357,7 +357,13 @@ constexpr int MS_IT = 13;                            // rotations per thread (od
 constexpr uint32_t CHUNK_CAP = MS_NT * MS_IT;        // 3328
 constexpr int BIG_NT = 1024;                         // threads of the big-chunk sort
 constexpr uint32_t BIG_CAP = BIG_NT * MS_IT;         // 13312
-constexpr uint32_t MAXCH = 1024;  // chunks per block (blocks above (MAXCH - 2) * CHUNK_CAP / 2 go plain)
+constexpr uint32_t MAXCH = 1024;  // chunks per block (blocks above about 1.6 M rotations go plain)
+constexpr uint32_t MAXB = 256;    // fine buckets per chunk (the chunk sort's bucket tables)
+
+// A chunk is packed by padded sizes: a bucket of s rotations takes
+// ceil(s / MS_IT) threads of the chunk sort (its team) and as many MS_IT-slot
+// runs, so a chunk's teams fit the sort's threads.
+__host__ __device__ constexpr uint32_t padded(uint32_t s) { return (s + MS_IT - 1) / MS_IT * MS_IT; }
 
 struct ChunkTables {
     uint16_t* cmap;        // [block][4096] chunk of each fine bucket
@@ -386,19 +392,20 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
             // (stopped at the first overflow bucket) shows how many still
             // fit in the open chunk, and those join it at once.
             const uint32_t lane = threadIdx.x;
-            uint32_t nch = 0, nemit = 0, len = 0, cstart = 0, b = 0;
+            uint32_t nch = 0, nemit = 0, len = 0, plen = 0, cstart = 0, cb0 = 0, nbo = 0, b = 0;
             bool open = false;  // a chunk is open (possibly holding only empty buckets)
             auto close = [&]() {  // the open chunk, if it holds rotations, becomes chunk nch
                 if (len > 0) {
                     if (lane == 0 && nch < MAXCH) {
                         cb[nch] = cstart;
-                        chunks[nemit] = GroupDesc{bi.off + cstart, len, blk, 0u};
+                        // pad: the chunk's first fine bucket and its number of buckets
+                        chunks[nemit] = GroupDesc{bi.off + cstart, len, blk, cb0 | (nbo << 16)};
                     }
                     if (nch < MAXCH) ++nemit;
                     ++nch;
                 }
                 open = false;
-                len = 0;
+                len = plen = nbo = 0;
             };
             while (b < (uint32_t)NBK) {
                 const uint32_t bb = b + lane;
@@ -411,7 +418,7 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
                         if (nch < MAXCH) cb[nch] = st[b];
                         const int li = sz <= BIG_CAP ? 1 : CLS_LARGE;  // big-chunk sort, else the overflow radix
                         const uint32_t slot = atomicAdd(&out.count[li], 1u);
-                        if (slot < out.cap[li]) out.list[li][slot] = GroupDesc{bi.off + st[b], sz, blk, 0u};
+                        if (slot < out.cap[li]) out.list[li][slot] = GroupDesc{bi.off + st[b], sz, blk, b | (1u << 16)};
                         else atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
                     }
                     ++nch;
@@ -419,21 +426,28 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
                     continue;
                 }
                 const uint32_t fb = bigm ? (uint32_t)(__ffs(bigm) - 1) : 32u;  // first stop lane (>= 1)
-                uint32_t incl = lane < fb ? sz : 0u;
+                uint32_t incl = lane < fb ? sz : 0u, pincl = lane < fb ? padded(sz) : 0u;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if ((int)lane >= o) incl += y;
+                    const uint32_t py = __shfl_up_sync(0xffffffffu, pincl, o);
+                    if ((int)lane >= o) {
+                        incl += y;
+                        pincl += py;
+                    }
                 }
-                const bool fit = lane < fb && len + incl <= CHUNK_CAP;
+                const bool fit = lane < fb && plen + pincl <= CHUNK_CAP && nbo + lane < MAXB;
                 const uint32_t k = __popc(__ballot_sync(0xffffffffu, fit));  // fits are a prefix of the lanes
                 if (k > 0) {
                     if (!open) {
                         open = true;
                         cstart = st[b];
+                        cb0 = b;
                     }
                     if (lane < k) cm[b + lane] = (uint16_t)min(nch, MAXCH - 1);
                     len += __shfl_sync(0xffffffffu, incl, k - 1);
+                    plen += __shfl_sync(0xffffffffu, pincl, k - 1);
+                    nbo += k;
                     b += k;
                 }
                 // lane k stopped: an overflow bucket (handled next step) or a
@@ -576,29 +590,13 @@ __device__ __forceinline__ bool ki_less(uint64_t ak, uint32_t ai, uint64_t bk, u
     return ak < bk || (ak == bk && ai < bi);
 }
 
-// Sorts sK/sI[0 .. NT * MS_IT) by (K, i), ascending, with NT threads: each
-// thread sorts its MS_IT consecutive entries in registers (a sorting
-// network), then log2(NT) rounds merge pairs of sorted runs, each
-// thread producing MS_IT outputs from its merge-path split (binary search
-// on its output diagonal, then a sequential merge). All threads call; the
-// arrays hold NT * MS_IT distinct entries (pad with (~0, 0xffff0000 + slot),
-// above every real pair, whose indices are below 2^30; (~0, ~0) stays free
-// as the merge's end-of-run sentinel).
-template <int NT>
-__device__ __forceinline__ void cta_merge_sort(uint64_t* sK, uint32_t* sI) {
-    const uint32_t t = threadIdx.x;
-    uint64_t k[MS_IT];
-    uint32_t v[MS_IT];
-#pragma unroll
-    for (int j = 0; j < MS_IT; ++j) {
-        k[j] = sK[t * MS_IT + j];
-        v[j] = sI[t * MS_IT + j];
-    }
-    // Batcher's odd-even merge sorting network for 16 inputs with every
-    // comparator that touches slots 13..15 dropped: those slots would hold
-    // +infinity, which a comparator never moves to a lower slot, so the rest
-    // sorts 13 entries (48 compare-exchanges instead of the 78 of odd-even
-    // transposition; checked on every 0/1 input, which suffices for a network)
+// Sorts a thread's MS_IT entries in registers by (K, i): Batcher's odd-even
+// merge sorting network for 16 inputs with every comparator that touches
+// slots 13..15 dropped (those slots would hold +infinity, which a comparator
+// never moves to a lower slot), 48 compare-exchanges instead of the 78 of
+// odd-even transposition (checked on every 0/1 input, which suffices for a
+// network).
+__device__ __forceinline__ void sort13(uint64_t (&k)[MS_IT], uint32_t (&v)[MS_IT]) {
     static_assert(MS_IT == 13, "the network below sorts 13 entries");
     constexpr int NET[48][2] = {
         {0, 1}, {2, 3}, {0, 2}, {1, 3}, {1, 2}, {4, 5}, {6, 7}, {4, 6}, {5, 7}, {5, 6}, {0, 4}, {2, 6}, {2, 4},
@@ -616,62 +614,33 @@ __device__ __forceinline__ void cta_merge_sort(uint64_t* sK, uint32_t* sI) {
         v[i] = x;
         v[j] = y;
     }
-#pragma unroll
-    for (int j = 0; j < MS_IT; ++j) {
-        sK[t * MS_IT + j] = k[j];
-        sI[t * MS_IT + j] = v[j];
-    }
-    __syncthreads();
-    for (uint32_t m = 2; m <= (uint32_t)NT; m <<= 1) {  // m threads per merged run of m * MS_IT
-        const uint32_t w = (m >> 1) * MS_IT;                // length of each input run
-        const uint32_t base = (t & ~(m - 1)) * MS_IT;
-        const uint32_t diag = (t & (m - 1)) * MS_IT;
-        const uint64_t* AK = sK + base;
-        const uint32_t* AI = sI + base;
-        const uint64_t* BK = AK + w;
-        const uint32_t* BI = AI + w;
-        uint32_t lo = diag > w ? diag - w : 0u, hi = diag < w ? diag : w;
-        while (lo < hi) {  // A entries among the first diag outputs (A first on ties)
-            const uint32_t mid = (lo + hi) >> 1;
-            const uint64_t a = AK[mid], b = BK[diag - 1 - mid];
-            const bool a_first = a != b ? a < b : AI[mid] <= BI[diag - 1 - mid];
-            if (a_first) lo = mid + 1; else hi = mid;
-        }
-        // an exhausted run reads as (~0, ~0), above every element (padding
-        // carries indices below ~0), so the choice needs no bounds test
-        uint32_t ia = lo, ib = diag - lo;
-        uint64_t ka = ia < w ? AK[ia] : ~0ull, kb = ib < w ? BK[ib] : ~0ull;
-        uint32_t va = ia < w ? AI[ia] : ~0u, vb = ib < w ? BI[ib] : ~0u;
-#pragma unroll
-        for (int j = 0; j < MS_IT; ++j) {
-            const bool take_b = ki_less(kb, vb, ka, va);  // elements are distinct; a tie cannot occur
-            k[j] = take_b ? kb : ka;
-            v[j] = take_b ? vb : va;
-            if (take_b) {
-                ++ib;
-                kb = ib < w ? BK[ib] : ~0ull;
-                vb = ib < w ? BI[ib] : ~0u;
-            } else {
-                ++ia;
-                ka = ia < w ? AK[ia] : ~0ull;
-                va = ia < w ? AI[ia] : ~0u;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < MS_IT; ++j) {
-            sK[t * MS_IT + j] = k[j];
-            sI[t * MS_IT + j] = v[j];
-        }
-        __syncthreads();
-    }
 }
 
 // One CTA per chunk: sort it by (K, i), write its SA, and name it (rank of
 // every rotation = block-local start of its group; groups of size > 1 go to
-// `bins` for the doubling rounds). NT threads sort chunks of up to NT * MS_IT
-// rotations taken from chunks.list[LIST] (256 threads: the packed chunks;
-// 1,024 threads: the single over-full buckets up to BIG_CAP).
+// `bins` for the doubling rounds). NT threads sort chunks of up to
+// NT * MS_IT rotations taken from chunks.list[LIST] (256 threads: the packed
+// chunks; 1,024 threads: the single over-full buckets up to BIG_CAP).
+//
+// A chunk is a run of whole fine buckets, and a fine bucket is a key range,
+// so the chunk is sorted bucket by bucket: no merge crosses a bucket edge.
+//   1. The bucket table: every bucket's chunk-relative start (from the
+//      block's scanned counts) and its team of ceil(size / MS_IT) threads
+//      (an exclusive scan by one warp), whose run of team * MS_IT slots holds
+//      the bucket, padded with entries above every real one.
+//   2. Every rotation's bucket in the chunk -- its top 12 key bits on the
+//      equal-width route, else #{chunk splitters <= K} by a short search --
+//      and a counting scatter into its bucket's run (one shared-memory
+//      reservation per bucket and warp step).
+//   3. Each thread sorts its MS_IT slots with the network; then merge
+//      rounds inside each team (merge path, as many rounds as the largest
+//      team needs: about 5 for learned buckets of ~220 rotations, against 8
+//      for the whole chunk at once).
+//   4. The last round writes its outputs compacted (the buckets in order,
+//      padding dropped), and the chunk is named as a sorted tile.
+// Padding entries are (~0, 0xffff0000 + slot): above every real pair (real
+// indices are below 2^30) and distinct; an exhausted run reads as (~0, ~0),
+// above both, so a merge step needs no bounds test on the entries.
 constexpr size_t CHUNK_SORT_SMEM = (size_t)CHUNK_CAP * 12;
 constexpr size_t BIG_SORT_SMEM = (size_t)BIG_CAP * 12;
 
@@ -680,40 +649,220 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
                                                               uint32_t* __restrict__ SA,
                                                               const BlockInfo* __restrict__ blocks, Bins chunks,
                                                               uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl,
-                                                              uint32_t* __restrict__ chunk_counter) {
+                                                              uint32_t* __restrict__ chunk_counter,
+                                                              const uint32_t* __restrict__ starts,
+                                                              const uint32_t* __restrict__ route,
+                                                              const uint64_t* __restrict__ splitters) {
     constexpr uint32_t CAP = NT * MS_IT;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* sK = reinterpret_cast<uint64_t*>(smem);
     uint32_t* sI = reinterpret_cast<uint32_t*>(smem + (size_t)CAP * 8);
+    __shared__ uint64_t cspl[MAXB];        // the chunk's inner splitters (learned route)
+    __shared__ uint32_t bstart[MAXB + 1];  // chunk-relative start of every bucket (and the chunk's end)
+    __shared__ uint32_t bthr[MAXB + 1];    // first thread of every bucket's team (and the threads used)
+    __shared__ uint32_t bcur[MAXB];        // scatter cursors
     __shared__ GroupDesc ebuf[NT / 32][NCLS * EMIT_BUF];
-    __shared__ uint32_t s_c;
+    __shared__ uint32_t s_c, s_rounds;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt_mask = lanemask_lt();
     if (ld_volatile(&ctrl[CTRL_ERR])) return;  // an earlier stage failed: the chunks are not permutations
     WarpEmitter em;
-    em.init(ebuf[threadIdx.x >> 5]);
+    em.init(ebuf[warp]);
     const uint32_t count = bin_count(chunks, LIST);
     // chunks in list order from an atomic counter (zeroed before the launch):
     // the chunks in flight stay within a few blocks, whose rank ranges stay
     // in L2 while their scattered rank writes land
     for (;;) {
-        if (threadIdx.x == 0) s_c = atomicAdd(chunk_counter, 1u);
+        if (tid == 0) s_c = atomicAdd(chunk_counter, 1u);
         __syncthreads();
         const uint32_t c = s_c;
         if (c >= count) break;
         const GroupDesc gd = chunks.list[LIST][c];
         const BlockInfo bi = blocks[gd.blk];
         const uint32_t len = min(gd.len, CAP);
-        BWT_DCHECK(gd.len <= CAP && gd.start - bi.off < bi.n && gd.start - bi.off + gd.len <= bi.n, &ctrl[CTRL_ERR]);
-        // unrolled, so a thread's loads are in flight together (the loop
-        // bound is a constant: every thread stores MS_IT entries)
+        const uint32_t b0 = gd.pad & 0xffffu, nbk = max(1u, min(gd.pad >> 16, MAXB));
+        BWT_DCHECK(gd.len <= CAP && (gd.pad >> 16) >= 1u && (gd.pad >> 16) <= MAXB && b0 + nbk <= (uint32_t)NBK &&
+                       gd.start - bi.off < bi.n && gd.start - bi.off + gd.len <= bi.n,
+                   &ctrl[CTRL_ERR]);
+        const bool flat = route[gd.blk] == 2u;
+        const uint32_t cstart = gd.start - bi.off;
+        const uint32_t* srow = starts + (size_t)gd.blk * NBK;
+        // ---- 1. the bucket table
+        for (uint32_t j = tid; j <= nbk; j += NT) {
+            const uint32_t st = j == nbk ? cstart + len : srow[min(b0 + j, (uint32_t)NBK - 1u)];
+            bstart[j] = min(st - cstart, len);
+        }
+        if (!flat)
+            for (uint32_t j = tid; j + 1 < nbk; j += NT) cspl[j] = splitters[b0 + j];
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t run = 0, mx = 0;
+            for (uint32_t j0 = 0; j0 < nbk; j0 += 32) {
+                const uint32_t j = j0 + lane;
+                const uint32_t sz = j < nbk ? bstart[j + 1] - bstart[j] : 0u;
+                const uint32_t t = (sz + MS_IT - 1) / MS_IT;
+                uint32_t incl = t;
 #pragma unroll
-        for (int j = 0; j < MS_IT; ++j) {
-            const uint32_t i = j * NT + threadIdx.x;
-            sK[i] = i < len ? K[gd.start + i] : ~0ull;
-            sI[i] = i < len ? SA[gd.start + i] : 0xffff0000u + i;  // padding: last, distinct
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if ((int)lane >= o) incl += y;
+                }
+                if (j < nbk) {
+                    bthr[j] = run + incl - t;
+                    bcur[j] = 0u;
+                }
+                mx = max(mx, t);
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) {
+                bthr[nbk] = min(run, (uint32_t)NT);
+                s_rounds = mx <= 1u ? 0u : 32u - __clz(mx - 1u);  // ceil(log2(largest team))
+                BWT_DCHECK(run <= (uint32_t)NT, &ctrl[CTRL_ERR]);
+            }
         }
         __syncthreads();
-        cta_merge_sort<NT>(sK, sI);
-        for (uint32_t i = threadIdx.x; i < len; i += NT) SA[gd.start + i] = sI[i];
+        const uint32_t T = bthr[nbk];
+        // this thread's team: the last bucket whose team starts at or before it
+        uint32_t team = 0;
+        {
+            uint32_t lo = 0, hi = nbk;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (bthr[mid] <= tid) lo = mid; else hi = mid;
+            }
+            team = lo;
+        }
+        const uint32_t tfirst = bthr[team], tsize = bstart[team + 1] - bstart[team];
+        const uint32_t lt = tid - tfirst;             // index inside the team
+        const uint32_t kteam = bthr[team + 1] - tfirst;  // threads of the team
+        const bool active = tid < T;
+        // ---- 2. loads (all in flight together), buckets, counting scatter
+        uint64_t k[MS_IT];
+        uint32_t v[MS_IT];
+#pragma unroll
+        for (int j = 0; j < MS_IT; ++j) {
+            const uint32_t i = j * NT + tid;
+            k[j] = i < len ? K[gd.start + i] : 0ull;
+            v[j] = i < len ? SA[gd.start + i] : 0u;
+        }
+        if (active) {  // the padding of this thread's slots (only a team's last run has any)
+#pragma unroll
+            for (int j = 0; j < MS_IT; ++j) {
+                const uint32_t pos = lt * MS_IT + j;  // position inside the team's run
+                if (pos >= tsize) {
+                    const uint32_t slot = tid * MS_IT + j;
+                    sK[slot] = ~0ull;
+                    sI[slot] = 0xffff0000u + slot;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < MS_IT; ++j) {
+            const uint32_t i = j * NT + tid;
+            const bool valid = i < len;
+            uint32_t lb = 0xffffffffu;
+            if (valid) {
+                if (flat) {
+                    lb = (uint32_t)(k[j] >> 52) - b0;
+                } else {
+                    uint32_t lo = 0, hi = nbk - 1;  // #{inner splitters <= K}
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (cspl[mid] <= k[j]) lo = mid + 1; else hi = mid;
+                    }
+                    lb = lo;
+                }
+                BWT_DCHECK(lb < nbk, &ctrl[CTRL_ERR]);
+                lb = min(lb, nbk - 1);
+            }
+            const uint32_t peers = __match_any_sync(0xffffffffu, lb);
+            const int leader = __ffs(peers) - 1;
+            uint32_t base = 0;
+            if (valid && (int)lane == leader) base = atomicAdd(&bcur[lb], (uint32_t)__popc(peers));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (valid) {
+                const uint32_t slot = min(bthr[lb] * MS_IT + base + __popc(peers & lt_mask), CAP - 1u);
+                sK[slot] = k[j];
+                sI[slot] = v[j];
+            }
+        }
+        __syncthreads();
+        // ---- 3. sorting network on this thread's slots, then merge rounds inside the team
+        const uint32_t R = s_rounds;
+        if (active) {
+#pragma unroll
+            for (int j = 0; j < MS_IT; ++j) {
+                k[j] = sK[tid * MS_IT + j];
+                v[j] = sI[tid * MS_IT + j];
+            }
+            sort13(k, v);
+        }
+        for (uint32_t r = 1; r <= R; ++r) {
+            if (active) {  // the sorted runs of the previous step back in place
+#pragma unroll
+                for (int j = 0; j < MS_IT; ++j) {
+                    sK[tid * MS_IT + j] = k[j];
+                    sI[tid * MS_IT + j] = v[j];
+                }
+            }
+            __syncthreads();
+            if (active) {
+                const uint32_t m = 1u << r;  // threads per merged run
+                const uint32_t pf = lt & ~(m - 1u);
+                const uint32_t w = (m >> 1) * MS_IT;  // input run length
+                const uint32_t L = kteam * MS_IT;
+                const uint32_t a0 = pf * MS_IT, a1 = min(a0 + w, L), b1 = min(a0 + 2u * w, L);
+                const uint32_t la = a1 - a0, lb = b1 - a1;
+                const uint32_t diag = (lt - pf) * MS_IT;
+                const uint64_t* AK = sK + tfirst * MS_IT + a0;
+                const uint32_t* AI = sI + tfirst * MS_IT + a0;
+                const uint64_t* BK = AK + la;
+                const uint32_t* BI = AI + la;
+                uint32_t lo = diag > lb ? diag - lb : 0u, hi = min(diag, la);
+                while (lo < hi) {  // A entries among the first diag outputs (A first on ties)
+                    const uint32_t mid = (lo + hi) >> 1;
+                    const uint64_t a = AK[mid], b = BK[diag - 1 - mid];
+                    const bool a_first = a != b ? a < b : AI[mid] <= BI[diag - 1 - mid];
+                    if (a_first) lo = mid + 1; else hi = mid;
+                }
+                uint32_t ia = lo, ib = diag - lo;
+                uint64_t ka = ia < la ? AK[ia] : ~0ull, kb = ib < lb ? BK[ib] : ~0ull;
+                uint32_t va = ia < la ? AI[ia] : ~0u, vb = ib < lb ? BI[ib] : ~0u;
+#pragma unroll
+                for (int j = 0; j < MS_IT; ++j) {
+                    const bool take_b = ki_less(kb, vb, ka, va);
+                    k[j] = take_b ? kb : ka;
+                    v[j] = take_b ? vb : va;
+                    if (take_b) {
+                        ++ib;
+                        kb = ib < lb ? BK[ib] : ~0ull;
+                        vb = ib < lb ? BI[ib] : ~0u;
+                    } else {
+                        ++ia;
+                        ka = ia < la ? AK[ia] : ~0ull;
+                        va = ia < la ? AI[ia] : ~0u;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (R == 0) __syncthreads();  // every thread has read its slots before any compacted write
+        // ---- 4. compacted: bucket after bucket, padding dropped
+        if (active) {
+#pragma unroll
+            for (int j = 0; j < MS_IT; ++j) {
+                const uint32_t pos = lt * MS_IT + j;
+                if (pos < tsize) {
+                    const uint32_t dst = bstart[team] + pos;
+                    sK[dst] = k[j];
+                    sI[dst] = v[j];
+                }
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < len; i += NT) SA[gd.start + i] = sI[i];
         name_tile<uint64_t, NT / 32>(sK, len, gd.start, gd.start, gd.start + len, sI, bi, gd.blk, rank, bins,
                                      bi.n > 8u, NO_OLD_START, em, &ctrl[CTRL_ERR]);
         __syncthreads();
@@ -749,7 +898,11 @@ __global__ void __launch_bounds__(1024) k_route_scan(const unsigned long long* _
             const uint64_t n = blocks[b].n;
             const unsigned long long* bl = bstats + 5 * (size_t)b;
             const unsigned long long* bf = bstats + 5 * ((size_t)nb + b);
-            const bool too_big = n * 2 > (uint64_t)(MAXCH - 2) * CHUNK_CAP;
+            // chunks are packed by padded sizes (at most 12 slots of padding a
+            // bucket) and close early at most NBK / MAXB times for the bucket
+            // limit, so a block of n rotations needs at most
+            // 2 (n + 12 NBK) / CHUNK_CAP + NBK / MAXB + 1 chunks
+            const bool too_big = (n + 12ull * NBK) * 2 > (uint64_t)(MAXCH - NBK / MAXB - 2) * CHUNK_CAP;
             const uint32_t r = too_big ? 1u : bl[0] * 4 <= n ? 0u : bf[0] * 4 <= n ? 2u : 1u;
             route[b] = r;
             const uint32_t nt = (uint32_t)((n + tile - 1) / tile);
@@ -1011,7 +1164,8 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     const bool timing = !p->events.empty() && !p->capturing && p->ev_used + 2 <= p->events.size();
     if (timing) CKL(cudaEventRecord(p->events[p->ev_used], st));
     k_chunk_sort_name<MS_NT, 4, 0><<<sms * p->chunk_sort_ctas, MS_NT, CHUNK_SORT_SMEM, st>>>(
-        p->keys[0], p->vals[0], p->blocks, aux, p->rank, bins_of(p, 0), ctrl, chunk_counter);
+        p->keys[0], p->vals[0], p->blocks, aux, p->rank, bins_of(p, 0), ctrl, chunk_counter, p->bucket_count,
+        p->route, p->splitters);
     CKL(cudaGetLastError());
     if (timing) {
         CKL(cudaEventRecord(p->events[p->ev_used + 1], st));
@@ -1023,7 +1177,8 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     }
     // over-full buckets up to BIG_CAP: one 1,024-thread CTA each
     k_chunk_sort_name<BIG_NT, 1, 1><<<sms, BIG_NT, BIG_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks, aux,
-                                                                        p->rank, bins_of(p, 0), ctrl, big_counter);
+                                                                        p->rank, bins_of(p, 0), ctrl, big_counter,
+                                                                        p->bucket_count, p->route, p->splitters);
     CKL(cudaGetLastError());
     p->stats.kernel_launches += 2;
 
