@@ -365,8 +365,17 @@ constexpr uint32_t MAXB = 256;    // fine buckets per chunk (the chunk sort's bu
 // runs, so a chunk's teams fit the sort's threads.
 __host__ __device__ constexpr uint32_t padded(uint32_t s) { return (s + MS_IT - 1) / MS_IT * MS_IT; }
 
+// The scatter tags every rotation it writes into a packed chunk with the low
+// 8 bits of its fine bucket (value bits 24..31; chunked blocks hold fewer
+// than 2^24 rotations), and a chunk spans at most MAXB = 256 consecutive
+// buckets, so the chunk sort reads each rotation's bucket in the chunk off
+// its value. Over-capacity buckets, flagged CM_OWN in the chunk map, are
+// written untagged.
+constexpr uint16_t CM_OWN = 0x8000;
+constexpr uint32_t TAG_SHIFT = 24, IDX_MASK = (1u << TAG_SHIFT) - 1u;
+
 struct ChunkTables {
-    uint16_t* cmap;        // [block][4096] chunk of each fine bucket
+    uint16_t* cmap;        // [block][4096] chunk of each fine bucket (| CM_OWN: a bucket sorted on its own)
     uint32_t* cbase;       // [block][MAXCH] block-relative start of each chunk
     uint32_t* ccur;        // [block][MAXCH] slots taken by the scatter
 };
@@ -414,7 +423,7 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
                 if (bigm & 1u) {  // bucket b is an overflow bucket: a chunk of its own, sorted by the radix path
                     close();
                     if (lane == 0) {
-                        cm[b] = (uint16_t)min(nch, MAXCH - 1);
+                        cm[b] = (uint16_t)(min(nch, MAXCH - 1) | CM_OWN);
                         if (nch < MAXCH) cb[nch] = st[b];
                         const int li = sz <= BIG_CAP ? 1 : CLS_LARGE;  // big-chunk sort, else the overflow radix
                         const uint32_t slot = atomicAdd(&out.count[li], 1u);
@@ -484,6 +493,7 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
 // positions and chunks only, 4 bytes a rotation; keys are re-packed from the
 // staged bytes on the way out), so each chunk's share of the tile is written
 // as one run, at a slot range reserved with one atomic per tile and chunk.
+// Values written to packed chunks carry their bucket's tag (CM_OWN above).
 constexpr size_t CHUNK_SCATTER_SMEM = NBK * 2 + 4 * MAXCH * 4 + TILE_BYTES + 4096 * 4;
 
 template <int ITEMS>
@@ -503,7 +513,7 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
     uint32_t* pre = lcount + MAXCH;                                      // [MAXCH] tile-local chunk offsets
     uint32_t* dbase = pre + MAXCH;                                       // [MAXCH] destination of pre[c]
     uint16_t* stQ = reinterpret_cast<uint16_t*>(dbase + MAXCH);          // [4096] tile position by rank
-    uint16_t* stC = stQ + 4096;                                          // [4096] its chunk
+    uint16_t* stC = stQ + 4096;                                          // [4096] its fine bucket
     __shared__ uint32_t scan_tmp[32];
     const uint32_t ntiles = *ntiles_dev;
     const uint32_t span = max(1u, min(16u, ntiles / (gridDim.x * 4u)));
@@ -522,7 +532,7 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
             }
             for (int i = threadIdx.x; i < (int)MAXCH; i += blockDim.x) lcount[i] = 0;
             const bool flat = route[td.blk] == 2u;
-            uint32_t bk[ITEMS];
+            uint32_t bk[ITEMS];  // fine bucket of each item
             if (!flat) {
 #pragma unroll
                 for (int j = 0; j < ITEMS; ++j) {
@@ -538,8 +548,8 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
                 const uint32_t q = j * 256 + threadIdx.x;
                 cs[j] = 0xffffffffu;
                 if (q < td.len) {
-                    const uint32_t b = flat ? (uint32_t)(pack8_smem(sb, shift + q) >> 52) : bk[j];
-                    const uint32_t c = cm[b];
+                    if (flat) bk[j] = (uint32_t)(pack8_smem(sb, shift + q) >> 52);
+                    const uint32_t c = cm[bk[j]] & (MAXCH - 1);
                     cs[j] = c | (atomicAdd(&lcount[c], 1u) << 10);
                 }
             }
@@ -570,16 +580,16 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
                     const uint32_t c = cs[j] & (MAXCH - 1);
                     const uint32_t pos = pre[c] + (cs[j] >> 10);
                     stQ[pos] = (uint16_t)(j * 256 + threadIdx.x);
-                    stC[pos] = (uint16_t)c;
+                    stC[pos] = (uint16_t)bk[j];
                 }
             }
             __syncthreads();
             for (uint32_t r = threadIdx.x; r < td.len; r += blockDim.x) {
-                const uint32_t q = stQ[r], c = stC[r];
+                const uint32_t q = stQ[r], b = stC[r], e = cm[b], c = e & (MAXCH - 1);
                 const uint32_t dst = dbase[c] + (r - pre[c]);
                 BWT_DCHECK(dst - bi.off < bi.n, err);  // inside the tile's block
                 K[dst] = pack8_smem(sb, shift + q);
-                I[dst] = i0 + q;
+                I[dst] = (i0 + q) | ((e & CM_OWN) ? 0u : (b & 0xffu) << TAG_SHIFT);
             }
             __syncthreads();
         }
@@ -628,10 +638,9 @@ __device__ __forceinline__ void sort13(uint64_t (&k)[MS_IT], uint32_t (&v)[MS_IT
 //      block's scanned counts) and its team of ceil(size / MS_IT) threads
 //      (an exclusive scan by one warp), whose run of team * MS_IT slots holds
 //      the bucket, padded with entries above every real one.
-//   2. Every rotation's bucket in the chunk -- its top 12 key bits on the
-//      equal-width route, else #{chunk splitters <= K} by a short search --
-//      and a counting scatter into its bucket's run (one shared-memory
-//      reservation per bucket and warp step).
+//   2. Every rotation's bucket in the chunk, read off the tag its value
+//      carries from the scatter, and a counting scatter into its bucket's
+//      run (one shared-memory reservation per bucket and warp step).
 //   3. Each thread sorts its MS_IT slots with the network; then merge
 //      rounds inside each team (merge path, as many rounds as the largest
 //      team needs: about 5 for learned buckets of ~220 rotations, against 8
@@ -650,14 +659,11 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
                                                               const BlockInfo* __restrict__ blocks, Bins chunks,
                                                               uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl,
                                                               uint32_t* __restrict__ chunk_counter,
-                                                              const uint32_t* __restrict__ starts,
-                                                              const uint32_t* __restrict__ route,
-                                                              const uint64_t* __restrict__ splitters) {
+                                                              const uint32_t* __restrict__ starts) {
     constexpr uint32_t CAP = NT * MS_IT;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* sK = reinterpret_cast<uint64_t*>(smem);
     uint32_t* sI = reinterpret_cast<uint32_t*>(smem + (size_t)CAP * 8);
-    __shared__ uint64_t cspl[MAXB];        // the chunk's inner splitters (learned route)
     __shared__ uint32_t bstart[MAXB + 1];  // chunk-relative start of every bucket (and the chunk's end)
     __shared__ uint32_t bthr[MAXB + 1];    // first thread of every bucket's team (and the threads used)
     __shared__ uint32_t bcur[MAXB];        // scatter cursors
@@ -684,7 +690,6 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
         BWT_DCHECK(gd.len <= CAP && (gd.pad >> 16) >= 1u && (gd.pad >> 16) <= MAXB && b0 + nbk <= (uint32_t)NBK &&
                        gd.start - bi.off < bi.n && gd.start - bi.off + gd.len <= bi.n,
                    &ctrl[CTRL_ERR]);
-        const bool flat = route[gd.blk] == 2u;
         const uint32_t cstart = gd.start - bi.off;
         const uint32_t* srow = starts + (size_t)gd.blk * NBK;
         // ---- 1. the bucket table
@@ -692,8 +697,6 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
             const uint32_t st = j == nbk ? cstart + len : srow[min(b0 + j, (uint32_t)NBK - 1u)];
             bstart[j] = min(st - cstart, len);
         }
-        if (!flat)
-            for (uint32_t j = tid; j + 1 < nbk; j += NT) cspl[j] = splitters[b0 + j];
         __syncthreads();
         if (warp == 0) {
             uint32_t run = 0, mx = 0;
@@ -764,17 +767,10 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
             const bool valid = i < len;
             uint32_t lb = 0xffffffffu;
             if (valid) {
-                if (flat) {
-                    lb = (uint32_t)(k[j] >> 52) - b0;
-                } else {
-                    uint32_t lo = 0, hi = nbk - 1;  // #{inner splitters <= K}
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (cspl[mid] <= k[j]) lo = mid + 1; else hi = mid;
-                    }
-                    lb = lo;
-                }
-                BWT_DCHECK(lb < nbk, &ctrl[CTRL_ERR]);
+                // packed chunks: the bucket tag; a bucket of its own: untagged
+                lb = LIST == 0 ? ((v[j] >> TAG_SHIFT) - b0) & 0xffu : 0u;
+                v[j] &= IDX_MASK;
+                BWT_DCHECK(lb < nbk && v[j] < bi.n, &ctrl[CTRL_ERR]);
                 lb = min(lb, nbk - 1);
             }
             const uint32_t peers = __match_any_sync(0xffffffffu, lb);
@@ -1164,8 +1160,7 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     const bool timing = !p->events.empty() && !p->capturing && p->ev_used + 2 <= p->events.size();
     if (timing) CKL(cudaEventRecord(p->events[p->ev_used], st));
     k_chunk_sort_name<MS_NT, 4, 0><<<sms * p->chunk_sort_ctas, MS_NT, CHUNK_SORT_SMEM, st>>>(
-        p->keys[0], p->vals[0], p->blocks, aux, p->rank, bins_of(p, 0), ctrl, chunk_counter, p->bucket_count,
-        p->route, p->splitters);
+        p->keys[0], p->vals[0], p->blocks, aux, p->rank, bins_of(p, 0), ctrl, chunk_counter, p->bucket_count);
     CKL(cudaGetLastError());
     if (timing) {
         CKL(cudaEventRecord(p->events[p->ev_used + 1], st));
@@ -1178,7 +1173,7 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     // over-full buckets up to BIG_CAP: one 1,024-thread CTA each
     k_chunk_sort_name<BIG_NT, 1, 1><<<sms, BIG_NT, BIG_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks, aux,
                                                                         p->rank, bins_of(p, 0), ctrl, big_counter,
-                                                                        p->bucket_count, p->route, p->splitters);
+                                                                        p->bucket_count);
     CKL(cudaGetLastError());
     p->stats.kernel_launches += 2;
 
