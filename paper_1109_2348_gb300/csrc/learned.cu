@@ -642,11 +642,11 @@ __device__ __forceinline__ void sort13(uint64_t (&k)[MS_IT], uint32_t (&v)[MS_IT
 //      carries from the scatter, and a counting scatter into its bucket's
 //      run (one shared-memory reservation per bucket and warp step).
 //   3. Each thread sorts its MS_IT slots with the network; then merge
-//      rounds inside each team (merge path, as many rounds as the largest
-//      team needs: about 5 for learned buckets of ~220 rotations, against 8
-//      for the whole chunk at once).
-//   4. The last round writes its outputs compacted (the buckets in order,
-//      padding dropped), and the chunk is named as a sorted tile.
+//      rounds inside each team (merge path; a team takes part in as many
+//      rounds as it needs, ceil(log2(threads)): about 5 for learned buckets
+//      of ~220 rotations, against 8 for the whole chunk at once).
+//   4. SA is written compacted (the buckets in order, padding dropped),
+//      and the chunk is named from the registers the last round left.
 // Padding entries are (~0, 0xffff0000 + slot): above every real pair (real
 // indices are below 2^30) and distinct; an exhausted run reads as (~0, ~0),
 // above both, so a merge step needs no bounds test on the entries.
@@ -668,6 +668,8 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
     __shared__ uint32_t bthr[MAXB + 1];    // first thread of every bucket's team (and the threads used)
     __shared__ uint32_t bcur[MAXB];        // scatter cursors
     __shared__ GroupDesc ebuf[NT / 32][NCLS * EMIT_BUF];
+    __shared__ uint64_t s_wlast[NT / 32], s_wfirst[NT / 32];  // each warp's last and first key
+    __shared__ uint32_t s_wmax[NT / 32];                      // each warp's last head + 1
     __shared__ uint32_t s_c, s_rounds;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt_mask = lanemask_lt();
@@ -796,7 +798,9 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
             sort13(k, v);
         }
         for (uint32_t r = 1; r <= R; ++r) {
-            if (active) {  // the sorted runs of the previous step back in place
+            // a team whose runs already form one sorted run sits the round out
+            const bool merging = active && (1u << (r - 1)) < kteam;
+            if (merging) {  // the sorted runs of the previous step back in place
 #pragma unroll
                 for (int j = 0; j < MS_IT; ++j) {
                     sK[tid * MS_IT + j] = k[j];
@@ -804,7 +808,7 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
                 }
             }
             __syncthreads();
-            if (active) {
+            if (merging) {
                 const uint32_t m = 1u << r;  // threads per merged run
                 const uint32_t pf = lt & ~(m - 1u);
                 const uint32_t w = (m >> 1) * MS_IT;  // input run length
@@ -845,22 +849,76 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
             __syncthreads();
         }
         if (R == 0) __syncthreads();  // every thread has read its slots before any compacted write
-        // ---- 4. compacted: bucket after bucket, padding dropped
+        // ---- 4. SA, compacted through shared memory (bucket after bucket,
+        //      padding dropped) for a coalesced write
+        const uint32_t base = bstart[team];  // the team's bucket, chunk-relative
+        if (active) {
+#pragma unroll
+            for (int j = 0; j < MS_IT; ++j) {
+                const uint32_t pos = lt * MS_IT + j;
+                if (pos < tsize) sI[base + pos] = v[j];
+            }
+        }
+        // the keys next to this thread's run, for lanes at a warp edge
+        uint64_t prev_last = __shfl_up_sync(0xffffffffu, k[MS_IT - 1], 1);
+        uint64_t next_first = __shfl_down_sync(0xffffffffu, k[0], 1);
+        if (lane == 31) s_wlast[warp] = k[MS_IT - 1];
+        if (lane == 0) s_wfirst[warp] = k[0];
+        __syncthreads();
+        for (uint32_t i = tid; i < len; i += NT) SA[gd.start + i] = sI[i];
+        if (lane == 0 && warp > 0) prev_last = s_wlast[warp - 1];
+        if (lane == 31 && warp + 1 < NT / 32) next_first = s_wfirst[warp + 1];
+        // ---- 5. naming, from the registers. A rotation heads a group where
+        //      its key differs from the one before it (a bucket's first
+        //      rotation always does: a bucket is a key range); it ends one
+        //      where the next key differs or its bucket ends. Its group start
+        //      is the last head at or before it: inside the thread by a
+        //      running value, across threads by a CTA max-scan of every
+        //      thread's last head.
+        uint32_t hm = 0, tm = 0, lh = 0;  // head bits, tail bits, last head + 1 (0: none)
         if (active) {
 #pragma unroll
             for (int j = 0; j < MS_IT; ++j) {
                 const uint32_t pos = lt * MS_IT + j;
                 if (pos < tsize) {
-                    const uint32_t dst = bstart[team] + pos;
-                    sK[dst] = k[j];
-                    sI[dst] = v[j];
+                    const uint64_t before = j == 0 ? prev_last : k[j > 0 ? j - 1 : 0];
+                    const uint64_t after = j == MS_IT - 1 ? next_first : k[j < MS_IT - 1 ? j + 1 : 0];
+                    if (pos == 0 || k[j] != before) {
+                        hm |= 1u << j;
+                        lh = base + pos + 1;
+                    }
+                    if (pos + 1 == tsize || k[j] != after) tm |= 1u << j;
                 }
             }
         }
+        uint32_t incl = lh;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl = max(incl, y);
+        }
+        if (lane == 31) s_wmax[warp] = incl;
         __syncthreads();
-        for (uint32_t i = tid; i < len; i += NT) SA[gd.start + i] = sI[i];
-        name_tile<uint64_t, NT / 32>(sK, len, gd.start, gd.start, gd.start + len, sI, bi, gd.blk, rank, bins,
-                                     bi.n > 8u, NO_OLD_START, em, &ctrl[CTRL_ERR]);
+        uint32_t cur = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) cur = 0u;
+        for (uint32_t w = 0; w < warp; ++w) cur = max(cur, s_wmax[w]);
+        const uint32_t boff = gd.start - bi.off;  // the chunk's block-relative start
+        const bool emit_ok = bi.n > 8u;
+#pragma unroll
+        for (int j = 0; j < MS_IT; ++j) {
+            const uint32_t pos = lt * MS_IT + j;
+            const bool real = active && pos < tsize;
+            const uint32_t P = base + pos;  // chunk-relative position
+            if (real && ((hm >> j) & 1u)) cur = P + 1;
+            const uint32_t gs = cur - 1;  // its group's start
+            if (real) {
+                BWT_DCHECK(v[j] < bi.n && cur > 0u, &ctrl[CTRL_ERR]);
+                if (v[j] < bi.n) rank[bi.off + v[j]] = boff + gs;
+            }
+            // a group of more than one rotation ends here: to the doubling rounds
+            const bool want = emit_ok && real && ((tm >> j) & 1u) && P > gs;
+            em.emit(bins, want, gd.start + gs, P - gs + 1, gd.blk, &ctrl[CTRL_ERR]);
+        }
         __syncthreads();
     }
     em.finish(bins, &ctrl[CTRL_ERR]);
