@@ -248,7 +248,7 @@ ONESWEEP_DRAM_BYTES_PER_KEY = 23.37
 # DRAM bytes (read + write) per rotation of the learned chunk sort
 # (k_chunk_sort_name<256, 4, 0>) as ncu counted them for the current kernel on
 # 24 blocks of the learned-eval workload; None when the kernel has changed since.
-CHUNK_SORT_DRAM_BYTES_PER_KEY = 18.0
+CHUNK_SORT_DRAM_BYTES_PER_KEY = None
 
 
 def reference_arm(args):
@@ -509,8 +509,9 @@ def ours(args):
     def chunk_sort_roofline():
         # the learned step's dominant kernel, the 256-thread chunk sort, timed
         # in host-driven learned mode with CUDA events around its launch:
-        # 20 algorithmic bytes per rotation it sorts (8-byte key and 4-byte
-        # index read, SA entry and rank written) over its event time
+        # 16 algorithmic bytes per rotation it sorts (8-byte key and 4-byte
+        # index read, SA entry written; ranks are stored only for the rare
+        # group members) over its event time
         th = R.plan(F_TIMING | F_LEARNED, rb_used, tk_used, model_path)
         R.warm(th, 3)
         ms = by = 0.0
@@ -533,7 +534,7 @@ def ours(args):
                 "peak_source": peak_kind + " hbm_gbs",
                 "traffic": None if CHUNK_SORT_DRAM_BYTES_PER_KEY is None else
                 round(CHUNK_SORT_DRAM_BYTES_PER_KEY * per_launch_keys),
-                "algorithmic_bytes_per_launch": round(by / la), "bytes_per_rotation": 20,
+                "algorithmic_bytes_per_launch": round(by / la), "bytes_per_rotation": 16,
                 "rotations_per_launch": round(per_launch_keys), "launches_timed": la,
                 "avg_launch_ms": round(ms / la, 4)}
 

@@ -112,8 +112,9 @@ typedef struct {
     double chunk_ms;            /* their summed device time */
     uint64_t chunk_keys;        /* learned bucketing: rotations in packed chunks (the ones that chunk
                                    sort sorts: the bucketed blocks' rotations outside over-full buckets) */
-    double chunk_bytes;         /* their algorithmic HBM bytes: 20 per rotation (8-byte key and 4-byte
-                                   index read, 4-byte SA entry and 4-byte rank written) */
+    double chunk_bytes;         /* their algorithmic HBM bytes: 16 per rotation (8-byte key and 4-byte
+                                   index read, 4-byte SA entry written; ranks are stored only for
+                                   rotations in groups of two or more) */
 } bwt_stats;
 
 /* Create a plan on CUDA device `device` (made current for the call). The plan

@@ -41,6 +41,12 @@ constexpr uint32_t ERR_CAPACITY = 2u;
 constexpr uint32_t ERR_INPUT = 4u;  // device-checked input out of range (the inverse's primary index)
 constexpr uint32_t ERR_BOUNDS = 8u; // a bounds check of the debug build failed (an internal error)
 
+// SA entries marked SA_FINAL (bit 31; blocks hold fewer than 2^31 bytes) are
+// rows that the learned chunk sort left as groups of one: their place is
+// final and their rank (the row itself) is not stored, but found on demand
+// (LazyRanks below). Readers of SA mask the bit.
+constexpr uint32_t SA_FINAL = 0x80000000u;
+
 // Bounds checks of the debug build (-DBWT_DEBUG): index < n for every
 // SA-derived index, destinations inside their segment. A failed check sets
 // ERR_BOUNDS in the error word *err (the call then returns BWT_EINTERNAL) and
@@ -91,6 +97,83 @@ struct Bins {
     uint32_t* count;                // -> ctrl + CTRL_BINS + NCLS * parity
     unsigned long long* active;     // -> ctrl + CTRL_ACTIVE
 };
+
+// ---- ranks after the learned first stage --------------------------------------
+//
+// Learned bucketing (Section 3.1's sort by a learned CDF) names each chunk of
+// whole key-range buckets in one CTA. Where a block's rotations are nearly
+// all distinct in their first 8 bytes, its rank array would be written in
+// full (one scattered store a rotation) for the few reads the doubling rounds
+// make, rank[(i + h) mod n] for the members i of groups. Such a block is
+// "lazy": the chunk sort stores ranks only for group members and marks its
+// groups of one SA_FINAL, and a rank read finds a rotation's row on demand:
+// its bucket (from its 8-byte key), then a lower bound for the key inside the
+// bucket's rows (already sorted). A row marked SA_FINAL is the rotation's
+// rank; otherwise the rotation is a group member with its rank stored.
+constexpr int LR_BUCKETS = 4096;  // learned buckets (the library's BWT_BUCKETS)
+constexpr int IDX_BITS = 16;      // splitter index on a key's first two bytes
+constexpr int IDX_CELLS = 1 << IDX_BITS;
+constexpr int IDX_WORDS = IDX_CELLS + 8;  // u16 entries (first[IDX_CELLS] = #splitters), padded to 16 bytes
+
+// Bucket of a key: #{j : spl[j] <= key}. first[c] = #{j : spl[j] < c << 48}
+// narrows the search to the splitters that share the key's first two bytes
+// (the ones below all count, the ones above none).
+__device__ __forceinline__ uint32_t bucket_of(const uint64_t* spl, const uint16_t* first, uint64_t key) {
+    const uint32_t c = (uint32_t)(key >> (64 - IDX_BITS));
+    uint32_t lo = first[c], hi = first[c + 1];
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (spl[mid] <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+struct LazyRanks {
+    const uint32_t* lazy = nullptr;      // [block] 1: ranks of groups of one are not stored (null: none)
+    const uint8_t* S = nullptr;          // the batch's bytes
+    const uint32_t* SA = nullptr;        // rows (SA_FINAL-marked)
+    const uint32_t* route = nullptr;     // [block] 0 learned buckets, 2 equal-width buckets
+    const uint32_t* starts = nullptr;    // [block][LR_BUCKETS] block-relative first row of every bucket
+    const uint64_t* splitters = nullptr; // learned splitters
+    const uint16_t* index = nullptr;     // their two-byte-prefix index
+    uint32_t own_cap = 0;                // largest bucket the chunk sorts name (larger: named in full)
+};
+
+// The 8-byte big-endian key of rotation j of a block (cyclic).
+__device__ __forceinline__ uint64_t rotation_key(const uint8_t* __restrict__ S, BlockInfo bi, uint32_t j) {
+    uint64_t k = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        uint32_t q = j + t;
+        while (q >= bi.n) q -= bi.n;
+        k = (k << 8) | S[bi.off + q];
+    }
+    return k;
+}
+
+static __device__ __noinline__ uint32_t lazy_rank_lookup(const LazyRanks lz, const uint32_t* __restrict__ rank, BlockInfo bi,
+                                                  uint32_t blk, uint32_t j) {
+    const uint64_t key = rotation_key(lz.S, bi, j);
+    const uint32_t b = lz.route[blk] == 2u ? (uint32_t)(key >> 52) : bucket_of(lz.splitters, lz.index, key);
+    const uint32_t* st = lz.starts + (size_t)blk * LR_BUCKETS;
+    uint32_t lo = st[min(b, (uint32_t)LR_BUCKETS - 1u)];
+    uint32_t hi = b + 1 < (uint32_t)LR_BUCKETS ? st[b + 1] : bi.n;
+    if (hi > bi.n || lo > hi || hi - lo > lz.own_cap) return rank[bi.off + j];  // named in full
+    while (lo < hi) {  // first row of the bucket whose key is not below this one
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint32_t r = lz.SA[bi.off + mid] & ~SA_FINAL;
+        if (rotation_key(lz.S, bi, r < bi.n ? r : 0u) < key) lo = mid + 1; else hi = mid;
+    }
+    const uint32_t x = lo < bi.n ? lz.SA[bi.off + lo] : 0u;
+    return (x & SA_FINAL) ? lo : rank[bi.off + j];
+}
+
+// rank[j] of block `blk`, stored or found.
+__device__ __forceinline__ uint32_t rank_at(const LazyRanks& lz, const uint32_t* __restrict__ rank, BlockInfo bi,
+                                            uint32_t blk, uint32_t j) {
+    if (lz.lazy == nullptr || lz.lazy[blk] == 0u) return rank[bi.off + j];
+    return lazy_rank_lookup(lz, rank, bi, blk, j);
+}
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;

@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(256) k_name_initial(const uint64_t* __restrict
 // ---- round: key gathers ------------------------------------------------------
 __global__ void __launch_bounds__(256) k_gather_micro(const uint32_t* __restrict__ SA, const uint32_t* __restrict__ rank,
                                                       const BlockInfo* __restrict__ blocks, Bins cur,
-                                                      const uint32_t* __restrict__ depth, uint32_t* __restrict__ key2) {
+                                                      const uint32_t* __restrict__ depth, uint32_t* __restrict__ key2,
+                                                      const LazyRanks lz) {
     const uint32_t h = *depth;
     const uint32_t count = bin_count(cur, 0);
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < count; g += gridDim.x * blockDim.x) {
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(256) k_gather_micro(const uint32_t* __restrict
             if (e < gd.len) {
                 uint32_t r = sa[e] + h;
                 if (r >= bi.n) r -= bi.n;
-                key2[gd.start + e] = r < bi.n ? rank[bi.off + r] : 0u;
+                key2[gd.start + e] = r < bi.n ? rank_at(lz, rank, bi, gd.blk, r) : 0u;
             }
         }
     }
@@ -196,7 +197,8 @@ __global__ void __launch_bounds__(256) k_gather_micro(const uint32_t* __restrict
 // tiny, small and medium groups: one warp per group
 __global__ void __launch_bounds__(256) k_gather_small(const uint32_t* __restrict__ SA, const uint32_t* __restrict__ rank,
                                                       const BlockInfo* __restrict__ blocks, Bins cur,
-                                                      const uint32_t* __restrict__ depth, uint32_t* __restrict__ key2) {
+                                                      const uint32_t* __restrict__ depth, uint32_t* __restrict__ key2,
+                                                      const LazyRanks lz) {
     const uint32_t h = *depth;
     const uint32_t c1 = bin_count(cur, 1), c2 = bin_count(cur, 2), c3 = bin_count(cur, 3);
     const uint32_t total = c1 + c2 + c3;
@@ -232,8 +234,8 @@ __global__ void __launch_bounds__(256) k_gather_small(const uint32_t* __restrict
                 uint32_t r0 = s0[u] + h, r1 = s1[u] + h;
                 if (r0 >= b0.n) r0 -= b0.n;
                 if (r1 >= b1.n) r1 -= b1.n;
-                s0[u] = v0 && r0 < b0.n ? rank[b0.off + r0] : 0u;
-                s1[u] = v1 && r1 < b1.n ? rank[b1.off + r1] : 0u;
+                s0[u] = v0 && r0 < b0.n ? rank_at(lz, rank, b0, gd0.blk, r0) : 0u;
+                s1[u] = v1 && r1 < b1.n ? rank_at(lz, rank, b1, gd1.blk, r1) : 0u;
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restri
                                                         const uint32_t* __restrict__ depth,
                                                         uint32_t* __restrict__ kbuf, uint32_t* __restrict__ vbuf,
                                                         uint32_t* __restrict__ hist, int passes,
-                                                        uint32_t* __restrict__ seg_varied) {
+                                                        uint32_t* __restrict__ seg_varied, const LazyRanks lz) {
     constexpr int RADIX = 1 << RBITS;
     const uint32_t h = *depth;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restri
         {
             uint32_t r = SA[td.segStart] + h;
             if (r >= bi.n) r -= bi.n;
-            k0 = r < bi.n ? rank[bi.off + r] : 0u;
+            k0 = r < bi.n ? rank_at(lz, rank, bi, td.blk, r) : 0u;
         }
         bool same = true;
         // PI elements a thread per step: their SA loads, then their rank
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(256) k_large_prologue(const uint32_t* __restri
                 if (q < td.len) {
                     uint32_t r = sa[j] + h;
                     if (r >= bi.n) r -= bi.n;
-                    k2[j] = r < bi.n ? rank[bi.off + r] : 0u;
+                    k2[j] = r < bi.n ? rank_at(lz, rank, bi, td.blk, r) : 0u;
                 }
             }
 #pragma unroll
@@ -800,6 +802,7 @@ __global__ void __launch_bounds__(256) k_gather_L(const uint8_t* __restrict__ S,
             }
 #pragma unroll
             for (int j = 0; j < PI; ++j) {
+                sa[j] &= ~SA_FINAL;
                 BWT_DCHECK(q0 + j * 256u + threadIdx.x >= td.len || sa[j] < bi.n, err);
                 const uint32_t src = sa[j] == 0 || sa[j] > bi.n ? bi.n - 1 : sa[j] - 1;
                 c[j] = S[bi.off + src];
@@ -863,7 +866,7 @@ cudaError_t launch_name_tiles(const uint64_t* K, const uint32_t* SA, const Block
 
 cudaError_t launch_gather_small(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks, Bins cur,
                                 const uint32_t* depth, uint32_t* key2, const uint32_t* host_counts, cudaStream_t st,
-                                int* launched) {
+                                int* launched, const LazyRanks& lz) {
     int g_micro = num_sms() * 8, g_warp = num_sms() * 16;
     if (host_counts) {
         g_micro = host_counts[0] ? grid_for(host_counts[0], 256, 8) : 0;
@@ -872,11 +875,11 @@ cudaError_t launch_gather_small(const uint32_t* SA, const uint32_t* rank, const 
     }
     *launched = 0;
     if (g_micro) {
-        k_gather_micro<<<g_micro, 256, 0, st>>>(SA, rank, blocks, cur, depth, key2);
+        k_gather_micro<<<g_micro, 256, 0, st>>>(SA, rank, blocks, cur, depth, key2, lz);
         ++*launched;
     }
     if (g_warp) {
-        k_gather_small<<<g_warp, 256, 0, st>>>(SA, rank, blocks, cur, depth, key2);
+        k_gather_small<<<g_warp, 256, 0, st>>>(SA, rank, blocks, cur, depth, key2, lz);
         ++*launched;
     }
     return cudaGetLastError();
@@ -891,15 +894,15 @@ cudaError_t launch_build_large_tiles(Bins cur, int tile, TileDesc* tiles, uint32
 cudaError_t launch_large_prologue(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks,
                                   const TileDesc* tiles, const uint32_t* num_tiles, const uint32_t* depth,
                                   uint32_t* kbuf, uint32_t* vbuf, uint32_t* hist, int radix_bits, int passes,
-                                  uint32_t* seg_varied, cudaStream_t st) {
+                                  uint32_t* seg_varied, cudaStream_t st, const LazyRanks& lz) {
     const size_t smem = (size_t)passes * (1u << radix_bits) * 4;
     const int grid = num_sms() * 8;
     if (radix_bits == 8) {
         k_large_prologue<8><<<grid, 256, smem, st>>>(SA, rank, blocks, tiles, num_tiles, depth, kbuf, vbuf, hist,
-                                                     passes, seg_varied);
+                                                     passes, seg_varied, lz);
     } else if (radix_bits == 10) {
         k_large_prologue<10><<<grid, 256, smem, st>>>(SA, rank, blocks, tiles, num_tiles, depth, kbuf, vbuf, hist,
-                                                      passes, seg_varied);
+                                                      passes, seg_varied, lz);
     } else if (radix_bits == 11) {
         static bool attr = [] {
             cudaFuncSetAttribute((void*)k_large_prologue<11>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -908,7 +911,7 @@ cudaError_t launch_large_prologue(const uint32_t* SA, const uint32_t* rank, cons
         }();
         (void)attr;
         k_large_prologue<11><<<grid, 256, smem, st>>>(SA, rank, blocks, tiles, num_tiles, depth, kbuf, vbuf, hist,
-                                                      passes, seg_varied);
+                                                      passes, seg_varied, lz);
     } else {
         return cudaErrorInvalidValue;
     }

@@ -104,9 +104,11 @@ cudaError_t launch_name_tiles(const uint64_t* K, const uint32_t* SA, const Block
 
 // Round with prefix length h = *depth: key2[k] = rank[(SA[k] + h) mod n] for
 // every element of the micro, tiny, small and medium groups in `cur`.
+// Ranks are read through `lz` (stored, or found on demand after a learned
+// first stage).
 cudaError_t launch_gather_small(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks, Bins cur,
                                 const uint32_t* depth, uint32_t* key2, const uint32_t* host_counts, cudaStream_t st,
-                                int* launched);
+                                int* launched, const LazyRanks& lz);
 
 // Builds the radix tile table of the large groups of `cur`, its count and
 // the number of keys in large groups; zeroes seg_varied[group] when given.
@@ -121,7 +123,7 @@ cudaError_t launch_build_large_tiles(Bins cur, int tile, TileDesc* tiles, uint32
 cudaError_t launch_large_prologue(const uint32_t* SA, const uint32_t* rank, const BlockInfo* blocks,
                                   const TileDesc* tiles, const uint32_t* num_tiles, const uint32_t* depth,
                                   uint32_t* kbuf, uint32_t* vbuf, uint32_t* hist, int radix_bits, int passes,
-                                  uint32_t* seg_varied, cudaStream_t st);
+                                  uint32_t* seg_varied, cudaStream_t st, const LazyRanks& lz);
 
 // Micro, tiny, small and medium groups: sort by (key2, SA), rename, emit
 // refined groups.

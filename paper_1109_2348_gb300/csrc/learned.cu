@@ -88,7 +88,8 @@ __global__ void k_make_samples(const uint8_t* __restrict__ S, const uint32_t* __
         if (blocks[mid].off <= k) lo = mid; else hi = mid;
     }
     const BlockInfo bi = blocks[lo];
-    const uint32_t i = SA[k] < bi.n ? SA[k] : 0u;
+    const uint32_t sa = SA[k] & ~SA_FINAL;
+    const uint32_t i = sa < bi.n ? sa : 0u;
     for (int j = 0; j < 8; ++j) {
         uint32_t q = i + j;
         while (q >= bi.n) q -= bi.n;
@@ -186,25 +187,12 @@ namespace {
 constexpr int NBK = BWT_BUCKETS;
 constexpr int NSP = BWT_SPLITTERS;
 
-// Bucket of a key: #{j : spl[j] <= key}. first[c] = #{j : spl[j] < c << 48}
-// narrows the search to the splitters that share the key's first two bytes
-// (the ones below all count, the ones above none). Text keys use a few
-// thousand of the 65,536 two-byte prefixes and the splitters spread over
-// them, so a search takes one or two steps (five or six with an index on the
-// top 12 bits, whose bank conflicts bound the counting kernel).
-constexpr int IDX_BITS = 16;
-constexpr int IDX_CELLS = 1 << IDX_BITS;
-constexpr int IDX_WORDS = IDX_CELLS + 8;  // u16 entries (first[IDX_CELLS] = NSP), padded for 16-byte copies
-
-__device__ __forceinline__ uint32_t bucket_of(const uint64_t* spl, const uint16_t* first, uint64_t key) {
-    const uint32_t c = (uint32_t)(key >> (64 - IDX_BITS));
-    uint32_t lo = first[c], hi = first[c + 1];
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (spl[mid] <= key) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
+// The splitter search (bucket_of) starts from an index on the key's first
+// two bytes: text keys use a few thousand of the 65,536 two-byte prefixes
+// and the splitters spread over them, so a search takes one or two steps
+// (five or six with an index on the top 12 bits, whose bank conflicts bound
+// the counting kernel).
+static_assert(NBK == LR_BUCKETS, "the lazy rank lookup indexes bucket starts by learned bucket");
 
 // The index of a splitter table (built once when the table is installed).
 __global__ void k_build_index(const uint64_t* __restrict__ spl, uint16_t* __restrict__ first) {
@@ -646,7 +634,13 @@ __device__ __forceinline__ void sort13(uint64_t (&k)[MS_IT], uint32_t (&v)[MS_IT
 //      rounds as it needs, ceil(log2(threads)): about 5 for learned buckets
 //      of ~220 rotations, against 8 for the whole chunk at once).
 //   4. SA is written compacted (the buckets in order, padding dropped),
-//      and the chunk is named from the registers the last round left.
+//      and the chunk is named from the registers the last round left: the
+//      ranks of group members are stored and their groups sent to the
+//      doubling rounds; groups of one are marked SA_FINAL and their ranks
+//      left to the on-demand lookup (LazyRanks), since nearly all rotations
+//      of text blocks are told apart by their first 8 bytes. members[block]
+//      counts the rotations sent on, which decides whether a block's ranks
+//      are filled in full after the chunk sorts (k_fill_ranks).
 // Padding entries are (~0, 0xffff0000 + slot): above every real pair (real
 // indices are below 2^30) and distinct; an exhausted run reads as (~0, ~0),
 // above both, so a merge step needs no bounds test on the entries.
@@ -659,7 +653,8 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
                                                               const BlockInfo* __restrict__ blocks, Bins chunks,
                                                               uint32_t* __restrict__ rank, Bins bins, uint32_t* ctrl,
                                                               uint32_t* __restrict__ chunk_counter,
-                                                              const uint32_t* __restrict__ starts) {
+                                                              const uint32_t* __restrict__ starts,
+                                                              uint32_t* __restrict__ members) {
     constexpr uint32_t CAP = NT * MS_IT;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* sK = reinterpret_cast<uint64_t*>(smem);
@@ -849,33 +844,23 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
             __syncthreads();
         }
         if (R == 0) __syncthreads();  // every thread has read its slots before any compacted write
-        // ---- 4. SA, compacted through shared memory (bucket after bucket,
-        //      padding dropped) for a coalesced write
-        const uint32_t base = bstart[team];  // the team's bucket, chunk-relative
-        if (active) {
-#pragma unroll
-            for (int j = 0; j < MS_IT; ++j) {
-                const uint32_t pos = lt * MS_IT + j;
-                if (pos < tsize) sI[base + pos] = v[j];
-            }
-        }
-        // the keys next to this thread's run, for lanes at a warp edge
-        uint64_t prev_last = __shfl_up_sync(0xffffffffu, k[MS_IT - 1], 1);
-        uint64_t next_first = __shfl_down_sync(0xffffffffu, k[0], 1);
-        if (lane == 31) s_wlast[warp] = k[MS_IT - 1];
-        if (lane == 0) s_wfirst[warp] = k[0];
-        __syncthreads();
-        for (uint32_t i = tid; i < len; i += NT) SA[gd.start + i] = sI[i];
-        if (lane == 0 && warp > 0) prev_last = s_wlast[warp - 1];
-        if (lane == 31 && warp + 1 < NT / 32) next_first = s_wfirst[warp + 1];
-        // ---- 5. naming, from the registers. A rotation heads a group where
+        // ---- 4. naming, from the registers. A rotation heads a group where
         //      its key differs from the one before it (a bucket's first
         //      rotation always does: a bucket is a key range); it ends one
         //      where the next key differs or its bucket ends. Its group start
         //      is the last head at or before it: inside the thread by a
         //      running value, across threads by a CTA max-scan of every
         //      thread's last head.
-        uint32_t hm = 0, tm = 0, lh = 0;  // head bits, tail bits, last head + 1 (0: none)
+        const uint32_t base = bstart[team];  // the team's bucket, chunk-relative
+        uint64_t prev_last = __shfl_up_sync(0xffffffffu, k[MS_IT - 1], 1);
+        uint64_t next_first = __shfl_down_sync(0xffffffffu, k[0], 1);
+        if (lane == 31) s_wlast[warp] = k[MS_IT - 1];
+        if (lane == 0) s_wfirst[warp] = k[0];
+        __syncthreads();
+        if (lane == 0 && warp > 0) prev_last = s_wlast[warp - 1];
+        if (lane == 31 && warp + 1 < NT / 32) next_first = s_wfirst[warp + 1];
+        const bool emit_ok = bi.n > 8u;   // smaller blocks: every group is final (whole equal rotations)
+        uint32_t hm = 0, fm = 0, lh = 0;  // head bits, final bits, last head + 1 (0: none)
         if (active) {
 #pragma unroll
             for (int j = 0; j < MS_IT; ++j) {
@@ -883,11 +868,17 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
                 if (pos < tsize) {
                     const uint64_t before = j == 0 ? prev_last : k[j > 0 ? j - 1 : 0];
                     const uint64_t after = j == MS_IT - 1 ? next_first : k[j < MS_IT - 1 ? j + 1 : 0];
-                    if (pos == 0 || k[j] != before) {
+                    const bool head = pos == 0 || k[j] != before;
+                    const bool tail = pos + 1 == tsize || k[j] != after;
+                    if (head) {
                         hm |= 1u << j;
                         lh = base + pos + 1;
                     }
-                    if (pos + 1 == tsize || k[j] != after) tm |= 1u << j;
+                    if (!tail) fm |= 2u << j;  // bit j + 1: not the group's last row
+                    const bool final_row = (head && tail) || !emit_ok;
+                    // SA, compacted through shared memory (bucket after bucket,
+                    // padding dropped) for a coalesced write
+                    sI[base + pos] = v[j] | (final_row ? SA_FINAL : 0u);
                 }
             }
         }
@@ -899,11 +890,11 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
         }
         if (lane == 31) s_wmax[warp] = incl;
         __syncthreads();
+        for (uint32_t i = tid; i < len; i += NT) SA[gd.start + i] = sI[i];
         uint32_t cur = __shfl_up_sync(0xffffffffu, incl, 1);
         if (lane == 0) cur = 0u;
         for (uint32_t w = 0; w < warp; ++w) cur = max(cur, s_wmax[w]);
         const uint32_t boff = gd.start - bi.off;  // the chunk's block-relative start
-        const bool emit_ok = bi.n > 8u;
 #pragma unroll
         for (int j = 0; j < MS_IT; ++j) {
             const uint32_t pos = lt * MS_IT + j;
@@ -911,17 +902,43 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
             const uint32_t P = base + pos;  // chunk-relative position
             if (real && ((hm >> j) & 1u)) cur = P + 1;
             const uint32_t gs = cur - 1;  // its group's start
-            if (real) {
-                BWT_DCHECK(v[j] < bi.n && cur > 0u, &ctrl[CTRL_ERR]);
-                if (v[j] < bi.n) rank[bi.off + v[j]] = boff + gs;
-            }
+            const bool tail = !((fm >> (j + 1)) & 1u);
+            const bool member = real && emit_ok && (P > gs || !tail);  // in a group of two or more
+            if (real) BWT_DCHECK(v[j] < bi.n && cur > 0u, &ctrl[CTRL_ERR]);
+            if (member && v[j] < bi.n) rank[bi.off + v[j]] = boff + gs;
             // a group of more than one rotation ends here: to the doubling rounds
-            const bool want = emit_ok && real && ((tm >> j) & 1u) && P > gs;
+            const bool want = member && tail;
+            if (want) atomicAdd(&members[gd.blk], P - gs + 1);
             em.emit(bins, want, gd.start + gs, P - gs + 1, gd.blk, &ctrl[CTRL_ERR]);
         }
         __syncthreads();
     }
     em.finish(bins, &ctrl[CTRL_ERR]);
+}
+
+// After the chunk sorts: a bucketed block whose chunk sorts sent more than
+// 1/32 of its rotations to the doubling rounds has the ranks of its groups
+// of one stored here (rank[SA] = row for the rows marked SA_FINAL), since its
+// rounds would read many of them; its other ranks are already stored. Such
+// blocks and plain-routed ones read ranks directly (lazy = 0); the others
+// find them on demand. One CTA per block.
+__global__ void __launch_bounds__(256) k_fill_ranks(const BlockInfo* __restrict__ blocks, uint32_t nb,
+                                                    const uint32_t* __restrict__ route,
+                                                    const uint32_t* __restrict__ members,
+                                                    const uint32_t* __restrict__ SA, uint32_t* __restrict__ rank,
+                                                    uint32_t* __restrict__ lazy) {
+    for (uint32_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+        const BlockInfo bi = blocks[blk];
+        const bool bucketed = route[blk] != 1u;
+        const bool fill = bucketed && (uint64_t)members[blk] * 32u > bi.n;
+        if (threadIdx.x == 0) lazy[blk] = bucketed && !fill ? 1u : 0u;
+        if (!fill) continue;
+        for (uint32_t q = threadIdx.x; q < bi.n; q += blockDim.x) {
+            const uint32_t x = SA[bi.off + q];
+            const uint32_t r = x & ~SA_FINAL;
+            if ((x & SA_FINAL) && r < bi.n) rank[bi.off + r] = q;
+        }
+    }
 }
 
 // Blocks routed to equal-width buckets (route 2) take their equal-width row
@@ -1060,6 +1077,8 @@ bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
     if (!p->chunk_base) CKL(cudaMalloc(&p->chunk_base, sizeof(uint32_t) * nbk));
     if (!p->route) CKL(cudaMalloc(&p->route, sizeof(uint32_t) * p->cap_b));
     if (!p->route_first) CKL(cudaMalloc(&p->route_first, sizeof(uint32_t) * 2 * p->cap_b));
+    if (!p->members) CKL(cudaMalloc(&p->members, sizeof(uint32_t) * p->cap_b));
+    if (!p->lazy) CKL(cudaMalloc(&p->lazy, sizeof(uint32_t) * p->cap_b));
     if (!p->bstats) CKL(cudaMalloc(&p->bstats, sizeof(unsigned long long) * 10 * p->cap_b));
     if (!p->tiles_aux) CKL(cudaMalloc(&p->tiles_aux, sizeof(TileDesc) * 2 * (size_t)p->cap_tiles0));
     if (!p->splitters_flat) {
@@ -1215,10 +1234,12 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     uint32_t* chunk_counter = ctrl + CTRL_TILE_CTR + 58;  // control words no radix pass uses
     uint32_t* big_counter = ctrl + CTRL_TILE_CTR + 59;
     CKL(cudaMemsetAsync(chunk_counter, 0, 8, st));
+    CKL(cudaMemsetAsync(p->members, 0, sizeof(uint32_t) * nb, st));
     const bool timing = !p->events.empty() && !p->capturing && p->ev_used + 2 <= p->events.size();
     if (timing) CKL(cudaEventRecord(p->events[p->ev_used], st));
     k_chunk_sort_name<MS_NT, 4, 0><<<sms * p->chunk_sort_ctas, MS_NT, CHUNK_SORT_SMEM, st>>>(
-        p->keys[0], p->vals[0], p->blocks, aux, p->rank, bins_of(p, 0), ctrl, chunk_counter, p->bucket_count);
+        p->keys[0], p->vals[0], p->blocks, aux, p->rank, bins_of(p, 0), ctrl, chunk_counter, p->bucket_count,
+        p->members);
     CKL(cudaGetLastError());
     if (timing) {
         CKL(cudaEventRecord(p->events[p->ev_used + 1], st));
@@ -1231,7 +1252,7 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     // over-full buckets up to BIG_CAP: one 1,024-thread CTA each
     k_chunk_sort_name<BIG_NT, 1, 1><<<sms, BIG_NT, BIG_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks, aux,
                                                                         p->rank, bins_of(p, 0), ctrl, big_counter,
-                                                                        p->bucket_count);
+                                                                        p->bucket_count, p->members);
     CKL(cudaGetLastError());
     p->stats.kernel_launches += 2;
 
@@ -1278,6 +1299,24 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
                           bins_of(p, 0), ctrl, st));
     p->stats.kernel_launches++;
     p->learned_overflow_passes = (uint32_t)PT;
+
+    // 4d. ranks: blocks with many group members get every rank stored; the
+    //     rest find the ranks of their groups of one on demand
+    nv.next("bucket_ranks");
+    k_fill_ranks<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->blocks, nb, p->route, p->members, p->vals[0],
+                                                                p->rank, p->lazy);
+    CKL(cudaGetLastError());
+    p->stats.kernel_launches++;
+    LazyRanks lz;
+    lz.lazy = p->lazy;
+    lz.S = d_in;
+    lz.SA = p->vals[0];
+    lz.route = p->route;
+    lz.starts = p->bucket_count;
+    lz.splitters = p->splitters;
+    lz.index = p->splitter_index;
+    lz.own_cap = BIG_CAP;
+    p->lazy_ranks = lz;
     return BWT_OK;
 }
 
@@ -1303,7 +1342,7 @@ void bwt::learned_stats(bwt_plan* p) {
             p->stats.chunk_keys += p->h_blocks[b].n - bs[0];
         }
     }
-    p->stats.chunk_bytes = 20.0 * (double)p->stats.chunk_keys;
+    p->stats.chunk_bytes = 16.0 * (double)p->stats.chunk_keys;
     p->stats.radix_keys += (uint64_t)p->learned_overflow_passes * p->stats.keys_overflowed;
 }
 

@@ -133,7 +133,7 @@ void bwt::free_plan_memory(bwt_plan* p) {
         FH(p->stage_parts[sl]);
         FH(p->stage_pfirst[sl]);
     }
-    F(p->splitters); F(p->splitter_index); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->route_first); F(p->bstats); F(p->tiles_aux); F(p->inv_slots); F(p->inv_items); F(p->mtf_lists);
+    F(p->splitters); F(p->splitter_index); F(p->splitters_flat); F(p->bucket_count); F(p->bucket_cursor); F(p->chunk_map); F(p->chunk_base); F(p->route); F(p->route_first); F(p->members); F(p->lazy); F(p->bstats); F(p->tiles_aux); F(p->inv_slots); F(p->inv_items); F(p->mtf_lists);
     drop_graph(p);
     FH(p->h_ctrl); FH(p->h_off);
     for (int s = 0; s < 2; ++s) {
@@ -469,6 +469,7 @@ static cudaError_t timed_onesweep(bwt_plan* p, int key_bytes, bool from_s, const
 }
 
 bwt_status bwt::reset_ctrl(bwt_plan* p, cudaStream_t st) {
+    p->lazy_ranks = LazyRanks{};  // every rank stored, unless a learned first stage says otherwise
     CK(launch_reset_ctrl(p->ctrl, p->spin_limit, (uint32_t)p->withhold, p->ntiles0, st));
     p->stats.kernel_launches++;
     return BWT_OK;
@@ -586,7 +587,8 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
     CK(cudaMemsetAsync(nxt.count, 0, sizeof(uint32_t) * NCLS, st));
     {
         int launched = 0;
-        CK(launch_gather_small(p->sa, p->rank, p->blocks, cur, depth, p->key2, host_counts, st, &launched));
+        CK(launch_gather_small(p->sa, p->rank, p->blocks, cur, depth, p->key2, host_counts, st, &launched,
+                               p->lazy_ranks));
         p->stats.kernel_launches += launched;
     }
     const bool large = !host_counts || host_counts[CLS_LARGE] > 0;
@@ -600,7 +602,7 @@ bwt_status bwt::enqueue_round(bwt_plan* p, int par, const uint32_t* host_counts,
         // with one pass only, that pass would read and write SA in place: it
         // reads a copy instead
         CK(launch_large_prologue(p->sa, p->rank, p->blocks, p->ltiles, ctrl + CTRL_NUM_LTILES, depth, p->kA,
-                                 P2 == 1 ? p->vA : nullptr, p->hist, rb, P2, p->seg_varied, ls));
+                                 P2 == 1 ? p->vA : nullptr, p->hist, rb, P2, p->seg_varied, ls, p->lazy_ranks));
         CK(launch_scan_rows(p->hist, RADIX, cur.count + CLS_LARGE, (uint32_t)P2, 0, (uint32_t)(p->cap_hist / RADIX),
                             ls));
         p->stats.kernel_launches += 4;

@@ -110,6 +110,9 @@ struct bwt_plan {
     uint32_t* chunk_base = nullptr;     // [block][BWT_BUCKETS] block-relative start of each chunk
     uint32_t* route = nullptr;          // [block] 0 = learned buckets, 1 = plain radix, 2 = equal-width buckets
     uint32_t* route_first = nullptr;    // [2][block] first tile of each block in its route's tile table
+    uint32_t* members = nullptr;        // [block] rotations the chunk sorts sent to the doubling rounds
+    uint32_t* lazy = nullptr;           // [block] 1: ranks of groups of one are found on demand
+    bwt::LazyRanks lazy_ranks;          // how this call's doubling rounds read ranks
     unsigned long long* bstats = nullptr;  // [2][block][5] overflow keys, overflow buckets, largest bucket,
                                            // sum of squared sizes, non-empty buckets
     bwt::TileDesc* tiles_aux = nullptr; // [2][tiles0]: tiles of plain-routed blocks, then of bucketed ones

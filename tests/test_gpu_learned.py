@@ -211,6 +211,46 @@ def test_overfull_buckets_big_chunk_sort_and_radix(small_model, graph):
     assert st["buckets_overflowed"] >= 2, st
 
 
+def _with_repeats(block, frac, seg, seed):
+    """A copy of `block` with segments of `seg` bytes copied elsewhere until
+    about `frac` of its rotations share their first 8 bytes with another."""
+    rng = np.random.default_rng(seed)
+    b = block.copy()
+    n = b.size
+    for _ in range(max(1, int(frac * n / (2 * seg)))):
+        src, dst = rng.integers(0, n - seg, 2)
+        b[dst:dst + seg] = b[src:src + seg]
+    return b
+
+
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("which", ["model", "equal_width"])
+def test_lazy_and_stored_ranks(small_model, which, graph):
+    """After the chunk sorts a bucketed block's doubling rounds read ranks
+    either stored in full (more than 1/32 of its rotations in groups: filled
+    after the chunk sorts) or found on demand (the bucket of the rotation's
+    key, then a search of the bucket's sorted rows). Markov blocks with
+    repeated segments put about 11% (stored), 0.9% and 0.9% (on demand) of
+    their rotations in groups of two or more, a plain one none; every output
+    is exact."""
+    spl = small_model.splitters if which == "model" else model.equal_width_splitters()
+    blocks = []
+    for i, frac in enumerate([0.12, 0.015, 0.002, 0.0]):
+        w = datagen.Workload("t", [datagen.MARKOV3_Z96], [40 + i], [120_000 + 7_001 * i])
+        b, _ = w.generate()
+        blocks.append(_with_repeats(b, frac, 600, 70 + i) if frac else b)
+    from gpu_util import batch_from_blocks
+    buf, off = batch_from_blocks(blocks)
+    for blk in blocks[:3]:  # the intended share of group members, on the host
+        keys = _prefix_keys(blk)
+        _, inv, cnt = np.unique(keys, return_inverse=True, return_counts=True)
+        share = (cnt[inv] > 1).mean()
+        assert share > 0.0005, share
+    L, prim, st = _learned_run(buf, off, spl, graph=graph)
+    assert_matches_oracle(buf, off, L, prim, f"lazy ranks {which} graph={graph}")
+    assert st["blocks_routed_plain"] == 0, st
+
+
 def test_learned_graph_equals_oracle_and_replays(small_model):
     """Learned + batched: the learned stage (device-side routing included) and
     the doubling loop captured as one CUDA graph. The first call captures, the
