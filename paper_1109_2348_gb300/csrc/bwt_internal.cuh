@@ -142,6 +142,11 @@ struct LazyRanks {
 // The 8-byte big-endian key of rotation j of a block (cyclic).
 __device__ __forceinline__ uint64_t rotation_key(const uint8_t* __restrict__ S, BlockInfo bi, uint32_t j) {
     uint64_t k = 0;
+    if ((uint64_t)j + 8 <= bi.n) {  // no wrap: eight independent loads
+#pragma unroll
+        for (int t = 0; t < 8; ++t) k = (k << 8) | S[bi.off + j + t];
+        return k;
+    }
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         uint32_t q = j + t;
