@@ -1014,6 +1014,19 @@ __global__ void k_set_cond_initial(const uint32_t* ctrl, uint32_t max_n, cudaGra
     cudaGraphSetConditional(cond, more ? 1u : 0u);
 }
 
+// Word copy into mapped pinned host memory by the SMs: a copy engine busy
+// with a large transfer on another stream would hold a memcpy node back, and
+// the graph with it.
+__global__ void k_words_to_host(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t launch_words_to_host(uint32_t* host_dst_dev_ptr, const uint32_t* src, uint32_t words, cudaStream_t st) {
+    if (!words) return cudaSuccess;
+    k_words_to_host<<<std::min<uint32_t>((words + 255) / 256, 64), 256, 0, st>>>(host_dst_dev_ptr, src, words);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reset_ctrl(uint32_t* ctrl, uint32_t spin, uint32_t withhold, uint32_t ntiles0, cudaStream_t st) {
     k_reset_ctrl<<<1, 128, 0, st>>>(ctrl, spin, withhold, ntiles0);
     return cudaGetLastError();

@@ -219,7 +219,7 @@ fail:
 void bwt::graph_stats(bwt_plan* p) {
     const uint64_t rounds_run = p->h_ctrl[CTRL_BODY_ITERS];
     p->stats.rounds = p->h_ctrl[CTRL_ROUNDS];
-    p->stats.kernel_launches =
-        p->graph_main_kernels + rounds_run * (p->graph_round_kernels + p->graph_large_kernels);
+    p->stats.kernel_launches =  // + the control-word copy after the graph
+        p->graph_main_kernels + rounds_run * (p->graph_round_kernels + p->graph_large_kernels) + 1;
     p->stats.radix_launches = p->graph_main_radix + rounds_run * p->graph_large_radix;
 }

@@ -141,6 +141,12 @@ cudaError_t launch_rename_large(const uint32_t* SA, const uint32_t* key2, uint32
 // Control words: reset before a batch; advance after a round (and set the
 // graph loop condition); set the condition before the loop.
 cudaError_t launch_reset_ctrl(uint32_t* ctrl, uint32_t spin, uint32_t withhold, uint32_t ntiles0, cudaStream_t st);
+
+// Copies `words` u32 from device memory to pinned host memory, written by a
+// kernel (host_dst_dev_ptr: the device view of the host buffer), so that no
+// copy engine is involved: stream-ordered, visible to the host once the
+// stream has passed the launch.
+cudaError_t launch_words_to_host(uint32_t* host_dst_dev_ptr, const uint32_t* src, uint32_t words, cudaStream_t st);
 // flags: 1 = set the loop condition `loop`, 2 = set `next_round`, 4 = count
 // the round (graph mode); both conditions get "another round is due".
 cudaError_t launch_round_end(uint32_t* ctrl, int par, uint32_t max_n, cudaGraphConditionalHandle loop,

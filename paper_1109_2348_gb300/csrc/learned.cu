@@ -1087,8 +1087,14 @@ bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
         CKL(cudaMalloc(&p->splitters_flat, sizeof(uint64_t) * NSP));
         CKL(cudaMemcpy(p->splitters_flat, flat.data(), sizeof(uint64_t) * NSP, cudaMemcpyHostToDevice));
     }
-    if (!p->h_route) CKL(cudaMallocHost(&p->h_route, sizeof(uint32_t) * p->cap_b));
-    if (!p->h_bstats) CKL(cudaMallocHost(&p->h_bstats, sizeof(unsigned long long) * 10 * p->cap_b));
+    if (!p->h_route) {
+        CKL(cudaMallocHost(&p->h_route, sizeof(uint32_t) * p->cap_b));
+        CKL(cudaHostGetDevicePointer((void**)&p->hd_route, p->h_route, 0));
+    }
+    if (!p->h_bstats) {
+        CKL(cudaMallocHost(&p->h_bstats, sizeof(unsigned long long) * 10 * p->cap_b));
+        CKL(cudaHostGetDevicePointer((void**)&p->hd_bstats, p->h_bstats, 0));
+    }
     // kernel attributes and occupancy: set up here, outside any stream capture
     static const int sort_ctas = [] {
         cudaFuncSetAttribute((void*)k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COUNT_SMEM);
@@ -1147,10 +1153,12 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     k_route_tiles<<<std::max(1, std::min<int>((nt + 255) / 256, sms * 4)), 256, 0, st>>>(
         p->tiles0, nt, nb, p->route, p->route_first, tilesP, tilesB);
     CKL(cudaGetLastError());
-    // for the statistics, read after the call
-    CKL(cudaMemcpyAsync(p->h_bstats, p->bstats, sizeof(unsigned long long) * 10 * nb, cudaMemcpyDeviceToHost, st));
-    CKL(cudaMemcpyAsync(p->h_route, p->route, sizeof(uint32_t) * nb, cudaMemcpyDeviceToHost, st));
-    p->stats.kernel_launches += 4;
+    // for the statistics, read after the call (written by kernels: a memcpy
+    // node here would wait behind any large copy queued on the same engine
+    // by another stream, and stall the whole call with it)
+    CKL(launch_words_to_host(p->hd_bstats, reinterpret_cast<const uint32_t*>(p->bstats), 20 * nb, st));
+    CKL(launch_words_to_host(p->hd_route, p->route, nb, st));
+    p->stats.kernel_launches += 6;
     const uint32_t* ntp = ctrl + CTRL_AUX0;
     const uint32_t* ntb = ctrl + CTRL_AUX1;
 

@@ -204,6 +204,10 @@ extern "C" bwt_status bwt_plan_create(const bwt_plan_desc* desc, int device, bwt
     for (int par = 0; par < 2; ++par)
         for (int c = 0; c < NCLS; ++c) A(dev_alloc(&p->bins[par][c], p->bincap[c], &total));
     A(host_alloc(&p->h_ctrl, CTRL_WORDS));
+    if (s == BWT_OK) {
+        const cudaError_t e = cudaHostGetDevicePointer((void**)&p->hd_ctrl, p->h_ctrl, 0);
+        if (e != cudaSuccess) s = record_cuda(e, "cudaHostGetDevicePointer");
+    }
     for (int sl = 0; sl < 2; ++sl) {
         A(host_alloc(&p->stage_tiles[sl], p->cap_tiles0));
         A(host_alloc(&p->stage_blocks[sl], B));
@@ -809,11 +813,11 @@ extern "C" bwt_status bwt_forward_batch(bwt_plan* p, const uint8_t* d_in, const 
     const bool learned = !per_block && (p->desc.flags & BWT_F_LEARNED);
     if (graph) {
         // stream-ordered: enqueue the graph, then a copy of the control words
-        // and an event; status and statistics are read when asked for
+        // (by a kernel, not a copy engine: see launch_words_to_host) and an
+        // event; status and statistics are read when asked for
         s = run_graph(p, d_in, d_L, d_primary, st);  // plain or learned first stage
         if (s == BWT_OK) {
-            cudaError_t e = cudaMemcpyAsync(p->h_ctrl, p->ctrl, sizeof(uint32_t) * CTRL_WORDS,
-                                            cudaMemcpyDeviceToHost, st);
+            cudaError_t e = launch_words_to_host(p->hd_ctrl, p->ctrl, CTRL_WORDS, st);
             if (e == cudaSuccess) e = cudaEventRecord(p->done_ev, st);
             if (e == cudaSuccess) {
                 p->pending = true;
@@ -822,7 +826,7 @@ extern "C" bwt_status bwt_forward_batch(bwt_plan* p, const uint8_t* d_in, const 
                 p->last = BWT_OK;
                 return BWT_OK;
             }
-            s = record_cuda(e, "cudaMemcpyAsync / cudaEventRecord");
+            s = record_cuda(e, "control-word copy / cudaEventRecord");
         }
         p->last = s;
         return s;

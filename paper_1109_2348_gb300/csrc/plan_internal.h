@@ -118,6 +118,8 @@ struct bwt_plan {
     bwt::TileDesc* tiles_aux = nullptr; // [2][tiles0]: tiles of plain-routed blocks, then of bucketed ones
     uint32_t* h_route = nullptr;
     unsigned long long* h_bstats = nullptr;
+    uint32_t* hd_route = nullptr;       // device views of the two pinned buffers above (written by kernels)
+    uint32_t* hd_bstats = nullptr;
     bool have_model = false;
     int chunk_sort_ctas = 1;            // resident chunk-sort CTAs per SM
     uint32_t learned_overflow_passes = 0;  // radix passes over the overflow buckets (index + key)
@@ -139,6 +141,7 @@ struct bwt_plan {
 
     // pinned host staging
     uint32_t* h_ctrl = nullptr;
+    uint32_t* hd_ctrl = nullptr;        // its device view (the graph path writes it with a kernel)
     bwt::TileDesc* h_tiles = nullptr;    // the staging slot of the last upload (block and tile tables)
     bwt::BlockInfo* h_blocks = nullptr;
     uint64_t* h_off = nullptr;
