@@ -261,9 +261,30 @@ __global__ void __launch_bounds__(COUNT_THREADS, 1) k_bucket_count(const uint8_t
     load_splitters(splitters, index, spl, first);
     for (int i = threadIdx.x; i < NBK; i += blockDim.x) h[i] = 0;
     const uint32_t nspan = (ntiles + span - 1) / span;
+    // One CTA an SM, so nothing else hides a tile's load: the next tile's
+    // bytes (one 16-byte word a thread, from the aligned addresses covering
+    // them) are loaded into registers while the current tile is counted.
+    auto fetch = [&](uint32_t t, uint4& w, uint32_t& shift, bool& fast) {
+        const TileDesc td = tiles[t];
+        const BlockInfo bi = blocks[td.blk];
+        const uint32_t i0 = td.start - bi.off;
+        const uintptr_t a = reinterpret_cast<uintptr_t>(S + bi.off + i0);
+        const uintptr_t a0 = a & ~(uintptr_t)15;
+        // the same test as stage_tile_bytes' vector path
+        fast = (uint64_t)i0 + td.len + 7 + 16 <= bi.n && a0 >= reinterpret_cast<uintptr_t>(S);
+        shift = (uint32_t)(a - a0);
+        const uint32_t nvec = (shift + td.len + 7 + 15) >> 4;
+        w = make_uint4(0, 0, 0, 0);
+        if (fast && threadIdx.x < nvec) w = __ldg(reinterpret_cast<const uint4*>(a0) + threadIdx.x);
+    };
+    static_assert((TILE_BYTES - 48) / 16 + 3 <= COUNT_THREADS, "one 16-byte word a thread covers a tile");
     for (uint32_t s = blockIdx.x; s < nspan; s += gridDim.x) {
         const uint32_t t0 = s * span, t1 = min(ntiles, t0 + span);
         uint32_t cur = tiles[t0].blk;
+        uint4 w;
+        uint32_t wshift;
+        bool wfast;
+        fetch(t0, w, wshift, wfast);
         for (uint32_t t = t0; t < t1; ++t) {
             const TileDesc td = tiles[t];
             if (td.blk != cur) {  // CTA-uniform; the histogram is complete (synced after the last tile)
@@ -271,8 +292,15 @@ __global__ void __launch_bounds__(COUNT_THREADS, 1) k_bucket_count(const uint8_t
                 cur = td.blk;
             }
             const BlockInfo bi = blocks[td.blk];
-            const uint32_t shift = stage_tile_bytes(S, bi, td.start - bi.off, td.len, sb, threadIdx.x, blockDim.x);
+            uint32_t shift;
+            if (wfast) {
+                if (threadIdx.x < (wshift + td.len + 7 + 15) >> 4) reinterpret_cast<uint4*>(sb)[threadIdx.x] = w;
+                shift = wshift;
+            } else {
+                shift = stage_tile_bytes(S, bi, td.start - bi.off, td.len, sb, threadIdx.x, blockDim.x);
+            }
             __syncthreads();
+            if (t + 1 < t1) fetch(t + 1, w, wshift, wfast);
             for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) {
                 const uint64_t key = pack8_smem(sb, shift + q);
                 const uint32_t b = bucket_of(spl, first, key);
