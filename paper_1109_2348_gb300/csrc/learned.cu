@@ -656,7 +656,7 @@ __device__ __forceinline__ void sort13(uint64_t (&k)[MS_IT], uint32_t (&v)[MS_IT
 //      the bucket, padded with entries above every real one.
 //   2. Every rotation's bucket in the chunk, read off the tag its value
 //      carries from the scatter, and a counting scatter into its bucket's
-//      run (one shared-memory reservation per bucket and warp step).
+//      run (a shared-memory atomic a rotation).
 //   3. Each thread sorts its MS_IT slots with the network; then merge
 //      rounds inside each team (merge path; a team takes part in as many
 //      rounds as it needs, ceil(log2(threads)): about 5 for learned buckets
@@ -695,7 +695,6 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
     __shared__ uint32_t s_wmax[NT / 32];                      // each warp's last head + 1
     __shared__ uint32_t s_c, s_rounds;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t lt_mask = lanemask_lt();
     if (ld_volatile(&ctrl[CTRL_ERR])) return;  // an earlier stage failed: the chunks are not permutations
     WarpEmitter em;
     em.init(ebuf[warp]);
@@ -798,13 +797,8 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
                 BWT_DCHECK(lb < nbk && v[j] < bi.n, &ctrl[CTRL_ERR]);
                 lb = min(lb, nbk - 1);
             }
-            const uint32_t peers = __match_any_sync(0xffffffffu, lb);
-            const int leader = __ffs(peers) - 1;
-            uint32_t base = 0;
-            if (valid && (int)lane == leader) base = atomicAdd(&bcur[lb], (uint32_t)__popc(peers));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (valid) {
-                const uint32_t slot = min(bthr[lb] * MS_IT + base + __popc(peers & lt_mask), CAP - 1u);
+            if (valid) {  // any order inside the run: the sort decides it
+                const uint32_t slot = min(bthr[lb] * MS_IT + atomicAdd(&bcur[lb], 1u), CAP - 1u);
                 sK[slot] = k[j];
                 sI[slot] = v[j];
             }
