@@ -493,6 +493,8 @@ def ours(args):
             acc["launches"] += st["first_launches"]
             acc["keys"] += n * st["first_launches"]
         th.close()
+        if acc["ms"] <= 0 or acc["launches"] == 0:
+            return None  # small blocks: the one-cluster first sort has no separately timed passes
         achieved = acc["bytes"] / (acc["ms"] / 1e3) / 1e9
         per_launch_keys = acc["keys"] / max(1, acc["launches"])
         kname = ("k_hist16 + k_scan16_cols + k_scan16_digits + k_scatter16 (plain first-sort 16-bit pass)"
