@@ -251,6 +251,42 @@ def test_lazy_and_stored_ranks(small_model, which, graph):
     assert st["blocks_routed_plain"] == 0, st
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_lazy_ranks_with_overfull_buckets(small_model, graph):
+    """On-demand ranks whose rotations lie in over-full buckets: a Markov block
+    with repeated segments (about 2% of its rotations in groups, so its
+    groups of one keep their ranks unstored) whose splitters are merged so
+    that one bucket goes to the 1,024-thread sort and one to the overflow
+    radix (ranks stored in full there). The group members' successors are
+    spread over the key range, so some lookups land in each kind of bucket."""
+    w = datagen.Workload("t", [datagen.MARKOV3_Z96], [21], [300_000])
+    base_block, _ = w.generate()
+    blk = _with_repeats(base_block, 0.02, 400, 22)
+    keys = _prefix_keys(blk)
+    spl = np.array(small_model.splitters, dtype=np.uint64).copy()
+    sizes = lambda sp: np.bincount(np.searchsorted(sp, keys, side="right"), minlength=sp.size + 1)  # noqa: E731
+    base = sizes(spl)
+    # merge buckets after 1000 until one holds 6,000..13,312, and after 2600 until one holds > 20,000
+    for j, lo, hi in ((1000, 6_000, 13_312), (2600, 20_000, 1 << 30)):
+        for m in range(1, spl.size - j - 1):
+            tot = int(base[j + 1:j + m + 2].sum())
+            if lo < tot <= hi:
+                spl[j + 1:j + 1 + m] = spl[j]
+                break
+        else:
+            raise AssertionError("could not build the bucket")
+        base = sizes(spl)
+    sz = sizes(spl)
+    assert ((sz > 3_328) & (sz <= 13_312)).any() and (sz > 13_312).any(), sz.max()
+    _, inv, cnt = np.unique(keys, return_inverse=True, return_counts=True)
+    share = (cnt[inv] > 1).mean()
+    assert 0.005 < share < 1 / 32, share  # groups exist, and the block's ranks stay on demand
+    buf, off = blk, np.array([0, blk.size], dtype=np.uint64)
+    L, prim, st = _learned_run(buf, off, spl, graph=graph)
+    assert_matches_oracle(buf, off, L, prim, f"lazy ranks with over-full buckets graph={graph}")
+    assert st["blocks_routed_plain"] == 0 and st["buckets_overflowed"] >= 2, st
+
+
 def test_learned_graph_equals_oracle_and_replays(small_model):
     """Learned + batched: the learned stage (device-side routing included) and
     the doubling loop captured as one CUDA graph. The first call captures, the
