@@ -227,15 +227,18 @@ constexpr size_t TILE_BYTES = 4096 + 48;
 constexpr size_t COUNT_SMEM = SPL_BYTES + CNT_BYTES + TILE_BYTES;
 constexpr int COUNT_THREADS = 1024;  // one CTA an SM: its shared memory holds the splitters and the index
 
-// Counts every rotation in two bucketings at once -- the learned splitters
-// and equal-width buckets (the top 12 key bits) -- and stores its learned
-// bucket in fb (u16 per rotation) for the scatter. The two histograms share
-// one shared-memory word per bucket (learned count in the low half, equal-
-// width count in the high half), so a CTA counts at most 65535 rotations
-// (`span` tiles) before it adds them to the block's rows: one global atomic
-// per non-empty bucket and span; a span that crosses into the next block
-// flushes at the boundary. counts: [2][block][4096] (learned rows, then
-// equal-width rows).
+// Counts every rotation's bucket. FLAT = false: the learned bucketing of
+// every block, storing each rotation's learned bucket in fb (u16 per
+// rotation) for the scatter; FLAT = true: the equal-width bucketing (the top
+// 12 key bits) of the blocks marked in `need` only (those the learned
+// buckets do not fit). Text keys crowd a few of the equal-width buckets, so
+// their shared-memory atomics conflict: counting them only where the routing
+// needs them keeps them off the common path. Counts gather in one shared-
+// memory word per bucket (learned in the low half, equal-width in the high
+// half), so a CTA counts at most 65535 rotations (`span` tiles) before it
+// adds them to the block's rows: one global atomic per non-empty bucket and
+// span; a span that crosses into the next block flushes at the boundary.
+// counts: [2][block][4096] (learned rows, then equal-width rows).
 __device__ __forceinline__ void flush_counts(uint32_t* h, uint32_t* __restrict__ counts, uint32_t nb, uint32_t blk) {
     for (int i = threadIdx.x; i < NBK; i += blockDim.x) {
         const uint32_t c = h[i];
@@ -245,6 +248,7 @@ __device__ __forceinline__ void flush_counts(uint32_t* h, uint32_t* __restrict__
     }
 }
 
+template <bool FLAT>
 __global__ void __launch_bounds__(COUNT_THREADS, 1) k_bucket_count(const uint8_t* __restrict__ S,
                                                                     const BlockInfo* __restrict__ blocks,
                                                                     const TileDesc* __restrict__ tiles,
@@ -252,14 +256,16 @@ __global__ void __launch_bounds__(COUNT_THREADS, 1) k_bucket_count(const uint8_t
                                                                     const uint64_t* __restrict__ splitters,
                                                                     const uint16_t* __restrict__ index,
                                                                     uint32_t nb, uint32_t* __restrict__ counts,
-                                                                    uint16_t* __restrict__ fb) {
+                                                                    uint16_t* __restrict__ fb,
+                                                                    const uint32_t* __restrict__ need) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* spl = reinterpret_cast<uint64_t*>(smem);
     uint16_t* first = reinterpret_cast<uint16_t*>(smem + 4096 * 8);
     uint32_t* h = reinterpret_cast<uint32_t*>(smem + SPL_BYTES);
     uint8_t* sb = smem + SPL_BYTES + CNT_BYTES;
-    load_splitters(splitters, index, spl, first);
+    if (!FLAT) load_splitters(splitters, index, spl, first);
     for (int i = threadIdx.x; i < NBK; i += blockDim.x) h[i] = 0;
+    __syncthreads();
     const uint32_t nspan = (ntiles + span - 1) / span;
     // One CTA an SM, so nothing else hides a tile's load: the next tile's
     // bytes (one 16-byte word a thread, from the aligned addresses covering
@@ -275,11 +281,22 @@ __global__ void __launch_bounds__(COUNT_THREADS, 1) k_bucket_count(const uint8_t
         shift = (uint32_t)(a - a0);
         const uint32_t nvec = (shift + td.len + 7 + 15) >> 4;
         w = make_uint4(0, 0, 0, 0);
+        if (FLAT && need[td.blk] == 0u) return;  // a tile that will be skipped: no bytes
         if (fast && threadIdx.x < nvec) w = __ldg(reinterpret_cast<const uint4*>(a0) + threadIdx.x);
     };
     static_assert((TILE_BYTES - 48) / 16 + 3 <= COUNT_THREADS, "one 16-byte word a thread covers a tile");
+    __shared__ uint32_t s_any;
     for (uint32_t s = blockIdx.x; s < nspan; s += gridDim.x) {
         const uint32_t t0 = s * span, t1 = min(ntiles, t0 + span);
+        if (FLAT) {  // whole spans of blocks the learned buckets fit are skipped, checked at once
+            if (threadIdx.x == 0) s_any = 0u;
+            __syncthreads();
+            if (t0 + threadIdx.x < t1 && need[tiles[t0 + threadIdx.x].blk]) s_any = 1u;
+            __syncthreads();
+            const bool any = s_any != 0u;
+            __syncthreads();  // every thread has read s_any before the next span resets it
+            if (!any) continue;
+        }
         uint32_t cur = tiles[t0].blk;
         uint4 w;
         uint32_t wshift;
@@ -290,6 +307,10 @@ __global__ void __launch_bounds__(COUNT_THREADS, 1) k_bucket_count(const uint8_t
             if (td.blk != cur) {  // CTA-uniform; the histogram is complete (synced after the last tile)
                 flush_counts(h, counts, nb, cur);
                 cur = td.blk;
+            }
+            if (FLAT && need[td.blk] == 0u) {  // CTA-uniform: a block the learned buckets fit
+                if (t + 1 < t1) fetch(t + 1, w, wshift, wfast);
+                continue;
             }
             const BlockInfo bi = blocks[td.blk];
             uint32_t shift;
@@ -303,10 +324,13 @@ __global__ void __launch_bounds__(COUNT_THREADS, 1) k_bucket_count(const uint8_t
             if (t + 1 < t1) fetch(t + 1, w, wshift, wfast);
             for (uint32_t q = threadIdx.x; q < td.len; q += blockDim.x) {
                 const uint64_t key = pack8_smem(sb, shift + q);
-                const uint32_t b = bucket_of(spl, first, key);
-                fb[td.start + q] = (uint16_t)b;
-                atomicAdd(&h[b], 1u);
-                atomicAdd(&h[(uint32_t)(key >> 52)], 1u << 16);
+                if (FLAT) {
+                    atomicAdd(&h[(uint32_t)(key >> 52)], 1u << 16);
+                } else {
+                    const uint32_t b = bucket_of(spl, first, key);
+                    fb[td.start + q] = (uint16_t)b;
+                    atomicAdd(&h[b], 1u);
+                }
             }
             __syncthreads();
         }
@@ -972,6 +996,15 @@ __global__ void k_select_rows(uint32_t* __restrict__ counts, const uint32_t* __r
                 counts[(size_t)blk * NBK + i] = counts[((size_t)nb + blk) * NBK + i];
 }
 
+// need[b] = 1 for the blocks whose learned over-capacity buckets hold more
+// than a quarter of the block (and that are not too large to chunk): the
+// ones whose equal-width counts the routing has to see.
+__global__ void k_flat_needed(const unsigned long long* __restrict__ bstats, const BlockInfo* __restrict__ blocks,
+                              uint32_t nb, uint32_t* __restrict__ need) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
+        need[b] = bstats[5 * (size_t)b] * 4 > blocks[b].n ? 1u : 0u;
+}
+
 // Routes every block and numbers its tiles in its route's tile table, in one
 // CTA: route 0 (learned buckets) if the learned over-capacity buckets hold at
 // most a quarter of the block, else 2 (equal-width buckets) if those do, else
@@ -1119,7 +1152,10 @@ bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
     }
     // kernel attributes and occupancy: set up here, outside any stream capture
     static const int sort_ctas = [] {
-        cudaFuncSetAttribute((void*)k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COUNT_SMEM);
+        cudaFuncSetAttribute((void*)k_bucket_count<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)COUNT_SMEM);
+        cudaFuncSetAttribute((void*)k_bucket_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)COUNT_SMEM);
         cudaFuncSetAttribute((void*)k_chunk_sort_name<MS_NT, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)CHUNK_SORT_SMEM);
         cudaFuncSetAttribute((void*)k_chunk_sort_name<BIG_NT, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1152,10 +1188,11 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     p->kB = reinterpret_cast<uint32_t*>(p->keys[0]);
     p->vB = p->kB + p->cap_n;
 
-    // 1. count both bucketings per block and store every rotation's learned
-    //    bucket (in the u16 view of keys[1], free until the scatter has run),
-    // 2. per-block statistics of both, 3. route every block and split the
-    //    tile table by route -- all on the device
+    // 1. count the learned bucketing per block and store every rotation's
+    //    learned bucket (in the u16 view of keys[1], free until the scatter
+    //    has run), then the equal-width bucketing of the blocks the learned
+    //    buckets do not fit, 2. per-block statistics of both, 3. route every
+    //    block and split the tile table by route -- all on the device
     NvtxStages nv;
     nv.next("bucket_count");
     uint16_t* fb = reinterpret_cast<uint16_t*>(p->keys[1]);
@@ -1164,11 +1201,18 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
         const uint32_t span_max = 65535u / T;  // packed 16-bit counts per span
         const uint32_t span = std::max(1u, std::min(span_max, nt / (uint32_t)(sms * 4)));
         const int grid = std::max(1, std::min<int>((nt + span - 1) / span, sms));
-        k_bucket_count<<<grid, COUNT_THREADS, COUNT_SMEM, st>>>(d_in, p->blocks, p->tiles0, nt, span, p->splitters,
-                                                                p->splitter_index, nb, p->bucket_count, fb);
+        k_bucket_count<false><<<grid, COUNT_THREADS, COUNT_SMEM, st>>>(
+            d_in, p->blocks, p->tiles0, nt, span, p->splitters, p->splitter_index, nb, p->bucket_count, fb, nullptr);
+        k_bucket_stats<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, nb, p->bstats);
+        // the equal-width counts, only where the learned buckets do not fit
+        // (route[] holds the flags until the routing overwrites it)
+        k_flat_needed<<<(nb + 255) / 256, 256, 0, st>>>(p->bstats, p->blocks, nb, p->route);
+        k_bucket_count<true><<<grid, COUNT_THREADS, COUNT_SMEM, st>>>(
+            d_in, p->blocks, p->tiles0, nt, span, p->splitters, p->splitter_index, nb, p->bucket_count, fb, p->route);
+        k_bucket_stats<<<std::min<uint32_t>(nb, 65535), 256, 0, st>>>(p->bucket_count + (size_t)nb * NBK, CHUNK_CAP,
+                                                                      nb, p->bstats + 5 * (size_t)nb);
     }
     nv.next("bucket_route");
-    k_bucket_stats<<<std::min<uint32_t>(2 * nb, 65535), 256, 0, st>>>(p->bucket_count, CHUNK_CAP, 2 * nb, p->bstats);
     k_route_scan<<<1, 1024, 0, st>>>(p->bstats, p->blocks, nb, T, p->route, p->route_first, ctrl);
     TileDesc* tilesP = p->tiles_aux;
     TileDesc* tilesB = p->tiles_aux + p->cap_tiles0;
@@ -1180,7 +1224,7 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     // by another stream, and stall the whole call with it)
     CKL(launch_words_to_host(p->hd_bstats, reinterpret_cast<const uint32_t*>(p->bstats), 20 * nb, st));
     CKL(launch_words_to_host(p->hd_route, p->route, nb, st));
-    p->stats.kernel_launches += 6;
+    p->stats.kernel_launches += 9;
     const uint32_t* ntp = ctrl + CTRL_AUX0;
     const uint32_t* ntb = ctrl + CTRL_AUX1;
 
