@@ -389,7 +389,8 @@ __global__ void __launch_bounds__(256) k_bucket_stats(const uint32_t* __restrict
 // key interval, so a chunk holds every rotation of its key range: its first
 // rotation starts a group and its last ends one, and naming needs nothing
 // outside the chunk. A fine bucket larger than CHUNK_CAP is a chunk of its
-// own: up to BIG_CAP rotations one 1,024-thread CTA sorts it the same way (a
+// own: up to BIG_CAP rotations one CTA sorts it the same way (512 threads up
+// to MID_CAP, 1,024 beyond; a
 // model's over-full buckets are mostly a few thousand distinct keys), beyond
 // that it goes to the overflow radix.
 constexpr int MS_NT = 256;                           // threads of the chunk sort
@@ -397,6 +398,8 @@ constexpr int MS_IT = 13;                            // rotations per thread (od
 constexpr uint32_t CHUNK_CAP = MS_NT * MS_IT;        // 3328
 constexpr int BIG_NT = 1024;                         // threads of the big-chunk sort
 constexpr uint32_t BIG_CAP = BIG_NT * MS_IT;         // 13312
+constexpr int MID_NT = 512;                          // over-full buckets up to MID_CAP: 512 threads
+constexpr uint32_t MID_CAP = MID_NT * MS_IT;         // 6656 (two such CTAs an SM)
 constexpr uint32_t MAXCH = 1024;  // chunks per block (blocks above about 1.6 M rotations go plain)
 constexpr uint32_t MAXB = 256;    // fine buckets per chunk (the chunk sort's bucket tables)
 
@@ -465,7 +468,8 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
                     if (lane == 0) {
                         cm[b] = (uint16_t)(min(nch, MAXCH - 1) | CM_OWN);
                         if (nch < MAXCH) cb[nch] = st[b];
-                        const int li = sz <= BIG_CAP ? 1 : CLS_LARGE;  // big-chunk sort, else the overflow radix
+                        // the 512- or 1,024-thread sort, else the overflow radix
+                        const int li = sz <= MID_CAP ? 2 : sz <= BIG_CAP ? 1 : CLS_LARGE;
                         const uint32_t slot = atomicAdd(&out.count[li], 1u);
                         if (slot < out.cap[li]) out.list[li][slot] = GroupDesc{bi.off + st[b], sz, blk, b | (1u << 16)};
                         else atomicOr(&ctrl[CTRL_ERR], ERR_CAPACITY);
@@ -698,6 +702,7 @@ __device__ __forceinline__ void sort13(uint64_t (&k)[MS_IT], uint32_t (&v)[MS_IT
 // above both, so a merge step needs no bounds test on the entries.
 constexpr size_t CHUNK_SORT_SMEM = (size_t)CHUNK_CAP * 12;
 constexpr size_t BIG_SORT_SMEM = (size_t)BIG_CAP * 12;
+constexpr size_t MID_SORT_SMEM = (size_t)MID_CAP * 12;
 
 template <int NT, int MINB, int LIST>
 __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __restrict__ K,
@@ -1160,6 +1165,8 @@ bwt_status bwt::ensure_learned_buffers(bwt_plan* p) {
                              (int)CHUNK_SORT_SMEM);
         cudaFuncSetAttribute((void*)k_chunk_sort_name<BIG_NT, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)BIG_SORT_SMEM);
+        cudaFuncSetAttribute((void*)k_chunk_sort_name<MID_NT, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)MID_SORT_SMEM);
         int per_sm = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_sort_name<MS_NT, 4, 0>, MS_NT,
                                                       CHUNK_SORT_SMEM);
@@ -1307,7 +1314,9 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
     nv.next("bucket_sort");
     uint32_t* chunk_counter = ctrl + CTRL_TILE_CTR + 58;  // control words no radix pass uses
     uint32_t* big_counter = ctrl + CTRL_TILE_CTR + 59;
+    uint32_t* mid_counter = ctrl + CTRL_TILE_CTR + 50;  // no radix pass of a learned call uses it either
     CKL(cudaMemsetAsync(chunk_counter, 0, 8, st));
+    CKL(cudaMemsetAsync(mid_counter, 0, 4, st));
     CKL(cudaMemsetAsync(p->members, 0, sizeof(uint32_t) * nb, st));
     const bool timing = !p->events.empty() && !p->capturing && p->ev_used + 2 <= p->events.size();
     if (timing) CKL(cudaEventRecord(p->events[p->ev_used], st));
@@ -1323,12 +1332,16 @@ bwt_status bwt::enqueue_learned(bwt_plan* p, const uint8_t* d_in, cudaStream_t s
         p->ev_meta.push_back(m);
         p->ev_used += 2;
     }
-    // over-full buckets up to BIG_CAP: one 1,024-thread CTA each
+    // over-full buckets: one CTA each, 512 threads up to MID_CAP (two an SM)
+    // and 1,024 up to BIG_CAP
+    k_chunk_sort_name<MID_NT, 2, 2><<<2 * sms, MID_NT, MID_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks, aux,
+                                                                            p->rank, bins_of(p, 0), ctrl, mid_counter,
+                                                                            p->bucket_count, p->members);
     k_chunk_sort_name<BIG_NT, 1, 1><<<sms, BIG_NT, BIG_SORT_SMEM, st>>>(p->keys[0], p->vals[0], p->blocks, aux,
                                                                         p->rank, bins_of(p, 0), ctrl, big_counter,
                                                                         p->bucket_count, p->members);
     CKL(cudaGetLastError());
-    p->stats.kernel_launches += 2;
+    p->stats.kernel_launches += 4;
 
     // overflow buckets: radix on the index, then on the key
     nv.next("bucket_overflow");

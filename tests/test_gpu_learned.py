@@ -173,7 +173,8 @@ def _prefix_keys(block):
 @pytest.mark.parametrize("graph", [False, True])
 def test_overfull_buckets_big_chunk_sort_and_radix(small_model, graph):
     """A bucket above the 3,328-rotation chunk capacity is sorted whole by one
-    1,024-thread CTA up to 13,312 rotations and by the overflow radix beyond.
+    CTA (512 threads up to 6,656 rotations, 1,024 up to 13,312) and by the
+    overflow radix beyond; here one bucket of each of the last two kinds.
     Splitters merged on purpose give a learned-routed Markov block one bucket of
     each kind (sizes checked on the host first)."""
     w = datagen.Workload("t", [datagen.MARKOV3_Z96, datagen.MARKOV3_Z96], [11, 12], [300_000, 250_000])
@@ -199,7 +200,7 @@ def test_overfull_buckets_big_chunk_sort_and_radix(small_model, graph):
                 break
         raise AssertionError("could not build the bucket")
 
-    spl, end1 = merge_to(spl, 1000, 6_000, 13_312)
+    spl, end1 = merge_to(spl, 1000, 6_700, 13_312)  # above the 512-thread sort's 6,656
     assert end1 < 2600
     spl, _ = merge_to(spl, 2600, 20_000, 1 << 30)
     sz = sizes(spl)
@@ -256,7 +257,7 @@ def test_lazy_ranks_with_overfull_buckets(small_model, graph):
     """On-demand ranks whose rotations lie in over-full buckets: a Markov block
     with repeated segments (about 2% of its rotations in groups, so its
     groups of one keep their ranks unstored) whose splitters are merged so
-    that one bucket goes to the 1,024-thread sort and one to the overflow
+    that one bucket goes to the 512-thread sort and one to the overflow
     radix (ranks stored in full there). The group members' successors are
     spread over the key range, so some lookups land in each kind of bucket."""
     w = datagen.Workload("t", [datagen.MARKOV3_Z96], [21], [300_000])
@@ -266,8 +267,9 @@ def test_lazy_ranks_with_overfull_buckets(small_model, graph):
     spl = np.array(small_model.splitters, dtype=np.uint64).copy()
     sizes = lambda sp: np.bincount(np.searchsorted(sp, keys, side="right"), minlength=sp.size + 1)  # noqa: E731
     base = sizes(spl)
-    # merge buckets after 1000 until one holds 6,000..13,312, and after 2600 until one holds > 20,000
-    for j, lo, hi in ((1000, 6_000, 13_312), (2600, 20_000, 1 << 30)):
+    # merge buckets after 1000 until one holds 3,400..6,656 (the 512-thread sort), and after 2600
+    # until one holds > 20,000 (the overflow radix)
+    for j, lo, hi in ((1000, 3_400, 6_656), (2600, 20_000, 1 << 30)):
         for m in range(1, spl.size - j - 1):
             tot = int(base[j + 1:j + m + 2].sum())
             if lo < tot <= hi:
@@ -277,7 +279,7 @@ def test_lazy_ranks_with_overfull_buckets(small_model, graph):
             raise AssertionError("could not build the bucket")
         base = sizes(spl)
     sz = sizes(spl)
-    assert ((sz > 3_328) & (sz <= 13_312)).any() and (sz > 13_312).any(), sz.max()
+    assert ((sz > 3_328) & (sz <= 6_656)).any() and (sz > 13_312).any(), sz.max()
     _, inv, cnt = np.unique(keys, return_inverse=True, return_counts=True)
     share = (cnt[inv] > 1).mean()
     assert 0.005 < share < 1 / 32, share  # groups exist, and the block's ranks stay on demand
