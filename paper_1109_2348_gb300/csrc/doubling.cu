@@ -175,22 +175,18 @@ __global__ void __launch_bounds__(256) k_gather_micro(const uint32_t* __restrict
                                                       const LazyRanks lz) {
     const uint32_t h = *depth;
     const uint32_t count = bin_count(cur, 0);
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < count; g += gridDim.x * blockDim.x) {
+    // one thread per member (a micro group has at most MICRO_MAX), so the
+    // members' rank reads -- a search each where ranks are found on demand --
+    // run side by side
+    const uint64_t total = (uint64_t)count * MICRO_MAX;
+    for (uint64_t x = blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = (uint32_t)(x / MICRO_MAX), e = (uint32_t)(x % MICRO_MAX);
         const GroupDesc gd = cur.list[0][g];
+        if (e >= gd.len) continue;
         const BlockInfo bi = blocks[gd.blk];
-        // a micro group has at most MICRO_MAX members: their SA loads, then
-        // their rank gathers, in flight together
-        uint32_t sa[MICRO_MAX];
-#pragma unroll
-        for (uint32_t e = 0; e < MICRO_MAX; ++e) sa[e] = e < gd.len ? SA[gd.start + e] : 0u;
-#pragma unroll
-        for (uint32_t e = 0; e < MICRO_MAX; ++e) {
-            if (e < gd.len) {
-                uint32_t r = sa[e] + h;
-                if (r >= bi.n) r -= bi.n;
-                key2[gd.start + e] = r < bi.n ? rank_at(lz, rank, bi, gd.blk, r) : 0u;
-            }
-        }
+        uint32_t r = SA[gd.start + e] + h;
+        if (r >= bi.n) r -= bi.n;
+        key2[gd.start + e] = r < bi.n ? rank_at(lz, rank, bi, gd.blk, r) : 0u;
     }
 }
 
@@ -869,7 +865,7 @@ cudaError_t launch_gather_small(const uint32_t* SA, const uint32_t* rank, const 
                                 int* launched, const LazyRanks& lz) {
     int g_micro = num_sms() * 8, g_warp = num_sms() * 16;
     if (host_counts) {
-        g_micro = host_counts[0] ? grid_for(host_counts[0], 256, 8) : 0;
+        g_micro = host_counts[0] ? grid_for(std::min(host_counts[0], 0x3fffffffu) * MICRO_MAX, 256, 8) : 0;
         const uint32_t n = host_counts[1] + host_counts[2] + host_counts[3];
         g_warp = n ? grid_for(n, 8, 16) : 0;
     }
