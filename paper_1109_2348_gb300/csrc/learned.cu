@@ -162,20 +162,22 @@ extern "C" bwt_status bwt_model_samples(bwt_plan* p, const uint8_t* d_in, const 
 // Learned bucketing of a batch (BWT_F_LEARNED).
 //
 //   count:   bucket b(i) = #{j : splitter[j] <= K_i} of every rotation, counted
-//            per block (a 12-step binary search over the splitters in shared
-//            memory);
+//            per block (a search of the splitters in shared memory from an
+//            index on the key's first two bytes), the bucket stored per
+//            rotation;
 //   route:   a block whose over-capacity buckets hold more than a quarter of
-//            its rotations is recounted with equal-width buckets (the top 12
-//            key bits), and sorted by the plain radix if those overflow too;
+//            its rotations is counted again with equal-width buckets (the top
+//            12 key bits), and sorted by the plain radix if those overflow too;
 //   plan:    consecutive buckets are grouped into chunks of at most 3328
-//            rotations (a bucket above that is an overflow bucket);
+//            padded rotations (a bucket above that is an overflow bucket);
 //   scatter: each tile's rotations go to their chunk's range in runs (one
-//            slot reservation per tile and chunk);
-//   sort:    one CTA per chunk merge-sorts it by (K, i) in shared memory,
-//            writes its SA and names it (a chunk is a whole key range, so
-//            its groups begin and end inside it); an overflow bucket of up
-//            to 13,312 rotations is sorted the same way by one 1,024-thread
-//            CTA;
+//            slot reservation per tile and chunk), tagged with their bucket;
+//   sort:    one CTA per chunk sorts every bucket by (K, i) with a team of
+//            its threads, writes the chunk's SA and names it (a chunk is a
+//            whole key range, so its groups begin and end inside it); groups
+//            of one keep no stored rank (they are found on demand); an
+//            overflow bucket of up to 13,312 rotations is sorted the same way
+//            by one 512- or 1,024-thread CTA;
 //   larger overflow buckets are sorted by the segmented radix: first by the
 //            rotation index (digits taken from the value), then by K, which
 //            leaves equal prefixes in index order as the doubling rounds
