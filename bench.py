@@ -588,7 +588,8 @@ def other_workloads(args, dev, local, flush, model_path):
     from paper_1109_2348_gb300 import F_GRAPH, F_LEARNED, F_PER_BLOCK_LAUNCH
     runs = {1: [("graph", F_GRAPH), ("graph_autotuned", F_GRAPH)],
             2: [("learned", F_LEARNED | F_GRAPH), ("graph", F_GRAPH)],
-            3: [("graph", F_GRAPH)], 4: [("graph", F_GRAPH), ("perblock", F_PER_BLOCK_LAUNCH)],
+            3: [("graph", F_GRAPH)],
+            4: [("graph", F_GRAPH), ("perblock", F_PER_BLOCK_LAUNCH), ("learned", F_LEARNED | F_GRAPH)],
             5: [("learned", F_LEARNED | F_GRAPH), ("graph", F_GRAPH)]}
     out = {}
     steps = max(3, min(args.steps, 10))

@@ -106,6 +106,27 @@ def test_workload5_learned_graph_as_benched(trained_model_path):
         assert np.array_equal(back.cpu().numpy(), buf)
 
 
+def test_workload4_learned_graph(trained_model_path):
+    """The uneven workload (256 order-3 Markov blocks of 10,000 to 900,000
+    bytes) through the learned bucketing in the batched graph, as bench.py
+    times it beside the plain and per-block modes: every block equals the
+    oracle, and every block is bucketed."""
+    import torch
+    w = datagen.config(4)
+    buf, off = w.generate()
+    sizes = np.diff(off.astype(np.int64))
+    with Plan(max_blocks=w.num_blocks, max_total_bytes=buf.size, max_block_bytes=int(sizes.max()),
+              flags=F_LEARNED | F_GRAPH, model_path=trained_model_path) as plan:
+        d_in = torch.from_numpy(buf).cuda()
+        L, prim = plan.forward(d_in, off)
+        torch.cuda.synchronize()
+        assert plan.last_status() == 0
+        st = plan.stats()
+        L, prim = L.cpu().numpy(), prim.cpu().numpy()
+    assert_matches_oracle(buf, off, L, prim, "workload 4 learned+graph")
+    assert st["blocks_routed_plain"] == 0, st
+
+
 def test_workload2_learned_graph_as_benched(trained_model_path):
     """The configuration bench.py times by default: learned bucketing inside the
     batched CUDA graph on the mixed workload, with a model trained as the bench
