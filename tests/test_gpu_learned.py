@@ -289,6 +289,17 @@ def test_lazy_ranks_with_overfull_buckets(small_model, graph):
     assert st["blocks_routed_plain"] == 0 and st["buckets_overflowed"] >= 2, st
 
 
+def test_large_blocks_near_and_over_the_chunk_limit(small_model):
+    """Chunked blocks hold at most 1,024 chunks: a 1,400,000-byte Markov block
+    still takes the learned buckets (about 450 chunks), a 1,700,000-byte one
+    is routed to the plain radix; both are exact."""
+    w = datagen.Workload("t", [datagen.MARKOV3_Z96, datagen.MARKOV3_Z96], [31, 32], [1_400_000, 1_700_000])
+    buf, off = w.generate()
+    L, prim, st = _learned_run(buf, off, small_model.splitters)
+    assert_matches_oracle(buf, off, L, prim, "1.4 MB and 1.7 MB blocks")
+    assert st["blocks_routed_plain"] == 1 and st["blocks_routed_flat"] == 0, st
+
+
 def test_learned_graph_equals_oracle_and_replays(small_model):
     """Learned + batched: the learned stage (device-side routing included) and
     the doubling loop captured as one CUDA graph. The first call captures, the
