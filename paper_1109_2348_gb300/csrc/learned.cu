@@ -652,6 +652,27 @@ __device__ __forceinline__ bool ki_less(uint64_t ak, uint32_t ai, uint64_t bk, u
 // never moves to a lower slot), 48 compare-exchanges instead of the 78 of
 // odd-even transposition (checked on every 0/1 input, which suffices for a
 // network).
+// The groups of two or more that end in a thread's rows (bit j of wm: its
+// row j, at chunk-relative position first + j) to the doubling rounds'
+// bins, each counted into members[blk]; hm marks the rows that head a group,
+// cur0 is the last head + 1 before the thread's first row, `real` rows are
+// the first `nreal`. All lanes of the warp call (the emitter's ballots).
+template <int IT>
+__device__ __noinline__ void emit_chunk_groups(WarpEmitter& em, const Bins& bins, uint32_t wm, uint32_t hm,
+                                               uint32_t cur0, uint32_t first, uint32_t nreal, uint32_t gstart,
+                                               uint32_t blk, uint32_t* members, uint32_t* err) {
+    uint32_t cur = cur0;
+#pragma unroll
+    for (int j = 0; j < IT; ++j) {
+        const uint32_t P = first + j;
+        if ((uint32_t)j < nreal && ((hm >> j) & 1u)) cur = P + 1;
+        const uint32_t gs = cur - 1;
+        const bool want = (wm >> j) & 1u;
+        if (want) atomicAdd(&members[blk], P - gs + 1);
+        em.emit(bins, want, gstart + gs, P - gs + 1, blk, err);
+    }
+}
+
 __device__ __forceinline__ void sort13(uint64_t (&k)[MS_IT], uint32_t (&v)[MS_IT]) {
     static_assert(MS_IT == 13, "the network below sorts 13 entries");
     constexpr int NET[48][2] = {
@@ -948,6 +969,8 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
         if (lane == 0) cur = 0u;
         for (uint32_t w = 0; w < warp; ++w) cur = max(cur, s_wmax[w]);
         const uint32_t boff = gd.start - bi.off;  // the chunk's block-relative start
+        const uint32_t cur0 = cur;
+        uint32_t wm = 0;  // rows that end a group of two or more
 #pragma unroll
         for (int j = 0; j < MS_IT; ++j) {
             const uint32_t pos = lt * MS_IT + j;
@@ -959,11 +982,13 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
             const bool member = real && emit_ok && (P > gs || !tail);  // in a group of two or more
             if (real) BWT_DCHECK(v[j] < bi.n && cur > 0u, &ctrl[CTRL_ERR]);
             if (member && v[j] < bi.n) rank[bi.off + v[j]] = boff + gs;
-            // a group of more than one rotation ends here: to the doubling rounds
-            const bool want = member && tail;
-            if (want) atomicAdd(&members[gd.blk], P - gs + 1);
-            em.emit(bins, want, gd.start + gs, P - gs + 1, gd.blk, &ctrl[CTRL_ERR]);
+            if (member && tail) wm |= 1u << j;
         }
+        // such groups go to the doubling rounds; on text they are rare, so the
+        // emitting walk is a call taken only by warps that have one
+        if (__any_sync(0xffffffffu, wm != 0u))
+            emit_chunk_groups<MS_IT>(em, bins, wm, hm, cur0, base + lt * MS_IT, active ? tsize - min(tsize, lt * MS_IT) : 0u,
+                                     gd.start, gd.blk, members, &ctrl[CTRL_ERR]);
         __syncthreads();
     }
     em.finish(bins, &ctrl[CTRL_ERR]);
