@@ -652,22 +652,33 @@ __device__ __forceinline__ bool ki_less(uint64_t ak, uint32_t ai, uint64_t bk, u
 // never moves to a lower slot), 48 compare-exchanges instead of the 78 of
 // odd-even transposition (checked on every 0/1 input, which suffices for a
 // network).
-// The groups of two or more that end in a thread's rows (bit j of wm: its
-// row j, at chunk-relative position first + j) to the doubling rounds'
-// bins, each counted into members[blk]; hm marks the rows that head a group,
-// cur0 is the last head + 1 before the thread's first row, `real` rows are
-// the first `nreal`. All lanes of the warp call (the emitter's ballots).
+// The rows of a thread that lie in groups of two or more (bit j of mm: its
+// row j, at chunk-relative position first + j): each gets its group's start
+// as its rank (its rotation read from the compacted SA in sI), and each
+// group that ends in these rows goes to the doubling rounds' bins and is
+// counted into members[blk]. hm marks the rows that head a group, fm (bit
+// j + 1) the rows that do not end one, cur0 is the last head + 1 before the
+// thread's first row; the first `nreal` rows are real. All lanes of the warp
+// call (the emitter's ballots).
 template <int IT>
-__device__ __noinline__ void emit_chunk_groups(WarpEmitter& em, const Bins& bins, uint32_t wm, uint32_t hm,
-                                               uint32_t cur0, uint32_t first, uint32_t nreal, uint32_t gstart,
-                                               uint32_t blk, uint32_t* members, uint32_t* err) {
+__device__ __noinline__ void name_chunk_members(WarpEmitter& em, const Bins& bins, uint32_t mm, uint32_t hm,
+                                                uint32_t fm, uint32_t cur0, uint32_t first, uint32_t nreal,
+                                                const uint32_t* sI, uint32_t* __restrict__ rank, BlockInfo bi,
+                                                uint32_t boff, uint32_t gstart, uint32_t blk, uint32_t* members,
+                                                uint32_t* err) {
     uint32_t cur = cur0;
 #pragma unroll
     for (int j = 0; j < IT; ++j) {
         const uint32_t P = first + j;
         if ((uint32_t)j < nreal && ((hm >> j) & 1u)) cur = P + 1;
         const uint32_t gs = cur - 1;
-        const bool want = (wm >> j) & 1u;
+        const bool member = (mm >> j) & 1u;
+        if (member) {
+            const uint32_t sa = sI[P] & ~SA_FINAL;
+            BWT_DCHECK(sa < bi.n && cur > 0u, err);
+            if (sa < bi.n) rank[bi.off + sa] = boff + gs;
+        }
+        const bool want = member && !((fm >> (j + 1)) & 1u);  // the group ends here
         if (want) atomicAdd(&members[blk], P - gs + 1);
         em.emit(bins, want, gstart + gs, P - gs + 1, blk, err);
     }
@@ -934,7 +945,7 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
         if (lane == 0 && warp > 0) prev_last = s_wlast[warp - 1];
         if (lane == 31 && warp + 1 < NT / 32) next_first = s_wfirst[warp + 1];
         const bool emit_ok = bi.n > 8u;   // smaller blocks: every group is final (whole equal rotations)
-        uint32_t hm = 0, fm = 0, lh = 0;  // head bits, final bits, last head + 1 (0: none)
+        uint32_t hm = 0, fm = 0, mm = 0, lh = 0;  // head, not-last and member bits, last head + 1 (0: none)
         if (active) {
 #pragma unroll
             for (int j = 0; j < MS_IT; ++j) {
@@ -950,6 +961,7 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
                     }
                     if (!tail) fm |= 2u << j;  // bit j + 1: not the group's last row
                     const bool final_row = (head && tail) || !emit_ok;
+                    if (!final_row) mm |= 1u << j;  // in a group of two or more, sent to the rounds
                     // SA, compacted through shared memory (bucket after bucket,
                     // padding dropped) for a coalesced write
                     sI[base + pos] = v[j] | (final_row ? SA_FINAL : 0u);
@@ -968,27 +980,13 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
         uint32_t cur = __shfl_up_sync(0xffffffffu, incl, 1);
         if (lane == 0) cur = 0u;
         for (uint32_t w = 0; w < warp; ++w) cur = max(cur, s_wmax[w]);
-        const uint32_t boff = gd.start - bi.off;  // the chunk's block-relative start
-        const uint32_t cur0 = cur;
-        uint32_t wm = 0;  // rows that end a group of two or more
-#pragma unroll
-        for (int j = 0; j < MS_IT; ++j) {
-            const uint32_t pos = lt * MS_IT + j;
-            const bool real = active && pos < tsize;
-            const uint32_t P = base + pos;  // chunk-relative position
-            if (real && ((hm >> j) & 1u)) cur = P + 1;
-            const uint32_t gs = cur - 1;  // its group's start
-            const bool tail = !((fm >> (j + 1)) & 1u);
-            const bool member = real && emit_ok && (P > gs || !tail);  // in a group of two or more
-            if (real) BWT_DCHECK(v[j] < bi.n && cur > 0u, &ctrl[CTRL_ERR]);
-            if (member && v[j] < bi.n) rank[bi.off + v[j]] = boff + gs;
-            if (member && tail) wm |= 1u << j;
-        }
-        // such groups go to the doubling rounds; on text they are rare, so the
-        // emitting walk is a call taken only by warps that have one
-        if (__any_sync(0xffffffffu, wm != 0u))
-            emit_chunk_groups<MS_IT>(em, bins, wm, hm, cur0, base + lt * MS_IT, active ? tsize - min(tsize, lt * MS_IT) : 0u,
-                                     gd.start, gd.blk, members, &ctrl[CTRL_ERR]);
+        // groups of two or more: their ranks stored and the groups sent to
+        // the doubling rounds; on text they are rare, so this is a call taken
+        // only by warps that hold a member
+        if (__any_sync(0xffffffffu, mm != 0u))
+            name_chunk_members<MS_IT>(em, bins, mm, hm, fm, cur, base + lt * MS_IT,
+                                      active ? tsize - min(tsize, lt * MS_IT) : 0u, sI, rank, bi,
+                                      gd.start - bi.off, gd.start, gd.blk, members, &ctrl[CTRL_ERR]);
         __syncthreads();
     }
     em.finish(bins, &ctrl[CTRL_ERR]);
