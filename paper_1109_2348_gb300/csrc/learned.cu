@@ -837,7 +837,7 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
             k[j] = i < len ? K[gd.start + i] : 0ull;
             v[j] = i < len ? SA[gd.start + i] : 0u;
         }
-        if (active) {  // the padding of this thread's slots (only a team's last run has any)
+        if (active && lt + 1 == kteam) {  // the padding: only a team's last thread has any
 #pragma unroll
             for (int j = 0; j < MS_IT; ++j) {
                 const uint32_t pos = lt * MS_IT + j;  // position inside the team's run
@@ -968,25 +968,31 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
                 }
             }
         }
-        uint32_t incl = lh;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((int)lane >= o) incl = max(incl, y);
-        }
-        if (lane == 31) s_wmax[warp] = incl;
-        __syncthreads();
+        // the barrier also tells whether the chunk holds a group of two or more
+        const bool any_member = __syncthreads_or(mm != 0u) != 0;
         for (uint32_t i = tid; i < len; i += NT) SA[gd.start + i] = sI[i];
-        uint32_t cur = __shfl_up_sync(0xffffffffu, incl, 1);
-        if (lane == 0) cur = 0u;
-        for (uint32_t w = 0; w < warp; ++w) cur = max(cur, s_wmax[w]);
-        // groups of two or more: their ranks stored and the groups sent to
-        // the doubling rounds; on text they are rare, so this is a call taken
-        // only by warps that hold a member
-        if (__any_sync(0xffffffffu, mm != 0u))
-            name_chunk_members<MS_IT>(em, bins, mm, hm, fm, cur, base + lt * MS_IT,
-                                      active ? tsize - min(tsize, lt * MS_IT) : 0u, sI, rank, bi,
-                                      gd.start - bi.off, gd.start, gd.blk, members, &ctrl[CTRL_ERR]);
+        if (any_member) {  // CTA-uniform; rare on text
+            // group starts: the last head at or before each row, by a CTA
+            // max-scan of every thread's last head
+            uint32_t incl = lh;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)lane >= o) incl = max(incl, y);
+            }
+            if (lane == 31) s_wmax[warp] = incl;
+            __syncthreads();
+            uint32_t cur = __shfl_up_sync(0xffffffffu, incl, 1);
+            if (lane == 0) cur = 0u;
+            for (uint32_t w = 0; w < warp; ++w) cur = max(cur, s_wmax[w]);
+            // groups of two or more: their ranks stored and the groups sent
+            // to the doubling rounds, by a call taken only by warps that
+            // hold a member
+            if (__any_sync(0xffffffffu, mm != 0u))
+                name_chunk_members<MS_IT>(em, bins, mm, hm, fm, cur, base + lt * MS_IT,
+                                          active ? tsize - min(tsize, lt * MS_IT) : 0u, sI, rank, bi,
+                                          gd.start - bi.off, gd.start, gd.blk, members, &ctrl[CTRL_ERR]);
+        }
         __syncthreads();
     }
     em.finish(bins, &ctrl[CTRL_ERR]);
