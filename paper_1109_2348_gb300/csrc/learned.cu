@@ -558,8 +558,7 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
     uint32_t* lcount = cb + MAXCH;                                       // [MAXCH] tile's rotations per chunk
     uint32_t* pre = lcount + MAXCH;                                      // [MAXCH] tile-local chunk offsets
     uint32_t* dbase = pre + MAXCH;                                       // [MAXCH] destination of pre[c]
-    uint16_t* stQ = reinterpret_cast<uint16_t*>(dbase + MAXCH);          // [4096] tile position by rank
-    uint16_t* stC = stQ + 4096;                                          // [4096] its fine bucket
+    uint32_t* stQC = dbase + MAXCH;  // [4096] by rank: tile position (low 16 bits) | fine bucket (high 16)
     __shared__ uint32_t scan_tmp[32];
     const uint32_t ntiles = *ntiles_dev;
     const uint32_t span = max(1u, min(16u, ntiles / (gridDim.x * 4u)));
@@ -625,13 +624,12 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
                 if (cs[j] != 0xffffffffu) {
                     const uint32_t c = cs[j] & (MAXCH - 1);
                     const uint32_t pos = pre[c] + (cs[j] >> 10);
-                    stQ[pos] = (uint16_t)(j * 256 + threadIdx.x);
-                    stC[pos] = (uint16_t)bk[j];
+                    stQC[pos] = (j * 256 + threadIdx.x) | (bk[j] << 16);
                 }
             }
             __syncthreads();
             for (uint32_t r = threadIdx.x; r < td.len; r += blockDim.x) {
-                const uint32_t q = stQ[r], b = stC[r], e = cm[b], c = e & (MAXCH - 1);
+                const uint32_t qc = stQC[r], q = qc & 0xffffu, b = qc >> 16, e = cm[b], c = e & (MAXCH - 1);
                 const uint32_t dst = dbase[c] + (r - pre[c]);
                 BWT_DCHECK(dst - bi.off < bi.n, err);  // inside the tile's block
                 K[dst] = pack8_smem(sb, shift + q);
