@@ -640,8 +640,20 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
     }
 }
 
-__device__ __forceinline__ bool ki_less(uint64_t ak, uint32_t ai, uint64_t bk, uint32_t bi) {
-    return ak < bk || (ak == bk && ai < bi);
+// (ak, ai) < (bk, bi) as an all-ones mask: the borrow out of the 96-bit
+// difference ak:ai - bk:bi (the index is the low word), one carry chain
+// instead of separate compares of the key halves and the index.
+__device__ __forceinline__ uint32_t ki_less_mask(uint64_t ak, uint32_t ai, uint64_t bk, uint32_t bi) {
+    uint32_t m;
+    asm("{\n\t.reg .u32 t;\n\t"
+        "sub.cc.u32 t, %1, %2;\n\t"
+        "subc.cc.u32 t, %3, %4;\n\t"
+        "subc.cc.u32 t, %5, %6;\n\t"
+        "subc.u32 %0, 0, 0;\n\t}"
+        : "=r"(m)
+        : "r"(ai), "r"(bi), "r"((uint32_t)ak), "r"((uint32_t)bk), "r"((uint32_t)(ak >> 32)),
+          "r"((uint32_t)(bk >> 32)));
+    return m;
 }
 
 // Sorts a thread's MS_IT entries in registers by (K, i): Batcher's odd-even
@@ -692,7 +704,7 @@ __device__ __forceinline__ void sort13(uint64_t (&k)[MS_IT], uint32_t (&v)[MS_IT
 #pragma unroll
     for (int c = 0; c < 48; ++c) {
         const int i = NET[c][0], j = NET[c][1];
-        const bool sw = ki_less(k[j], v[j], k[i], v[i]);
+        const bool sw = ki_less_mask(k[j], v[j], k[i], v[i]) != 0u;
         const uint64_t a = sw ? k[j] : k[i], b = sw ? k[i] : k[j];
         const uint32_t x = sw ? v[j] : v[i], y = sw ? v[i] : v[j];
         k[i] = a;
@@ -730,11 +742,13 @@ __device__ __forceinline__ void sort13(uint64_t (&k)[MS_IT], uint32_t (&v)[MS_IT
 //      counts the rotations sent on, which decides whether a block's ranks
 //      are filled in full after the chunk sorts (k_fill_ranks).
 // Padding entries are (~0, 0xffff0000 + slot): above every real pair (real
-// indices are below 2^30) and distinct; an exhausted run reads as (~0, ~0),
-// above both, so a merge step needs no bounds test on the entries.
-constexpr size_t CHUNK_SORT_SMEM = (size_t)CHUNK_CAP * 12;
-constexpr size_t BIG_SORT_SMEM = (size_t)BIG_CAP * 12;
-constexpr size_t MID_SORT_SMEM = (size_t)MID_CAP * 12;
+// indices are below 2^30) and distinct. A merge step reloads the head it
+// consumed without a bounds test, so a head may sit one entry past its run
+// (the other run, the next team's slots, or the 16 bytes of slack after the
+// arrays); the choice tests the bounds and never takes such a head.
+constexpr size_t CHUNK_SORT_SMEM = (size_t)CHUNK_CAP * 12 + 16;
+constexpr size_t BIG_SORT_SMEM = (size_t)BIG_CAP * 12 + 16;
+constexpr size_t MID_SORT_SMEM = (size_t)MID_CAP * 12 + 16;
 
 template <int NT, int MINB, int LIST>
 __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __restrict__ K,
@@ -905,22 +919,25 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
                     const bool a_first = a != b ? a < b : AI[mid] <= BI[diag - 1 - mid];
                     if (a_first) lo = mid + 1; else hi = mid;
                 }
+                // heads may sit one past their run (valid shared memory: the
+                // other run, the next team, or the slack entry after the
+                // arrays); the bounds in the choice keep them out
                 uint32_t ia = lo, ib = diag - lo;
-                uint64_t ka = ia < la ? AK[ia] : ~0ull, kb = ib < lb ? BK[ib] : ~0ull;
-                uint32_t va = ia < la ? AI[ia] : ~0u, vb = ib < lb ? BI[ib] : ~0u;
+                uint64_t ka = AK[ia], kb = BK[ib];
+                uint32_t va = AI[ia], vb = BI[ib];
 #pragma unroll
                 for (int j = 0; j < MS_IT; ++j) {
-                    const bool take_b = ki_less(kb, vb, ka, va);
+                    const bool take_b = ib < lb && (ia >= la || ki_less_mask(kb, vb, ka, va) != 0u);
                     k[j] = take_b ? kb : ka;
                     v[j] = take_b ? vb : va;
                     if (take_b) {
                         ++ib;
-                        kb = ib < lb ? BK[ib] : ~0ull;
-                        vb = ib < lb ? BI[ib] : ~0u;
+                        kb = BK[ib];
+                        vb = BI[ib];
                     } else {
                         ++ia;
-                        ka = ia < la ? AK[ia] : ~0ull;
-                        va = ia < la ? AI[ia] : ~0u;
+                        ka = AK[ia];
+                        va = AI[ia];
                     }
                 }
             }
