@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(256) k_chunk_plan(const uint32_t* __restrict__
 constexpr size_t CHUNK_SCATTER_SMEM = NBK * 2 + 4 * MAXCH * 4 + TILE_BYTES + 4096 * 4;
 
 template <int ITEMS>
-__global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict__ S,
+__global__ void __launch_bounds__(256, 4) k_chunk_scatter(const uint8_t* __restrict__ S,
                                                        const BlockInfo* __restrict__ blocks,
                                                        const TileDesc* __restrict__ tiles,
                                                        const uint32_t* __restrict__ ntiles_dev,
@@ -587,25 +587,32 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
             }
             const uint32_t shift = stage_tile_bytes(S, bi, i0, td.len, sb, threadIdx.x, 256);
             __syncthreads();
-            uint32_t cs[ITEMS];  // chunk (low 10 bits) | slot within the tile's share of the chunk << 10
+            // chunk (low 10 bits) | slot within the tile's share of the chunk << 10;
+            // every item's chunk is looked up before the first count, so the
+            // lookups overlap
+            uint32_t cs[ITEMS];
 #pragma unroll
             for (int j = 0; j < ITEMS; ++j) {
                 const uint32_t q = j * 256 + threadIdx.x;
                 cs[j] = 0xffffffffu;
                 if (q < td.len) {
                     if (flat) bk[j] = (uint32_t)(pack8_smem(sb, shift + q) >> 52);
-                    const uint32_t c = cm[bk[j]] & (MAXCH - 1);
-                    cs[j] = c | (atomicAdd(&lcount[c], 1u) << 10);
+                    cs[j] = cm[bk[j]] & (MAXCH - 1);
                 }
             }
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j)
+                if (cs[j] != 0xffffffffu) cs[j] |= atomicAdd(&lcount[cs[j]], 1u) << 10;
             __syncthreads();
-            // tile-local exclusive prefix over chunks and the global reservation
+            // the global reservation (issued first: its round trip overlaps
+            // the scan) and the tile-local exclusive prefix over chunks
             {
                 constexpr int PER = MAXCH / 256;
-                uint32_t v[PER], sum = 0;
+                uint32_t v[PER], g[PER], sum = 0;
 #pragma unroll
                 for (int i = 0; i < PER; ++i) {
                     v[i] = lcount[threadIdx.x * PER + i];
+                    g[i] = v[i] ? atomicAdd(&ct.ccur[(size_t)td.blk * MAXCH + threadIdx.x * PER + i], v[i]) : 0u;
                     sum += v[i];
                 }
                 uint32_t total;
@@ -614,7 +621,7 @@ __global__ void __launch_bounds__(256) k_chunk_scatter(const uint8_t* __restrict
                 for (int i = 0; i < PER; ++i) {
                     const uint32_t c = threadIdx.x * PER + i;
                     pre[c] = ex;
-                    if (v[i]) dbase[c] = bi.off + cb[c] + atomicAdd(&ct.ccur[(size_t)td.blk * MAXCH + c], v[i]);
+                    if (v[i]) dbase[c] = bi.off + cb[c] + g[i];
                     ex += v[i];
                 }
             }
