@@ -248,7 +248,7 @@ ONESWEEP_DRAM_BYTES_PER_KEY = 23.37
 # DRAM bytes (read + write) per rotation of the learned chunk sort
 # (k_chunk_sort_name<256, 4, 0>) as ncu counted them for the current kernel on
 # 24 blocks of the learned-eval workload; None when the kernel has changed since.
-CHUNK_SORT_DRAM_BYTES_PER_KEY = 14.70
+CHUNK_SORT_DRAM_BYTES_PER_KEY = 15.63
 
 
 def reference_arm(args):
