@@ -566,17 +566,19 @@ __global__ void __launch_bounds__(256, 4) k_chunk_scatter(const uint8_t* __restr
     for (uint32_t s = blockIdx.x; s < nspan; s += gridDim.x) {
         const uint32_t t0 = s * span, t1 = min(ntiles, t0 + span);
         uint32_t cur = 0xffffffffu;
+        BlockInfo bi{};     // of block cur, with its route: read once a block, so a
+        bool flat = false;  // tile's loads wait only on its own descriptor
         for (uint32_t t = t0; t < t1; ++t) {
             const TileDesc td = tiles[t];
-            const BlockInfo bi = blocks[td.blk];
-            const uint32_t i0 = td.start - bi.off;
             if (td.blk != cur) {  // CTA-uniform
                 cur = td.blk;
+                bi = blocks[cur];
+                flat = route[cur] == 2u;
                 for (int i = threadIdx.x; i < NBK; i += blockDim.x) cm[i] = ct.cmap[(size_t)cur * NBK + i];
                 for (int i = threadIdx.x; i < (int)MAXCH; i += blockDim.x) cb[i] = ct.cbase[(size_t)cur * MAXCH + i];
             }
+            const uint32_t i0 = td.start - bi.off;
             for (int i = threadIdx.x; i < (int)MAXCH; i += blockDim.x) lcount[i] = 0;
-            const bool flat = route[td.blk] == 2u;
             uint32_t bk[ITEMS];  // fine bucket of each item
             if (!flat) {
 #pragma unroll
