@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
     __shared__ GroupDesc ebuf[NT / 32][NCLS * EMIT_BUF];
     __shared__ uint64_t s_wlast[NT / 32], s_wfirst[NT / 32];  // each warp's last and first key
     __shared__ uint32_t s_wmax[NT / 32];                      // each warp's last head + 1
-    __shared__ uint32_t s_c[2], s_rounds;  // this chunk's and the next chunk's list index
+    __shared__ uint32_t s_c, s_rounds;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ld_volatile(&ctrl[CTRL_ERR])) return;  // an earlier stage failed: the chunks are not permutations
     WarpEmitter em;
@@ -785,16 +785,12 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
     const uint32_t count = bin_count(chunks, LIST);
     // chunks in list order from an atomic counter (zeroed before the launch):
     // the chunks in flight stay within a few blocks, whose rank ranges stay
-    // in L2 while their scattered rank writes land. The next chunk is
-    // reserved when a chunk starts and its index published when it ends, so
-    // the counter's round trip overlaps the sort.
-    if (tid == 0) s_c[0] = atomicAdd(chunk_counter, 1u);
-    __syncthreads();
-    for (uint32_t it = 0;; ++it) {
-        const uint32_t c = s_c[it & 1u];
+    // in L2 while their scattered rank writes land
+    for (;;) {
+        if (tid == 0) s_c = atomicAdd(chunk_counter, 1u);
+        __syncthreads();
+        const uint32_t c = s_c;
         if (c >= count) break;
-        uint32_t next = 0;
-        if (tid == 0) next = atomicAdd(chunk_counter, 1u);
         const GroupDesc gd = chunks.list[LIST][c];
         const BlockInfo bi = blocks[gd.blk];
         const uint32_t len = min(gd.len, CAP);
@@ -1021,8 +1017,6 @@ __global__ void __launch_bounds__(NT, MINB) k_chunk_sort_name(const uint64_t* __
                                           active ? tsize - min(tsize, lt * MS_IT) : 0u, sI, rank, bi,
                                           gd.start - bi.off, gd.start, gd.blk, members, &ctrl[CTRL_ERR]);
         }
-        // the other slot was last read before the previous chunk's final barrier
-        if (tid == 0) s_c[(it + 1) & 1u] = next;
         __syncthreads();
     }
     em.finish(bins, &ctrl[CTRL_ERR]);
